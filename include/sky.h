@@ -1,0 +1,213 @@
+/*
+ * sky.h -- C ABI of libsky: exact grid-pruned skyline computation on one GPU.
+ *
+ * The method is SkyCell (Li, Gu, Qi, Yu, arXiv 2107.09993). Given n points
+ * P in R^d, it returns the skyline S, the points that no other point
+ * dominates (Definitions 1 and 2, Sec. 3): p dominates q when
+ * p[k] <= q[k] in every dimension k and p[l] < q[l] in at least one
+ * ("smaller is better").
+ *
+ * The hot path has four steps, each behind one of the calls below:
+ *   (a) map every point to its cell of the finest grid layer (Eq. 1);
+ *   (b) mark occupied cells in a bitmap;
+ *   (c) prune every cell dominated by an occupied cell (Definition 3),
+ *       which holds no skyline point (Sec. 3, cell types);
+ *   (d) run exact point-vs-point dominance tests on the survivors and
+ *       compact the skyline's row indices in ascending order.
+ *
+ * Conventions shared by every call
+ *   Points     device pointer to float32, row-major, n rows of d values with
+ *              a row stride of `ld` floats (ld >= d). The pointer must be
+ *              4-byte aligned; 16-byte alignment with ld == d selects the
+ *              bulk-copy (TMA) streaming path. 1 <= d <= 16, 0 <= n < 2^31.
+ *              NaN or +-inf anywhere -> SKY_ERR_NONFINITE.
+ *   Output     ascending 0-based int32 row indices. The set is unique and
+ *              the order canonical, so results compare bit for bit.
+ *   Ownership  the caller owns every buffer it passes and keeps it alive
+ *              until the call (or, for a grid handle, sky_grid_destroy)
+ *              returns; the library never frees caller memory. Handles own
+ *              their device workspace.
+ *   Streams    `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *              default stream). All device work is enqueued on it.
+ *   Errors     every call returns a sky_status; no C++ exception crosses the
+ *              boundary. sky_last_error() gives a thread-local detail string.
+ *              Calls are re-entrant across distinct handles; one handle must
+ *              not be used from two threads at once.
+ */
+#ifndef SKY_H_
+#define SKY_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SKY_API __attribute__((visibility("default")))
+#else
+#define SKY_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sky_status {
+    SKY_OK = 0,
+    SKY_ERR_INVALID_ARGUMENT = 1, /* bad pointer, size, stride or option      */
+    SKY_ERR_NONFINITE = 2,        /* NaN or infinity in the input              */
+    SKY_ERR_CAPACITY = 3,         /* output buffer too small; count is set     */
+    SKY_ERR_OUT_OF_MEMORY = 4,    /* device workspace allocation failed        */
+    SKY_ERR_CUDA = 5,             /* a CUDA runtime call failed                */
+    SKY_ERR_TOO_LARGE = 6,        /* grid of 2^(log2_g*d) cells above 2^27     */
+    SKY_ERR_TIMEOUT = 7,          /* a bounded device-side wait ran out        */
+    SKY_ERR_NO_DEVICE = 8         /* no CUDA device, or not an sm_103 device   */
+} sky_status;
+
+/* Options of one skyline computation. Zero-initialise, then set fields. */
+typedef struct sky_options {
+    /* Cells per dimension = 2^log2_g, i.e. the finest grid layer rho of
+     * Sec. 3 / Algorithm 1. -1 picks it from n and d (automatic). The grid
+     * must satisfy log2_g * d <= 27 (dense bitmap), else SKY_ERR_TOO_LARGE. */
+    int32_t log2_g;
+    /* 1: the data is taken to lie in the unit cube and Eq. 1 is used as
+     * printed (column = floor(x * 2^log2_g)); values outside [0,1) are
+     * clamped to the first or last column, so the result stays exact for any
+     * finite input. 0: each dimension is first normalised by its min and max
+     * (one extra read pass). */
+    int32_t assume_unit;
+    /* Optional pre-filter proposals: n_filter points of d floats (device,
+     * row-major). Any coordinates are accepted. Each proposal f is replaced by
+     * the data point q <= f (every dimension) with the smallest coordinate
+     * sum, or dropped when there is none; then every point dominated by such
+     * a q is removed before step (d). Since every q is a real data point this
+     * never changes the result, only the work. NULL / 0 = no filter. */
+    const float* d_filter_pts;
+    int32_t n_filter;             /* 0..16 */
+    /* Refinement tile configuration (0 = default). See sky_tile_configs(). */
+    int32_t tile_cfg;
+} sky_options;
+
+/* Opaque grid handle: steps (a)-(c) for one point set. Owns its workspace. */
+typedef struct sky_grid sky_grid;
+
+/* Statistics of a grid handle (filled by sky_grid_stats). */
+typedef struct sky_grid_stats_t {
+    int32_t log2_g;               /* chosen layer: 2^log2_g cells per dimension */
+    int32_t d;
+    int64_t n;
+    int64_t occupied_cells;       /* cells holding at least one point          */
+    int64_t surviving_cells;      /* occupied cells not dominated (Def. 3)     */
+    int64_t surviving_points;     /* points handed to step (d)                 */
+    int32_t n_filter_used;        /* proposals that snapped to a data point    */
+    int32_t error_flags;          /* device error bits (see sky_status)        */
+} sky_grid_stats_t;
+
+/* Device views into a grid handle, for inspection and tests. Valid until
+ * sky_grid_destroy. All arrays live on the device. */
+typedef struct sky_grid_view {
+    const uint32_t* cell_key;     /* [n] key of each point's cell: sum_k c[k] << (log2_g*k) */
+    const uint32_t* occupied;     /* [words] bit c set when cell c holds a point            */
+    const uint32_t* dominated;    /* [words] bit c set when cell c is dominated (Def. 3)    */
+    const int32_t* survivors;     /* [surviving_points] row ids after step (c), ascending    */
+    const float* cell_offset;     /* [d] value -> column map: t = (x - offset) * scale      */
+    const float* cell_scale;      /* [d]                                                    */
+    int64_t words;                /* 32-bit words per bitmap = max(1, 2^(log2_g*d) / 32)    */
+} sky_grid_view;
+
+/*
+ * Steps (a) and (b) [Eq. 1; Sec. 4, Algorithm 1 line 1]: map each point to
+ * its cell of layer log2_g and mark occupied cells. Allocates the handle and
+ * its workspace; enqueues the work on `stream` and returns without waiting.
+ * `d_pts` is borrowed and must stay valid until sky_grid_destroy.
+ */
+SKY_API sky_status sky_build_grid(const float* d_pts, int64_t n, int32_t d, int64_t ld,
+                          const sky_options* opt, void* stream, sky_grid** out);
+
+/*
+ * Step (c) [Definition 3; Sec. 3 "dominated cells"; Corollary 4]: mark every
+ * cell dominated by an occupied cell and compact the rows of the remaining
+ * points (survivors). A cell c is dominated iff some occupied cell c' has
+ * c'[k] < c[k] in every dimension; computed as an inclusive prefix-OR of the
+ * occupancy bitmap over all d dimensions, read one cell down the diagonal.
+ * Optional proposals (see sky_options.d_filter_pts) additionally remove points
+ * dominated by their snapped data points. Asynchronous on `stream`.
+ */
+SKY_API sky_status sky_prune_cells(sky_grid* grid, const float* d_filter_pts, int32_t n_filter,
+                           void* stream);
+
+/* Synchronises the grid's stream and reports its statistics. */
+SKY_API sky_status sky_grid_stats(const sky_grid* grid, sky_grid_stats_t* out);
+
+/* Device pointers into the handle (no synchronisation). */
+SKY_API sky_status sky_grid_get_view(const sky_grid* grid, sky_grid_view* out);
+
+/* Arrays of a grid handle that sky_grid_copy_out can copy. */
+typedef enum sky_grid_array {
+    SKY_GRID_CELL_KEY = 0,        /* uint32[n]                                  */
+    SKY_GRID_OCCUPIED = 1,        /* uint32[words]                              */
+    SKY_GRID_DOMINATED = 2,       /* uint32[words] (after sky_prune_cells)      */
+    SKY_GRID_SURVIVORS = 3,       /* int32[surviving_points] (after pruning)    */
+    SKY_GRID_CELL_MAP = 4         /* float[32]: offset[16] then scale[16]       */
+} sky_grid_array;
+
+/* Copies one array of the handle into caller memory d_dst (device) of
+ * `bytes` bytes; synchronises the handle's stream. Returns SKY_ERR_CAPACITY
+ * when `bytes` is smaller than the array. */
+SKY_API sky_status sky_grid_copy_out(const sky_grid* grid, sky_grid_array which, void* d_dst, size_t bytes);
+
+/* Frees the handle and its workspace (NULL is accepted). Synchronises the
+ * handle's stream first. */
+SKY_API void sky_grid_destroy(sky_grid* grid);
+
+/*
+ * Steps (a)-(d) [Algorithm 1; Definitions 1-3]: the skyline of the n points.
+ * Writes the ascending row indices of the skyline to d_out_idx (device,
+ * capacity out_capacity entries) and the skyline size to *h_out_count (host).
+ * If out_capacity is smaller than the skyline, returns SKY_ERR_CAPACITY with
+ * *h_out_count set to the size needed; the buffer's contents are then
+ * undefined. Synchronises `stream` once, to read the count. The workspace is
+ * taken from the device's stream-ordered pool and returned before the call
+ * ends.
+ */
+SKY_API sky_status sky_skyline(const float* d_pts, int64_t n, int32_t d, int64_t ld,
+                       const sky_options* opt, int32_t* d_out_idx, int64_t out_capacity,
+                       int64_t* h_out_count, void* stream);
+
+/*
+ * Same as sky_skyline, with host buffers: copies the points to the device,
+ * runs steps (a)-(d) and copies the indices back. h_pts (n*ld floats) and
+ * h_out_idx (out_capacity ints) are host memory; page-locked memory makes the
+ * copies asynchronous. Synchronises `stream` before returning.
+ */
+SKY_API sky_status sky_skyline_host(const float* h_pts, int64_t n, int32_t d, int64_t ld,
+                            const sky_options* opt, int32_t* h_out_idx, int64_t out_capacity,
+                            int64_t* h_out_count, void* stream);
+
+/* Work counters of the last sky_skyline / sky_skyline_host call made on the
+ * calling thread (for measurement; not part of the result). */
+typedef struct sky_run_stats {
+    int64_t n;
+    int32_t d;
+    int32_t log2_g;               /* layer used                                 */
+    int64_t survivors;            /* points left after step (c)                 */
+    int64_t skyline;              /* points in the result                       */
+    int64_t pairs;                /* candidate pairs examined in step (d)       */
+    int32_t n_filter_used;        /* proposals that snapped to a data point     */
+    int32_t reserved;
+} sky_run_stats;
+
+SKY_API sky_status sky_last_run_stats(sky_run_stats* out);
+
+/* Static text for a status code. */
+SKY_API const char* sky_status_string(sky_status status);
+
+/* Thread-local detail of the last error raised on this thread ("" if none). */
+SKY_API const char* sky_last_error(void);
+
+/* Library version string. */
+SKY_API const char* sky_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKY_H_ */

@@ -1,0 +1,682 @@
+// k_grid.cu -- steps (a), (b), (c) of the skyline path (sm_103a).
+//
+//   k_minmax        per-dimension min / max and the finiteness check
+//                   (normalisation for data outside the unit cube)
+//   k_params        value -> column scales (Eq. 1), code and sort-key scales
+//   k_map_mark      step (a)+(b): cell key of every point (Eq. 1) and the
+//                   occupancy bitmap of the finest layer; streams the points
+//                   through shared memory with 1-D bulk (TMA) copies
+//   k_prefix_or_dim step (c): inclusive prefix-OR of the bitmap along one
+//                   dimension; after all d dimensions, bit c holds "some
+//                   occupied cell c' <= c componentwise"
+//   k_dominated     materialises Def. 3's dominated bitmap for inspection
+//   k_snap          pre-filter proposals -> real data points
+//   k_survivors     step (c) output: rows whose cell is not dominated (and
+//                   that no snapped proposal dominates), compacted in row
+//                   order by a decoupled look-back scan, with a Morton key
+//                   for the refinement's spatial sort
+#include <cfloat>
+#include <cstdint>
+
+#include "sky_common.cuh"
+#include "sky_internal.h"
+
+namespace sky {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float scale_for(float levels, float range)
+{
+    if (range == 0.0f) return 0.0f;
+    if (isinf(range)) return __fdiv_rn(levels, FLT_MAX);
+    return __fdiv_rn(levels, range);
+}
+
+// Row loader: d floats of row r into x[0..DP), zero padded. Vector loads only
+// when every row starts 16-byte aligned and holds exactly DP floats.
+template <int DP>
+__device__ __forceinline__ void load_row(const float* __restrict__ row, int d, bool vec4, float (&x)[DP])
+{
+    if (vec4) {
+#pragma unroll
+        for (int k = 0; k < DP; k += 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(row + k));
+            x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < DP; ++k) x[k] = (k < d) ? __ldg(row + k) : 0.0f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <int DP>
+__global__ void __launch_bounds__(kThreads) k_minmax(const float* __restrict__ pts, int64_t n, int d,
+                                                     int64_t ld, bool vec4, uint32_t* mm_min,
+                                                     uint32_t* mm_max, uint32_t* err)
+{
+    float mn[DP], mx[DP];
+#pragma unroll
+    for (int k = 0; k < DP; ++k) { mn[k] = INFINITY; mx[k] = -INFINITY; }
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float x[DP];
+        load_row<DP>(pts + i * ld, d, vec4, x);
+#pragma unroll
+        for (int k = 0; k < DP; ++k) {
+            if (k < d) {
+                bad |= !isfinite(x[k]);
+                mn[k] = fminf(mn[k], x[k]);
+                mx[k] = fmaxf(mx[k], x[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[k] = fminf(mn[k], __shfl_xor_sync(kFull, mn[k], o));
+            mx[k] = fmaxf(mx[k], __shfl_xor_sync(kFull, mx[k], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < DP; ++k) {
+            if (k < d && mn[k] <= mx[k]) {
+                atomicMin(&mm_min[k], float_to_ordered(mn[k]));
+                atomicMax(&mm_max[k], float_to_ordered(mx[k]));
+            }
+        }
+    }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, SKY_DEV_ERR_NONFINITE);
+}
+
+// params layout: [0,16) offset, [16,32) cell scale, [32,48) 7-bit code scale,
+// [48,64) Morton scale.
+__global__ void k_params(const uint32_t* mm_min, const uint32_t* mm_max, int d, int log2g,
+                         int mbits, int assume_unit, float* params)
+{
+    const int k = threadIdx.x;
+    if (k >= kMaxDim) return;
+    float off = 0.0f, cs = 0.0f, qs = 0.0f, ms = 0.0f;
+    if (k < d) {
+        const float G = (float)(1u << log2g);
+        const float M = (float)(1u << mbits);
+        if (assume_unit) {
+            off = 0.0f; cs = G; qs = 128.0f; ms = M;
+        } else {
+            const float lo = ordered_to_float(mm_min[k]);
+            const float hi = ordered_to_float(mm_max[k]);
+            const float range = __fsub_rn(hi, lo);
+            off = lo;
+            cs = scale_for(G, range);
+            qs = scale_for(128.0f, range);
+            ms = scale_for(M, range);
+        }
+    }
+    params[k] = off;
+    params[16 + k] = cs;
+    params[32 + k] = qs;
+    params[48 + k] = ms;
+}
+
+// ---------------------------------------------------------------------------
+// Steps (a)+(b). One point -> key -> bit. The bit is read before the atomic
+// so that hot cells (correlated data) cost a load, not a serialised atomic.
+template <int DP>
+__device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, const float* s_off,
+                                        const float* s_sc, int64_t row, uint32_t* __restrict__ keys,
+                                        uint32_t* occ, bool& bad)
+{
+    const uint32_t G = 1u << log2g;
+    uint32_t key = 0;
+#pragma unroll
+    for (int k = DP - 1; k >= 0; --k) {
+        if (k < d) {
+            bad |= !isfinite(x[k]);
+            key = (key << log2g) | column_of(x[k], s_off[k], s_sc[k], G);
+        }
+    }
+    keys[row] = key;
+    uint32_t* w = occ + (key >> 5);
+    const uint32_t bit = 1u << (key & 31u);
+    if (!(ld_cg_u32(w) & bit)) atomicOr(w, bit);
+}
+
+template <int DP>
+__global__ void __launch_bounds__(kThreads) k_map_mark_plain(const float* __restrict__ pts, int64_t n,
+                                                             int d, int64_t ld, bool vec4, int log2g,
+                                                             const float* params, uint32_t* keys,
+                                                             uint32_t* occ, uint32_t* err)
+{
+    __shared__ float s_off[kMaxDim], s_sc[kMaxDim];
+    if (threadIdx.x < kMaxDim) {
+        s_off[threadIdx.x] = params[threadIdx.x];
+        s_sc[threadIdx.x] = params[16 + threadIdx.x];
+    }
+    __syncthreads();
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float x[DP];
+        load_row<DP>(pts + i * ld, d, vec4, x);
+        map_one<DP>(x, d, log2g, s_off, s_sc, i, keys, occ, bad);
+    }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, SKY_DEV_ERR_NONFINITE);
+}
+
+// Bulk-copy streaming version: rows are contiguous (ld == d) and the base is
+// 16-byte aligned. Chunks of kThreads rows (kThreads*d*4 bytes, a multiple of
+// 16) go through kStages shared-memory buffers; one thread issues the copies.
+constexpr int kMapStages = 4;
+
+template <int DP>
+__global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restrict__ pts, int64_t n,
+                                                           int d, int log2g, const float* params,
+                                                           uint32_t* keys, uint32_t* occ, uint32_t* err)
+{
+    extern __shared__ __align__(128) float s_buf[];  // [kMapStages][kThreads * d]
+    __shared__ float s_off[kMaxDim], s_sc[kMaxDim];
+    __shared__ __align__(8) uint64_t s_bar[kMapStages];
+    const int tid = threadIdx.x;
+    if (tid < kMaxDim) {
+        s_off[tid] = params[tid];
+        s_sc[tid] = params[16 + tid];
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kMapStages; ++s) mbar_init(&s_bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    const int64_t nfull = n / kThreads;
+    const uint32_t chunk_bytes = (uint32_t)(kThreads * d * sizeof(float));
+    const int64_t my_chunks = (nfull > blockIdx.x) ? (nfull - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (tid == 0) {
+        for (int64_t i = 0; i < my_chunks && i < kMapStages; ++i) {
+            const int64_t c = blockIdx.x + i * gridDim.x;
+            mbar_arrive_expect_tx(&s_bar[i], chunk_bytes);
+            bulk_g2s(s_buf + i * kThreads * d, pts + c * kThreads * d, chunk_bytes, &s_bar[i]);
+        }
+    }
+    bool bad = false;
+    bool timed_out = false;
+    for (int64_t i = 0; i < my_chunks; ++i) {
+        const int s = (int)(i % kMapStages);
+        const uint32_t parity = (uint32_t)((i / kMapStages) & 1);
+        if (!mbar_wait(&s_bar[s], parity, err)) { timed_out = true; }
+        if (__syncthreads_or(timed_out)) {
+            // Let every copy already issued land before the block exits.
+            if (tid == 0) {
+                for (int64_t j = i; j < my_chunks && j < i + kMapStages; ++j)
+                    mbar_wait(&s_bar[j % kMapStages], (uint32_t)((j / kMapStages) & 1), nullptr);
+            }
+            __syncthreads();
+            return;
+        }
+        const int64_t c = blockIdx.x + i * gridDim.x;
+        const float* r = s_buf + s * kThreads * d + tid * d;
+        float x[DP];
+#pragma unroll
+        for (int k = 0; k < DP; ++k) x[k] = (k < d) ? r[k] : 0.0f;
+        map_one<DP>(x, d, log2g, s_off, s_sc, c * kThreads + tid, keys, occ, bad);
+        __syncthreads();  // every thread is done with stage s
+        if (tid == 0 && i + kMapStages < my_chunks) {
+            const int64_t c2 = blockIdx.x + (i + kMapStages) * gridDim.x;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&s_bar[s], chunk_bytes);
+            bulk_g2s(s_buf + s * kThreads * d, pts + c2 * kThreads * d, chunk_bytes, &s_bar[s]);
+        }
+    }
+    // Tail rows (fewer than one chunk): the last block loads them directly.
+    if (blockIdx.x == gridDim.x - 1) {
+        const int64_t i = nfull * kThreads + tid;
+        if (i < n) {
+            float x[DP];
+            load_row<DP>(pts + i * d, d, false, x);
+            map_one<DP>(x, d, log2g, s_off, s_sc, i, keys, occ, bad);
+        }
+    }
+    if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(err, SKY_DEV_ERR_NONFINITE);
+}
+
+// ---------------------------------------------------------------------------
+// Inclusive prefix-OR along dimension k of the 2^(log2g*d)-bit grid.
+// Bit stride of dimension k: 2^(log2g*k).
+__global__ void __launch_bounds__(kThreads) k_prefix_or_dim(uint32_t* R, int64_t words, int log2g, int k)
+{
+    const int slog = log2g * k;
+    const uint32_t G = 1u << log2g;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    if (slog >= 5) {
+        // whole words: word stride sw, G words per line
+        const int64_t sw = 1ll << (slog - 5);
+        const int64_t ncol = words / G;
+        for (int64_t c = tid; c < ncol; c += nthr) {
+            const int64_t lo = c % sw, hi = c / sw;
+            uint32_t* p = R + hi * (int64_t)G * sw + lo;
+            uint32_t acc = *p;
+            for (uint32_t j = 1; j < G; ++j) {
+                p += sw;
+                acc |= *p;
+                *p = acc;
+            }
+        }
+    } else if (slog + log2g <= 5) {
+        // every line inside one word: log2(G) doubling steps with masks that
+        // keep each shifted bit inside its own line
+        uint32_t mask[6];
+        int nsteps = 0;
+        for (uint32_t j = 1; j < G; j <<= 1) {
+            uint32_t m = 0;
+            for (int b = 0; b < 32; ++b)
+                if (((uint32_t)(b >> slog) & (G - 1u)) >= j) m |= 1u << b;
+            mask[nsteps++] = m;
+        }
+        for (int64_t w = tid; w < words; w += nthr) {
+            uint32_t x = R[w];
+            int st = 0;
+            for (uint32_t j = 1; j < G; j <<= 1, ++st) x |= (x << (j << slog)) & mask[st];
+            R[w] = x;
+        }
+    } else {
+        // a line spans Lw consecutive words holding e = 32 >> slog of its
+        // elements each (2^slog interleaved lines): scan inside each word, then
+        // carry the last element group from word to word
+        const int64_t Lw = 1ll << (slog + log2g - 5);
+        const int e = 32 >> slog;
+        const int sbits = 1 << slog;
+        uint32_t rep = 0;
+        for (int t = 0; t < e; ++t) rep |= 1u << (t << slog);
+        const int64_t ngroups = words / Lw;
+        for (int64_t g = tid; g < ngroups; g += nthr) {
+            uint32_t* p = R + g * Lw;
+            uint32_t carry = 0;
+            for (int64_t t = 0; t < Lw; ++t) {
+                uint32_t x = p[t];
+                for (int j = 1; j < e; j <<= 1) x |= x << (j << slog);
+                x |= carry;
+                p[t] = x;
+                const uint32_t top = x >> (32 - sbits);
+                carry = top * rep;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t ones_key(int log2g, int d)
+{
+    uint32_t o = 0;
+    for (int k = 0; k < d; ++k) o |= 1u << (log2g * k);
+    return o;
+}
+
+__device__ __forceinline__ bool all_columns_positive(uint32_t key, int log2g, int d)
+{
+    const uint32_t m = (1u << log2g) - 1u;
+    bool ok = true;
+    for (int k = 0; k < d; ++k) ok &= ((key >> (log2g * k)) & m) != 0u;
+    return ok;
+}
+
+// dominated[c] = prefix[c - (1,..,1)] when every column of c is >= 1 (Def. 3).
+__global__ void __launch_bounds__(kThreads) k_dominated(const uint32_t* R, uint32_t* dom, int64_t words,
+                                                        int log2g, int d)
+{
+    const uint32_t ones = ones_key(log2g, d);
+    const int64_t total = 1ll << (log2g * d);
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t out = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t c = w * 32 + b;
+            if (c >= total) break;
+            if (!all_columns_positive((uint32_t)c, log2g, d)) continue;
+            const uint32_t src = (uint32_t)c - ones;
+            if ((R[src >> 5] >> (src & 31u)) & 1u) out |= 1u << b;
+        }
+        dom[w] = out;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cell_stats(const uint32_t* occ, const uint32_t* dom,
+                                                         int64_t words, DevResult* res)
+{
+    uint32_t occ_c = 0, surv_c = 0;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        occ_c += __popc(occ[w]);
+        surv_c += __popc(occ[w] & ~dom[w]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        occ_c += __shfl_xor_sync(kFull, occ_c, o);
+        surv_c += __shfl_xor_sync(kFull, surv_c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&res->occupied_cells, occ_c);
+        atomicAdd(&res->surviving_cells, surv_c);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pre-filter proposals. For proposal f_j, the data point q <= f_j (all
+// dimensions) with the smallest binary32 coordinate sum, ties to the lower
+// row, found by a packed 64-bit atomic min.
+template <int DP>
+__global__ void __launch_bounds__(kThreads) k_snap(const float* __restrict__ pts, int64_t n, int d,
+                                                   int64_t ld, bool vec4, const float* __restrict__ prop,
+                                                   int n_prop, unsigned long long* snap)
+{
+    __shared__ float s_f[16 * kMaxDim];
+    for (int t = threadIdx.x; t < n_prop * d; t += blockDim.x) s_f[t] = prop[t];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_round = ((n + 31) / 32) * 32;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+        const bool valid = i < n;
+        float x[DP];
+        float sum = 0.0f;
+        if (valid) {
+            load_row<DP>(pts + i * ld, d, vec4, x);
+#pragma unroll
+            for (int k = 0; k < DP; ++k)
+                if (k < d) sum = __fadd_rn(sum, x[k]);
+        }
+        const unsigned long long packed =
+            ((unsigned long long)float_to_ordered(sum) << 32) | (unsigned long long)(uint32_t)i;
+        for (int j = 0; j < n_prop; ++j) {
+            bool le = valid;
+            if (valid) {
+#pragma unroll
+                for (int k = 0; k < DP; ++k)
+                    if (k < d) le &= x[k] <= s_f[j * d + k];
+            }
+            if (__any_sync(kFull, le)) {
+                unsigned long long v = le ? packed : ~0ull;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+                    v = w < v ? w : v;
+                }
+                if ((threadIdx.x & 31) == 0) atomicMin(&snap[j], v);
+            }
+        }
+    }
+}
+
+__global__ void k_snap_finalize(const float* __restrict__ pts, int d, int64_t ld,
+                                const unsigned long long* snap, int n_prop, float* filt, DevResult* res)
+{
+    if (threadIdx.x != 0) return;
+    int used = 0;
+    for (int j = 0; j < n_prop; ++j) {
+        if (snap[j] == ~0ull) continue;
+        const int64_t row = (int64_t)(snap[j] & 0xffffffffull);
+        for (int k = 0; k < kMaxDim; ++k) filt[used * kMaxDim + k] = (k < d) ? pts[row * ld + k] : 0.0f;
+        ++used;
+    }
+    res->n_filter_used = (uint32_t)used;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of one value per thread (kThreads threads).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t& total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < kThreads / 32) ? s_warp[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kThreads / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    total = s_warp[kThreads / 32 - 1];
+    const uint32_t before = warp ? s_warp[warp - 1] : 0u;
+    return before + x - v;
+}
+
+// Survivors of step (c), compacted in row order. Morton key: b bits of each
+// dimension interleaved, dimension d-1 first at every bit level.
+template <int DP>
+__global__ void __launch_bounds__(kThreads) k_survivors(
+    const float* __restrict__ pts, int64_t n, int d, int64_t ld, bool vec4, int log2g, int mbits,
+    const uint32_t* __restrict__ keys, const uint32_t* __restrict__ pre, const float* __restrict__ params,
+    const float* __restrict__ filt, int n_filter_max, DevResult* res, unsigned long long* states,
+    uint32_t* tile_counter, uint32_t* surv_key, uint32_t* surv_idx)
+{
+    __shared__ uint32_t s_warp[kThreads / 32];
+    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ float s_off[kMaxDim], s_ms[kMaxDim];
+    __shared__ float s_f[16 * kMaxDim];
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    if (tid < kMaxDim) {
+        s_off[tid] = params[tid];
+        s_ms[tid] = params[48 + tid];
+    }
+    const int nf = n_filter_max ? (int)res->n_filter_used : 0;
+    for (int t = tid; t < nf * kMaxDim; t += kThreads) s_f[t] = filt[t];
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint32_t ones = ones_key(log2g, d);
+    const int64_t base = (int64_t)tile * kScanTile + (int64_t)tid * kScanItems;
+    uint32_t flags = 0, mk[kScanItems];
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int64_t i = base + j;
+        mk[j] = 0;
+        if (i >= n) continue;
+        const uint32_t key = keys[i];
+        bool dominated = false;
+        if (all_columns_positive(key, log2g, d)) {
+            const uint32_t src = key - ones;
+            dominated = (pre[src >> 5] >> (src & 31u)) & 1u;
+        }
+        if (dominated) continue;
+        float x[DP];
+        load_row<DP>(pts + i * ld, d, vec4, x);
+        bool filtered = false;
+        for (int f = 0; f < nf && !filtered; ++f) {
+            bool le = true, lt = false;
+#pragma unroll
+            for (int k = 0; k < DP; ++k) {
+                if (k < d) {
+                    const float q = s_f[f * kMaxDim + k];
+                    le &= q <= x[k];
+                    lt |= q < x[k];
+                }
+            }
+            filtered = le && lt;  // Definition 1: the snapped point dominates x
+        }
+        if (filtered) continue;
+        const uint32_t M = 1u << mbits;
+        uint32_t mq[DP];
+#pragma unroll
+        for (int k = 0; k < DP; ++k) mq[k] = (k < d) ? column_of(x[k], s_off[k], s_ms[k], M) : 0u;
+        uint32_t code = 0;
+        for (int l = mbits - 1; l >= 0; --l)
+#pragma unroll
+            for (int k = DP - 1; k >= 0; --k)
+                if (k < d) code = (code << 1) | ((mq[k] >> l) & 1u);
+        mk[j] = code;
+        flags |= 1u << j;
+    }
+    uint32_t total;
+    const uint32_t excl = block_excl_scan((uint32_t)__popc(flags), s_warp, total);
+    if (tid < 32) {
+        const uint32_t prefix = lookback_prefix(states, tile, total, &res->err);
+        if (tid == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    uint32_t pos = s_prefix + excl;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (flags & (1u << j)) {
+            surv_key[pos] = mk[j];
+            surv_idx[pos] = (uint32_t)(base + j);
+            ++pos;
+        }
+    }
+    const uint32_t ntiles = (uint32_t)((n + kScanTile - 1) / kScanTile);
+    if (tile == ntiles - 1 && tid == 0) res->survivors = s_prefix + total;
+}
+
+int grid_for(int64_t work, int per_block, int max_blocks)
+{
+    int64_t b = (work + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+int g_num_sms = 0;
+int num_sms()
+{
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    return g_num_sms;
+}
+
+}  // namespace
+
+#define SKY_DISPATCH_DP(d, ...)                                 \
+    switch (pad4(d)) {                                          \
+        case 4: { constexpr int DP = 4; __VA_ARGS__; } break;   \
+        case 8: { constexpr int DP = 8; __VA_ARGS__; } break;   \
+        case 12: { constexpr int DP = 12; __VA_ARGS__; } break; \
+        default: { constexpr int DP = 16; __VA_ARGS__; } break; \
+    }
+
+static bool vec4_ok(const Plan& p)
+{
+    return (p.d % 4 == 0) && (p.ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.pts) & 15u) == 0);
+}
+
+cudaError_t launch_minmax(const Plan& p, cudaStream_t s)
+{
+    cudaMemsetAsync(p.mm_min, 0xff, sizeof(uint32_t) * kMaxDim, s);
+    cudaMemsetAsync(p.mm_max, 0x00, sizeof(uint32_t) * kMaxDim, s);
+    if (p.n == 0) return cudaGetLastError();
+    const int blocks = grid_for(p.n, kThreads * 8, num_sms() * 8);
+    const bool v = vec4_ok(p);
+    SKY_DISPATCH_DP(p.d, k_minmax<DP><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, p.mm_min,
+                                                                   p.mm_max, &p.res->err));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_params(const Plan& p, cudaStream_t s)
+{
+    k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, p.assume_unit ? 1 : 0,
+                              p.params);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_map_mark(const Plan& p, cudaStream_t s)
+{
+    cudaMemsetAsync(p.occ, 0, sizeof(uint32_t) * p.words, s);
+    if (p.n == 0) return cudaGetLastError();
+    if (p.tma_ok && p.n >= kThreads) {
+        const size_t smem = (size_t)kMapStages * kThreads * p.d * sizeof(float);
+        const int64_t nchunks = p.n / kThreads;
+        const int blocks = grid_for(nchunks, 1, num_sms() * 4);
+        SKY_DISPATCH_DP(p.d, {
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaFuncSetAttribute(k_map_mark_tma<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kMapStages * kThreads * 16 * (int)sizeof(float));
+                attr_set = true;
+            }
+            k_map_mark_tma<DP><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.log2g, p.params, p.keys,
+                                                              p.occ, &p.res->err);
+        });
+    } else {
+        const int blocks = grid_for(p.n, kThreads * 4, num_sms() * 8);
+        const bool v = vec4_ok(p);
+        SKY_DISPATCH_DP(p.d, k_map_mark_plain<DP><<<blocks, kThreads, 0, s>>>(
+                                 p.pts, p.n, p.d, p.ld, v, p.log2g, p.params, p.keys, p.occ, &p.res->err));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prefix_or(const Plan& p, cudaStream_t s)
+{
+    cudaMemcpyAsync(p.pre, p.occ, sizeof(uint32_t) * p.words, cudaMemcpyDeviceToDevice, s);
+    for (int k = 0; k < p.d; ++k) {
+        const int blocks = grid_for(p.words, kThreads, num_sms() * 8);
+        k_prefix_or_dim<<<blocks, kThreads, 0, s>>>(p.pre, p.words, p.log2g, k);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dominated(const Plan& p, cudaStream_t s)
+{
+    const int blocks = grid_for(p.words, kThreads, num_sms() * 8);
+    k_dominated<<<blocks, kThreads, 0, s>>>(p.pre, p.dom, p.words, p.log2g, p.d);
+    k_cell_stats<<<blocks, kThreads, 0, s>>>(p.occ, p.dom, p.words, p.res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snap(const Plan& p, const float* d_prop, int n_prop, cudaStream_t s)
+{
+    cudaMemsetAsync(p.snap, 0xff, sizeof(unsigned long long) * 16, s);
+    if (n_prop > 0 && p.n > 0) {
+        const int blocks = grid_for(p.n, kThreads * 4, num_sms() * 8);
+        const bool v = vec4_ok(p);
+        SKY_DISPATCH_DP(p.d, k_snap<DP><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, d_prop, n_prop,
+                                                                     p.snap));
+    }
+    k_snap_finalize<<<1, 32, 0, s>>>(p.pts, p.d, p.ld, p.snap, n_prop, p.filt, p.res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_survivors(const Plan& p, int n_filter, cudaStream_t s)
+{
+    if (p.n == 0) return cudaGetLastError();
+    const int64_t ntiles = (p.n + kScanTile - 1) / kScanTile;
+    cudaMemsetAsync(p.lb_states, 0, sizeof(unsigned long long) * ntiles, s);
+    cudaMemsetAsync(p.lb_counter, 0, sizeof(uint32_t), s);
+    const bool v = vec4_ok(p);
+    SKY_DISPATCH_DP(p.d, k_survivors<DP><<<(unsigned)ntiles, kThreads, 0, s>>>(
+                             p.pts, p.n, p.d, p.ld, v, p.log2g, p.morton_bits, p.keys, p.pre, p.params,
+                             p.filt, n_filter, p.res, p.lb_states, p.lb_counter, p.surv_key, p.surv_idx));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_stats(const Plan& p, cudaStream_t s)
+{
+    return launch_dominated(p, s);
+}
+
+int auto_log2g(int64_t n, int d)
+{
+    int r = 24 / d;
+    if (r < 1) r = 1;
+    if (r > 16) r = 16;
+    while (r > 1 && (double)(1ull << (r * d)) > 32.0 * (double)(n > 1 ? n : 1)) --r;
+    return r;
+}
+
+int morton_bits_for(int d)
+{
+    int b = 32 / d;
+    if (b > 16) b = 16;
+    if (b < 1) b = 1;
+    return b;
+}
+
+}  // namespace sky

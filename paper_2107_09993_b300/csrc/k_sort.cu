@@ -1,0 +1,195 @@
+// k_sort.cu -- stable LSD radix sort of the survivors by Morton key (sm_103a).
+//
+// The refinement compares tiles of points whose bounding boxes overlap; a
+// Morton (Z-order) arrangement of the survivors makes consecutive points
+// spatially close, so most tile pairs can be skipped by one box test. The
+// sort is deterministic (stable, no atomics on the output positions): per
+// 8-bit digit, (1) per-block digit histograms, (2) one exclusive scan over
+// the [digit][block] matrix, (3) a stable scatter that ranks keys inside the
+// block with warp match masks and writes digit runs contiguously. The number
+// of survivors is read on the device, so no host synchronisation is needed.
+#include <cstdint>
+
+#include "sky_common.cuh"
+#include "sky_internal.h"
+
+namespace sky {
+
+namespace {
+
+constexpr int kT = kSortThreads;
+constexpr int kI = kSortItems;
+constexpr int kTile = kSortTile;
+constexpr int kWarps = kT / 32;
+
+__global__ void __launch_bounds__(kT) k_radix_hist(const uint32_t* __restrict__ keys, const DevResult* res,
+                                                   int shift, uint32_t* hist, int64_t nblk_max)
+{
+    __shared__ uint32_t s_h[256];
+    const uint32_t m = res->survivors;
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    if (base >= m) return;
+    s_h[threadIdx.x] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kI; ++r) {
+        const int64_t i = base + r * kT + threadIdx.x;
+        if (i < m) atomicAdd(&s_h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblk_max + blockIdx.x] = s_h[threadIdx.x];
+}
+
+// Exclusive scan over the logical sequence hist[digit][0..nblk), digit-major.
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* hist, const DevResult* res, int64_t nblk_max)
+{
+    __shared__ uint32_t s_part[1024];
+    const uint32_t m = res->survivors;
+    const int64_t nblk = ((int64_t)m + kTile - 1) / kTile;
+    if (nblk == 0) return;
+    const int64_t total = 256 * nblk;
+    const int64_t per = (total + 1023) / 1024;
+    const int64_t lo = threadIdx.x * per;
+    const int64_t hi = lo + per < total ? lo + per : total;
+    uint32_t sum = 0;
+    {
+        int64_t dg = lo / nblk, b = lo % nblk;
+        for (int64_t L = lo; L < hi; ++L) {
+            sum += hist[dg * nblk_max + b];
+            if (++b == nblk) { b = 0; ++dg; }
+        }
+    }
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const uint32_t v = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        s_part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = s_part[threadIdx.x] - sum;
+    {
+        int64_t dg = lo / nblk, b = lo % nblk;
+        for (int64_t L = lo; L < hi; ++L) {
+            uint32_t* p = &hist[dg * nblk_max + b];
+            const uint32_t v = *p;
+            *p = run;
+            run += v;
+            if (++b == nblk) { b = 0; ++dg; }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kT) k_radix_scatter(const uint32_t* __restrict__ kin,
+                                                      const uint32_t* __restrict__ vin, uint32_t* kout,
+                                                      uint32_t* vout, const DevResult* res, int shift,
+                                                      const uint32_t* __restrict__ hist, int64_t nblk_max)
+{
+    __shared__ uint32_t s_wcnt[kWarps][256];
+    __shared__ uint32_t s_run[256];
+    __shared__ uint32_t s_start[256];
+    __shared__ uint32_t s_key[kTile];
+    __shared__ uint32_t s_val[kTile];
+    __shared__ uint32_t s_warp[kWarps];
+    const uint32_t m = res->survivors;
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    if (base >= m) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int w = 0; w < kWarps; ++w) s_wcnt[w][tid] = 0;
+    s_run[tid] = 0;
+    __syncthreads();
+
+    uint32_t key[kI], val[kI], rank[kI];
+#pragma unroll
+    for (int r = 0; r < kI; ++r) {
+        const int64_t i = base + r * kT + tid;
+        const bool valid = i < m;
+        key[r] = valid ? kin[i] : 0u;
+        val[r] = valid ? vin[i] : 0u;
+        const uint32_t digit = valid ? ((key[r] >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(kFull, digit);
+        const uint32_t below = __popc(peers & lanemask_lt());
+        const bool leader = (__ffs(peers) - 1) == lane;
+        if (valid && leader) s_wcnt[warp][digit] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pre = s_run[digit];
+            for (int w = 0; w < warp; ++w) pre += s_wcnt[w][digit];
+            rank[r] = pre + below;
+        }
+        __syncthreads();
+        {
+            uint32_t tot = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                tot += s_wcnt[w][tid];
+                s_wcnt[w][tid] = 0;
+            }
+            s_run[tid] += tot;
+        }
+        __syncthreads();
+    }
+    // local digit starts (exclusive scan of the block's digit counts)
+    {
+        const uint32_t c = s_run[tid];
+        uint32_t x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += s_warp[w];
+        s_start[tid] = before + x - c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kI; ++r) {
+        const int64_t i = base + r * kT + tid;
+        if (i < m) {
+            const uint32_t digit = (key[r] >> shift) & 255u;
+            const uint32_t pos = s_start[digit] + rank[r];
+            s_key[pos] = key[r];
+            s_val[pos] = val[r];
+        }
+    }
+    __syncthreads();
+    const int64_t cnt = (m - base) < kTile ? (m - base) : kTile;
+    for (int j = tid; j < cnt; j += kT) {
+        const uint32_t k = s_key[j];
+        const uint32_t digit = (k >> shift) & 255u;
+        const uint32_t g = hist[(int64_t)digit * nblk_max + blockIdx.x] + (j - s_start[digit]);
+        kout[g] = k;
+        vout[g] = s_val[j];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sort(Plan& p, cudaStream_t s)
+{
+    const int bits = p.morton_bits * p.d;
+    const int passes = (bits + 7) / 8;
+    const uint32_t* kin = p.surv_key;
+    const uint32_t* vin = p.surv_idx;
+    uint32_t* kout = p.sort_key2;
+    uint32_t* vout = p.sort_val2;
+    const unsigned nblk = (unsigned)p.sort_blocks;
+    for (int ps = 0; ps < passes; ++ps) {
+        const int shift = ps * 8;
+        k_radix_hist<<<nblk, kT, 0, s>>>(kin, p.res, shift, p.hist, p.sort_blocks);
+        k_radix_scan<<<1, 1024, 0, s>>>(p.hist, p.res, p.sort_blocks);
+        k_radix_scatter<<<nblk, kT, 0, s>>>(kin, vin, kout, vout, p.res, shift, p.hist, p.sort_blocks);
+        // ping-pong
+        const uint32_t* tk = kout;
+        const uint32_t* tv = vout;
+        kout = const_cast<uint32_t*>(kin);
+        vout = const_cast<uint32_t*>(vin);
+        kin = tk;
+        vin = tv;
+    }
+    p.sorted_val = vin;
+    return cudaGetLastError();
+}
+
+}  // namespace sky

@@ -1,0 +1,432 @@
+// sky_api.cu -- the C ABI of libsky (include/sky.h): argument checks, workspace
+// layout, and the order in which the kernels of steps (a)-(d) are enqueued.
+#include <algorithm>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "../../include/sky.h"
+#include "sky_common.cuh"
+#include "sky_internal.h"
+
+using namespace sky;
+
+namespace {
+
+thread_local std::string t_err;
+thread_local sky_run_stats t_stats = {};
+
+sky_status fail(sky_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+sky_status fail(sky_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return s;
+}
+
+sky_status cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(SKY_ERR_OUT_OF_MEMORY, "%s: %s", what, cudaGetErrorString(e));
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver)
+        return fail(SKY_ERR_NO_DEVICE, "%s: %s", what, cudaGetErrorString(e));
+    return fail(SKY_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SKY_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t count)
+    {
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += align256(count * sizeof(T) + 16);
+        return p;
+    }
+};
+
+// One layout function serves both sizing (base == nullptr) and carving.
+size_t layout(Plan& p, char* base, bool grid_api)
+{
+    Carver c{base};
+    const int64_t n = p.n > 0 ? p.n : 1;
+    const int dp = pad4(p.d);
+    const int64_t n_pad = ((n + kRefineTile - 1) / kRefineTile) * kRefineTile;
+    const int64_t tiles = n_pad / kRefineTile;
+    p.words = std::max<int64_t>(1, (1ll << (p.log2g * p.d)) / 32);
+    p.lb_tiles = (n + kScanTile - 1) / kScanTile;
+    p.sort_blocks = (n + kSortTile - 1) / kSortTile;
+    p.mm_min = c.take<uint32_t>(kMaxDim);
+    p.mm_max = c.take<uint32_t>(kMaxDim);
+    p.params = c.take<float>(64);
+    p.res = c.take<DevResult>(1);
+    p.filt = c.take<float>(16 * kMaxDim);
+    p.snap = c.take<unsigned long long>(16);
+    p.lb_counter = c.take<uint32_t>(4);
+    p.lb_states = c.take<unsigned long long>(p.lb_tiles);
+    p.occ = c.take<uint32_t>(p.words);
+    p.pre = c.take<uint32_t>(p.words);
+    p.dom = grid_api ? c.take<uint32_t>(p.words) : nullptr;
+    p.keys = c.take<uint32_t>(n);
+    p.surv_key = c.take<uint32_t>(n);
+    p.surv_idx = c.take<uint32_t>(n);
+    p.sort_key2 = c.take<uint32_t>(n);
+    p.sort_val2 = c.take<uint32_t>(n);
+    p.hist = c.take<uint32_t>(256 * p.sort_blocks);
+    p.X = c.take<float>(n_pad * dp);
+    p.C = c.take<uint32_t>(n_pad * (dp / 4));
+    p.ids = c.take<int32_t>(n_pad);
+    p.bbox = c.take<float>(tiles * 2 * dp);
+    p.keep = c.take<uint8_t>(n + 16);
+    return c.off;
+}
+
+void enable_pool_cache()
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return;
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+sky_status check_points(const float* pts, int64_t n, int32_t d, int64_t ld)
+{
+    if (d < 1 || d > kMaxDim) return fail(SKY_ERR_INVALID_ARGUMENT, "d = %d outside [1, 16]", d);
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(SKY_ERR_INVALID_ARGUMENT, "n = %lld outside [0, 2^31)", (long long)n);
+    if (ld < d) return fail(SKY_ERR_INVALID_ARGUMENT, "ld = %lld < d = %d", (long long)ld, d);
+    if (n > 0 && !pts) return fail(SKY_ERR_INVALID_ARGUMENT, "points pointer is NULL");
+    if (reinterpret_cast<uintptr_t>(pts) & 3u) return fail(SKY_ERR_INVALID_ARGUMENT, "points pointer not 4-byte aligned");
+    return SKY_OK;
+}
+
+sky_status make_plan(Plan& p, const float* pts, int64_t n, int32_t d, int64_t ld, const sky_options* opt)
+{
+    p.pts = pts;
+    p.n = n;
+    p.d = d;
+    p.ld = ld;
+    p.assume_unit = opt && opt->assume_unit;
+    int lg = (opt && opt->log2_g >= 0) ? opt->log2_g : auto_log2g(n, d);
+    if (opt && opt->log2_g > 16) return fail(SKY_ERR_TOO_LARGE, "log2_g = %d above 16", opt->log2_g);
+    if (lg * d > 27) return fail(SKY_ERR_TOO_LARGE, "grid of 2^%d cells exceeds the dense limit 2^27", lg * d);
+    p.log2g = lg;
+    p.morton_bits = morton_bits_for(d);
+    p.tma_ok = (ld == d) && ((reinterpret_cast<uintptr_t>(pts) & 15u) == 0);
+    p.refine_cfg = opt ? opt->tile_cfg : 0;
+    if (opt && (opt->n_filter < 0 || opt->n_filter > 16))
+        return fail(SKY_ERR_INVALID_ARGUMENT, "n_filter = %d outside [0, 16]", opt->n_filter);
+    if (opt && opt->n_filter > 0 && !opt->d_filter_pts)
+        return fail(SKY_ERR_INVALID_ARGUMENT, "n_filter > 0 with a NULL proposal pointer");
+    return SKY_OK;
+}
+
+// Steps (a)+(b): normalisation (optional), parameters, map + mark.
+sky_status run_build(Plan& p, cudaStream_t s)
+{
+    SKY_CUDA(cudaMemsetAsync(p.res, 0, sizeof(DevResult), s));
+    if (!p.assume_unit) SKY_CUDA(launch_minmax(p, s));
+    SKY_CUDA(launch_params(p, s));
+    SKY_CUDA(launch_map_mark(p, s));
+    return SKY_OK;
+}
+
+// Step (c) (+ the optional proposal filter).
+sky_status run_prune(Plan& p, const float* prop, int n_prop, cudaStream_t s, bool grid_api)
+{
+    SKY_CUDA(launch_snap(p, prop, n_prop, s));
+    SKY_CUDA(launch_prefix_or(p, s));
+    if (grid_api) {
+        SKY_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(p.res) + offsetof(DevResult, occupied_cells), 0,
+                                 2 * sizeof(uint32_t), s));
+        SKY_CUDA(launch_dominated(p, s));
+    }
+    SKY_CUDA(launch_survivors(p, n_prop, s));
+    return SKY_OK;
+}
+
+sky_status status_from_flags(uint32_t err)
+{
+    if (err & SKY_DEV_ERR_NONFINITE) return fail(SKY_ERR_NONFINITE, "input holds NaN or infinity");
+    if (err & SKY_DEV_ERR_TIMEOUT) return fail(SKY_ERR_TIMEOUT, "a bounded device wait ran out");
+    return SKY_OK;
+}
+
+DevResult* host_result()
+{
+    thread_local DevResult* h = nullptr;
+    if (!h) {
+        if (cudaMallocHost(&h, sizeof(DevResult)) != cudaSuccess) h = nullptr;
+    }
+    return h;
+}
+
+// Whole path on device-resident points (workspace from the stream-ordered pool).
+sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, const sky_options* opt,
+                          int32_t* out, int64_t capacity, int64_t* count, cudaStream_t s)
+{
+    Plan p;
+    sky_status st = make_plan(p, pts, n, d, ld, opt);
+    if (st != SKY_OK) return st;
+    t_stats = {};
+    t_stats.n = n;
+    t_stats.d = d;
+    t_stats.log2_g = p.log2g;
+    if (n == 0) {
+        *count = 0;
+        return SKY_OK;
+    }
+    enable_pool_cache();
+    const size_t bytes = layout(p, nullptr, false);
+    void* ws = nullptr;
+    SKY_CUDA(cudaMallocAsync(&ws, bytes, s));
+    layout(p, static_cast<char*>(ws), false);
+    const int n_prop = opt ? opt->n_filter : 0;
+    st = run_build(p, s);
+    if (st == SKY_OK) st = run_prune(p, n_prop ? opt->d_filter_pts : nullptr, n_prop, s, false);
+    if (st == SKY_OK) {
+        cudaError_t e = launch_sort(p, s);
+        if (e == cudaSuccess) e = launch_gather(p, s);
+        if (e == cudaSuccess) e = launch_refine(p, s);
+        if (e == cudaSuccess) e = launch_emit(p, out, capacity, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "kernel launch");
+    }
+    DevResult* h = host_result();
+    DevResult local{};
+    if (st == SKY_OK) {
+        cudaError_t e = cudaMemcpyAsync(h ? h : &local, p.res, sizeof(DevResult), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "result copy");
+    }
+    cudaFreeAsync(ws, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (st != SKY_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    const DevResult r = h ? *h : local;
+    t_stats.survivors = r.survivors;
+    t_stats.skyline = r.count;
+    t_stats.pairs = (int64_t)r.pairs;
+    t_stats.n_filter_used = (int32_t)r.n_filter_used;
+    st = status_from_flags(r.err);
+    if (st != SKY_OK) return st;
+    *count = r.count;
+    if ((int64_t)r.count > capacity)
+        return fail(SKY_ERR_CAPACITY, "skyline has %u points, capacity %lld", r.count, (long long)capacity);
+    return SKY_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+struct sky_grid {
+    Plan plan;
+    void* ws = nullptr;
+    cudaStream_t stream = nullptr;
+    bool pruned = false;
+};
+
+extern "C" {
+
+const char* sky_status_string(sky_status s)
+{
+    switch (s) {
+        case SKY_OK: return "ok";
+        case SKY_ERR_INVALID_ARGUMENT: return "invalid argument";
+        case SKY_ERR_NONFINITE: return "non-finite input";
+        case SKY_ERR_CAPACITY: return "output capacity too small";
+        case SKY_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case SKY_ERR_CUDA: return "CUDA error";
+        case SKY_ERR_TOO_LARGE: return "grid too large";
+        case SKY_ERR_TIMEOUT: return "device wait timed out";
+        case SKY_ERR_NO_DEVICE: return "no usable CUDA device";
+    }
+    return "unknown status";
+}
+
+const char* sky_last_error(void) { return t_err.c_str(); }
+
+const char* sky_version(void) { return "libsky 0.1 (sm_103a)"; }
+
+sky_status sky_last_run_stats(sky_run_stats* out)
+{
+    if (!out) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL stats pointer");
+    *out = t_stats;
+    return SKY_OK;
+}
+
+sky_status sky_build_grid(const float* d_pts, int64_t n, int32_t d, int64_t ld, const sky_options* opt,
+                          void* stream, sky_grid** out)
+{
+    if (!out) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL handle pointer");
+    *out = nullptr;
+    sky_status st = check_points(d_pts, n, d, ld);
+    if (st != SKY_OK) return st;
+    sky_grid* g = new (std::nothrow) sky_grid();
+    if (!g) return fail(SKY_ERR_OUT_OF_MEMORY, "host allocation failed");
+    st = make_plan(g->plan, d_pts, n, d, ld, opt);
+    if (st != SKY_OK) { delete g; return st; }
+    g->stream = static_cast<cudaStream_t>(stream);
+    const size_t bytes = layout(g->plan, nullptr, true);
+    cudaError_t e = cudaMalloc(&g->ws, bytes);
+    if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaMalloc(grid workspace)"); }
+    layout(g->plan, static_cast<char*>(g->ws), true);
+    st = run_build(g->plan, g->stream);
+    if (st != SKY_OK) { cudaFree(g->ws); delete g; return st; }
+    *out = g;
+    return SKY_OK;
+}
+
+sky_status sky_prune_cells(sky_grid* g, const float* d_filter_pts, int32_t n_filter, void* stream)
+{
+    if (!g) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL grid");
+    if (n_filter < 0 || n_filter > 16) return fail(SKY_ERR_INVALID_ARGUMENT, "n_filter = %d outside [0, 16]", n_filter);
+    if (n_filter > 0 && !d_filter_pts) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL proposal pointer");
+    if (stream) g->stream = static_cast<cudaStream_t>(stream);
+    if (g->plan.n == 0) { g->pruned = true; return SKY_OK; }
+    sky_status st = run_prune(g->plan, d_filter_pts, n_filter, g->stream, true);
+    if (st == SKY_OK) g->pruned = true;
+    return st;
+}
+
+sky_status sky_grid_stats(const sky_grid* g, sky_grid_stats_t* out)
+{
+    if (!g || !out) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->log2_g = g->plan.log2g;
+    out->d = g->plan.d;
+    out->n = g->plan.n;
+    if (g->plan.n == 0) return SKY_OK;
+    DevResult r{};
+    SKY_CUDA(cudaMemcpyAsync(&r, g->plan.res, sizeof(r), cudaMemcpyDeviceToHost, g->stream));
+    SKY_CUDA(cudaStreamSynchronize(g->stream));
+    out->occupied_cells = g->pruned ? (int64_t)r.occupied_cells : -1;
+    out->surviving_cells = g->pruned ? (int64_t)r.surviving_cells : -1;
+    out->surviving_points = g->pruned ? (int64_t)r.survivors : -1;
+    out->n_filter_used = (int32_t)r.n_filter_used;
+    out->error_flags = (int32_t)r.err;
+    return status_from_flags(r.err);
+}
+
+sky_status sky_grid_get_view(const sky_grid* g, sky_grid_view* out)
+{
+    if (!g || !out) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL argument");
+    out->cell_key = g->plan.keys;
+    out->occupied = g->plan.occ;
+    out->dominated = g->plan.dom;
+    out->survivors = reinterpret_cast<const int32_t*>(g->plan.surv_idx);
+    out->cell_offset = g->plan.params;
+    out->cell_scale = g->plan.params + 16;
+    out->words = g->plan.words;
+    return SKY_OK;
+}
+
+sky_status sky_grid_copy_out(const sky_grid* g, sky_grid_array which, void* d_dst, size_t bytes)
+{
+    if (!g || (!d_dst && bytes)) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL argument");
+    const Plan& p = g->plan;
+    const void* src = nullptr;
+    size_t need = 0;
+    switch (which) {
+        case SKY_GRID_CELL_KEY: src = p.keys; need = sizeof(uint32_t) * (size_t)p.n; break;
+        case SKY_GRID_OCCUPIED: src = p.occ; need = sizeof(uint32_t) * (size_t)p.words; break;
+        case SKY_GRID_DOMINATED:
+            if (!g->pruned) return fail(SKY_ERR_INVALID_ARGUMENT, "grid not pruned yet");
+            src = p.dom; need = sizeof(uint32_t) * (size_t)p.words; break;
+        case SKY_GRID_SURVIVORS: {
+            if (!g->pruned) return fail(SKY_ERR_INVALID_ARGUMENT, "grid not pruned yet");
+            DevResult r{};
+            if (p.n > 0) {
+                SKY_CUDA(cudaMemcpyAsync(&r, p.res, sizeof(r), cudaMemcpyDeviceToHost, g->stream));
+                SKY_CUDA(cudaStreamSynchronize(g->stream));
+            }
+            src = p.surv_idx; need = sizeof(int32_t) * (size_t)r.survivors; break;
+        }
+        case SKY_GRID_CELL_MAP: src = p.params; need = sizeof(float) * 32; break;
+        default: return fail(SKY_ERR_INVALID_ARGUMENT, "unknown array %d", (int)which);
+    }
+    if (bytes < need) return fail(SKY_ERR_CAPACITY, "array needs %zu bytes, got %zu", need, bytes);
+    if (need) SKY_CUDA(cudaMemcpyAsync(d_dst, src, need, cudaMemcpyDeviceToDevice, g->stream));
+    SKY_CUDA(cudaStreamSynchronize(g->stream));
+    return SKY_OK;
+}
+
+void sky_grid_destroy(sky_grid* g)
+{
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    cudaFree(g->ws);
+    delete g;
+}
+
+sky_status sky_skyline(const float* d_pts, int64_t n, int32_t d, int64_t ld, const sky_options* opt,
+                       int32_t* d_out_idx, int64_t out_capacity, int64_t* h_out_count, void* stream)
+{
+    if (!h_out_count) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL count pointer");
+    if (out_capacity < 0 || (out_capacity > 0 && !d_out_idx))
+        return fail(SKY_ERR_INVALID_ARGUMENT, "bad output buffer");
+    sky_status st = check_points(d_pts, n, d, ld);
+    if (st != SKY_OK) return st;
+    return skyline_device(d_pts, n, d, ld, opt, d_out_idx, out_capacity, h_out_count,
+                          static_cast<cudaStream_t>(stream));
+}
+
+sky_status sky_skyline_host(const float* h_pts, int64_t n, int32_t d, int64_t ld, const sky_options* opt,
+                            int32_t* h_out_idx, int64_t out_capacity, int64_t* h_out_count, void* stream)
+{
+    if (!h_out_count) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL count pointer");
+    if (out_capacity < 0 || (out_capacity > 0 && !h_out_idx))
+        return fail(SKY_ERR_INVALID_ARGUMENT, "bad output buffer");
+    sky_status st = check_points(h_pts, n, d, ld);
+    if (st != SKY_OK) return st;
+    if (n == 0) { *h_out_count = 0; return SKY_OK; }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    enable_pool_cache();
+    const size_t in_bytes = (size_t)((n - 1) * ld + d) * sizeof(float);
+    float* d_pts = nullptr;
+    int32_t* d_out = nullptr;
+    SKY_CUDA(cudaMallocAsync(&d_pts, align256(in_bytes), s));
+    cudaError_t e = cudaMallocAsync(&d_out, sizeof(int32_t) * (size_t)n, s);
+    if (e != cudaSuccess) { cudaFreeAsync(d_pts, s); return cuda_fail(e, "cudaMallocAsync(out)"); }
+    e = cudaMemcpyAsync(d_pts, h_pts, in_bytes, cudaMemcpyHostToDevice, s);
+    int64_t cnt = 0;
+    if (e == cudaSuccess) st = skyline_device(d_pts, n, d, ld, opt, d_out, n, &cnt, s);
+    else st = cuda_fail(e, "host-to-device copy");
+    if (st == SKY_OK) {
+        *h_out_count = cnt;
+        const int64_t ncopy = cnt < out_capacity ? cnt : out_capacity;
+        if (ncopy > 0) {
+            e = cudaMemcpyAsync(h_out_idx, d_out, sizeof(int32_t) * (size_t)ncopy, cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "device-to-host copy");
+        }
+        if (st == SKY_OK && cnt > out_capacity)
+            st = fail(SKY_ERR_CAPACITY, "skyline has %lld points, capacity %lld", (long long)cnt,
+                      (long long)out_capacity);
+    }
+    cudaFreeAsync(d_pts, s);
+    cudaFreeAsync(d_out, s);
+    e = cudaStreamSynchronize(s);
+    if (st == SKY_OK && e != cudaSuccess) st = cuda_fail(e, "stream synchronize");
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,192 @@
+// sky_common.cuh -- device helpers shared by libsky's kernels (sm_103a).
+//
+// Inline PTX for the Blackwell async-copy machinery (mbarrier + 1-D bulk
+// copies through the TMA unit), release/acquire flags for the decoupled
+// look-back scan, and a few bit tricks. Every wait here is bounded: after
+// kWaitLimit polls it records SKY_DEV_ERR_TIMEOUT in the call's error word and
+// gives up, so no kernel of this library can spin forever.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sky {
+
+constexpr int kMaxDim = 16;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Device error bits (OR-ed into one uint32 per call).
+constexpr uint32_t SKY_DEV_ERR_NONFINITE = 1u;
+constexpr uint32_t SKY_DEV_ERR_TIMEOUT = 2u;
+constexpr uint32_t SKY_DEV_ERR_CAPACITY = 4u;
+
+// Upper bound on polls of any flag or barrier (each poll may suspend briefly).
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---- mbarrier ---------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on a barrier phase. Returns false (and flags a timeout) when
+// the limit runs out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err)
+{
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 32) __nanosleep(64);
+    }
+    if (err) atomicOr(err, SKY_DEV_ERR_TIMEOUT);
+    return false;
+}
+
+// 1-D bulk copy global -> shared through the TMA unit, completing on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ---- release / acquire flags ----------------------------------------------
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t* p)
+{
+    return __ldcg(p);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---- decoupled look-back (single-pass prefix over tiles) --------------------
+// State word per tile: high 32 bits = flag (0 empty, 1 aggregate, 2 inclusive),
+// low 32 bits = value. Tiles are numbered in claim order (an atomic counter),
+// so every predecessor of a tile belongs to a CTA that is already running and
+// the wait below always ends; it is bounded all the same.
+constexpr unsigned long long kFlagAgg = 1ull << 32;
+constexpr unsigned long long kFlagInc = 2ull << 32;
+
+// Called by all 32 lanes of ONE warp. Returns the exclusive prefix of `tile`.
+__device__ __forceinline__ uint32_t lookback_prefix(unsigned long long* states, uint32_t tile,
+                                                    uint32_t aggregate, uint32_t* err)
+{
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) st_release_u64(&states[0], kFlagInc | aggregate);
+        return 0;
+    }
+    if (lane == 0) st_release_u64(&states[tile], kFlagAgg | aggregate);
+    uint32_t exclusive = 0;
+    long long base = (long long)tile - 1;
+    uint32_t polls = 0;
+    while (true) {
+        long long i = base - lane;
+        unsigned long long v = (i >= 0) ? ld_acquire_u64(&states[i]) : (kFlagInc | 0ull);
+        while (__any_sync(kFull, (v >> 32) == 0)) {
+            if (++polls > kWaitLimit) {
+                if (lane == 0 && err) atomicOr(err, SKY_DEV_ERR_TIMEOUT);
+                v = kFlagInc;  // give up: the result is flagged as invalid
+                break;
+            }
+            __nanosleep(32);
+            if ((v >> 32) == 0) v = ld_acquire_u64(&states[i]);
+        }
+        const uint32_t inc_mask = __ballot_sync(kFull, (v >> 32) == 2);
+        uint32_t val = (uint32_t)(v & 0xffffffffull);
+        if (inc_mask) {
+            const int first = __ffs(inc_mask) - 1;
+            if (lane > first) val = 0;
+            for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(kFull, val, o);
+            exclusive += val;
+            break;
+        }
+        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(kFull, val, o);
+        exclusive += val;
+        base -= 32;
+    }
+    if (lane == 0) st_release_u64(&states[tile], kFlagInc | (unsigned long long)(exclusive + aggregate));
+    return exclusive;
+}
+
+// ---- value -> column map (Eq. 1 with min/max normalisation) ----------------
+// t = (x - off) * s in binary32 round-to-nearest with no contraction, then
+// floor and clamp to [0, G-1]. Monotone non-decreasing in x.
+__device__ __forceinline__ uint32_t column_of(float x, float off, float s, uint32_t G)
+{
+    if (s == 0.0f) return 0u;
+    const float t = __fmul_rn(__fsub_rn(x, off), s);
+    if (!(t > 0.0f)) return 0u;
+    if (t >= (float)G) return G - 1u;
+    const uint32_t c = (uint32_t)__float2int_rd(t);
+    return c > G - 1u ? G - 1u : c;
+}
+
+// Order-preserving float <-> uint32 (for atomic min/max on floats).
+__device__ __forceinline__ uint32_t float_to_ordered(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(uint32_t u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__host__ __device__ constexpr inline int pad4(int d) { return (d + 3) & ~3; }
+
+}  // namespace sky

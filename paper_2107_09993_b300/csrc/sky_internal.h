@@ -1,0 +1,96 @@
+// sky_internal.h -- kernel launchers and workspace layout of libsky (host side).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sky {
+
+// Per-call result block, copied to the host once at the end of a call.
+struct DevResult {
+    uint32_t survivors;        // points left after step (c) (and the filter)
+    uint32_t count;            // skyline size
+    uint32_t err;              // SKY_DEV_ERR_* bits
+    uint32_t n_filter_used;    // proposals that snapped to a data point
+    unsigned long long pairs;  // candidate pairs examined by the refinement
+    uint32_t occupied_cells;   // filled on request (grid statistics)
+    uint32_t surviving_cells;
+};
+
+// Everything one skyline computation needs on the device.
+struct Plan {
+    // problem
+    const float* pts = nullptr;
+    int64_t n = 0;
+    int d = 0;
+    int64_t ld = 0;
+    int log2g = 0;
+    bool assume_unit = false;
+    bool tma_ok = false;       // 16-byte aligned and ld == d
+    int morton_bits = 0;       // bits per dimension of the sort key
+    int refine_cfg = 0;
+
+    // workspace (device)
+    uint32_t* mm_min = nullptr;      // [d] ordered-uint min
+    uint32_t* mm_max = nullptr;      // [d] ordered-uint max
+    float* params = nullptr;         // [4][16]: offset, cell scale, code scale, morton scale
+    uint32_t* keys = nullptr;        // [n] cell key per point
+    uint32_t* occ = nullptr;         // [words] occupancy bitmap
+    uint32_t* pre = nullptr;         // [words] inclusive prefix-OR of occ
+    uint32_t* dom = nullptr;         // [words] dominated bitmap (grid API only)
+    int64_t words = 0;
+    unsigned long long* lb_states = nullptr;  // look-back states (max of both scans)
+    uint32_t* lb_counter = nullptr;           // [2] tile counters
+    int64_t lb_tiles = 0;
+    uint32_t* surv_key = nullptr;    // [n] morton key of survivors
+    uint32_t* surv_idx = nullptr;    // [n] row id of survivors (ascending)
+    uint32_t* sort_key2 = nullptr;   // [n] ping-pong buffers
+    uint32_t* sort_val2 = nullptr;
+    uint32_t* hist = nullptr;        // [256][sort_blocks]
+    int64_t sort_blocks = 0;
+    float* X = nullptr;              // [n_pad][dp] sorted survivor coordinates
+    uint32_t* C = nullptr;           // [n_pad][dp/4] 7-bit codes
+    int32_t* ids = nullptr;          // [n_pad] row id per sorted survivor
+    float* bbox = nullptr;           // [tiles][2][dp]
+    uint8_t* keep = nullptr;         // [n] 1 = skyline
+    float* filt = nullptr;           // [16][16] snapped filter points
+    unsigned long long* snap = nullptr;  // [16] packed (sum, row) argmin
+    DevResult* res = nullptr;
+    // last sort output
+    const uint32_t* sorted_val = nullptr;
+};
+
+constexpr int kRefineTile = 128;   // points per refinement tile
+constexpr int kScanItems = 8;      // items per thread in the look-back scans
+constexpr int kScanThreads = 256;
+constexpr int kScanTile = kScanItems * kScanThreads;
+constexpr int kSortItems = 8;
+constexpr int kSortThreads = 256;
+constexpr int kSortTile = kSortItems * kSortThreads;
+
+// Workspace bytes for a plan (all buffers, 256-byte aligned each).
+size_t plan_workspace_bytes(int64_t n, int d, int log2g, bool grid_api);
+// Carves `ws` into the plan's buffers.
+void plan_carve(Plan& p, void* ws, bool grid_api);
+
+// Launchers (k_grid.cu)
+cudaError_t launch_minmax(const Plan& p, cudaStream_t s);
+cudaError_t launch_params(const Plan& p, cudaStream_t s);
+cudaError_t launch_map_mark(const Plan& p, cudaStream_t s);
+cudaError_t launch_prefix_or(const Plan& p, cudaStream_t s);
+cudaError_t launch_dominated(const Plan& p, cudaStream_t s);
+cudaError_t launch_snap(const Plan& p, const float* d_prop, int n_prop, cudaStream_t s);
+cudaError_t launch_survivors(const Plan& p, int n_filter, cudaStream_t s);
+cudaError_t launch_cell_stats(const Plan& p, cudaStream_t s);
+// k_sort.cu
+cudaError_t launch_sort(Plan& p, cudaStream_t s);
+// k_refine.cu
+cudaError_t launch_gather(const Plan& p, cudaStream_t s);
+cudaError_t launch_refine(const Plan& p, cudaStream_t s);
+cudaError_t launch_emit(const Plan& p, int32_t* out, int64_t capacity, cudaStream_t s);
+
+int auto_log2g(int64_t n, int d);
+int morton_bits_for(int d);
+
+}  // namespace sky
