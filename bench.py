@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Exact skyline throughput on B300: points/s through the libsky C ABI.
+
+Workload (one "step"): the whole skyline path (steps (a)-(d): map, mark,
+prune, refine + compact) over n = 1,000,000 points, d = 8, float32, for each
+of the three synthetic distributions of the paper's experiments
+(independent, correlated, anti-correlated; seed 1) -- 3,000,000 input points
+per step. Inputs are resident in HBM when the timed region starts; L2 (126 MB)
+is flushed before every timed step by writing a 512 MB buffer.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sky|reference]
+
+N > 1 runs independent replicas (the skyline of one point set is computed on
+one GPU), launched under torchrun, weak scaling.
+`--impl reference` times the CPU oracle (sort-first skyline) on the host cores
+on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import skydata  # noqa: E402
+
+N_POINTS = 1_000_000
+DIM = 8
+SEED = 1
+KINDS = ("independent", "correlated", "anticorrelated")
+METRIC = "skyline input points/s (exact)"
+UNIT = "points/s"
+CPU_SAMPLE_ROWS = 100_000
+
+
+def workload_config(extra=None):
+    cfg = {"workload": "plain SkyCell, n=1,000,000 x d=8 float32, independent + correlated + "
+                       "anti-correlated (seed 1), 3e6 points per step",
+           "n": N_POINTS, "d": DIM, "distributions": list(KINDS), "seed": SEED,
+           "l2": "flushed before every timed step (512 MB write)", "options": "default (min/max normalisation, automatic grid)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def datasets():
+    return [skydata.generate(k, N_POINTS, DIM, SEED) for k in KINDS]
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_uuid):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        sel = ["-i", gpu_uuid] if gpu_uuid else []
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", *sel, f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------- roofline --
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def refine_source_hash():
+    src = os.path.join(ROOT, "paper_2107_09993_b300", "csrc", "k_refine.cu")
+    with open(src, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """dram bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f)
+    e = t.get(kernel)
+    if not e or e.get("source_sha256_16") != refine_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def ops_per_pair(d):
+    # one pair test = ceil(d/4) word subtracts + the AND tree (3-input LOP3) + one compare
+    dw = (d + 3) // 4
+    return dw + (dw + 1) // 2 + 1
+
+
+# ------------------------------------------------------------------ sky arm --
+def run_sky(args):
+    import torch
+    import paper_2107_09993_b300 as sky
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    host = datasets()
+    xs = [torch.from_numpy(P).to(dev) for P in host]
+    outs = [torch.empty(N_POINTS, dtype=torch.int32, device=dev) for _ in xs]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def step():
+        sizes = []
+        for x, o in zip(xs, outs):
+            r = sky.skyline(x, out=o)
+            sizes.append(int(r.numel()))
+        return sizes
+
+    for _ in range(args.warmup):
+        step()
+    sky.set_phase_timing(True)
+    phase_sum = {}
+    pairs = 0
+    launches = 0
+    b_prune = 0
+    sizes = None
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "") or "")
+    if uuid and not uuid.startswith("GPU-"):
+        uuid = "GPU-" + uuid
+    clocks = ClockSampler(uuid) if rank == 0 else None
+    total_ms = 0.0
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sizes = []
+        per_call = []
+        for x, o in zip(xs, outs):
+            r = sky.skyline(x, out=o)
+            sizes.append(int(r.numel()))
+            st = sky.last_run_stats()
+            ph = sky.last_phase_times()
+            per_call.append((st, ph))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        total_ms += e0.elapsed_time(e1)
+        for st, ph in per_call:
+            pairs += st["pairs"]
+            launches += st["kernels"]
+            n, d, m = st["n"], st["d"], st["survivors"]
+            # normalise read + map read + key write/read + survivor-row re-read + (morton, id) write
+            b_prune += 4 * n * d * 2 + 8 * n + 4 * d * m + 8 * m
+            for k, v in ph.items():
+                phase_sum[k] = phase_sum.get(k, 0.0) + v
+    barrier()
+    clk = clocks.stop() if clocks else None
+    sky.set_phase_timing(False)
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max_ms = float(t.item())
+    pts_per_step = N_POINTS * len(KINDS)
+    value = world * args.steps * pts_per_step / (t_max_ms / 1e3)
+
+    # ---- end to end through the host-buffer entry point (pinned memory)
+    pinned = [torch.from_numpy(P).pin_memory() for P in host]
+    hout = [torch.empty(N_POINTS, dtype=torch.int32).pin_memory() for _ in host]
+    for P, o in zip(pinned, hout):
+        sky.skyline_host(P, out=o)
+    e2e_ms = 0.0
+    d2h = 0
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        d2h = 0
+        for P, o in zip(pinned, hout):
+            r = sky.skyline_host(P, out=o)
+            d2h += 4 * int(r.numel()) + 8
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    barrier()
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps * pts_per_step / (float(te.item()) / 1e3)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = measured_peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1900.0
+    # dominant kernel: the phase with the largest device time
+    dom_phase = max(phase_sum, key=phase_sum.get)
+    refine_s = phase_sum["refine_ms"] / 1e3
+    alu_peak_gops = 148 * 128 * sm_mhz * 1e6 / 1e9  # int32 lane ops/s, measured median SM clock
+    refine_gops = pairs * ops_per_pair(DIM) / refine_s / 1e9 if refine_s > 0 else 0.0
+    prune_s = (phase_sum["normalize_ms"] + phase_sum["map_mark_ms"] + phase_sum["prune_ms"]
+               + phase_sum["survivors_ms"]) / 1e3
+    prune_gbs = b_prune / prune_s / 1e9 if prune_s > 0 else 0.0
+    launches_refine = args.steps * len(KINDS)
+    traffic = profiled_traffic("k_refine")
+    roof_refine = {"kernel": "k_refine", "bound": "alu", "achieved": round(refine_gops, 1),
+                   "peak": round(alu_peak_gops, 1), "unit": "Gop/s",
+                   "frac": round(refine_gops / alu_peak_gops, 4),
+                   "traffic": traffic,
+                   "peak_source": f"148 SMs x 128 int32 lanes x {sm_mhz:.0f} MHz (median SM clock sampled during the run)",
+                   "work": f"{pairs / launches_refine:.4g} candidate pair tests per launch x {ops_per_pair(DIM)} ops",
+                   "ms_per_launch": round(phase_sum['refine_ms'] / launches_refine, 4)}
+    roof_prune = {"kernel": "pruning pass (k_minmax + k_map_mark_tma + k_prefix_or_dim + k_survivors)",
+                  "bound": "hbm", "achieved": round(prune_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                  "frac": round(prune_gbs / peaks["hbm_gbs"], 4), "traffic": None,
+                  "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json)" if peak_src == "measured"
+                  else "fallback 6.4 TB/s",
+                  "note": "32 MB inputs fit in L2, so the second read of each point can hit L2"}
+    roofline = roof_refine if dom_phase == "refine_ms" else roof_prune
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (skydata generators, seed 1)",
+        "config": workload_config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
+                "h2d_bytes_per_step": sum(int(P.nbytes) for P in host), "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "roofline_prune": roof_prune,
+        "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in phase_sum.items()},
+        "skyline_sizes": sizes,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(host, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------- CPU baseline --
+def cpu_sample_step(host, rows):
+    import oracle
+    t0 = time.perf_counter()
+    for P in host:
+        oracle.skyline_sfs(P[:rows])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(host, seconds):
+    import oracle
+    rows = CPU_SAMPLE_ROWS
+    spent, reps = 0.0, 0
+    while spent < seconds or reps == 0:
+        spent += cpu_sample_step(host, rows)
+        reps += 1
+    value = reps * rows * len(host) / spent
+    return {"value": round(value, 1), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"sort-first skyline oracle on the first {rows:,} rows of each of the 3 datasets, "
+                      f"{reps} repetition(s), {spent:.1f} s"}
+
+
+# -------------------------------------------------------------- reference --
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    host = datasets()
+    rows = CPU_SAMPLE_ROWS
+    for _ in range(args.warmup):
+        cpu_sample_step(host, rows // 10)
+    t = 0.0
+    for _ in range(args.steps):
+        t += cpu_sample_step(host, rows)
+    value = args.steps * rows * len(host) / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (skydata generators, seed 1)",
+        "config": workload_config({"sample": f"first {rows:,} rows of each dataset per step"}),
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"first {rows:,} rows of each of the 3 datasets per step"},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["sky", "reference"], default="sky")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_sky(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -192,10 +192,27 @@ typedef struct sky_run_stats {
     int64_t skyline;              /* points in the result                       */
     int64_t pairs;                /* candidate pairs examined in step (d)       */
     int32_t n_filter_used;        /* proposals that snapped to a data point     */
-    int32_t reserved;
+    int32_t kernels;              /* kernels of this library the call launched  */
 } sky_run_stats;
 
 SKY_API sky_status sky_last_run_stats(sky_run_stats* out);
+
+/* Per-phase device times of the last sky_skyline call on the calling thread,
+ * taken with CUDA events recorded on the call's stream between the phases.
+ * Recording is off until sky_set_phase_timing(1) is called on that thread. */
+typedef struct sky_phase_times {
+    float normalize_ms;           /* min/max pass + map parameters             */
+    float map_mark_ms;            /* steps (a)+(b)                             */
+    float prune_ms;               /* step (c): proposal snap + prefix-OR       */
+    float survivors_ms;           /* step (c): survivor compaction             */
+    float sort_ms;                /* Morton sort of the survivors              */
+    float gather_ms;              /* survivor layout + tile boxes              */
+    float refine_ms;              /* step (d): dominance tests                 */
+    float emit_ms;                /* step (d): index compaction                */
+} sky_phase_times;
+
+SKY_API sky_status sky_set_phase_timing(int32_t enable);
+SKY_API sky_status sky_last_phase_times(sky_phase_times* out);
 
 /* Static text for a status code. */
 SKY_API const char* sky_status_string(sky_status status);

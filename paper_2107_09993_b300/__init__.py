@@ -51,7 +51,12 @@ class GridStats(ctypes.Structure):
 
 class RunStats(ctypes.Structure):
     _fields_ = [("n", _i64), ("d", _i32), ("log2_g", _i32), ("survivors", _i64), ("skyline", _i64),
-                ("pairs", _i64), ("n_filter_used", _i32), ("reserved", _i32)]
+                ("pairs", _i64), ("n_filter_used", _i32), ("kernels", _i32)]
+
+
+class PhaseTimes(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("normalize_ms", "map_mark_ms", "prune_ms", "survivors_ms",
+                                               "sort_ms", "gather_ms", "refine_ms", "emit_ms")]
 
 
 _lib = None
@@ -75,6 +80,8 @@ def load():
         "sky_grid_copy_out": ([_vp, _i32, _vp, _sz], _i32),
         "sky_grid_destroy": ([_vp], None),
         "sky_last_run_stats": ([P(RunStats)], _i32),
+        "sky_set_phase_timing": ([_i32], _i32),
+        "sky_last_phase_times": ([P(PhaseTimes)], _i32),
         "sky_status_string": ([_i32], ctypes.c_char_p),
         "sky_last_error": ([], ctypes.c_char_p),
         "sky_version": ([], ctypes.c_char_p),
@@ -171,7 +178,18 @@ def skyline_host(points, log2_g=None, assume_unit=False, capacity=None, tile_cfg
 def last_run_stats() -> dict:
     s = RunStats()
     _check(load().sky_last_run_stats(ctypes.byref(s)))
-    return {f: getattr(s, f) for f, _ in RunStats._fields_ if f != "reserved"}
+    return {f: getattr(s, f) for f, _ in RunStats._fields_}
+
+
+def set_phase_timing(enable: bool = True):
+    """Record CUDA events between the phases of later skyline calls on this thread."""
+    _check(load().sky_set_phase_timing(1 if enable else 0))
+
+
+def last_phase_times() -> dict:
+    t = PhaseTimes()
+    _check(load().sky_last_phase_times(ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in PhaseTimes._fields_}
 
 
 class Grid:

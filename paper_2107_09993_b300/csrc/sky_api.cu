@@ -19,6 +19,40 @@ namespace {
 
 thread_local std::string t_err;
 thread_local sky_run_stats t_stats = {};
+thread_local sky_phase_times t_phase = {};
+thread_local bool t_timing = false;
+thread_local cudaEvent_t t_ev[9] = {};
+
+// Optional per-phase events on the call's stream.
+struct PhaseClock {
+    cudaStream_t s;
+    bool on;
+    int next = 0;
+    explicit PhaseClock(cudaStream_t st) : s(st), on(t_timing)
+    {
+        if (!on) return;
+        for (auto& e : t_ev)
+            if (!e && cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
+        mark();
+    }
+    void mark()
+    {
+        if (on && next < 9) cudaEventRecord(t_ev[next++], s);
+    }
+    void collect()
+    {
+        if (!on) return;
+        float ms[8] = {};
+        for (int i = 0; i + 1 < next; ++i) cudaEventElapsedTime(&ms[i], t_ev[i], t_ev[i + 1]);
+        t_phase = {ms[0], ms[1], ms[2], ms[3], ms[4], ms[5], ms[6], ms[7]};
+    }
+};
+
+int count_kernels(const Plan& p, int n_prop)
+{
+    const int passes = (p.morton_bits * p.d + 7) / 8;
+    return (p.assume_unit ? 0 : 1) + 1 + 1 + (n_prop > 0 ? 1 : 0) + 1 + p.d + 1 + 3 * passes + 1 + 1 + 1;
+}
 
 sky_status fail(sky_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 sky_status fail(sky_status s, const char* fmt, ...)
@@ -203,15 +237,31 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
     SKY_CUDA(cudaMallocAsync(&ws, bytes, s));
     layout(p, static_cast<char*>(ws), false);
     const int n_prop = opt ? opt->n_filter : 0;
-    st = run_build(p, s);
-    if (st == SKY_OK) st = run_prune(p, n_prop ? opt->d_filter_pts : nullptr, n_prop, s, false);
-    if (st == SKY_OK) {
-        cudaError_t e = launch_sort(p, s);
+    PhaseClock clk(s);
+    st = SKY_OK;
+    {
+        cudaError_t e = cudaMemsetAsync(p.res, 0, sizeof(DevResult), s);
+        if (e == cudaSuccess && !p.assume_unit) e = launch_minmax(p, s);
+        if (e == cudaSuccess) e = launch_params(p, s);
+        clk.mark();
+        if (e == cudaSuccess) e = launch_map_mark(p, s);
+        clk.mark();
+        if (e == cudaSuccess) e = launch_snap(p, n_prop ? opt->d_filter_pts : nullptr, n_prop, s);
+        if (e == cudaSuccess) e = launch_prefix_or(p, s);
+        clk.mark();
+        if (e == cudaSuccess) e = launch_survivors(p, n_prop, s);
+        clk.mark();
+        if (e == cudaSuccess) e = launch_sort(p, s);
+        clk.mark();
         if (e == cudaSuccess) e = launch_gather(p, s);
+        clk.mark();
         if (e == cudaSuccess) e = launch_refine(p, s);
+        clk.mark();
         if (e == cudaSuccess) e = launch_emit(p, out, capacity, s);
+        clk.mark();
         if (e != cudaSuccess) st = cuda_fail(e, "kernel launch");
     }
+    t_stats.kernels = count_kernels(p, n_prop);
     DevResult* h = host_result();
     DevResult local{};
     if (st == SKY_OK) {
@@ -223,6 +273,7 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
     if (st != SKY_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
     const DevResult r = h ? *h : local;
+    clk.collect();
     t_stats.survivors = r.survivors;
     t_stats.skyline = r.count;
     t_stats.pairs = (int64_t)r.pairs;
@@ -271,6 +322,19 @@ sky_status sky_last_run_stats(sky_run_stats* out)
 {
     if (!out) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL stats pointer");
     *out = t_stats;
+    return SKY_OK;
+}
+
+sky_status sky_set_phase_timing(int32_t enable)
+{
+    t_timing = enable != 0;
+    return SKY_OK;
+}
+
+sky_status sky_last_phase_times(sky_phase_times* out)
+{
+    if (!out) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL pointer");
+    *out = t_phase;
     return SKY_OK;
 }
 
