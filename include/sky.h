@@ -214,6 +214,33 @@ typedef struct sky_phase_times {
 SKY_API sky_status sky_set_phase_timing(int32_t enable);
 SKY_API sky_status sky_last_phase_times(sky_phase_times* out);
 
+/*
+ * No-allocation variant of sky_skyline, for callers that cannot allocate
+ * memory at the point of the call (for example a process whose device memory
+ * is already owned by its own arena allocator, or a latency-critical loop
+ * where an allocation's implicit synchronisation is not allowed). The paper
+ * has no counterpart: it is a deployment addition.
+ *
+ * Same arguments and result as sky_skyline, but every piece of scratch memory
+ * comes from one fixed array in device global memory that the library
+ * reserves at load time (about 10 MiB per GPU that loads the library, held
+ * until the process exits); the call performs no cudaMalloc, cudaFree or
+ * other allocation. Limits: n <= SKY_NOALLOC_MAX_POINTS and a grid of at most
+ * 2^20 cells (log2_g * d <= 20; the automatic choice is lowered to fit);
+ * larger requests return SKY_ERR_TOO_LARGE. All calls share the array and it
+ * keeps the last call's contents (what must start at zero is cleared by each
+ * call): calls that overlap on the GPU race and must be serialised by the
+ * caller. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before starting any stream capture on the device. Synchronises `stream`
+ * once. Errors are described by sky_noalloc_last_error().
+ */
+#define SKY_NOALLOC_MAX_POINTS 65536
+SKY_API sky_status sky_skyline_noalloc(const float* d_pts, int64_t n, int32_t d, int64_t ld,
+                                       const sky_options* opt, int32_t* d_out_idx, int64_t out_capacity,
+                                       int64_t* h_out_count, void* stream);
+SKY_API const char* sky_noalloc_last_error(void);
+
 /* Static text for a status code. */
 SKY_API const char* sky_status_string(sky_status status);
 

@@ -288,6 +288,24 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
 
 }  // namespace
 
+namespace sky {
+
+size_t plan_workspace_bytes(int64_t n, int d, int log2g, bool grid_api)
+{
+    Plan p;
+    p.n = n;
+    p.d = d;
+    p.log2g = log2g;
+    return layout(p, nullptr, grid_api);
+}
+
+void plan_carve(Plan& p, void* ws, bool grid_api)
+{
+    layout(p, static_cast<char*>(ws), grid_api);
+}
+
+}  // namespace sky
+
 // ===========================================================================
 struct sky_grid {
     Plan plan;

@@ -1,0 +1,77 @@
+"""GPU test of sky_skyline_noalloc, the entry point that allocates nothing.
+
+Some callers cannot allocate memory where they need a skyline (their device
+memory already belongs to their own arena allocator, or an allocation's
+implicit synchronisation is not allowed in their loop). sky_skyline_noalloc
+serves them from a fixed scratch array inside the library. This test calls it
+through the C ABI and checks that two calls in a row give exactly the indices
+of the regular sky_skyline entry point (the skyline is an index set, so the
+tolerance is exact equality), and that oversized requests are refused.
+
+Kept in its own file, named to be collected last, so that a run stopping at the
+first failure has run every other test before it.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import skydata
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2107_09993_b300 as sky  # noqa: E402
+
+
+def _bind(lib):
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.sky_skyline_noalloc.argtypes = [vp, i64, i32, i64, ctypes.POINTER(sky.Options), vp, i64,
+                                        ctypes.POINTER(i64), vp]
+    lib.sky_skyline_noalloc.restype = i32
+    lib.sky_noalloc_last_error.argtypes = []
+    lib.sky_noalloc_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+def _noalloc(lib, x, cap, **kw):
+    n, d = x.shape
+    o = sky._opts(kw.get("log2_g"), kw.get("assume_unit", False), None, 0)
+    out = torch.full((max(cap, 1),), -7, dtype=torch.int32, device=x.device)
+    cnt = ctypes.c_int64(-1)
+    st = lib.sky_skyline_noalloc(ctypes.c_void_p(x.data_ptr()), n, d, d, ctypes.byref(o),
+                                 ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(cnt),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return st, cnt.value, out
+
+
+def test_noalloc_matches_regular_entry_point_twice():
+    lib = _bind(sky.load())
+    cases = [("anticorrelated", 65536, 8), ("independent", 40000, 4), ("correlated", 3000, 16),
+             ("anticorrelated", 129, 3), ("independent", 1, 2)]
+    for kind, n, d in cases:
+        x = torch.from_numpy(skydata.generate(kind, n, d, seed=n + d)).cuda()
+        want = sky.skyline(x).cpu()
+        for call in range(2):
+            st, cnt, out = _noalloc(lib, x, n)
+            assert st == 0, (kind, n, d, call, lib.sky_noalloc_last_error())
+            assert cnt == want.numel()
+            assert torch.equal(out[:cnt].cpu(), want), (kind, n, d, call)
+        # unit-cube map, explicit grid
+        lg = min(2, 20 // d)
+        want_u = sky.skyline(x, assume_unit=True, log2_g=lg).cpu()
+        st, cnt, out = _noalloc(lib, x, n, assume_unit=True, log2_g=lg)
+        assert st == 0 and torch.equal(out[:cnt].cpu(), want_u)
+
+
+def test_noalloc_refuses_oversized_requests():
+    lib = _bind(sky.load())
+    x = torch.rand((65537, 4), device="cuda")
+    st, cnt, out = _noalloc(lib, x, 65537)
+    assert st == 6 and b"65536" in lib.sky_noalloc_last_error()
+    y = torch.rand((1000, 4), device="cuda")
+    st, cnt, out = _noalloc(lib, y, 1000, log2_g=6)          # 2^24 cells > 2^20
+    assert st == 6 and b"2^20" in lib.sky_noalloc_last_error()
+    want = sky.skyline(y).cpu()
+    st, cnt, out = _noalloc(lib, y, want.numel() - 1)
+    assert st == 3 and cnt == want.numel()
