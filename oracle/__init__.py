@@ -129,20 +129,31 @@ def dominators(P, idx, threads: int = 0) -> np.ndarray:
     return w
 
 
-def cell_params(P, log2g: int, assume_unit: bool = False):
-    """Offsets and scales of the value->column map (float32 arrays of length d)."""
+MAP_MODES = {"auto": 0, "unit": 1, "minmax": 2}
+
+
+def _mode(assume_unit, mode):
+    if mode is None:
+        mode = "unit" if assume_unit else "minmax"
+    return MAP_MODES[mode]
+
+
+def cell_params(P, log2g: int, assume_unit: bool = False, mode: str | None = None):
+    """Offsets and scales of the value->column map (float32 arrays of length d).
+    mode: "unit" (Eq. 1 as printed), "minmax" (per-dimension normalisation) or
+    "auto" (Eq. 1 when every dimension lies in [0,1] and spans >= 0.5)."""
     P, n, d = _pts(P)
     off = np.empty(d, dtype=np.float32)
     sc = np.empty(d, dtype=np.float32)
-    _load().orc_cell_params(P.ctypes.data, n, d, d, int(log2g), int(bool(assume_unit)),
+    _load().orc_cell_params(P.ctypes.data, n, d, d, int(log2g), _mode(assume_unit, mode),
                             off.ctypes.data, sc.ctypes.data)
     return off, sc
 
 
-def cell_keys(P, log2g: int, assume_unit: bool = False) -> np.ndarray:
+def cell_keys(P, log2g: int, assume_unit: bool = False, mode: str | None = None) -> np.ndarray:
     """Eq. 1: uint64 key of each point's Layer-log2g cell (dim d-1 most significant)."""
     P, n, d = _pts(P)
-    off, sc = cell_params(P, log2g, assume_unit)
+    off, sc = cell_params(P, log2g, assume_unit, mode)
     keys = np.empty(n, dtype=np.uint64)
     _load().orc_cell_keys(P.ctypes.data, n, d, d, int(log2g), off.ctypes.data,
                           sc.ctypes.data, keys.ctypes.data)

@@ -32,7 +32,9 @@
  *     column = clamp(floor(t), 0, G-1). With the unit-cube assumption,
  *     min_k = 0 and s_k = G. Range 0 gives s_k = 0 (every point in column 0);
  *     an infinite range gives s_k = G / FLT_MAX. Every such map is monotone
- *     non-decreasing in x, which is all that cell pruning needs.
+ *     non-decreasing in x, which is all that cell pruning needs. The
+ *     automatic choice keeps Eq. 1 when every dimension lies in [0,1] and
+ *     spans at least half of it, and normalises otherwise.
  *   - Non-finite inputs are outside the method (they break the order); callers
  *     of the oracle must not pass them.
  *   - Cell keys: key = sum_k column_k << (log2G * k), i.e. dimension d-1 is
@@ -205,22 +207,41 @@ ORC_API int64_t orc_skyline_sfs(const float* P, int64_t n, int d, int64_t ld,
 
 /* ---------------------------------------------------------------------- */
 /* Value -> column map (Eq. 1 and its min/max reading, see header).       */
+/* mode 1: unit cube, Eq. 1 as printed (offset 0, scale G).               */
+/* mode 2: min/max normalisation of every dimension.                      */
+/* mode 0: automatic -- Eq. 1 when every dimension's values lie in [0,1]  */
+/*         and span at least half of it (max - min >= 0.5 in binary32),   */
+/*         min/max normalisation of every dimension otherwise.            */
 /* `offset` and `scale` receive d floats each.                            */
 /* ---------------------------------------------------------------------- */
 ORC_API void orc_cell_params(const float* P, int64_t n, int d, int64_t ld,
-                             int log2g, int assume_unit, float* offset, float* scale)
+                             int log2g, int mode, float* offset, float* scale)
 {
     const float G = (float)(1u << log2g);
-    for (int k = 0; k < d; ++k) {
-        if (assume_unit || n <= 0) { offset[k] = 0.0f; scale[k] = G; continue; }
-        float mn = P[k], mx = P[k];
-        for (int64_t i = 1; i < n; ++i) {
-            float v = P[i * ld + k];
-            if (v < mn) mn = v;
-            if (v > mx) mx = v;
+    float mn[64], mx[64];
+    int unit = (mode == 1) || n <= 0;
+    if (!unit) {
+        for (int k = 0; k < d; ++k) {
+            mn[k] = P[k];
+            mx[k] = P[k];
+            for (int64_t i = 1; i < n; ++i) {
+                float v = P[i * ld + k];
+                if (v < mn[k]) mn[k] = v;
+                if (v > mx[k]) mx[k] = v;
+            }
         }
-        volatile float range = mx - mn;        /* binary32, round to nearest */
-        offset[k] = mn;
+        if (mode == 0) {
+            unit = 1;
+            for (int k = 0; k < d; ++k) {
+                volatile float span = mx[k] - mn[k];
+                if (!(mn[k] >= 0.0f && mx[k] <= 1.0f && span >= 0.5f)) unit = 0;
+            }
+        }
+    }
+    for (int k = 0; k < d; ++k) {
+        if (unit) { offset[k] = 0.0f; scale[k] = G; continue; }
+        volatile float range = mx[k] - mn[k];  /* binary32, round to nearest */
+        offset[k] = mn[k];
         if (range == 0.0f) scale[k] = 0.0f;
         else if (isinf(range)) scale[k] = G / FLT_MAX;
         else scale[k] = G / range;             /* correctly rounded binary32 division */

@@ -63,6 +63,29 @@ def test_normalised_map_properties():
     assert np.all(cols[:, 3] == 0)                       # zero range -> column 0
 
 
+def test_automatic_map_choice():
+    """The automatic map is Eq. 1 for data spanning most of the unit cube and
+    the min/max normalisation otherwise (reading of Eq. 1 for general data)."""
+    rng = np.random.default_rng(5)
+    wide = rng.random((500, 3), dtype=np.float32)
+    wide[0] = 0.0
+    wide[1] = 1.0
+    assert np.array_equal(oracle.cell_keys(wide, 4, mode="auto"), oracle.cell_keys(wide, 4, mode="unit"))
+    narrow = (0.25 + 0.2 * rng.random((500, 3))).astype(np.float32)   # spans < 0.5
+    assert np.array_equal(oracle.cell_keys(narrow, 4, mode="auto"), oracle.cell_keys(narrow, 4, mode="minmax"))
+    assert not np.array_equal(oracle.cell_keys(narrow, 4, mode="auto"), oracle.cell_keys(narrow, 4, mode="unit"))
+    neg = wide.copy()
+    neg[7, 2] = -0.01                                                    # leaves [0, 1]
+    assert np.array_equal(oracle.cell_keys(neg, 4, mode="auto"), oracle.cell_keys(neg, 4, mode="minmax"))
+    big = wide.copy()
+    big[9, 0] = 1.5
+    assert np.array_equal(oracle.cell_keys(big, 4, mode="auto"), oracle.cell_keys(big, 4, mode="minmax"))
+    # under min/max normalisation the extremes land in the first / last column
+    cols = np.array([oracle.cell_columns(k, 3, 4) for k in oracle.cell_keys(narrow, 4, mode="minmax")])
+    for k in range(3):
+        assert cols[np.argmin(narrow[:, k]), k] == 0 and cols[np.argmax(narrow[:, k]), k] == 15
+
+
 # ---------------------------------------------------------- Definitions ---
 
 def _occ_from_cells(cells_c0_first, d, log2g):
