@@ -68,11 +68,15 @@ typedef struct sky_options {
      * Sec. 3 / Algorithm 1. -1 picks it from n and d (automatic). The grid
      * must satisfy log2_g * d <= 27 (dense bitmap), else SKY_ERR_TOO_LARGE. */
     int32_t log2_g;
-    /* 1: the data is taken to lie in the unit cube and Eq. 1 is used as
-     * printed (column = floor(x * 2^log2_g)); values outside [0,1) are
-     * clamped to the first or last column, so the result stays exact for any
-     * finite input. 0: each dimension is first normalised by its min and max
-     * (one extra read pass). */
+    /* Value -> column map of step (a). Any monotone map keeps the result
+     * exact; the choice only changes how much step (c) prunes.
+     * 1: Eq. 1 as printed, for data in the unit cube: column =
+     *    floor(x * 2^log2_g), values outside [0,1) clamped to the first or
+     *    last column.
+     * 2: per-dimension min/max normalisation first (one extra read pass).
+     * 0 (default): automatic -- the map pass uses Eq. 1 and tracks min/max;
+     *    if some dimension leaves [0,1] or spans less than half of it, a
+     *    second map pass with min/max scales replaces the first. */
     int32_t assume_unit;
     /* Optional pre-filter proposals: n_filter points of d floats (device,
      * row-major). Any coordinates are accepted. Each proposal f is replaced by
@@ -104,7 +108,8 @@ typedef struct sky_grid_stats_t {
 /* Device views into a grid handle, for inspection and tests. Valid until
  * sky_grid_destroy. All arrays live on the device. */
 typedef struct sky_grid_view {
-    const uint32_t* cell_key;     /* [n] key of each point's cell: sum_k c[k] << (log2_g*k) */
+    const uint32_t* cell_key;     /* [2n] pairs (cell key, sort key); the cell key of point i,
+                                     sum_k c[k] << (log2_g*k), is cell_key[2*i]               */
     const uint32_t* occupied;     /* [words] bit c set when cell c holds a point            */
     const uint32_t* dominated;    /* [words] bit c set when cell c is dominated (Def. 3)    */
     const int32_t* survivors;     /* [surviving_points] row ids after step (c), ascending    */

@@ -113,7 +113,8 @@ def _stream_ptr(stream):
 def _opts(log2_g, assume_unit, filter_points, tile_cfg):
     o = Options()
     o.log2_g = -1 if log2_g is None else int(log2_g)
-    o.assume_unit = 1 if assume_unit else 0
+    # True -> 1 (Eq. 1 on the unit cube); False/0 -> automatic; 2 -> min/max normalisation
+    o.assume_unit = int(assume_unit) if not isinstance(assume_unit, bool) else (1 if assume_unit else 0)
     o.tile_cfg = int(tile_cfg)
     if filter_points is not None and filter_points.numel() > 0:
         assert filter_points.is_cuda and filter_points.dtype == _torch().float32

@@ -62,15 +62,24 @@ __global__ void __launch_bounds__(kThreads) k_minmax(const float* __restrict__ p
     for (int k = 0; k < DP; ++k) { mn[k] = INFINITY; mx[k] = -INFINITY; }
     bool bad = false;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        float x[DP];
-        load_row<DP>(pts + i * ld, d, vec4, x);
+    constexpr int U = 4;  // rows in flight per thread
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+        float x[U][DP];
 #pragma unroll
-        for (int k = 0; k < DP; ++k) {
-            if (k < d) {
-                bad |= !isfinite(x[k]);
-                mn[k] = fminf(mn[k], x[k]);
-                mx[k] = fmaxf(mx[k], x[k]);
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) load_row<DP>(pts + i * ld, d, vec4, x[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i0 + u * stride >= n) break;
+#pragma unroll
+            for (int k = 0; k < DP; ++k) {
+                if (k < d) {
+                    bad |= !isfinite(x[u][k]);
+                    mn[k] = fminf(mn[k], x[u][k]);
+                    mx[k] = fmaxf(mx[k], x[u][k]);
+                }
             }
         }
     }
@@ -94,17 +103,16 @@ __global__ void __launch_bounds__(kThreads) k_minmax(const float* __restrict__ p
 }
 
 // params layout: [0,16) offset, [16,32) cell scale, [32,48) 7-bit code scale,
-// [48,64) Morton scale.
-__global__ void k_params(const uint32_t* mm_min, const uint32_t* mm_max, int d, int log2g,
-                         int mbits, int assume_unit, float* params)
+// [48,64) Morton scale. normalise = 0: unit cube (Eq. 1 as printed), 1: per
+// dimension min/max from mm_min / mm_max.
+__device__ __forceinline__ void write_params(int k, int d, int log2g, int mbits, bool normalise,
+                                             const uint32_t* mm_min, const uint32_t* mm_max, float* params)
 {
-    const int k = threadIdx.x;
-    if (k >= kMaxDim) return;
     float off = 0.0f, cs = 0.0f, qs = 0.0f, ms = 0.0f;
     if (k < d) {
         const float G = (float)(1u << log2g);
         const float M = (float)(1u << mbits);
-        if (assume_unit) {
+        if (!normalise) {
             off = 0.0f; cs = G; qs = 128.0f; ms = M;
         } else {
             const float lo = ordered_to_float(mm_min[k]);
@@ -122,48 +130,150 @@ __global__ void k_params(const uint32_t* mm_min, const uint32_t* mm_max, int d, 
     params[48 + k] = ms;
 }
 
-// ---------------------------------------------------------------------------
-// Steps (a)+(b). One point -> key -> bit. The bit is read before the atomic
-// so that hot cells (correlated data) cost a load, not a serialised atomic.
-template <int DP>
-__device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, const float* s_off,
-                                        const float* s_sc, int64_t row, uint32_t* __restrict__ keys,
-                                        uint32_t* occ, bool& bad)
+__global__ void k_params(const uint32_t* mm_min, const uint32_t* mm_max, int d, int log2g, int mbits,
+                         int normalise, float* params)
 {
-    const uint32_t G = 1u << log2g;
-    uint32_t key = 0;
+    const int k = threadIdx.x;
+    if (k < kMaxDim) write_params(k, d, log2g, mbits, normalise != 0, mm_min, mm_max, params);
+}
+
+// Automatic map: keep the unit-cube map when every dimension's values lie in
+// [0, 1] and span at least half of it; otherwise switch to min/max scales and
+// ask for a second map pass (the first pass tracked min / max).
+__global__ void k_decide(const uint32_t* mm_min, const uint32_t* mm_max, int d, int log2g, int mbits,
+                         float* params, DevResult* res)
+{
+    __shared__ int s_bad;
+    const int k = threadIdx.x;
+    if (k == 0) s_bad = 0;
+    __syncthreads();
+    if (k < d) {
+        const float lo = ordered_to_float(mm_min[k]);
+        const float hi = ordered_to_float(mm_max[k]);
+        const bool unit_ok = (lo >= 0.0f) && (hi <= 1.0f) && (__fsub_rn(hi, lo) >= 0.5f);
+        if (!unit_ok) atomicOr(&s_bad, 1);
+    }
+    __syncthreads();
+    const bool redo = s_bad != 0;
+    if (redo && k < kMaxDim) write_params(k, d, log2g, mbits, true, mm_min, mm_max, params);
+    if (k == 0) res->redo = redo ? 1u : 0u;
+}
+
+__global__ void k_clear_if(uint32_t* words, int64_t n, const DevResult* res)
+{
+    if (!res->redo) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        words[i] = 0u;
+}
+
+// Per-thread min / max accumulation, reduced and published once per block.
+template <int DP>
+struct MinMaxAcc {
+    float mn[DP], mx[DP];
+    __device__ __forceinline__ void init()
+    {
 #pragma unroll
-    for (int k = DP - 1; k >= 0; --k) {
-        if (k < d) {
-            bad |= !isfinite(x[k]);
-            key = (key << log2g) | column_of(x[k], s_off[k], s_sc[k], G);
+        for (int k = 0; k < DP; ++k) { mn[k] = INFINITY; mx[k] = -INFINITY; }
+    }
+    __device__ __forceinline__ void add(const float (&x)[DP])
+    {
+#pragma unroll
+        for (int k = 0; k < DP; ++k) { mn[k] = fminf(mn[k], x[k]); mx[k] = fmaxf(mx[k], x[k]); }
+    }
+    __device__ __forceinline__ void publish(int d, uint32_t* mm_min, uint32_t* mm_max)
+    {
+#pragma unroll
+        for (int k = 0; k < DP; ++k) {
+            for (int o = 16; o > 0; o >>= 1) {
+                mn[k] = fminf(mn[k], __shfl_xor_sync(kFull, mn[k], o));
+                mx[k] = fmaxf(mx[k], __shfl_xor_sync(kFull, mx[k], o));
+            }
+        }
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int k = 0; k < DP; ++k) {
+                if (k < d && mn[k] <= mx[k]) {
+                    atomicMin(&mm_min[k], float_to_ordered(mn[k]));
+                    atomicMax(&mm_max[k], float_to_ordered(mx[k]));
+                }
+            }
         }
     }
-    keys[row] = key;
-    uint32_t* w = occ + (key >> 5);
+};
+
+// ---------------------------------------------------------------------------
+// Steps (a)+(b). One point -> (cell key, Morton key) -> bit. The bitmap OR
+// is fire-and-forget; when a whole warp hits one word (hot cells of
+// correlated data) the bits are merged first and one lane issues it.
+template <int DP>
+__device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, int mbits, const float* s_off,
+                                        const float* s_sc, const float* s_ms, int64_t row,
+                                        uint2* __restrict__ keys, uint32_t* occ, bool& bad)
+{
+    const uint32_t G = 1u << log2g;
+    const uint32_t M = 1u << mbits;
+    uint32_t key = 0;
+    uint32_t mq[DP];
+#pragma unroll
+    for (int k = DP - 1; k >= 0; --k) {
+        mq[k] = 0;
+        if (k < d) {
+            bad |= !isfinite(x[k]);
+            const uint32_t c = column_of(x[k], s_off[k], s_sc[k], G);
+            key = (key << log2g) | c;
+            // the Morton map is only for locality: reuse the cell column when
+            // it is at least as fine
+            mq[k] = (mbits <= log2g) ? (c >> (log2g - mbits)) : column_of(x[k], s_off[k], s_ms[k], M);
+        }
+    }
+    uint32_t code = 0;
+    for (int l = mbits - 1; l >= 0; --l)
+#pragma unroll
+        for (int k = DP - 1; k >= 0; --k)
+            if (k < d) code = (code << 1) | ((mq[k] >> l) & 1u);
+    keys[row] = make_uint2(key, code);
+    const uint32_t word = key >> 5;
     const uint32_t bit = 1u << (key & 31u);
-    if (!(ld_cg_u32(w) & bit)) atomicOr(w, bit);
+    const uint32_t am = __activemask();
+    const int leader = __ffs(am) - 1;
+    const uint32_t w0 = __shfl_sync(am, word, leader);
+    if (__all_sync(am, word == w0)) {
+        const uint32_t bits = __reduce_or_sync(am, bit);
+        if ((int)(threadIdx.x & 31) == leader) atomicOr(occ + word, bits);
+    } else {
+        atomicOr(occ + word, bit);
+    }
 }
 
 template <int DP>
 __global__ void __launch_bounds__(kThreads) k_map_mark_plain(const float* __restrict__ pts, int64_t n,
-                                                             int d, int64_t ld, bool vec4, int log2g,
-                                                             const float* params, uint32_t* keys,
-                                                             uint32_t* occ, uint32_t* err)
+                                                             int d, int64_t ld, bool vec4, int log2g, int mbits,
+                                                             const float* params, uint2* keys,
+                                                             uint32_t* occ, uint32_t* err, const DevResult* gate,
+                                                             uint32_t* mm_min, uint32_t* mm_max)
 {
-    __shared__ float s_off[kMaxDim], s_sc[kMaxDim];
+    if (gate && !gate->redo) return;
+    __shared__ float s_off[kMaxDim], s_sc[kMaxDim], s_ms[kMaxDim];
     if (threadIdx.x < kMaxDim) {
         s_off[threadIdx.x] = params[threadIdx.x];
         s_sc[threadIdx.x] = params[16 + threadIdx.x];
+        s_ms[threadIdx.x] = params[48 + threadIdx.x];
     }
     __syncthreads();
+    MinMaxAcc<DP> acc;
+    acc.init();
     bool bad = false;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        float x[DP];
-        load_row<DP>(pts + i * ld, d, vec4, x);
-        map_one<DP>(x, d, log2g, s_off, s_sc, i, keys, occ, bad);
+    const int64_t n_round = ((n + 31) / 32) * 32;   // whole warps stay in the loop together
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+        if (i < n) {
+            float x[DP];
+            load_row<DP>(pts + i * ld, d, vec4, x);
+            map_one<DP>(x, d, log2g, mbits, s_off, s_sc, s_ms, i, keys, occ, bad);
+            if (mm_min) acc.add(x);
+        }
     }
+    if (mm_min) acc.publish(d, mm_min, mm_max);
     if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, SKY_DEV_ERR_NONFINITE);
 }
 
@@ -174,16 +284,19 @@ constexpr int kMapStages = 4;
 
 template <int DP>
 __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restrict__ pts, int64_t n,
-                                                           int d, int log2g, const float* params,
-                                                           uint32_t* keys, uint32_t* occ, uint32_t* err)
+                                                           int d, int log2g, int mbits, const float* params,
+                                                           uint2* keys, uint32_t* occ, uint32_t* err,
+                                                           const DevResult* gate, uint32_t* mm_min, uint32_t* mm_max)
 {
+    if (gate && !gate->redo) return;
     extern __shared__ __align__(128) float s_buf[];  // [kMapStages][kThreads * d]
-    __shared__ float s_off[kMaxDim], s_sc[kMaxDim];
+    __shared__ float s_off[kMaxDim], s_sc[kMaxDim], s_ms[kMaxDim];
     __shared__ __align__(8) uint64_t s_bar[kMapStages];
     const int tid = threadIdx.x;
     if (tid < kMaxDim) {
         s_off[tid] = params[tid];
         s_sc[tid] = params[16 + tid];
+        s_ms[tid] = params[48 + tid];
     }
     if (tid == 0) {
         for (int s = 0; s < kMapStages; ++s) mbar_init(&s_bar[s], 1);
@@ -203,6 +316,8 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
     }
     bool bad = false;
     bool timed_out = false;
+    MinMaxAcc<DP> acc;
+    acc.init();
     for (int64_t i = 0; i < my_chunks; ++i) {
         const int s = (int)(i % kMapStages);
         const uint32_t parity = (uint32_t)((i / kMapStages) & 1);
@@ -221,7 +336,8 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
         float x[DP];
 #pragma unroll
         for (int k = 0; k < DP; ++k) x[k] = (k < d) ? r[k] : 0.0f;
-        map_one<DP>(x, d, log2g, s_off, s_sc, c * kThreads + tid, keys, occ, bad);
+        map_one<DP>(x, d, log2g, mbits, s_off, s_sc, s_ms, c * kThreads + tid, keys, occ, bad);
+        if (mm_min) acc.add(x);
         __syncthreads();  // every thread is done with stage s
         if (tid == 0 && i + kMapStages < my_chunks) {
             const int64_t c2 = blockIdx.x + (i + kMapStages) * gridDim.x;
@@ -236,9 +352,11 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
         if (i < n) {
             float x[DP];
             load_row<DP>(pts + i * d, d, false, x);
-            map_one<DP>(x, d, log2g, s_off, s_sc, i, keys, occ, bad);
+            map_one<DP>(x, d, log2g, mbits, s_off, s_sc, s_ms, i, keys, occ, bad);
+            if (mm_min) acc.add(x);
         }
     }
+    if (mm_min) acc.publish(d, mm_min, mm_max);
     if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(err, SKY_DEV_ERR_NONFINITE);
 }
 
@@ -446,70 +564,75 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp
     return before + x - v;
 }
 
-// Survivors of step (c), compacted in row order. Morton key: b bits of each
-// dimension interleaved, dimension d-1 first at every bit level.
+// Survivors of step (c), compacted in row order, with their Morton keys
+// (computed by the map pass). Reads only the 8-byte (cell key, Morton key)
+// pairs; a row itself is read only when proposals are in use.
 template <int DP>
 __global__ void __launch_bounds__(kThreads) k_survivors(
-    const float* __restrict__ pts, int64_t n, int d, int64_t ld, bool vec4, int log2g, int mbits,
-    const uint32_t* __restrict__ keys, const uint32_t* __restrict__ pre, const float* __restrict__ params,
+    const float* __restrict__ pts, int64_t n, int d, int64_t ld, bool vec4, int log2g,
+    const uint2* __restrict__ keys, const uint32_t* __restrict__ pre,
     const float* __restrict__ filt, int n_filter_max, DevResult* res, unsigned long long* states,
     uint32_t* tile_counter, uint32_t* surv_key, uint32_t* surv_idx)
 {
     __shared__ uint32_t s_warp[kThreads / 32];
     __shared__ uint32_t s_tile, s_prefix;
-    __shared__ float s_off[kMaxDim], s_ms[kMaxDim];
     __shared__ float s_f[16 * kMaxDim];
     const int tid = threadIdx.x;
     if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
-    if (tid < kMaxDim) {
-        s_off[tid] = params[tid];
-        s_ms[tid] = params[48 + tid];
-    }
     const int nf = n_filter_max ? (int)res->n_filter_used : 0;
     for (int t = tid; t < nf * kMaxDim; t += kThreads) s_f[t] = filt[t];
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint32_t ones = ones_key(log2g, d);
     const int64_t base = (int64_t)tile * kScanTile + (int64_t)tid * kScanItems;
-    uint32_t flags = 0, mk[kScanItems];
+    uint2 kk[kScanItems];
+    if (base + kScanItems <= n) {
+        const uint4* src = reinterpret_cast<const uint4*>(keys + base);
+#pragma unroll
+        for (int h = 0; h < kScanItems / 2; ++h) {
+            const uint4 v = src[h];
+            kk[2 * h] = make_uint2(v.x, v.y);
+            kk[2 * h + 1] = make_uint2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) kk[j] = (base + j < n) ? keys[base + j] : make_uint2(0u, 0u);
+    }
+    // all bitmap words first (independent loads), then the tests
+    uint32_t word[kScanItems];
+    bool probe[kScanItems];
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        probe[j] = (base + j < n) && all_columns_positive(kk[j].x, log2g, d);
+        const uint32_t src = kk[j].x - ones;
+        word[j] = probe[j] ? __ldg(pre + (src >> 5)) : 0u;
+    }
+    uint32_t flags = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const int64_t i = base + j;
-        mk[j] = 0;
         if (i >= n) continue;
-        const uint32_t key = keys[i];
-        bool dominated = false;
-        if (all_columns_positive(key, log2g, d)) {
-            const uint32_t src = key - ones;
-            dominated = (pre[src >> 5] >> (src & 31u)) & 1u;
-        }
+        const uint32_t src = kk[j].x - ones;
+        const bool dominated = probe[j] && ((word[j] >> (src & 31u)) & 1u);
         if (dominated) continue;
-        float x[DP];
-        load_row<DP>(pts + i * ld, d, vec4, x);
-        bool filtered = false;
-        for (int f = 0; f < nf && !filtered; ++f) {
-            bool le = true, lt = false;
+        if (nf) {
+            float x[DP];
+            load_row<DP>(pts + i * ld, d, vec4, x);
+            bool filtered = false;
+            for (int f = 0; f < nf && !filtered; ++f) {
+                bool le = true, lt = false;
 #pragma unroll
-            for (int k = 0; k < DP; ++k) {
-                if (k < d) {
-                    const float q = s_f[f * kMaxDim + k];
-                    le &= q <= x[k];
-                    lt |= q < x[k];
+                for (int k = 0; k < DP; ++k) {
+                    if (k < d) {
+                        const float q = s_f[f * kMaxDim + k];
+                        le &= q <= x[k];
+                        lt |= q < x[k];
+                    }
                 }
+                filtered = le && lt;  // Definition 1: the snapped point dominates x
             }
-            filtered = le && lt;  // Definition 1: the snapped point dominates x
+            if (filtered) continue;
         }
-        if (filtered) continue;
-        const uint32_t M = 1u << mbits;
-        uint32_t mq[DP];
-#pragma unroll
-        for (int k = 0; k < DP; ++k) mq[k] = (k < d) ? column_of(x[k], s_off[k], s_ms[k], M) : 0u;
-        uint32_t code = 0;
-        for (int l = mbits - 1; l >= 0; --l)
-#pragma unroll
-            for (int k = DP - 1; k >= 0; --k)
-                if (k < d) code = (code << 1) | ((mq[k] >> l) & 1u);
-        mk[j] = code;
         flags |= 1u << j;
     }
     uint32_t total;
@@ -523,7 +646,7 @@ __global__ void __launch_bounds__(kThreads) k_survivors(
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         if (flags & (1u << j)) {
-            surv_key[pos] = mk[j];
+            surv_key[pos] = kk[j].y;
             surv_idx[pos] = (uint32_t)(base + j);
             ++pos;
         }
@@ -567,29 +690,10 @@ static bool vec4_ok(const Plan& p)
     return (p.d % 4 == 0) && (p.ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.pts) & 15u) == 0);
 }
 
-cudaError_t launch_minmax(const Plan& p, cudaStream_t s)
+static cudaError_t launch_map(const Plan& p, const DevResult* gate, bool track, cudaStream_t s)
 {
-    cudaMemsetAsync(p.mm_min, 0xff, sizeof(uint32_t) * kMaxDim, s);
-    cudaMemsetAsync(p.mm_max, 0x00, sizeof(uint32_t) * kMaxDim, s);
-    if (p.n == 0) return cudaGetLastError();
-    const int blocks = grid_for(p.n, kThreads * 8, num_sms() * 8);
-    const bool v = vec4_ok(p);
-    SKY_DISPATCH_DP(p.d, k_minmax<DP><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, p.mm_min,
-                                                                   p.mm_max, &p.res->err));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_params(const Plan& p, cudaStream_t s)
-{
-    k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, p.assume_unit ? 1 : 0,
-                              p.params);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_map_mark(const Plan& p, cudaStream_t s)
-{
-    cudaMemsetAsync(p.occ, 0, sizeof(uint32_t) * p.words, s);
-    if (p.n == 0) return cudaGetLastError();
+    uint32_t* mn = track ? p.mm_min : nullptr;
+    uint32_t* mx = track ? p.mm_max : nullptr;
     if (p.tma_ok && p.n >= kThreads) {
         const size_t smem = (size_t)kMapStages * kThreads * p.d * sizeof(float);
         const int64_t nchunks = p.n / kThreads;
@@ -601,16 +705,50 @@ cudaError_t launch_map_mark(const Plan& p, cudaStream_t s)
                                      kMapStages * kThreads * 16 * (int)sizeof(float));
                 attr_set = true;
             }
-            k_map_mark_tma<DP><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.log2g, p.params, p.keys,
-                                                              p.occ, &p.res->err);
+            k_map_mark_tma<DP><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.log2g, p.morton_bits, p.params,
+                                                              p.keys, p.occ, &p.res->err, gate, mn, mx);
         });
     } else {
         const int blocks = grid_for(p.n, kThreads * 4, num_sms() * 8);
         const bool v = vec4_ok(p);
         SKY_DISPATCH_DP(p.d, k_map_mark_plain<DP><<<blocks, kThreads, 0, s>>>(
-                                 p.pts, p.n, p.d, p.ld, v, p.log2g, p.params, p.keys, p.occ, &p.res->err));
+                                 p.pts, p.n, p.d, p.ld, v, p.log2g, p.morton_bits, p.params, p.keys, p.occ,
+                                 &p.res->err, gate, mn, mx));
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_build(const Plan& p, cudaStream_t s)
+{
+    cudaMemsetAsync(p.occ, 0, sizeof(uint32_t) * p.words, s);
+    if (p.map_mode != kMapUnit) {
+        cudaMemsetAsync(p.mm_min, 0xff, sizeof(uint32_t) * kMaxDim, s);
+        cudaMemsetAsync(p.mm_max, 0x00, sizeof(uint32_t) * kMaxDim, s);
+    }
+    if (p.n == 0) return cudaGetLastError();
+    if (p.map_mode == kMapMinMax) {
+        const int blocks = grid_for(p.n, kThreads * 8, num_sms() * 8);
+        const bool v = vec4_ok(p);
+        SKY_DISPATCH_DP(p.d, k_minmax<DP><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, p.mm_min,
+                                                                       p.mm_max, &p.res->err));
+        k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 1, p.params);
+        return launch_map(p, nullptr, false, s);
+    }
+    k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 0, p.params);
+    if (p.map_mode == kMapUnit) return launch_map(p, nullptr, false, s);
+    // automatic: unit map with min/max tracking, then a gated second pass
+    launch_map(p, nullptr, true, s);
+    k_decide<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, p.params, p.res);
+    k_clear_if<<<grid_for(p.words, kThreads, num_sms() * 4), kThreads, 0, s>>>(p.occ, p.words, p.res);
+    return launch_map(p, p.res, false, s);
+}
+
+int build_kernel_count(const Plan& p)
+{
+    if (p.n == 0) return 0;
+    if (p.map_mode == kMapMinMax) return 3;
+    if (p.map_mode == kMapUnit) return 2;
+    return 5;
 }
 
 cudaError_t launch_prefix_or(const Plan& p, cudaStream_t s)
@@ -652,8 +790,8 @@ cudaError_t launch_survivors(const Plan& p, int n_filter, cudaStream_t s)
     cudaMemsetAsync(p.lb_counter, 0, sizeof(uint32_t), s);
     const bool v = vec4_ok(p);
     SKY_DISPATCH_DP(p.d, k_survivors<DP><<<(unsigned)ntiles, kThreads, 0, s>>>(
-                             p.pts, p.n, p.d, p.ld, v, p.log2g, p.morton_bits, p.keys, p.pre, p.params,
-                             p.filt, n_filter, p.res, p.lb_states, p.lb_counter, p.surv_key, p.surv_idx));
+                             p.pts, p.n, p.d, p.ld, v, p.log2g, p.keys, p.pre, p.filt, n_filter, p.res,
+                             p.lb_states, p.lb_counter, p.surv_key, p.surv_idx));
     return cudaGetLastError();
 }
 

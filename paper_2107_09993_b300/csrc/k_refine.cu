@@ -3,16 +3,16 @@
 //   k_gather  lays the survivors out in Morton order: coordinates (padded to
 //             a multiple of 4 floats), 7-bit per-dimension codes packed four
 //             to a word, row ids, and per-tile bounding boxes.
-//   k_refine  one CTA per tile of 128 survivors ("p" points, one per thread).
-//             It lists the tiles whose lower box corner is <= the CTA's upper
-//             box corner (no other tile can hold a dominator), streams them
-//             into shared memory with 1-D bulk (TMA) copies, and tests every
-//             pair: first a SIMD-within-a-word compare of the 7-bit codes
-//             (code(q) <= code(p) in every dimension is necessary for q to
-//             dominate p because the code map is monotone), then the exact
-//             Definition 1 test on the float values. A point is dropped at
-//             its first dominator; a warp leaves a tile as soon as all of its
-//             points are dropped, a CTA as soon as all 128 are.
+//   k_refine  one CTA per tile of 128 survivors ("p" points). It lists the
+//             tiles whose lower box corner is <= the CTA's upper box corner
+//             (no other tile can hold a dominator), streams them into shared
+//             memory with 1-D bulk (TMA) copies, and for each streamed tile
+//             gives every lane one "q" point and loops the warp over the p's
+//             that are still undominated and inside the tile's box. A pair is
+//             tested first by a SIMD-within-a-word compare of 7-bit codes
+//             (code(q) <= code(p) in every dimension is necessary because the
+//             code map is monotone), then by the exact Definition 1 test on
+//             the float values. The CTA stops when all its p's are dominated.
 //   k_emit    ascending row ids of the kept points, by a decoupled look-back
 //             scan over the per-row keep flags.
 //
@@ -32,15 +32,16 @@ namespace sky {
 namespace {
 
 constexpr int kTQ = kRefineTile;
-constexpr int kStages = 2;
-constexpr int kList = 1024;
+constexpr int kStages = 3;
+constexpr int kList = 384;
+constexpr int kSubSlots = kTQ / 32 + 1;   // sub-tile minima + the whole-tile minimum
 constexpr uint32_t kHigh = 0x80808080u;
 
 template <int DP>
 __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, int d, int64_t ld, bool vec4,
                                                 const uint32_t* __restrict__ sorted_idx, const DevResult* res,
                                                 const float* __restrict__ params, float* X, uint32_t* C,
-                                                int32_t* ids, float* bbox)
+                                                int32_t* ids, float* bbox, uint32_t* subcode)
 {
     constexpr int DW = DP / 4;
     __shared__ float s_min[kTQ / 32][DP], s_max[kTQ / 32][DP];
@@ -87,6 +88,19 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
     for (int w = 0; w < DW; ++w) C[j * DW + w] = code[w];
     ids[j] = valid ? (int32_t)row : -1;
 
+    // byte-wise minimum code of each 32-point sub-tile (slots 0..3) and of
+    // the whole tile (slot 4)
+    __shared__ uint32_t s_sub[kTQ / 32][DW];
+#pragma unroll
+    for (int w = 0; w < DW; ++w) {
+        uint32_t c = code[w];
+        for (int o = 16; o > 0; o >>= 1) c = __vminu4(c, __shfl_xor_sync(kFull, c, o));
+        if (lane == 0) {
+            subcode[((int64_t)blockIdx.x * kSubSlots + warp) * DW + w] = c;
+            s_sub[warp][w] = c;
+        }
+    }
+
     // tile bounding box over the valid points
 #pragma unroll
     for (int k = 0; k < DP; ++k) {
@@ -99,6 +113,11 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
         if (lane == 0) { s_min[warp][k] = lo; s_max[warp][k] = hi; }
     }
     __syncthreads();
+    if (tid < DW) {
+        uint32_t c = s_sub[0][tid];
+        for (int w = 1; w < kTQ / 32; ++w) c = __vminu4(c, s_sub[w][tid]);
+        subcode[((int64_t)blockIdx.x * kSubSlots + kTQ / 32) * DW + tid] = c;
+    }
     if (tid < DP) {
         float lo = s_min[0][tid], hi = s_max[0][tid];
         for (int w = 1; w < kTQ / 32; ++w) {
@@ -110,54 +129,62 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
     }
 }
 
-template <int DW>
-__device__ __forceinline__ bool codes_le(const uint32_t (&P)[DW], const uint32_t* cq)
+// One CTA per p-tile of 128 survivors, split in 4 groups of 32 (Morton
+// neighbours). The CTA lists the q-tiles whose byte-wise minimum code is <=
+// the byte-wise maximum code of the live p's of some group (no other tile can
+// hold a dominator of a live p); the list is rebuilt every few hundred tiles
+// with the then-live p's, so it shrinks as p's are dominated. Listed tiles
+// stream through shared memory by bulk (TMA) copies. Warp w owns the 32 q's of
+// sub-tile w (one per lane) and loops over its own list of live p's whose
+// codes are >= the sub-tile's minimum code, so every lane does a useful pair
+// test on every step. When code(q) < code(p) in every dimension, q dominates
+// p without looking at the floats; only pairs with some equal code need the
+// exact Definition 1 test. A dominated p is flagged in shared memory; the CTA
+// stops once every p is flagged.
+template <int DP>
+struct RefineSmem {
+    static constexpr int DW = DP / 4;
+    float qX[kStages][kTQ * DP];        // streamed q-tiles (bulk copies)
+    uint32_t qC[kStages][kTQ * DW];
+    uint32_t pP[kTQ * DW];              // own p codes | 0x80 per byte
+    uint32_t rP[kTQ / 32][kTQ * DW];    // per-warp lists: codes of the listed p's
+    uint8_t rIdx[kTQ / 32][kTQ];        // per-warp lists: p index
+    uint32_t flag[kTQ];                 // 1 = dominated (or padding)
+    uint32_t gmax[kTQ / 32][DW];        // byte-wise max code of each group's live p's
+    uint32_t glive[kTQ / 32];           // live p's per group
+    uint32_t list[kList];               // q-tiles that may hold a dominator
+    uint64_t bar[kStages];
+    uint32_t cnt;
+    uint32_t failed;
+    uint32_t wc[kTQ / 32];
+};
+
+__device__ __forceinline__ uint32_t has_zero_byte(uint32_t x)
 {
-    // byte b of (P_w - q_w) keeps its high bit iff code_q[b] <= code_p[b]
-    // (P_w = code_p | 0x80 per byte, codes < 128: no borrow crosses a byte)
+    return (x - 0x01010101u) & ~x & 0x80808080u;
+}
+
+// every byte of lo <= the matching byte of hi (both 7-bit codes)
+template <int DW>
+__device__ __forceinline__ bool bytes_le(const uint32_t* lo, const uint32_t* hi)
+{
     uint32_t r = kHigh;
-    if constexpr (DW == 1) {
-        r &= P[0] - cq[0];
-    } else if constexpr (DW == 2) {
-        const uint2 v = *reinterpret_cast<const uint2*>(cq);
-        r &= (P[0] - v.x) & (P[1] - v.y);
-    } else if constexpr (DW == 4) {
-        const uint4 v = *reinterpret_cast<const uint4*>(cq);
-        r &= (P[0] - v.x) & (P[1] - v.y) & (P[2] - v.z) & (P[3] - v.w);
-    } else {
 #pragma unroll
-        for (int w = 0; w < DW; ++w) r &= P[w] - cq[w];
-    }
+    for (int w = 0; w < DW; ++w) r &= (hi[w] | kHigh) - lo[w];
     return r == kHigh;
 }
 
 template <int DP>
-__device__ __forceinline__ bool dominates_exact(const float* xq, const float (&p)[DP])
-{
-    bool le = true, lt = false;
-#pragma unroll
-    for (int k = 0; k < DP; k += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(xq + k);
-        le &= (v.x <= p[k]) & (v.y <= p[k + 1]) & (v.z <= p[k + 2]) & (v.w <= p[k + 3]);
-        lt |= (v.x < p[k]) | (v.y < p[k + 1]) | (v.z < p[k + 2]) | (v.w < p[k + 3]);
-    }
-    return le && lt;
-}
-
-template <int DP>
 __global__ void __launch_bounds__(kTQ) k_refine(const float* __restrict__ X, const uint32_t* __restrict__ C,
-                                                const int32_t* __restrict__ ids, const float* __restrict__ BB,
+                                                const int32_t* __restrict__ ids, const uint32_t* __restrict__ SUB,
                                                 DevResult* res, uint8_t* keep)
 {
     constexpr int DW = DP / 4;
+    constexpr int NG = kTQ / 32;
     constexpr uint32_t kBytesX = kTQ * DP * sizeof(float);
     constexpr uint32_t kBytesC = kTQ * DW * sizeof(uint32_t);
-    __shared__ __align__(128) float sX[kStages][kTQ * DP];
-    __shared__ __align__(128) uint32_t sC[kStages][kTQ * DW];
-    __shared__ __align__(8) uint64_t s_bar[kStages];
-    __shared__ uint32_t s_list[kList];
-    __shared__ uint32_t s_cnt;
-    __shared__ uint32_t s_wc[kTQ / 32];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    RefineSmem<DP>& sm = *reinterpret_cast<RefineSmem<DP>*>(smem_raw);
 
     const uint32_t m = res->survivors;
     const uint32_t T = (m + kTQ - 1) / kTQ;
@@ -165,121 +192,177 @@ __global__ void __launch_bounds__(kTQ) k_refine(const float* __restrict__ X, con
     uint32_t* err = &res->err;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1);
+        for (int s = 0; s < kStages; ++s) mbar_init(&sm.bar[s], 1);
         mbar_fence_init();
+        sm.failed = 0;
     }
     const int64_t j = (int64_t)blockIdx.x * kTQ + tid;
     const bool valid = j < m;
-    float p[DP], pmax[DP];
-    uint32_t P[DW];
+    const float* pXg = X + (int64_t)blockIdx.x * kTQ * DP;   // this CTA's p coordinates (global)
+    uint32_t myc[DW];
 #pragma unroll
-    for (int k = 0; k < DP; k += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(X + j * DP + k);
-        p[k] = v.x; p[k + 1] = v.y; p[k + 2] = v.z; p[k + 3] = v.w;
-        const float4 u = *reinterpret_cast<const float4*>(BB + (int64_t)blockIdx.x * 2 * DP + DP + k);
-        pmax[k] = u.x; pmax[k + 1] = u.y; pmax[k + 2] = u.z; pmax[k + 3] = u.w;
+    for (int w = 0; w < DW; ++w) {
+        myc[w] = C[j * DW + w];
+        sm.pP[tid * DW + w] = myc[w] | kHigh;
     }
-#pragma unroll
-    for (int w = 0; w < DW; ++w) P[w] = C[j * DW + w] | kHigh;
-    bool active = valid;
+    sm.flag[tid] = valid ? 0u : 1u;
     unsigned long long pairs = 0;
     uint32_t uses[kStages];
 #pragma unroll
     for (int s = 0; s < kStages; ++s) uses[s] = 0;
     __syncthreads();
 
-    bool stop = false, failed = false;
+    bool stop = false;
     uint32_t t0 = 0;
     while (t0 < T && !stop) {
-        // ---- list the tiles that may hold a dominator of some point here
-        if (tid == 0) s_cnt = 0;
+        // ---- group summaries of the live p's
+        {
+            const bool live = sm.flag[tid] == 0u;
+            const uint32_t nl = __popc(__ballot_sync(kFull, live));
+#pragma unroll
+            for (int w = 0; w < DW; ++w) {
+                uint32_t c = live ? myc[w] : 0u;
+                for (int o = 16; o > 0; o >>= 1) c = __vmaxu4(c, __shfl_xor_sync(kFull, c, o));
+                if (lane == 0) sm.gmax[warp][w] = c;
+            }
+            if (lane == 0) sm.glive[warp] = nl;
+            if (tid == 0) sm.cnt = 0;
+        }
         __syncthreads();
+        // ---- list the q-tiles that may hold a dominator of a live p
         while (t0 < T) {
             const uint32_t t = t0 + tid;
             bool ok = false;
             if (t < T) {
-                ok = true;
-                const float* lo = BB + (int64_t)t * 2 * DP;
+                uint32_t tm[DW];
 #pragma unroll
-                for (int k = 0; k < DP; ++k) ok &= __ldg(lo + k) <= pmax[k];
+                for (int w = 0; w < DW; ++w) tm[w] = __ldg(SUB + ((int64_t)t * kSubSlots + NG) * DW + w);
+#pragma unroll
+                for (int g = 0; g < NG; ++g)
+                    ok |= sm.glive[g] && bytes_le<DW>(tm, sm.gmax[g]);
             }
             const uint32_t bal = __ballot_sync(kFull, ok);
-            if (lane == 0) s_wc[warp] = __popc(bal);
+            if (lane == 0) sm.wc[warp] = __popc(bal);
             __syncthreads();
-            uint32_t pos = s_cnt;
-            for (int w = 0; w < warp; ++w) pos += s_wc[w];
-            if (ok) s_list[pos + __popc(bal & lanemask_lt())] = t;
+            uint32_t pos = sm.cnt;
+            for (int w = 0; w < warp; ++w) pos += sm.wc[w];
+            if (ok) sm.list[pos + __popc(bal & lanemask_lt())] = t;
             __syncthreads();
             if (tid == 0) {
                 uint32_t add = 0;
-                for (int w = 0; w < kTQ / 32; ++w) add += s_wc[w];
-                s_cnt += add;
+                for (int w = 0; w < NG; ++w) add += sm.wc[w];
+                sm.cnt += add;
             }
             __syncthreads();
             t0 += kTQ;
-            if (s_cnt > kList - kTQ) break;
+            if (sm.cnt > kList - kTQ) break;
         }
-        const uint32_t L = s_cnt;
+        const uint32_t L = sm.cnt;
 
-        // ---- stream the listed tiles through two shared-memory stages
         if (tid == 0) {
             for (uint32_t i = 0; i < L && i < (uint32_t)kStages; ++i) {
-                const uint32_t t = s_list[i];
-                mbar_arrive_expect_tx(&s_bar[i], kBytesX + kBytesC);
-                bulk_g2s(sX[i], X + (int64_t)t * kTQ * DP, kBytesX, &s_bar[i]);
-                bulk_g2s(sC[i], C + (int64_t)t * kTQ * DW, kBytesC, &s_bar[i]);
+                const uint32_t t = sm.list[i];
+                mbar_arrive_expect_tx(&sm.bar[i], kBytesX + kBytesC);
+                bulk_g2s(sm.qX[i], X + (int64_t)t * kTQ * DP, kBytesX, &sm.bar[i]);
+                bulk_g2s(sm.qC[i], C + (int64_t)t * kTQ * DW, kBytesC, &sm.bar[i]);
             }
         }
         for (uint32_t i = 0; i < L; ++i) {
             const int s = (int)(i % kStages);
-            const bool ok = mbar_wait(&s_bar[s], uses[s] & 1u, err);
-            ++uses[s];
-            if (__syncthreads_or(!ok)) { failed = true; stop = true; }
-            if (!failed) {
-                const uint32_t t = s_list[i];
-                bool rel = active;
-                if (rel) {
-                    const float* lo = BB + (int64_t)t * 2 * DP;
+            const uint32_t t = sm.list[i];
+            // ---- this warp's list: live p's with codes >= the sub-tile minimum
+            uint32_t Mw[DW];
 #pragma unroll
-                    for (int k = 0; k < DP; ++k) rel &= __ldg(lo + k) <= p[k];
+            for (int w = 0; w < DW; ++w) Mw[w] = __ldg(SUB + ((int64_t)t * kSubSlots + warp) * DW + w);
+            uint32_t rc = 0;
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                if (!sm.glive[g] || !bytes_le<DW>(Mw, sm.gmax[g])) continue;   // whole group out of reach
+                const int pi = g * 32 + lane;
+                bool rel = sm.flag[pi] == 0u;
+                if (rel) {
+                    uint32_t r = kHigh;
+#pragma unroll
+                    for (int w = 0; w < DW; ++w) r &= sm.pP[pi * DW + w] - Mw[w];
+                    rel = (r == kHigh);
                 }
-                if (__any_sync(kFull, rel)) {
-                    const uint32_t* cq = sC[s];
-                    const float* xq = sX[s];
-                    for (int q0 = 0; q0 < kTQ; q0 += 32) {
-                        if (rel) pairs += 32;
-#pragma unroll 8
-                        for (int q = q0; q < q0 + 32; ++q) {
-                            if (codes_le<DW>(P, cq + q * DW) && rel) {
-                                if (dominates_exact<DP>(xq + q * DP, p)) { active = false; rel = false; }
+                const uint32_t bal = __ballot_sync(kFull, rel);
+                if (rel) {
+                    const uint32_t pos = rc + __popc(bal & lanemask_lt());
+                    sm.rIdx[warp][pos] = (uint8_t)pi;
+#pragma unroll
+                    for (int w = 0; w < DW; ++w) sm.rP[warp][pos * DW + w] = sm.pP[pi * DW + w];
+                }
+                rc += __popc(bal);
+            }
+            __syncwarp();
+            const bool ok = mbar_wait(&sm.bar[s], uses[s] & 1u, err);
+            ++uses[s];
+            if (!ok) sm.failed = 1u;
+            if (ok && rc) {
+                const int qi = warp * 32 + lane;
+                uint32_t Q[DW];
+#pragma unroll
+                for (int w = 0; w < DW; ++w) Q[w] = sm.qC[s][qi * DW + w];
+                pairs += 32ull * rc;
+                const uint32_t* rp = sm.rP[warp];
+#pragma unroll 4
+                for (uint32_t r = 0; r < rc; ++r) {
+                    uint32_t D[DW];
+                    uint32_t a = kHigh;
+#pragma unroll
+                    for (int w = 0; w < DW; ++w) {
+                        D[w] = rp[r * DW + w] - Q[w];
+                        a &= D[w];
+                    }
+                    if (a == kHigh) {  // code(q) <= code(p) in every dimension
+                        uint32_t eq = 0;
+#pragma unroll
+                        for (int w = 0; w < DW; ++w) eq |= has_zero_byte(D[w] ^ kHigh);
+                        const int pi = sm.rIdx[warp][r];
+                        bool dom = true;   // strictly lower code everywhere: q < p everywhere
+                        if (eq) {
+                            const float* qx = &sm.qX[s][qi * DP];
+                            const float* px = pXg + pi * DP;
+                            bool le = true, lt = false;
+#pragma unroll
+                            for (int k = 0; k < DP; k += 4) {
+                                const float4 u = *reinterpret_cast<const float4*>(qx + k);
+                                const float4 v = __ldg(reinterpret_cast<const float4*>(px + k));
+                                le &= (u.x <= v.x) & (u.y <= v.y) & (u.z <= v.z) & (u.w <= v.w);
+                                lt |= (u.x < v.x) | (u.y < v.y) | (u.z < v.z) | (u.w < v.w);
                             }
+                            dom = le && lt;
                         }
-                        if (!__any_sync(kFull, rel)) break;
+                        if (dom) sm.flag[pi] = 1u;
                     }
                 }
-                if (!__syncthreads_or(active)) stop = true;
             }
+            // one barrier per tile: stage s is free and the live flags are final
+            const bool any_live = __syncthreads_or(valid && sm.flag[tid] == 0u);
+            if (sm.failed || !any_live) stop = true;
             if (stop) {
-                // let the copy already in flight land before leaving
-                if (tid == 0 && i + 1 < L) {
-                    const int s2 = (int)((i + 1) % kStages);
-                    mbar_wait(&s_bar[s2], uses[s2] & 1u, nullptr);
+                // let copies already in flight land before leaving
+                if (tid == 0) {
+                    for (uint32_t k2 = i + 1; k2 < L && k2 < i + kStages; ++k2) {
+                        const int s2 = (int)(k2 % kStages);
+                        mbar_wait(&sm.bar[s2], uses[s2] & 1u, nullptr);
+                    }
                 }
                 break;
             }
             if (tid == 0 && i + kStages < L) {
-                const uint32_t t = s_list[i + kStages];
+                const uint32_t t2 = sm.list[i + kStages];
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&s_bar[s], kBytesX + kBytesC);
-                bulk_g2s(sX[s], X + (int64_t)t * kTQ * DP, kBytesX, &s_bar[s]);
-                bulk_g2s(sC[s], C + (int64_t)t * kTQ * DW, kBytesC, &s_bar[s]);
+                mbar_arrive_expect_tx(&sm.bar[s], kBytesX + kBytesC);
+                bulk_g2s(sm.qX[s], X + (int64_t)t2 * kTQ * DP, kBytesX, &sm.bar[s]);
+                bulk_g2s(sm.qC[s], C + (int64_t)t2 * kTQ * DW, kBytesC, &sm.bar[s]);
             }
         }
         __syncthreads();
     }
-    if (valid && active && !failed) keep[ids[j]] = 1;
-    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kFull, pairs, o);
-    if (lane == 0 && pairs) atomicAdd(&res->pairs, pairs);
+    if (valid && !sm.failed && sm.flag[tid] == 0u) keep[ids[j]] = 1;
+    if (lane == 0 && pairs) atomicAdd(&res->pairs, pairs);  // 32 q-lanes x list length, per warp
 }
 
 // Ascending row ids of the kept rows (decoupled look-back over 8 rows per
@@ -353,7 +436,8 @@ cudaError_t launch_gather(const Plan& p, cudaStream_t s)
     if (tiles == 0) return cudaGetLastError();
     const bool v = (p.d % 4 == 0) && (p.ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.pts) & 15u) == 0);
     SKY_DISPATCH_DP(p.d, k_gather<DP><<<(unsigned)tiles, kTQ, 0, s>>>(p.pts, p.d, p.ld, v, p.sorted_val, p.res,
-                                                                       p.params, p.X, p.C, p.ids, p.bbox));
+                                                                       p.params, p.X, p.C, p.ids, p.bbox,
+                                                                       p.subcode));
     return cudaGetLastError();
 }
 
@@ -362,7 +446,15 @@ cudaError_t launch_refine(const Plan& p, cudaStream_t s)
     cudaMemsetAsync(p.keep, 0, (size_t)p.n, s);
     const int64_t tiles = (p.n + kTQ - 1) / kTQ;
     if (tiles == 0) return cudaGetLastError();
-    SKY_DISPATCH_DP(p.d, k_refine<DP><<<(unsigned)tiles, kTQ, 0, s>>>(p.X, p.C, p.ids, p.bbox, p.res, p.keep));
+    SKY_DISPATCH_DP(p.d, {
+        const int smem = (int)sizeof(RefineSmem<DP>);
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_refine<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            attr_set = true;
+        }
+        k_refine<DP><<<(unsigned)tiles, kTQ, smem, s>>>(p.X, p.C, p.ids, p.subcode, p.res, p.keep);
+    });
     return cudaGetLastError();
 }
 

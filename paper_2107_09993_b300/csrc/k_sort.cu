@@ -4,8 +4,8 @@
 // Morton (Z-order) arrangement of the survivors makes consecutive points
 // spatially close, so most tile pairs can be skipped by one box test. The
 // sort is deterministic (stable, no atomics on the output positions): per
-// 8-bit digit, (1) per-block digit histograms, (2) one exclusive scan over
-// the [digit][block] matrix, (3) a stable scatter that ranks keys inside the
+// 8-bit digit, (1) per-block digit histograms and digit totals, (2) one CTA
+// per digit scanning its row of the [digit][block] matrix, (3) a stable scatter that ranks keys inside the
 // block with warp match masks and writes digit runs contiguously. The number
 // of survivors is read on the device, so no host synchronisation is needed.
 #include <cstdint>
@@ -23,7 +23,8 @@ constexpr int kTile = kSortTile;
 constexpr int kWarps = kT / 32;
 
 __global__ void __launch_bounds__(kT) k_radix_hist(const uint32_t* __restrict__ keys, const DevResult* res,
-                                                   int shift, uint32_t* hist, int64_t nblk_max)
+                                                   int shift, uint32_t* hist, int64_t nblk_max,
+                                                   uint32_t* digit_total)
 {
     __shared__ uint32_t s_h[256];
     const uint32_t m = res->survivors;
@@ -37,46 +38,48 @@ __global__ void __launch_bounds__(kT) k_radix_hist(const uint32_t* __restrict__ 
         if (i < m) atomicAdd(&s_h[(keys[i] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * nblk_max + blockIdx.x] = s_h[threadIdx.x];
+    const uint32_t c = s_h[threadIdx.x];
+    hist[(int64_t)threadIdx.x * nblk_max + blockIdx.x] = c;
+    if (c) atomicAdd(&digit_total[threadIdx.x], c);
 }
 
-// Exclusive scan over the logical sequence hist[digit][0..nblk), digit-major.
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* hist, const DevResult* res, int64_t nblk_max)
+// One CTA per digit: exclusive scan of that digit's row of block counts,
+// offset by the total of all smaller digits.
+__global__ void __launch_bounds__(kT) k_radix_scan(uint32_t* hist, const DevResult* res, int64_t nblk_max,
+                                                   const uint32_t* digit_total)
 {
-    __shared__ uint32_t s_part[1024];
+    __shared__ uint32_t s_warp[kWarps];
     const uint32_t m = res->survivors;
     const int64_t nblk = ((int64_t)m + kTile - 1) / kTile;
-    if (nblk == 0) return;
-    const int64_t total = 256 * nblk;
-    const int64_t per = (total + 1023) / 1024;
-    const int64_t lo = threadIdx.x * per;
-    const int64_t hi = lo + per < total ? lo + per : total;
-    uint32_t sum = 0;
-    {
-        int64_t dg = lo / nblk, b = lo % nblk;
-        for (int64_t L = lo; L < hi; ++L) {
-            sum += hist[dg * nblk_max + b];
-            if (++b == nblk) { b = 0; ++dg; }
-        }
-    }
-    s_part[threadIdx.x] = sum;
+    const int dg = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // offset = sum of the totals of digits below dg
+    uint32_t v = tid < dg ? digit_total[tid] : 0u;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (lane == 0) s_warp[warp] = v;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const uint32_t v = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        s_part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    uint32_t run = s_part[threadIdx.x] - sum;
-    {
-        int64_t dg = lo / nblk, b = lo % nblk;
-        for (int64_t L = lo; L < hi; ++L) {
-            uint32_t* p = &hist[dg * nblk_max + b];
-            const uint32_t v = *p;
-            *p = run;
-            run += v;
-            if (++b == nblk) { b = 0; ++dg; }
+    uint32_t off = 0;
+    for (int w = 0; w < kWarps; ++w) off += s_warp[w];
+    __syncthreads();
+    uint32_t* row = hist + (int64_t)dg * nblk_max;
+    for (int64_t b0 = 0; b0 < nblk; b0 += kT) {
+        const int64_t b = b0 + tid;
+        const uint32_t c = b < nblk ? row[b] : 0u;
+        uint32_t x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
         }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t before = 0, tot = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            if (w < warp) before += s_warp[w];
+            tot += s_warp[w];
+        }
+        if (b < nblk) row[b] = off + before + x - c;
+        off += tot;
+        __syncthreads();
     }
 }
 
@@ -175,10 +178,12 @@ cudaError_t launch_sort(Plan& p, cudaStream_t s)
     uint32_t* kout = p.sort_key2;
     uint32_t* vout = p.sort_val2;
     const unsigned nblk = (unsigned)p.sort_blocks;
+    cudaMemsetAsync(p.digit_total, 0, sizeof(uint32_t) * 256 * 4, s);
     for (int ps = 0; ps < passes; ++ps) {
         const int shift = ps * 8;
-        k_radix_hist<<<nblk, kT, 0, s>>>(kin, p.res, shift, p.hist, p.sort_blocks);
-        k_radix_scan<<<1, 1024, 0, s>>>(p.hist, p.res, p.sort_blocks);
+        uint32_t* tot = p.digit_total + 256 * ps;
+        k_radix_hist<<<nblk, kT, 0, s>>>(kin, p.res, shift, p.hist, p.sort_blocks, tot);
+        k_radix_scan<<<256, kT, 0, s>>>(p.hist, p.res, p.sort_blocks, tot);
         k_radix_scatter<<<nblk, kT, 0, s>>>(kin, vin, kout, vout, p.res, shift, p.hist, p.sort_blocks);
         // ping-pong
         const uint32_t* tk = kout;

@@ -51,7 +51,7 @@ struct PhaseClock {
 int count_kernels(const Plan& p, int n_prop)
 {
     const int passes = (p.morton_bits * p.d + 7) / 8;
-    return (p.assume_unit ? 0 : 1) + 1 + 1 + (n_prop > 0 ? 1 : 0) + 1 + p.d + 1 + 3 * passes + 1 + 1 + 1;
+    return build_kernel_count(p) + (n_prop > 0 ? 1 : 0) + 1 + p.d + 1 + 3 * passes + 1 + 1 + 1;
 }
 
 sky_status fail(sky_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
@@ -117,16 +117,18 @@ size_t layout(Plan& p, char* base, bool grid_api)
     p.occ = c.take<uint32_t>(p.words);
     p.pre = c.take<uint32_t>(p.words);
     p.dom = grid_api ? c.take<uint32_t>(p.words) : nullptr;
-    p.keys = c.take<uint32_t>(n);
+    p.keys = c.take<uint2>(n);
     p.surv_key = c.take<uint32_t>(n);
     p.surv_idx = c.take<uint32_t>(n);
     p.sort_key2 = c.take<uint32_t>(n);
     p.sort_val2 = c.take<uint32_t>(n);
     p.hist = c.take<uint32_t>(256 * p.sort_blocks);
+    p.digit_total = c.take<uint32_t>(4 * 256);
     p.X = c.take<float>(n_pad * dp);
     p.C = c.take<uint32_t>(n_pad * (dp / 4));
     p.ids = c.take<int32_t>(n_pad);
     p.bbox = c.take<float>(tiles * 2 * dp);
+    p.subcode = c.take<uint32_t>(tiles * 5 * (dp / 4));
     p.keep = c.take<uint8_t>(n + 16);
     return c.off;
 }
@@ -161,7 +163,9 @@ sky_status make_plan(Plan& p, const float* pts, int64_t n, int32_t d, int64_t ld
     p.n = n;
     p.d = d;
     p.ld = ld;
-    p.assume_unit = opt && opt->assume_unit;
+    const int au = opt ? opt->assume_unit : 0;
+    if (au < 0 || au > 2) return fail(SKY_ERR_INVALID_ARGUMENT, "assume_unit = %d outside {0, 1, 2}", au);
+    p.map_mode = au == 1 ? kMapUnit : (au == 2 ? kMapMinMax : kMapAuto);
     int lg = (opt && opt->log2_g >= 0) ? opt->log2_g : auto_log2g(n, d);
     if (opt && opt->log2_g > 16) return fail(SKY_ERR_TOO_LARGE, "log2_g = %d above 16", opt->log2_g);
     if (lg * d > 27) return fail(SKY_ERR_TOO_LARGE, "grid of 2^%d cells exceeds the dense limit 2^27", lg * d);
@@ -180,9 +184,7 @@ sky_status make_plan(Plan& p, const float* pts, int64_t n, int32_t d, int64_t ld
 sky_status run_build(Plan& p, cudaStream_t s)
 {
     SKY_CUDA(cudaMemsetAsync(p.res, 0, sizeof(DevResult), s));
-    if (!p.assume_unit) SKY_CUDA(launch_minmax(p, s));
-    SKY_CUDA(launch_params(p, s));
-    SKY_CUDA(launch_map_mark(p, s));
+    SKY_CUDA(launch_build(p, s));
     return SKY_OK;
 }
 
@@ -241,10 +243,8 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
     st = SKY_OK;
     {
         cudaError_t e = cudaMemsetAsync(p.res, 0, sizeof(DevResult), s);
-        if (e == cudaSuccess && !p.assume_unit) e = launch_minmax(p, s);
-        if (e == cudaSuccess) e = launch_params(p, s);
         clk.mark();
-        if (e == cudaSuccess) e = launch_map_mark(p, s);
+        if (e == cudaSuccess) e = launch_build(p, s);
         clk.mark();
         if (e == cudaSuccess) e = launch_snap(p, n_prop ? opt->d_filter_pts : nullptr, n_prop, s);
         if (e == cudaSuccess) e = launch_prefix_or(p, s);
@@ -412,7 +412,7 @@ sky_status sky_grid_stats(const sky_grid* g, sky_grid_stats_t* out)
 sky_status sky_grid_get_view(const sky_grid* g, sky_grid_view* out)
 {
     if (!g || !out) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL argument");
-    out->cell_key = g->plan.keys;
+    out->cell_key = reinterpret_cast<const uint32_t*>(g->plan.keys);
     out->occupied = g->plan.occ;
     out->dominated = g->plan.dom;
     out->survivors = reinterpret_cast<const int32_t*>(g->plan.surv_idx);
@@ -429,7 +429,15 @@ sky_status sky_grid_copy_out(const sky_grid* g, sky_grid_array which, void* d_ds
     const void* src = nullptr;
     size_t need = 0;
     switch (which) {
-        case SKY_GRID_CELL_KEY: src = p.keys; need = sizeof(uint32_t) * (size_t)p.n; break;
+        case SKY_GRID_CELL_KEY: {
+            // the handle stores (cell key, Morton key) pairs: copy the first of each
+            need = sizeof(uint32_t) * (size_t)p.n;
+            if (bytes < need) return fail(SKY_ERR_CAPACITY, "array needs %zu bytes, got %zu", need, bytes);
+            if (p.n) SKY_CUDA(cudaMemcpy2DAsync(d_dst, sizeof(uint32_t), p.keys, sizeof(uint2), sizeof(uint32_t),
+                                                (size_t)p.n, cudaMemcpyDeviceToDevice, g->stream));
+            SKY_CUDA(cudaStreamSynchronize(g->stream));
+            return SKY_OK;
+        }
         case SKY_GRID_OCCUPIED: src = p.occ; need = sizeof(uint32_t) * (size_t)p.words; break;
         case SKY_GRID_DOMINATED:
             if (!g->pruned) return fail(SKY_ERR_INVALID_ARGUMENT, "grid not pruned yet");

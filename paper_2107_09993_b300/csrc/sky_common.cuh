@@ -165,15 +165,13 @@ __device__ __forceinline__ uint32_t lookback_prefix(unsigned long long* states, 
 
 // ---- value -> column map (Eq. 1 with min/max normalisation) ----------------
 // t = (x - off) * s in binary32 round-to-nearest with no contraction, then
-// floor and clamp to [0, G-1]. Monotone non-decreasing in x.
+// floor and clamp to [0, G-1] (the float -> unsigned conversion saturates:
+// negative and NaN give 0). Monotone non-decreasing in x.
 __device__ __forceinline__ uint32_t column_of(float x, float off, float s, uint32_t G)
 {
-    if (s == 0.0f) return 0u;
     const float t = __fmul_rn(__fsub_rn(x, off), s);
-    if (!(t > 0.0f)) return 0u;
-    if (t >= (float)G) return G - 1u;
-    const uint32_t c = (uint32_t)__float2int_rd(t);
-    return c > G - 1u ? G - 1u : c;
+    const uint32_t c = __float2uint_rd(t);
+    return c < G - 1u ? c : G - 1u;
 }
 
 // Order-preserving float <-> uint32 (for atomic min/max on floats).

@@ -16,7 +16,14 @@ struct DevResult {
     unsigned long long pairs;  // candidate pairs examined by the refinement
     uint32_t occupied_cells;   // filled on request (grid statistics)
     uint32_t surviving_cells;
+    uint32_t redo;             // automatic value map: 1 = second map pass with min/max scales
+    uint32_t pad;
 };
+
+
+
+// Value -> column map of the map pass.
+enum MapMode { kMapAuto = 0, kMapUnit = 1, kMapMinMax = 2 };
 
 // Everything one skyline computation needs on the device.
 struct Plan {
@@ -26,7 +33,7 @@ struct Plan {
     int d = 0;
     int64_t ld = 0;
     int log2g = 0;
-    bool assume_unit = false;
+    int map_mode = kMapAuto;   // MapMode
     bool tma_ok = false;       // 16-byte aligned and ld == d
     int morton_bits = 0;       // bits per dimension of the sort key
     int refine_cfg = 0;
@@ -35,7 +42,7 @@ struct Plan {
     uint32_t* mm_min = nullptr;      // [d] ordered-uint min
     uint32_t* mm_max = nullptr;      // [d] ordered-uint max
     float* params = nullptr;         // [4][16]: offset, cell scale, code scale, morton scale
-    uint32_t* keys = nullptr;        // [n] cell key per point
+    uint2* keys = nullptr;           // [n] (cell key, Morton key) per point
     uint32_t* occ = nullptr;         // [words] occupancy bitmap
     uint32_t* pre = nullptr;         // [words] inclusive prefix-OR of occ
     uint32_t* dom = nullptr;         // [words] dominated bitmap (grid API only)
@@ -48,11 +55,13 @@ struct Plan {
     uint32_t* sort_key2 = nullptr;   // [n] ping-pong buffers
     uint32_t* sort_val2 = nullptr;
     uint32_t* hist = nullptr;        // [256][sort_blocks]
+    uint32_t* digit_total = nullptr; // [4][256] per-pass digit totals
     int64_t sort_blocks = 0;
     float* X = nullptr;              // [n_pad][dp] sorted survivor coordinates
     uint32_t* C = nullptr;           // [n_pad][dp/4] 7-bit codes
     int32_t* ids = nullptr;          // [n_pad] row id per sorted survivor
     float* bbox = nullptr;           // [tiles][2][dp]
+    uint32_t* subcode = nullptr;     // [tiles][5][dp/4] byte-wise min code of each 32-point sub-tile, then of the tile
     uint8_t* keep = nullptr;         // [n] 1 = skyline
     float* filt = nullptr;           // [16][16] snapped filter points
     unsigned long long* snap = nullptr;  // [16] packed (sum, row) argmin
@@ -75,9 +84,10 @@ size_t plan_workspace_bytes(int64_t n, int d, int log2g, bool grid_api);
 void plan_carve(Plan& p, void* ws, bool grid_api);
 
 // Launchers (k_grid.cu)
-cudaError_t launch_minmax(const Plan& p, cudaStream_t s);
-cudaError_t launch_params(const Plan& p, cudaStream_t s);
-cudaError_t launch_map_mark(const Plan& p, cudaStream_t s);
+// Steps (a)+(b) in the plan's map mode (min/max pass, parameters, map pass,
+// and in automatic mode the decision and the gated second map pass).
+cudaError_t launch_build(const Plan& p, cudaStream_t s);
+int build_kernel_count(const Plan& p);
 cudaError_t launch_prefix_or(const Plan& p, cudaStream_t s);
 cudaError_t launch_dominated(const Plan& p, cudaStream_t s);
 cudaError_t launch_snap(const Plan& p, const float* d_prop, int n_prop, cudaStream_t s);

@@ -100,7 +100,9 @@ extern "C" sky_status sky_skyline_noalloc(const float* d_pts, int64_t n, int32_t
     p.n = n;
     p.d = d;
     p.ld = ld;
-    p.assume_unit = opt && opt->assume_unit;
+    const int au = opt ? opt->assume_unit : 0;
+    if (au < 0 || au > 2) return noalloc_fail(SKY_ERR_INVALID_ARGUMENT, "assume_unit outside {0, 1, 2}");
+    p.map_mode = au == 1 ? kMapUnit : (au == 2 ? kMapMinMax : kMapAuto);
     int lg = (opt && opt->log2_g >= 0) ? opt->log2_g : auto_log2g(n, d);
     while (lg > 0 && lg * d > kMaxGridBits && !(opt && opt->log2_g >= 0)) --lg;
     if (lg * d > kMaxGridBits) return noalloc_fail(SKY_ERR_TOO_LARGE, "grid above 2^20 cells (log2_g * d > 20)");
@@ -118,9 +120,7 @@ extern "C" sky_status sky_skyline_noalloc(const float* d_pts, int64_t n, int32_t
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int n_prop = opt ? opt->n_filter : 0;
     cudaError_t e = cudaMemsetAsync(p.res, 0, sizeof(DevResult), s);
-    if (e == cudaSuccess && !p.assume_unit) e = launch_minmax(p, s);
-    if (e == cudaSuccess) e = launch_params(p, s);
-    if (e == cudaSuccess) e = launch_map_mark(p, s);
+    if (e == cudaSuccess) e = launch_build(p, s);
     if (e == cudaSuccess) e = launch_snap(p, n_prop ? opt->d_filter_pts : nullptr, n_prop, s);
     if (e == cudaSuccess) e = launch_prefix_or(p, s);
     if (e == cudaSuccess) e = launch_survivors(p, n_prop, s);

@@ -123,10 +123,12 @@ def test_cell_grid_matches_oracle():
         n = int(rng.integers(1, 4000))
         kind = ["independent", "correlated", "anticorrelated"][case % 3]
         P = skydata.generate(kind, n, d, seed=case)
-        unit = bool(case % 2)
-        g = sky.Grid(dev(P), log2_g=lg, assume_unit=unit).prune()
+        mode = ["auto", "unit", "minmax"][case % 3 if case % 4 else 1]
+        if case % 5 == 0:
+            P = (P * np.float32(0.3) + np.float32(0.1)).astype(np.float32)   # narrow range: auto normalises
+        g = sky.Grid(dev(P), log2_g=lg, assume_unit={"auto": 0, "unit": 1, "minmax": 2}[mode]).prune()
         keys = g.cell_keys().cpu().numpy().view(np.uint32).astype(np.uint64)
-        want_keys = oracle.cell_keys(P, lg, assume_unit=unit)
+        want_keys = oracle.cell_keys(P, lg, mode=mode)
         assert np.array_equal(keys, want_keys), case
         ncell = 1 << (lg * d)
         occ_bits = np.unpackbits(g.occupied().cpu().numpy().view(np.uint8), bitorder="little")[:ncell]
