@@ -129,34 +129,36 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
     }
 }
 
-// One CTA per p-tile of 128 survivors, split in 4 groups of 32 (Morton
-// neighbours). The CTA lists the q-tiles whose byte-wise minimum code is <=
-// the byte-wise maximum code of the live p's of some group (no other tile can
-// hold a dominator of a live p); the list is rebuilt every few hundred tiles
-// with the then-live p's, so it shrinks as p's are dominated. Listed tiles
-// stream through shared memory by bulk (TMA) copies. Warp w owns the 32 q's of
-// sub-tile w (one per lane) and loops over its own list of live p's whose
-// codes are >= the sub-tile's minimum code, so every lane does a useful pair
-// test on every step. When code(q) < code(p) in every dimension, q dominates
-// p without looking at the floats; only pairs with some equal code need the
-// exact Definition 1 test. A dominated p is flagged in shared memory; the CTA
-// stops once every p is flagged.
+// One CTA per p-tile of 128 survivors (Morton neighbours), split in 4 groups
+// of 32, plus a producer warp. The producer scans the q-tiles in Morton
+// order, keeps those whose byte-wise minimum code is <= the byte-wise maximum
+// code of the live p's of some group (no other tile can hold a dominator of
+// a live p), and streams them into a ring of shared-memory stages by bulk
+// (TMA) copies, gated by full/empty mbarriers. Consumer warp w owns the 32
+// q's of sub-tile w of each streamed tile (one per lane); it marks, by ballot,
+// the live p's whose codes are >= the sub-tile's minimum code and loops over
+// them, so every lane does a useful pair test on every step. When
+// code(q) < code(p) in every dimension, q dominates p without looking at the
+// floats; only pairs with some equal code need the exact Definition 1 test.
+// A dominated p is flagged; when none is left the producer stops issuing and
+// the consumers drain the ring. No block-wide barrier in the steady state.
+constexpr int kRingStages = 4;
+constexpr uint32_t kEndTile = 0xffffffffu;
+
 template <int DP>
 struct RefineSmem {
     static constexpr int DW = DP / 4;
-    float qX[kStages][kTQ * DP];        // streamed q-tiles (bulk copies)
-    uint32_t qC[kStages][kTQ * DW];
-    uint32_t pP[kTQ * DW];              // own p codes | 0x80 per byte
-    uint32_t rP[kTQ / 32][kTQ * DW];    // per-warp lists: codes of the listed p's
-    uint8_t rIdx[kTQ / 32][kTQ];        // per-warp lists: p index
-    uint32_t flag[kTQ];                 // 1 = dominated (or padding)
-    uint32_t gmax[kTQ / 32][DW];        // byte-wise max code of each group's live p's
-    uint32_t glive[kTQ / 32];           // live p's per group
-    uint32_t list[kList];               // q-tiles that may hold a dominator
-    uint64_t bar[kStages];
-    uint32_t cnt;
+    float qX[kRingStages][kTQ * DP];     // streamed q-tiles
+    uint32_t qC[kRingStages][kTQ * DW];
+    uint32_t pP[kTQ * DW];               // own p codes | 0x80 per byte
+    uint32_t flag[kTQ];                  // 1 = dominated (or padding)
+    uint32_t gmax[kTQ / 32][DW];         // byte-wise max code of each group's live p's (producer)
+    uint32_t glive[kTQ / 32];            // live p's per group (producer)
+    uint32_t stage_tile[kRingStages];
+    uint64_t full[kRingStages];
+    uint64_t empty[kRingStages];
+    uint32_t live;                       // live p's of the CTA
     uint32_t failed;
-    uint32_t wc[kTQ / 32];
 };
 
 __device__ __forceinline__ uint32_t has_zero_byte(uint32_t x)
@@ -175,12 +177,14 @@ __device__ __forceinline__ bool bytes_le(const uint32_t* lo, const uint32_t* hi)
 }
 
 template <int DP>
-__global__ void __launch_bounds__(kTQ) k_refine(const float* __restrict__ X, const uint32_t* __restrict__ C,
-                                                const int32_t* __restrict__ ids, const uint32_t* __restrict__ SUB,
-                                                DevResult* res, uint8_t* keep)
+__global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X, const uint32_t* __restrict__ C,
+                                                     const int32_t* __restrict__ ids,
+                                                     const uint32_t* __restrict__ SUB, DevResult* res,
+                                                     uint8_t* keep)
 {
     constexpr int DW = DP / 4;
     constexpr int NG = kTQ / 32;
+    constexpr int S = kRingStages;
     constexpr uint32_t kBytesX = kTQ * DP * sizeof(float);
     constexpr uint32_t kBytesC = kTQ * DW * sizeof(uint32_t);
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -191,178 +195,183 @@ __global__ void __launch_bounds__(kTQ) k_refine(const float* __restrict__ X, con
     if (blockIdx.x >= T) return;
     uint32_t* err = &res->err;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t pbase = (int64_t)blockIdx.x * kTQ;
+    if (tid < kTQ) {
+        const bool valid = pbase + tid < m;
+#pragma unroll
+        for (int w = 0; w < DW; ++w) sm.pP[tid * DW + w] = C[(pbase + tid) * DW + w] | kHigh;
+        sm.flag[tid] = valid ? 0u : 1u;
+    }
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&sm.bar[s], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], NG);
+        }
         mbar_fence_init();
+        sm.live = (m - pbase) < (uint32_t)kTQ ? (m - (uint32_t)pbase) : (uint32_t)kTQ;
         sm.failed = 0;
     }
-    const int64_t j = (int64_t)blockIdx.x * kTQ + tid;
-    const bool valid = j < m;
-    const float* pXg = X + (int64_t)blockIdx.x * kTQ * DP;   // this CTA's p coordinates (global)
-    uint32_t myc[DW];
-#pragma unroll
-    for (int w = 0; w < DW; ++w) {
-        myc[w] = C[j * DW + w];
-        sm.pP[tid * DW + w] = myc[w] | kHigh;
-    }
-    sm.flag[tid] = valid ? 0u : 1u;
-    unsigned long long pairs = 0;
-    uint32_t uses[kStages];
-#pragma unroll
-    for (int s = 0; s < kStages; ++s) uses[s] = 0;
     __syncthreads();
 
-    bool stop = false;
-    uint32_t t0 = 0;
-    while (t0 < T && !stop) {
-        // ---- group summaries of the live p's
-        {
-            const bool live = sm.flag[tid] == 0u;
-            const uint32_t nl = __popc(__ballot_sync(kFull, live));
+    if (warp == NG) {
+        // ------------------------------------------------------------ producer
+        uint32_t issued = 0;
+        auto summarise = [&]() {
 #pragma unroll
-            for (int w = 0; w < DW; ++w) {
-                uint32_t c = live ? myc[w] : 0u;
-                for (int o = 16; o > 0; o >>= 1) c = __vmaxu4(c, __shfl_xor_sync(kFull, c, o));
-                if (lane == 0) sm.gmax[warp][w] = c;
+            for (int g = 0; g < NG; ++g) {
+                const int pi = g * 32 + lane;
+                const bool live = sm.flag[pi] == 0u;
+                const uint32_t nl = __popc(__ballot_sync(kFull, live));
+#pragma unroll
+                for (int w = 0; w < DW; ++w) {
+                    uint32_t c = live ? (sm.pP[pi * DW + w] & 0x7f7f7f7fu) : 0u;
+                    for (int o = 16; o > 0; o >>= 1) c = __vmaxu4(c, __shfl_xor_sync(kFull, c, o));
+                    if (lane == 0) sm.gmax[g][w] = c;
+                }
+                if (lane == 0) sm.glive[g] = nl;
             }
-            if (lane == 0) sm.glive[warp] = nl;
-            if (tid == 0) sm.cnt = 0;
-        }
-        __syncthreads();
-        // ---- list the q-tiles that may hold a dominator of a live p
-        while (t0 < T) {
-            const uint32_t t = t0 + tid;
-            bool ok = false;
+            __syncwarp();
+        };
+        // claims the next ring slot (waits until the consumers released it)
+        auto claim = [&](int& s) -> bool {
+            s = (int)(issued % S);
+            bool ok = true;
+            if (issued >= (uint32_t)S) ok = mbar_wait(&sm.empty[s], ((issued / S) & 1u) ^ 1u, err);
+            return __all_sync(kFull, ok);
+        };
+        summarise();
+        bool stop = false;
+        uint32_t since = 0;
+        // shared flags are read by lane 0 and broadcast, so that every branch
+        // around the warp-wide votes below stays uniform
+        auto all_dead = [&]() -> bool {
+            return __shfl_sync(kFull, (sm.live == 0u || sm.failed != 0u) ? 1 : 0, 0) != 0;
+        };
+        for (uint32_t t0 = 0; t0 < T && !stop; t0 += 32) {
+            if (all_dead()) break;
+            if (since >= 32) { summarise(); since = 0; }
+            const uint32_t t = t0 + lane;
+            bool rel = false;
             if (t < T) {
                 uint32_t tm[DW];
 #pragma unroll
                 for (int w = 0; w < DW; ++w) tm[w] = __ldg(SUB + ((int64_t)t * kSubSlots + NG) * DW + w);
 #pragma unroll
-                for (int g = 0; g < NG; ++g)
-                    ok |= sm.glive[g] && bytes_le<DW>(tm, sm.gmax[g]);
+                for (int g = 0; g < NG; ++g) rel |= (sm.glive[g] != 0u) && bytes_le<DW>(tm, sm.gmax[g]);
             }
-            const uint32_t bal = __ballot_sync(kFull, ok);
-            if (lane == 0) sm.wc[warp] = __popc(bal);
-            __syncthreads();
-            uint32_t pos = sm.cnt;
-            for (int w = 0; w < warp; ++w) pos += sm.wc[w];
-            if (ok) sm.list[pos + __popc(bal & lanemask_lt())] = t;
-            __syncthreads();
-            if (tid == 0) {
-                uint32_t add = 0;
-                for (int w = 0; w < NG; ++w) add += sm.wc[w];
-                sm.cnt += add;
-            }
-            __syncthreads();
-            t0 += kTQ;
-            if (sm.cnt > kList - kTQ) break;
-        }
-        const uint32_t L = sm.cnt;
-
-        if (tid == 0) {
-            for (uint32_t i = 0; i < L && i < (uint32_t)kStages; ++i) {
-                const uint32_t t = sm.list[i];
-                mbar_arrive_expect_tx(&sm.bar[i], kBytesX + kBytesC);
-                bulk_g2s(sm.qX[i], X + (int64_t)t * kTQ * DP, kBytesX, &sm.bar[i]);
-                bulk_g2s(sm.qC[i], C + (int64_t)t * kTQ * DW, kBytesC, &sm.bar[i]);
+            uint32_t mask = __ballot_sync(kFull, rel);
+            while (mask) {
+                const int b = __ffs(mask) - 1;
+                mask &= mask - 1;
+                int s;
+                if (!claim(s)) { if (lane == 0) sm.failed = 1u; stop = true; break; }
+                if (lane == 0) {
+                    const uint32_t tt = t0 + b;
+                    sm.stage_tile[s] = tt;
+                    mbar_arrive_expect_tx(&sm.full[s], kBytesX + kBytesC);
+                    bulk_g2s(sm.qX[s], X + (int64_t)tt * kTQ * DP, kBytesX, &sm.full[s]);
+                    bulk_g2s(sm.qC[s], C + (int64_t)tt * kTQ * DW, kBytesC, &sm.full[s]);
+                }
+                __syncwarp();
+                ++issued;
+                ++since;
+                if (all_dead()) { stop = true; break; }
             }
         }
-        for (uint32_t i = 0; i < L; ++i) {
-            const int s = (int)(i % kStages);
-            const uint32_t t = sm.list[i];
-            // ---- this warp's list: live p's with codes >= the sub-tile minimum
-            uint32_t Mw[DW];
-#pragma unroll
-            for (int w = 0; w < DW; ++w) Mw[w] = __ldg(SUB + ((int64_t)t * kSubSlots + warp) * DW + w);
-            uint32_t rc = 0;
-#pragma unroll
-            for (int g = 0; g < NG; ++g) {
-                if (!sm.glive[g] || !bytes_le<DW>(Mw, sm.gmax[g])) continue;   // whole group out of reach
-                const int pi = g * 32 + lane;
-                bool rel = sm.flag[pi] == 0u;
-                if (rel) {
-                    uint32_t r = kHigh;
-#pragma unroll
-                    for (int w = 0; w < DW; ++w) r &= sm.pP[pi * DW + w] - Mw[w];
-                    rel = (r == kHigh);
-                }
-                const uint32_t bal = __ballot_sync(kFull, rel);
-                if (rel) {
-                    const uint32_t pos = rc + __popc(bal & lanemask_lt());
-                    sm.rIdx[warp][pos] = (uint8_t)pi;
-#pragma unroll
-                    for (int w = 0; w < DW; ++w) sm.rP[warp][pos * DW + w] = sm.pP[pi * DW + w];
-                }
-                rc += __popc(bal);
+        // end-of-stream marker
+        int s;
+        const bool marked = claim(s);
+        if (marked) {
+            if (lane == 0) {
+                sm.stage_tile[s] = kEndTile;
+                mbar_arrive(&sm.full[s]);
             }
-            __syncwarp();
-            const bool ok = mbar_wait(&sm.bar[s], uses[s] & 1u, err);
-            ++uses[s];
-            if (!ok) sm.failed = 1u;
-            if (ok && rc) {
-                const int qi = warp * 32 + lane;
+        } else if (lane == 0) {
+            sm.failed = 1u;
+        }
+        // Every bulk copy issued by this warp has landed before the CTA can
+        // exit. (On the normal path the consumers have waited for all of them;
+        // this matters after a timeout.) The slot reused by the marker was
+        // released by the consumers, so its copy has landed already.
+        if (lane == 0) {
+            uint32_t first = issued > (uint32_t)S ? issued - S : 0u;
+            if (marked && issued >= (uint32_t)S) first += 1;
+            for (uint32_t k = first; k < issued; ++k) mbar_wait(&sm.full[k % S], (k / S) & 1u, nullptr);
+        }
+    } else {
+        // ------------------------------------------------------------ consumers
+        const int qi = warp * 32 + lane;
+        const float* pXg = X + pbase * DP;
+        unsigned long long pairs = 0;
+        for (uint32_t k = 0;; ++k) {
+            const int s = (int)(k % S);
+            const bool ok = mbar_wait(&sm.full[s], (k / S) & 1u, err);
+            if (!__all_sync(kFull, ok)) {
+                if (lane == 0) sm.failed = 1u;
+                break;
+            }
+            const uint32_t tt = sm.stage_tile[s];
+            if (tt == kEndTile) break;
+            const bool any_live = __shfl_sync(kFull, sm.live != 0u ? 1 : 0, 0) != 0;
+            if (any_live) {
+                uint32_t Mw[DW];
+#pragma unroll
+                for (int w = 0; w < DW; ++w) Mw[w] = __ldg(SUB + ((int64_t)tt * kSubSlots + warp) * DW + w);
                 uint32_t Q[DW];
 #pragma unroll
                 for (int w = 0; w < DW; ++w) Q[w] = sm.qC[s][qi * DW + w];
-                pairs += 32ull * rc;
-                const uint32_t* rp = sm.rP[warp];
-#pragma unroll 4
-                for (uint32_t r = 0; r < rc; ++r) {
-                    uint32_t D[DW];
-                    uint32_t a = kHigh;
 #pragma unroll
-                    for (int w = 0; w < DW; ++w) {
-                        D[w] = rp[r * DW + w] - Q[w];
-                        a &= D[w];
+                for (int g = 0; g < NG; ++g) {
+                    const int pg = g * 32 + lane;
+                    bool rel = sm.flag[pg] == 0u;
+                    if (rel) {
+                        uint32_t r = kHigh;
+#pragma unroll
+                        for (int w = 0; w < DW; ++w) r &= sm.pP[pg * DW + w] - Mw[w];
+                        rel = (r == kHigh);
                     }
-                    if (a == kHigh) {  // code(q) <= code(p) in every dimension
-                        uint32_t eq = 0;
+                    uint32_t mask = __ballot_sync(kFull, rel);
+                    pairs += 32ull * __popc(mask);
+                    while (mask) {
+                        const int pi = g * 32 + __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        uint32_t D[DW];
+                        uint32_t a = kHigh;
 #pragma unroll
-                        for (int w = 0; w < DW; ++w) eq |= has_zero_byte(D[w] ^ kHigh);
-                        const int pi = sm.rIdx[warp][r];
-                        bool dom = true;   // strictly lower code everywhere: q < p everywhere
-                        if (eq) {
-                            const float* qx = &sm.qX[s][qi * DP];
-                            const float* px = pXg + pi * DP;
-                            bool le = true, lt = false;
-#pragma unroll
-                            for (int k = 0; k < DP; k += 4) {
-                                const float4 u = *reinterpret_cast<const float4*>(qx + k);
-                                const float4 v = __ldg(reinterpret_cast<const float4*>(px + k));
-                                le &= (u.x <= v.x) & (u.y <= v.y) & (u.z <= v.z) & (u.w <= v.w);
-                                lt |= (u.x < v.x) | (u.y < v.y) | (u.z < v.z) | (u.w < v.w);
-                            }
-                            dom = le && lt;
+                        for (int w = 0; w < DW; ++w) {
+                            D[w] = sm.pP[pi * DW + w] - Q[w];
+                            a &= D[w];
                         }
-                        if (dom) sm.flag[pi] = 1u;
+                        if (a == kHigh) {  // code(q) <= code(p) in every dimension
+                            uint32_t eq = 0;
+#pragma unroll
+                            for (int w = 0; w < DW; ++w) eq |= has_zero_byte(D[w] ^ kHigh);
+                            bool dom = true;   // strictly lower code everywhere: q < p everywhere
+                            if (eq) {
+                                const float* qx = &sm.qX[s][qi * DP];
+                                const float* px = pXg + pi * DP;
+                                bool le = true, lt = false;
+#pragma unroll
+                                for (int kk = 0; kk < DP; kk += 4) {
+                                    const float4 u = *reinterpret_cast<const float4*>(qx + kk);
+                                    const float4 v = __ldg(reinterpret_cast<const float4*>(px + kk));
+                                    le &= (u.x <= v.x) & (u.y <= v.y) & (u.z <= v.z) & (u.w <= v.w);
+                                    lt |= (u.x < v.x) | (u.y < v.y) | (u.z < v.z) | (u.w < v.w);
+                                }
+                                dom = le && lt;
+                            }
+                            if (dom && atomicExch(&sm.flag[pi], 1u) == 0u) atomicSub(&sm.live, 1u);
+                        }
                     }
                 }
             }
-            // one barrier per tile: stage s is free and the live flags are final
-            const bool any_live = __syncthreads_or(valid && sm.flag[tid] == 0u);
-            if (sm.failed || !any_live) stop = true;
-            if (stop) {
-                // let copies already in flight land before leaving
-                if (tid == 0) {
-                    for (uint32_t k2 = i + 1; k2 < L && k2 < i + kStages; ++k2) {
-                        const int s2 = (int)(k2 % kStages);
-                        mbar_wait(&sm.bar[s2], uses[s2] & 1u, nullptr);
-                    }
-                }
-                break;
-            }
-            if (tid == 0 && i + kStages < L) {
-                const uint32_t t2 = sm.list[i + kStages];
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&sm.bar[s], kBytesX + kBytesC);
-                bulk_g2s(sm.qX[s], X + (int64_t)t2 * kTQ * DP, kBytesX, &sm.bar[s]);
-                bulk_g2s(sm.qC[s], C + (int64_t)t2 * kTQ * DW, kBytesC, &sm.bar[s]);
-            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.empty[s]);
         }
-        __syncthreads();
+        if (lane == 0 && pairs) atomicAdd(&res->pairs, pairs);  // 32 q-lanes per listed p, per warp
     }
-    if (valid && !sm.failed && sm.flag[tid] == 0u) keep[ids[j]] = 1;
-    if (lane == 0 && pairs) atomicAdd(&res->pairs, pairs);  // 32 q-lanes x list length, per warp
+    __syncthreads();
+    if (tid < kTQ && pbase + tid < m && !sm.failed && sm.flag[tid] == 0u) keep[ids[pbase + tid]] = 1;
 }
 
 // Ascending row ids of the kept rows (decoupled look-back over 8 rows per
@@ -453,7 +462,7 @@ cudaError_t launch_refine(const Plan& p, cudaStream_t s)
             cudaFuncSetAttribute(k_refine<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             attr_set = true;
         }
-        k_refine<DP><<<(unsigned)tiles, kTQ, smem, s>>>(p.X, p.C, p.ids, p.subcode, p.res, p.keep);
+        k_refine<DP><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, p.res, p.keep);
     });
     return cudaGetLastError();
 }
