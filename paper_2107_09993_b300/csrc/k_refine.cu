@@ -155,6 +155,7 @@ struct RefineSmem {
     uint32_t gmax[kTQ / 32][DW];         // byte-wise max code of each group's live p's (producer)
     uint32_t glive[kTQ / 32];            // live p's per group (producer)
     uint32_t stage_tile[kRingStages];
+    uint32_t stage_mask[kRingStages];    // bit 4w+g: sub-tile w may dominate a live p of group g
     uint64_t full[kRingStages];
     uint64_t empty[kRingStages];
     uint32_t live;                       // live p's of the CTA
@@ -251,23 +252,38 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
             if (all_dead()) break;
             if (since >= 32) { summarise(); since = 0; }
             const uint32_t t = t0 + lane;
-            bool rel = false;
+            // relevance of each (sub-tile, group) pair of this q-tile
+            uint32_t rmask = 0;
             if (t < T) {
                 uint32_t tm[DW];
 #pragma unroll
                 for (int w = 0; w < DW; ++w) tm[w] = __ldg(SUB + ((int64_t)t * kSubSlots + NG) * DW + w);
+                bool any = false;
 #pragma unroll
-                for (int g = 0; g < NG; ++g) rel |= (sm.glive[g] != 0u) && bytes_le<DW>(tm, sm.gmax[g]);
+                for (int g = 0; g < NG; ++g) any |= (sm.glive[g] != 0u) && bytes_le<DW>(tm, sm.gmax[g]);
+                if (any) {
+#pragma unroll
+                    for (int q = 0; q < NG; ++q) {
+                        uint32_t sc[DW];
+#pragma unroll
+                        for (int w = 0; w < DW; ++w) sc[w] = __ldg(SUB + ((int64_t)t * kSubSlots + q) * DW + w);
+#pragma unroll
+                        for (int g = 0; g < NG; ++g)
+                            if (sm.glive[g] != 0u && bytes_le<DW>(sc, sm.gmax[g])) rmask |= 1u << (q * NG + g);
+                    }
+                }
             }
-            uint32_t mask = __ballot_sync(kFull, rel);
+            uint32_t mask = __ballot_sync(kFull, rmask != 0u);
             while (mask) {
                 const int b = __ffs(mask) - 1;
                 mask &= mask - 1;
+                const uint32_t bmask = __shfl_sync(kFull, rmask, b);
                 int s;
                 if (!claim(s)) { if (lane == 0) sm.failed = 1u; stop = true; break; }
                 if (lane == 0) {
                     const uint32_t tt = t0 + b;
                     sm.stage_tile[s] = tt;
+                    sm.stage_mask[s] = bmask;
                     mbar_arrive_expect_tx(&sm.full[s], kBytesX + kBytesC);
                     bulk_g2s(sm.qX[s], X + (int64_t)tt * kTQ * DP, kBytesX, &sm.full[s]);
                     bulk_g2s(sm.qC[s], C + (int64_t)tt * kTQ * DW, kBytesC, &sm.full[s]);
@@ -312,8 +328,9 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
             }
             const uint32_t tt = sm.stage_tile[s];
             if (tt == kEndTile) break;
+            const uint32_t gm = (sm.stage_mask[s] >> (warp * NG)) & ((1u << NG) - 1u);
             const bool any_live = __shfl_sync(kFull, sm.live != 0u ? 1 : 0, 0) != 0;
-            if (any_live) {
+            if (any_live && gm) {
                 uint32_t Mw[DW];
 #pragma unroll
                 for (int w = 0; w < DW; ++w) Mw[w] = __ldg(SUB + ((int64_t)tt * kSubSlots + warp) * DW + w);
@@ -322,6 +339,7 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
                 for (int w = 0; w < DW; ++w) Q[w] = sm.qC[s][qi * DW + w];
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
+                    if (!((gm >> g) & 1u)) continue;   // no live p of group g within reach
                     const int pg = g * 32 + lane;
                     bool rel = sm.flag[pg] == 0u;
                     if (rel) {
