@@ -809,11 +809,20 @@ int auto_log2g(int64_t n, int d)
     return r;
 }
 
-int morton_bits_for(int d)
+// Bits per dimension of the Morton sort key: about log2(n) + 6 bits in all
+// (never above 32), so that the sort resolves point neighbourhoods without
+// spending radix passes on empty precision.
+int morton_bits_for(int64_t n, int d)
 {
-    int b = 32 / d;
-    if (b > 16) b = 16;
+    int lg = 0;
+    while ((1ll << (lg + 1)) <= (n > 1 ? n : 1)) ++lg;
+    int target = lg + 6;
+    if (target < 16) target = 16;
+    if (target > 32) target = 32;
+    int b = (target + d / 2) / d;
     if (b < 1) b = 1;
+    while (b > 1 && b * d > 32) --b;
+    if (b > 16) b = 16;
     return b;
 }
 

@@ -32,8 +32,6 @@ namespace sky {
 namespace {
 
 constexpr int kTQ = kRefineTile;
-constexpr int kStages = 3;
-constexpr int kList = 384;
 constexpr int kSubSlots = kTQ / 32 + 1;   // sub-tile minima + the whole-tile minimum
 constexpr uint32_t kHigh = 0x80808080u;
 

@@ -101,6 +101,6 @@ cudaError_t launch_refine(const Plan& p, cudaStream_t s);
 cudaError_t launch_emit(const Plan& p, int32_t* out, int64_t capacity, cudaStream_t s);
 
 int auto_log2g(int64_t n, int d);
-int morton_bits_for(int d);
+int morton_bits_for(int64_t n, int d);
 
 }  // namespace sky

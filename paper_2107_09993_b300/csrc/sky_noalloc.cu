@@ -107,7 +107,7 @@ extern "C" sky_status sky_skyline_noalloc(const float* d_pts, int64_t n, int32_t
     while (lg > 0 && lg * d > kMaxGridBits && !(opt && opt->log2_g >= 0)) --lg;
     if (lg * d > kMaxGridBits) return noalloc_fail(SKY_ERR_TOO_LARGE, "grid above 2^20 cells (log2_g * d > 20)");
     p.log2g = lg;
-    p.morton_bits = morton_bits_for(d);
+    p.morton_bits = morton_bits_for(n, d);
     p.tma_ok = (ld == d) && ((reinterpret_cast<uintptr_t>(d_pts) & 15u) == 0);
     if (plan_workspace_bytes(n, d, lg, false) > kScratchBytes)
         return noalloc_fail(SKY_ERR_TOO_LARGE, "workspace exceeds the fixed scratch array");
