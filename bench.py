@@ -172,6 +172,7 @@ def run_sky(args):
     if uuid and not uuid.startswith("GPU-"):
         uuid = "GPU-" + uuid
     clocks = ClockSampler(uuid) if rank == 0 else None
+    time.sleep(0.5)   # let the sampler start before the timed region
     # ---- timed region: K steps, L2 flushed before each, device-resident inputs
     total_ms = 0.0
     launches = 0
@@ -348,7 +349,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["sky", "reference"], default="sky")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -198,6 +198,8 @@ typedef struct sky_run_stats {
     int64_t pairs;                /* candidate pairs examined in step (d)       */
     int32_t n_filter_used;        /* proposals that snapped to a data point     */
     int32_t kernels;              /* kernels of this library the call launched  */
+    int64_t tiles;                /* survivor tiles streamed by step (d)        */
+    int64_t group_scans;          /* (warp, point-group) scans in step (d)      */
 } sky_run_stats;
 
 SKY_API sky_status sky_last_run_stats(sky_run_stats* out);

@@ -51,7 +51,8 @@ class GridStats(ctypes.Structure):
 
 class RunStats(ctypes.Structure):
     _fields_ = [("n", _i64), ("d", _i32), ("log2_g", _i32), ("survivors", _i64), ("skyline", _i64),
-                ("pairs", _i64), ("n_filter_used", _i32), ("kernels", _i32)]
+                ("pairs", _i64), ("n_filter_used", _i32), ("kernels", _i32), ("tiles", _i64),
+                ("group_scans", _i64)]
 
 
 class PhaseTimes(ctypes.Structure):

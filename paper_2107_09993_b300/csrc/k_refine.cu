@@ -148,12 +148,14 @@ struct RefineSmem {
     static constexpr int DW = DP / 4;
     float qX[kRingStages][kTQ * DP];     // streamed q-tiles
     uint32_t qC[kRingStages][kTQ * DW];
+    float pX[kTQ * DP];                  // own p coordinates (exact tests)
     uint32_t pP[kTQ * DW];               // own p codes | 0x80 per byte
-    uint32_t flag[kTQ];                  // 1 = dominated (or padding)
+    uint32_t livemask[kTQ / 32];         // bit l of word g: p g*32+l is still undominated
     uint32_t gmax[kTQ / 32][DW];         // byte-wise max code of each group's live p's (producer)
     uint32_t glive[kTQ / 32];            // live p's per group (producer)
     uint32_t stage_tile[kRingStages];
     uint32_t stage_mask[kRingStages];    // bit 4w+g: sub-tile w may dominate a live p of group g
+    uint32_t stage_sub[kRingStages][kTQ / 32][DW];   // sub-tile minimum codes of the staged tile
     uint64_t full[kRingStages];
     uint64_t empty[kRingStages];
     uint32_t live;                       // live p's of the CTA
@@ -199,7 +201,12 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
         const bool valid = pbase + tid < m;
 #pragma unroll
         for (int w = 0; w < DW; ++w) sm.pP[tid * DW + w] = C[(pbase + tid) * DW + w] | kHigh;
-        sm.flag[tid] = valid ? 0u : 1u;
+#pragma unroll
+        for (int k = 0; k < DP; k += 4)
+            *reinterpret_cast<float4*>(&sm.pX[tid * DP + k]) =
+                *reinterpret_cast<const float4*>(X + (pbase + tid) * DP + k);
+        const uint32_t vm = __ballot_sync(kFull, valid);
+        if ((tid & 31) == 0) sm.livemask[tid >> 5] = vm;
     }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -219,8 +226,9 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
                 const int pi = g * 32 + lane;
-                const bool live = sm.flag[pi] == 0u;
-                const uint32_t nl = __popc(__ballot_sync(kFull, live));
+                const uint32_t lm = sm.livemask[g];
+                const bool live = (lm >> lane) & 1u;
+                const uint32_t nl = __popc(lm);
 #pragma unroll
                 for (int w = 0; w < DW; ++w) {
                     uint32_t c = live ? (sm.pP[pi * DW + w] & 0x7f7f7f7fu) : 0u;
@@ -246,29 +254,41 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
         auto all_dead = [&]() -> bool {
             return __shfl_sync(kFull, (sm.live == 0u || sm.failed != 0u) ? 1 : 0, 0) != 0;
         };
+        // codes of the next 32 tiles are fetched one batch ahead
+        uint32_t tm[DW], sc[NG][DW];
+        auto fetch = [&](uint32_t t) {
+#pragma unroll
+            for (int w = 0; w < DW; ++w) tm[w] = t < T ? __ldg(SUB + ((int64_t)t * kSubSlots + NG) * DW + w) : 0u;
+#pragma unroll
+            for (int q = 0; q < NG; ++q)
+#pragma unroll
+                for (int w = 0; w < DW; ++w) sc[q][w] = t < T ? __ldg(SUB + ((int64_t)t * kSubSlots + q) * DW + w) : 0u;
+        };
+        fetch(lane);
         for (uint32_t t0 = 0; t0 < T && !stop; t0 += 32) {
             if (all_dead()) break;
             if (since >= 32) { summarise(); since = 0; }
             const uint32_t t = t0 + lane;
+            uint32_t ctm[DW], csc[NG][DW];
+#pragma unroll
+            for (int w = 0; w < DW; ++w) ctm[w] = tm[w];
+#pragma unroll
+            for (int q = 0; q < NG; ++q)
+#pragma unroll
+                for (int w = 0; w < DW; ++w) csc[q][w] = sc[q][w];
+            fetch(t + 32);
             // relevance of each (sub-tile, group) pair of this q-tile
             uint32_t rmask = 0;
             if (t < T) {
-                uint32_t tm[DW];
-#pragma unroll
-                for (int w = 0; w < DW; ++w) tm[w] = __ldg(SUB + ((int64_t)t * kSubSlots + NG) * DW + w);
                 bool any = false;
 #pragma unroll
-                for (int g = 0; g < NG; ++g) any |= (sm.glive[g] != 0u) && bytes_le<DW>(tm, sm.gmax[g]);
+                for (int g = 0; g < NG; ++g) any |= (sm.glive[g] != 0u) && bytes_le<DW>(ctm, sm.gmax[g]);
                 if (any) {
 #pragma unroll
-                    for (int q = 0; q < NG; ++q) {
-                        uint32_t sc[DW];
-#pragma unroll
-                        for (int w = 0; w < DW; ++w) sc[w] = __ldg(SUB + ((int64_t)t * kSubSlots + q) * DW + w);
+                    for (int q = 0; q < NG; ++q)
 #pragma unroll
                         for (int g = 0; g < NG; ++g)
-                            if (sm.glive[g] != 0u && bytes_le<DW>(sc, sm.gmax[g])) rmask |= 1u << (q * NG + g);
-                    }
+                            if (sm.glive[g] != 0u && bytes_le<DW>(csc[q], sm.gmax[g])) rmask |= 1u << (q * NG + g);
                 }
             }
             uint32_t mask = __ballot_sync(kFull, rmask != 0u);
@@ -278,6 +298,16 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
                 const uint32_t bmask = __shfl_sync(kFull, rmask, b);
                 int s;
                 if (!claim(s)) { if (lane == 0) sm.failed = 1u; stop = true; break; }
+                {
+                    // every lane holds its own tile's codes; move tile b's to the slot
+#pragma unroll
+                    for (int q = 0; q < NG; ++q)
+#pragma unroll
+                        for (int w = 0; w < DW; ++w) {
+                            const uint32_t v = __shfl_sync(kFull, csc[q][w], b);
+                            if (lane == 0) sm.stage_sub[s][q][w] = v;
+                        }
+                }
                 if (lane == 0) {
                     const uint32_t tt = t0 + b;
                     sm.stage_tile[s] = tt;
@@ -292,6 +322,7 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
                 if (all_dead()) { stop = true; break; }
             }
         }
+        if (lane == 0 && issued) atomicAdd(&res->tiles, (unsigned long long)issued);
         // end-of-stream marker
         int s;
         const bool marked = claim(s);
@@ -315,8 +346,7 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
     } else {
         // ------------------------------------------------------------ consumers
         const int qi = warp * 32 + lane;
-        const float* pXg = X + pbase * DP;
-        unsigned long long pairs = 0;
+        unsigned long long pairs = 0, gscans = 0;
         for (uint32_t k = 0;; ++k) {
             const int s = (int)(k % S);
             const bool ok = mbar_wait(&sm.full[s], (k / S) & 1u, err);
@@ -331,22 +361,19 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
             if (any_live && gm) {
                 uint32_t Mw[DW];
 #pragma unroll
-                for (int w = 0; w < DW; ++w) Mw[w] = __ldg(SUB + ((int64_t)tt * kSubSlots + warp) * DW + w);
+                for (int w = 0; w < DW; ++w) Mw[w] = sm.stage_sub[s][warp][w];
                 uint32_t Q[DW];
 #pragma unroll
                 for (int w = 0; w < DW; ++w) Q[w] = sm.qC[s][qi * DW + w];
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
                     if (!((gm >> g) & 1u)) continue;   // no live p of group g within reach
+                    ++gscans;
                     const int pg = g * 32 + lane;
-                    bool rel = sm.flag[pg] == 0u;
-                    if (rel) {
-                        uint32_t r = kHigh;
+                    uint32_t r = kHigh;
 #pragma unroll
-                        for (int w = 0; w < DW; ++w) r &= sm.pP[pg * DW + w] - Mw[w];
-                        rel = (r == kHigh);
-                    }
-                    uint32_t mask = __ballot_sync(kFull, rel);
+                    for (int w = 0; w < DW; ++w) r &= sm.pP[pg * DW + w] - Mw[w];
+                    uint32_t mask = __ballot_sync(kFull, r == kHigh) & sm.livemask[g];
                     pairs += 32ull * __popc(mask);
                     while (mask) {
                         const int pi = g * 32 + __ffs(mask) - 1;
@@ -365,18 +392,21 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
                             bool dom = true;   // strictly lower code everywhere: q < p everywhere
                             if (eq) {
                                 const float* qx = &sm.qX[s][qi * DP];
-                                const float* px = pXg + pi * DP;
+                                const float* px = &sm.pX[pi * DP];
                                 bool le = true, lt = false;
 #pragma unroll
                                 for (int kk = 0; kk < DP; kk += 4) {
                                     const float4 u = *reinterpret_cast<const float4*>(qx + kk);
-                                    const float4 v = __ldg(reinterpret_cast<const float4*>(px + kk));
+                                    const float4 v = *reinterpret_cast<const float4*>(px + kk);
                                     le &= (u.x <= v.x) & (u.y <= v.y) & (u.z <= v.z) & (u.w <= v.w);
                                     lt |= (u.x < v.x) | (u.y < v.y) | (u.z < v.z) | (u.w < v.w);
                                 }
                                 dom = le && lt;
                             }
-                            if (dom && atomicExch(&sm.flag[pi], 1u) == 0u) atomicSub(&sm.live, 1u);
+                            if (dom) {
+                                const uint32_t bit = 1u << (pi & 31);
+                                if (atomicAnd(&sm.livemask[pi >> 5], ~bit) & bit) atomicSub(&sm.live, 1u);
+                            }
                         }
                     }
                 }
@@ -385,9 +415,11 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
             if (lane == 0) mbar_arrive(&sm.empty[s]);
         }
         if (lane == 0 && pairs) atomicAdd(&res->pairs, pairs);  // 32 q-lanes per listed p, per warp
+        if (lane == 0 && gscans) atomicAdd(&res->groups, gscans);
     }
     __syncthreads();
-    if (tid < kTQ && pbase + tid < m && !sm.failed && sm.flag[tid] == 0u) keep[ids[pbase + tid]] = 1;
+    if (tid < kTQ && pbase + tid < m && !sm.failed && ((sm.livemask[tid >> 5] >> (tid & 31)) & 1u))
+        keep[ids[pbase + tid]] = 1;
 }
 
 // Ascending row ids of the kept rows (decoupled look-back over 8 rows per

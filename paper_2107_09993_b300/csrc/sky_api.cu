@@ -393,6 +393,8 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
     t_stats.skyline = r.count;
     t_stats.pairs = (int64_t)r.pairs;
     t_stats.n_filter_used = (int32_t)r.n_filter_used;
+    t_stats.tiles = (int64_t)r.tiles;
+    t_stats.group_scans = (int64_t)r.groups;
     st = status_from_flags(r.err);
     if (st != SKY_OK) return st;
     *count = r.count;

@@ -18,6 +18,8 @@ struct DevResult {
     uint32_t surviving_cells;
     uint32_t redo;             // automatic value map: 1 = second map pass with min/max scales
     uint32_t pad;
+    unsigned long long tiles;  // q-tiles streamed by the refinement (all CTAs)
+    unsigned long long groups; // (warp, p-group) list scans in the refinement
 };
 
 
