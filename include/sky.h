@@ -187,6 +187,90 @@ SKY_API sky_status sky_skyline_host(const float* h_pts, int64_t n, int32_t d, in
                             const sky_options* opt, int32_t* h_out_idx, int64_t out_capacity,
                             int64_t* h_out_count, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched skylines (a project addition; the paper has no batched form).     */
+/* Many skyline queries over row ranges and attribute subsets of one table   */
+/* run as one CUDA-graph launch: every phase of steps (a)-(d) is one kernel  */
+/* over all queries, and step (d) is a persistent kernel that pulls          */
+/* (query, tile) work items, largest queries first.                          */
+/* ------------------------------------------------------------------------ */
+
+/* One query: rows [row_begin, row_begin + row_count) of the table, with the
+ * columns whose bits are set in dim_mask (1 to 16 columns) as attributes. */
+typedef struct sky_query {
+    int64_t row_begin;
+    int64_t row_count;
+    uint32_t dim_mask;
+    uint32_t reserved;            /* must be 0 */
+} sky_query;
+
+/* Tuning knobs (zero-initialise; see paper_2107_09993_b300/tune.py). */
+typedef struct sky_batch_tuning {
+    const int32_t* h_log2g;       /* per-query grid layer (host array), or NULL:
+                                     automatic; log2_g * d <= 18 in batches     */
+    int32_t refine_ctas_per_sm;   /* persistent refinement CTAs per SM (0 = max
+                                     resident)                                  */
+    int32_t reserved[3];
+} sky_batch_tuning;
+
+typedef struct sky_batch sky_batch;
+
+typedef struct sky_batch_stats_t {
+    int32_t n_queries;
+    int32_t kernels;              /* kernels in the captured graph              */
+    int32_t graph_launches_per_call;
+    int32_t reserved;
+    int64_t points;               /* sum of row_count                           */
+    int64_t survivors;            /* points left after step (c), all queries    */
+    int64_t skyline;              /* indices returned, all queries              */
+    int64_t pairs;                /* candidate pairs examined in step (d)       */
+} sky_batch_stats_t;
+
+/*
+ * Plans a batch on the host. d_table: n_rows x n_cols float32 on the device,
+ * element (r, c) at d_table[r * row_stride + c * col_stride]; the table is
+ * row-major (col_stride 1) or column-major (row_stride 1, faster: each query
+ * then reads only its own columns). h_queries: host array. Nothing runs on
+ * the device. *ws_bytes receives the workspace size the batch needs. The
+ * table must stay valid (and unchanged in layout) for the batch's lifetime;
+ * its contents may change between launches.
+ */
+SKY_API sky_status sky_batch_create(const float* d_table, int64_t n_rows, int32_t n_cols, int64_t row_stride,
+                                    int64_t col_stride, const sky_query* h_queries, int32_t n_queries,
+                                    const sky_batch_tuning* tuning, sky_batch** out, size_t* ws_bytes);
+
+/* Workspace bytes for a batch (same planning as sky_batch_create; 0 on error). */
+SKY_API size_t sky_batched_workspace_size(int64_t n_rows, int32_t n_cols, int64_t row_stride, int64_t col_stride,
+                                          const sky_query* h_queries, int32_t n_queries,
+                                          const sky_batch_tuning* tuning);
+
+/*
+ * Binds the caller's buffers (all device memory, owned by the caller):
+ * d_ws (ws_bytes >= the size from sky_batch_create, 256-byte aligned),
+ * d_out_idx (out_capacity int32), d_out_offsets (n_queries + 1 int64, CSR:
+ * query q's skyline is d_out_idx[offsets[q] .. offsets[q+1]), ascending
+ * global row ids), d_query_status (n_queries int32 sky_status codes). Uploads
+ * the plan, runs the batch once and captures its kernel sequence into a CUDA
+ * graph. Synchronises `stream`.
+ */
+SKY_API sky_status sky_batch_bind(sky_batch* batch, void* d_ws, size_t ws_bytes, int32_t* d_out_idx,
+                                  int64_t out_capacity, int64_t* d_out_offsets, int32_t* d_query_status,
+                                  void* stream);
+
+/*
+ * Steps (a)-(d) for every query of a bound batch: one CUDA-graph launch on
+ * `stream`. Never allocates and never synchronises; results are valid once
+ * the stream reaches this point. Queries whose indices do not fit in
+ * out_capacity report SKY_ERR_CAPACITY in d_query_status (offsets stay exact).
+ */
+SKY_API sky_status sky_skyline_batched(sky_batch* batch, void* stream);
+
+/* Synchronises `stream` and sums the per-query work counters. */
+SKY_API sky_status sky_batch_stats(const sky_batch* batch, void* stream, sky_batch_stats_t* out);
+
+SKY_API void sky_batch_destroy(sky_batch* batch);        /* NULL accepted */
+SKY_API const char* sky_batch_last_error(void);          /* thread-local detail */
+
 /* Work counters of the last sky_skyline / sky_skyline_host call made on the
  * calling thread (for measurement; not part of the result). */
 typedef struct sky_run_stats {

@@ -259,3 +259,127 @@ class Grid:
 
 def version() -> str:
     return load().sky_version().decode()
+
+
+# ---------------------------------------------------------------- batched --
+class Query(ctypes.Structure):
+    _fields_ = [("row_begin", _i64), ("row_count", _i64), ("dim_mask", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("h_log2g", _vp), ("refine_ctas_per_sm", _i32), ("reserved", _i32 * 3)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("n_queries", _i32), ("kernels", _i32), ("graph_launches_per_call", _i32), ("reserved", _i32),
+                ("points", _i64), ("survivors", _i64), ("skyline", _i64), ("pairs", _i64)]
+
+
+def _load_batched():
+    lib = load()
+    if getattr(lib, "_batched_bound", False):
+        return lib
+    P = ctypes.POINTER
+    sig = {
+        "sky_batch_create": ([_vp, _i64, _i32, _i64, _i64, _vp, _i32, P(BatchTuning), P(_vp), P(_sz)], _i32),
+        "sky_batched_workspace_size": ([_i64, _i32, _i64, _i64, _vp, _i32, P(BatchTuning)], _sz),
+        "sky_batch_bind": ([_vp, _vp, _sz, _vp, _i64, _vp, _vp, _vp], _i32),
+        "sky_skyline_batched": ([_vp, _vp], _i32),
+        "sky_batch_stats": ([_vp, _vp, P(BatchStats)], _i32),
+        "sky_batch_destroy": ([_vp], None),
+        "sky_batch_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    lib._batched_bound = True
+    return lib
+
+
+def _bcheck(status: int):
+    if status != SKY_OK:
+        raise SkyError(status, _load_batched().sky_batch_last_error().decode())
+
+
+class Batch:
+    """Many skylines over row ranges x attribute subsets of one device table,
+    run as one CUDA-graph launch (sky_batch_create / bind / sky_skyline_batched).
+
+    table: 2-D float32 CUDA tensor, row-major (stride (ld, 1)) or column-major
+    (stride (1, ld)). queries: int array [n_queries, 3] of (row_begin,
+    row_count, dim_mask). Results: global ascending row ids per query."""
+
+    def __init__(self, table, queries, log2g=None, refine_ctas_per_sm=0, capacity=None, stream=None):
+        import numpy as np
+        torch = _torch()
+        lib = _load_batched()
+        if table.dim() != 2 or table.dtype != torch.float32 or not table.is_cuda:
+            raise ValueError("table must be a 2-D float32 CUDA tensor")
+        self.table = table
+        q = np.asarray(queries, dtype=np.int64).reshape(-1, 3)
+        self.nq = q.shape[0]
+        arr = (Query * max(self.nq, 1))()
+        for i in range(self.nq):
+            arr[i].row_begin, arr[i].row_count, arr[i].dim_mask, arr[i].reserved = int(q[i, 0]), int(q[i, 1]), \
+                int(q[i, 2]) & 0xffffffff, 0
+        self._queries = arr
+        tune = BatchTuning()
+        self._lg = None
+        if log2g is not None:
+            self._lg = np.ascontiguousarray(np.asarray(log2g, dtype=np.int32).reshape(-1))
+            assert self._lg.size == self.nq
+            tune.h_log2g = self._lg.ctypes.data
+        tune.refine_ctas_per_sm = int(refine_ctas_per_sm)
+        self._h = _vp()
+        ws = _sz(0)
+        n_rows, n_cols = table.shape
+        _bcheck(lib.sky_batch_create(_vp(table.data_ptr()), n_rows, n_cols, table.stride(0), table.stride(1),
+                                     ctypes.cast(arr, _vp), self.nq, ctypes.byref(tune), ctypes.byref(self._h),
+                                     ctypes.byref(ws)))
+        dev = table.device
+        self.ws_bytes = ws.value
+        self.ws = torch.empty(max(self.ws_bytes, 1) + 256, dtype=torch.uint8, device=dev)
+        base = self.ws.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        total_rows = int(q[:, 1].sum()) if self.nq else 0
+        self.capacity = total_rows if capacity is None else int(capacity)
+        self.out = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=dev)
+        self.offsets = torch.zeros(self.nq + 1, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(max(self.nq, 1), dtype=torch.int32, device=dev)
+        with torch.cuda.device(dev):
+            _bcheck(lib.sky_batch_bind(self._h, _vp(self._ws_ptr), self.ws_bytes, _vp(self.out.data_ptr()),
+                                       self.capacity, _vp(self.offsets.data_ptr()), _vp(self.status.data_ptr()),
+                                       _stream_ptr(stream)))
+
+    def run(self, stream=None):
+        """One CUDA-graph launch of the whole batch (asynchronous)."""
+        _bcheck(_load_batched().sky_skyline_batched(self._h, _stream_ptr(stream)))
+
+    def results(self):
+        """Per-query ascending global row ids (CPU int32 arrays); synchronises."""
+        torch = _torch()
+        torch.cuda.synchronize(self.table.device)
+        off = self.offsets.cpu().numpy()
+        out = self.out.cpu().numpy()
+        return [out[off[i]:off[i + 1]] for i in range(self.nq)]
+
+    def query_status(self):
+        return self.status[:self.nq].cpu().numpy()
+
+    def stats(self, stream=None) -> dict:
+        s = BatchStats()
+        _bcheck(_load_batched().sky_batch_stats(self._h, _stream_ptr(stream), ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in BatchStats._fields_ if f != "reserved"}
+
+    def close(self):
+        if self._h:
+            _load_batched().sky_batch_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,452 @@
+// k_batched.cu -- many skylines (row ranges x attribute subsets of one table)
+// in one CUDA-graph launch (sm_103a).
+//
+// Every phase of the single-set path runs once for the whole batch: each
+// kernel walks a flat list of (query, block) work items, found from per-query
+// prefix counts by binary search, so small and large queries share the same
+// launches. The refinement is a persistent kernel per padded dimension class
+// that pulls (query, p-tile) items from a global counter, largest queries
+// first, and runs the same per-tile refinement as the single-set kernel.
+// Look-back scans stay inside one query (its tiles are claimed in order).
+//
+// The value -> column map is Eq. 1 on the unit cube with clamping (exact for
+// any finite data; pruning is best for data in [0,1]).
+#include <algorithm>
+#include <cstdint>
+
+#include "sky_common.cuh"
+#include "sky_internal.h"
+#include "sky_refine.cuh"
+#include "sky_sort.cuh"
+
+namespace sky {
+namespace batched {
+
+constexpr int kT = 256;
+constexpr int kChunk = kScanTile;           // 2048 rows: map, survivors, sort and emit blocks
+static_assert(kChunk == kSortTile, "survivor and sort blocks share one granularity");
+using refine::kTQ;
+using refine::kSubSlots;
+
+// Query of flat item `item` given the exclusive prefix of per-query counts.
+__device__ __forceinline__ int find_query(const int64_t* prefix, int nq, int64_t item)
+{
+    int lo = 0, hi = nq;  // prefix[lo] <= item < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float elem(const QueryPlan& q, int64_t r, int k)
+{
+    return __ldg(q.base + r * q.rs + (int64_t)q.col[k] * q.cs);
+}
+
+// ---------------------------------------------------------------- (a)+(b)
+__global__ void __launch_bounds__(kT) kb_map(const QueryPlan* __restrict__ qps, int nq,
+                                             const int64_t* __restrict__ pchunk, int64_t nitems)
+{
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int qi = find_query(pchunk, nq, item);
+        const QueryPlan& q = qps[qi];
+        const int64_t r0 = (item - pchunk[qi]) * kChunk;
+        const uint32_t G = 1u << q.log2g, M = 1u << q.mbits;
+        const float sc = (float)G, sm = (float)M;
+        bool bad = false;
+        for (int64_t r = r0 + threadIdx.x; r < r0 + kChunk && r < q.n; r += kT) {
+            uint32_t key = 0, mq[kMaxDim];
+#pragma unroll
+            for (int k = kMaxDim - 1; k >= 0; --k) {
+                mq[k] = 0;
+                if (k < q.d) {
+                    const float x = elem(q, r, k);
+                    bad |= !isfinite(x);
+                    const uint32_t c = column_of(x, 0.0f, sc, G);
+                    key = (key << q.log2g) | c;
+                    mq[k] = (q.mbits <= q.log2g) ? (c >> (q.log2g - q.mbits)) : column_of(x, 0.0f, sm, M);
+                }
+            }
+            uint32_t code = 0;
+            for (int l = q.mbits - 1; l >= 0; --l)
+#pragma unroll
+                for (int k = kMaxDim - 1; k >= 0; --k)
+                    if (k < q.d) code = (code << 1) | ((mq[k] >> l) & 1u);
+            q.keys[r] = make_uint2(key, code);
+            atomicOr(q.occ + (key >> 5), 1u << (key & 31u));
+        }
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&q.res->err, SKY_DEV_ERR_NONFINITE);
+    }
+}
+
+// One CTA per query: the d prefix-OR passes in shared memory.
+__global__ void __launch_bounds__(512) kb_prefix(const QueryPlan* __restrict__ qps)
+{
+    extern __shared__ uint32_t s_words[];
+    const QueryPlan& q = qps[blockIdx.x];
+    if (q.n == 0) return;
+    for (int64_t w = threadIdx.x; w < q.words; w += blockDim.x) s_words[w] = q.occ[w];
+    __syncthreads();
+    for (int k = 0; k < q.d; ++k) {
+        prefix_or_dim(s_words, q.words, q.log2g, k, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
+    for (int64_t w = threadIdx.x; w < q.words; w += blockDim.x) q.pre[w] = s_words[w];
+}
+
+// -------------------------------------------------------------------- (c)
+__global__ void __launch_bounds__(kT) kb_survivors(const QueryPlan* __restrict__ qps, int nq,
+                                                   const int64_t* __restrict__ pchunk, uint32_t* claim)
+{
+    __shared__ uint32_t s_warp[kT / 32];
+    __shared__ uint32_t s_prefix;
+    __shared__ int64_t s_item;
+    if (threadIdx.x == 0) s_item = atomicAdd(claim, 1u);
+    __syncthreads();
+    const int64_t item = s_item;
+    const int qi = find_query(pchunk, nq, item);
+    const QueryPlan& q = qps[qi];
+    const uint32_t tile = (uint32_t)(item - pchunk[qi]);
+    const uint32_t ones = ones_key(q.log2g, q.d);
+    const int64_t base = (int64_t)tile * kChunk + (int64_t)threadIdx.x * kScanItems;
+    uint32_t flags = 0, mk[kScanItems];
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int64_t i = base + j;
+        mk[j] = 0;
+        if (i >= q.n) continue;
+        const uint2 kk = q.keys[i];
+        mk[j] = kk.y;
+        bool dominated = false;
+        if (all_columns_positive(kk.x, q.log2g, q.d)) {
+            const uint32_t src = kk.x - ones;
+            dominated = (q.pre[src >> 5] >> (src & 31u)) & 1u;
+        }
+        if (!dominated) flags |= 1u << j;
+    }
+    uint32_t total;
+    const uint32_t excl = block_excl_scan<kT>((uint32_t)__popc(flags), s_warp, total);
+    if (threadIdx.x < 32) {
+        const uint32_t prefix = lookback_prefix(q.lb_a, tile, total, &q.res->err);
+        if (threadIdx.x == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    uint32_t pos = s_prefix + excl;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (flags & (1u << j)) {
+            q.surv_key[pos] = mk[j];
+            q.surv_idx[pos] = (uint32_t)(base + j);
+            ++pos;
+        }
+    }
+    if (tile == q.chunks - 1 && threadIdx.x == 0) q.res->survivors = s_prefix + total;
+}
+
+// ------------------------------------------------------------------- sort
+__device__ __forceinline__ void pass_buffers(const QueryPlan& q, int ps, const uint32_t*& kin,
+                                             const uint32_t*& vin, uint32_t*& kout, uint32_t*& vout)
+{
+    const bool even = (ps & 1) == 0;
+    kin = even ? q.surv_key : q.key2;
+    vin = even ? q.surv_idx : q.val2;
+    kout = even ? q.key2 : q.surv_key;
+    vout = even ? q.val2 : q.surv_idx;
+}
+
+__global__ void __launch_bounds__(kT) kb_radix_hist(const QueryPlan* __restrict__ qps, int nq,
+                                                    const int64_t* __restrict__ pchunk, int ps)
+{
+    const int64_t item = blockIdx.x;
+    const int qi = find_query(pchunk, nq, item);
+    const QueryPlan& q = qps[qi];
+    if (ps >= q.passes) return;
+    const uint32_t* kin; const uint32_t* vin; uint32_t* kout; uint32_t* vout;
+    pass_buffers(q, ps, kin, vin, kout, vout);
+    radix::radix_hist_block(kin, q.res->survivors, 8 * ps, q.hist, q.chunks, q.digit_total + 256 * ps,
+                            (uint32_t)(item - pchunk[qi]));
+}
+
+// One CTA per query; thread t owns digit t and walks its row of blocks.
+__global__ void __launch_bounds__(256) kb_radix_scan(const QueryPlan* __restrict__ qps, int ps)
+{
+    __shared__ uint32_t s_warp[8];
+    const QueryPlan& q = qps[blockIdx.x];
+    if (ps >= q.passes || q.n == 0) return;
+    const uint32_t m = q.res->survivors;
+    const int64_t nblk = ((int64_t)m + kChunk - 1) / kChunk;
+    uint32_t total;
+    uint32_t off = block_excl_scan<256>(q.digit_total[256 * ps + threadIdx.x], s_warp, total);
+    uint32_t* row = q.hist + (int64_t)threadIdx.x * q.chunks;
+    for (int64_t b = 0; b < nblk; ++b) {
+        const uint32_t v = row[b];
+        row[b] = off;
+        off += v;
+    }
+}
+
+__global__ void __launch_bounds__(kT) kb_radix_scatter(const QueryPlan* __restrict__ qps, int nq,
+                                                       const int64_t* __restrict__ pchunk, int ps)
+{
+    const int64_t item = blockIdx.x;
+    const int qi = find_query(pchunk, nq, item);
+    const QueryPlan& q = qps[qi];
+    if (ps >= q.passes) return;
+    const uint32_t* kin; const uint32_t* vin; uint32_t* kout; uint32_t* vout;
+    pass_buffers(q, ps, kin, vin, kout, vout);
+    radix::radix_scatter_block(kin, vin, kout, vout, q.res->survivors, 8 * ps, q.hist, q.chunks,
+                               (uint32_t)(item - pchunk[qi]));
+}
+
+// ----------------------------------------------------------------- layout
+// Survivors of one query in Morton order: coordinates padded to dp, 7-bit
+// codes, local row ids, sub-tile and tile minimum codes.
+__global__ void __launch_bounds__(kTQ) kb_gather(const QueryPlan* __restrict__ qps, int nq,
+                                                 const int64_t* __restrict__ ptile)
+{
+    __shared__ uint32_t s_sub[kTQ / 32][4];
+    const int64_t item = blockIdx.x;
+    const int qi = find_query(ptile, nq, item);
+    const QueryPlan& q = qps[qi];
+    const uint32_t t = (uint32_t)(item - ptile[qi]);
+    const uint32_t m = q.res->survivors;
+    if (t >= (m + kTQ - 1) / kTQ) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int dp = q.dp, dw = dp / 4;
+    const int64_t j = (int64_t)t * kTQ + tid;
+    const bool valid = j < m;
+    const uint32_t* sorted = (q.passes & 1) ? q.val2 : q.surv_idx;
+    const uint32_t row = valid ? sorted[j] : 0u;
+    float x[kMaxDim];
+    uint32_t code[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < kMaxDim; ++k) {
+        x[k] = 0.0f;
+        if (k < dp) {
+            uint32_t c = 127u;
+            if (valid) {
+                c = 0u;
+                if (k < q.d) {
+                    x[k] = elem(q, row, k);
+                    c = column_of(x[k], 0.0f, 128.0f, 128u);
+                }
+            } else {
+                x[k] = INFINITY;
+            }
+            code[k / 4] |= c << (8 * (k % 4));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxDim; k += 4)
+        if (k < dp)
+            *reinterpret_cast<float4*>(q.X + j * dp + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        if (w < dw) {
+            q.C[j * dw + w] = code[w];
+            uint32_t c = code[w];
+            for (int o = 16; o > 0; o >>= 1) c = __vminu4(c, __shfl_xor_sync(kFull, c, o));
+            if (lane == 0) {
+                q.sub[((int64_t)t * kSubSlots + warp) * dw + w] = c;
+                s_sub[warp][w] = c;
+            }
+        }
+    }
+    q.ids[j] = valid ? (int32_t)row : -1;
+    __syncthreads();
+    if (tid < dw) {
+        uint32_t c = s_sub[0][tid];
+        for (int w = 1; w < kTQ / 32; ++w) c = __vminu4(c, s_sub[w][tid]);
+        q.sub[((int64_t)t * kSubSlots + kTQ / 32) * dw + tid] = c;
+    }
+}
+
+// -------------------------------------------------------------------- (d)
+template <int DP>
+__global__ void __launch_bounds__(kTQ + 32) kb_refine(const QueryPlan* __restrict__ qps,
+                                                      const int2* __restrict__ items, int nitems, uint32_t* claim)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    refine::RefineSmem<DP>& sm = *reinterpret_cast<refine::RefineSmem<DP>*>(smem_raw);
+    __shared__ int s_item;
+    while (true) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(claim, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const int2 w = items[it];
+        const QueryPlan& q = qps[w.x];
+        const uint32_t m = q.res->survivors;
+        if ((uint32_t)w.y < (m + kTQ - 1) / kTQ)
+            refine::refine_ptile<DP>(sm, q.X, q.C, q.ids, q.sub, m, (uint32_t)w.y, q.res, q.keep);
+    }
+}
+
+__global__ void __launch_bounds__(kT) kb_emit(const QueryPlan* __restrict__ qps, int nq,
+                                              const int64_t* __restrict__ pchunk, uint32_t* claim)
+{
+    __shared__ uint32_t s_warp[kT / 32];
+    __shared__ uint32_t s_prefix;
+    __shared__ int64_t s_item;
+    if (threadIdx.x == 0) s_item = atomicAdd(claim, 1u);
+    __syncthreads();
+    const int64_t item = s_item;
+    const int qi = find_query(pchunk, nq, item);
+    const QueryPlan& q = qps[qi];
+    const uint32_t tile = (uint32_t)(item - pchunk[qi]);
+    const int64_t base = (int64_t)tile * kChunk + (int64_t)threadIdx.x * kScanItems;
+    uint32_t flags = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        if (base + j < q.n && q.keep[base + j]) flags |= 1u << j;
+    uint32_t total;
+    const uint32_t excl = block_excl_scan<kT>((uint32_t)__popc(flags), s_warp, total);
+    if (threadIdx.x < 32) {
+        const uint32_t prefix = lookback_prefix(q.lb_b, tile, total, &q.res->err);
+        if (threadIdx.x == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    uint32_t pos = s_prefix + excl;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        if (flags & (1u << j)) q.stage[pos++] = (int32_t)(q.row_begin + base + j);
+    if (tile == q.chunks - 1 && threadIdx.x == 0) q.res->count = s_prefix + total;
+}
+
+// Output offsets (exclusive scan of the counts in query order) and status.
+__global__ void __launch_bounds__(1024) kb_finish(const QueryPlan* __restrict__ qps, int nq, int64_t capacity,
+                                                  int64_t* offsets, int32_t* status)
+{
+    __shared__ int64_t s_part[1024];
+    const int per = (nq + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(nq, lo + per);
+    int64_t sum = 0;
+    for (int q = lo; q < hi; ++q) sum += qps[q].n ? qps[q].res->count : 0;
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int64_t v = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : 0;
+        __syncthreads();
+        s_part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = s_part[threadIdx.x] - sum;
+    for (int q = lo; q < hi; ++q) {
+        const QueryPlan& p = qps[q];
+        const int64_t c = p.n ? p.res->count : 0;
+        offsets[q] = run;
+        const uint32_t err = p.n ? p.res->err : 0u;
+        int32_t st = 0;                                   // SKY_OK
+        if (err & SKY_DEV_ERR_NONFINITE) st = 2;          // SKY_ERR_NONFINITE
+        else if (err & SKY_DEV_ERR_TIMEOUT) st = 7;       // SKY_ERR_TIMEOUT
+        else if (run + c > capacity) st = 3;              // SKY_ERR_CAPACITY
+        status[q] = st;
+        run += c;
+    }
+    if (threadIdx.x == 1023) offsets[nq] = s_part[1023];
+}
+
+__global__ void __launch_bounds__(kT) kb_copy(const QueryPlan* __restrict__ qps, int nq,
+                                              const int64_t* __restrict__ pchunk, int64_t nitems,
+                                              const int64_t* __restrict__ offsets, int32_t* out, int64_t capacity)
+{
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int qi = find_query(pchunk, nq, item);
+        const QueryPlan& q = qps[qi];
+        const int64_t c = q.res->count;
+        const int64_t off = offsets[qi];
+        const int64_t i0 = (item - pchunk[qi]) * kChunk;
+        for (int64_t i = i0 + threadIdx.x; i < i0 + kChunk && i < c; i += kT)
+            if (off + i < capacity) out[off + i] = q.stage[i];
+    }
+}
+
+}  // namespace batched
+
+// ============================================================ host side ===
+namespace {
+
+int sm_count()
+{
+    int dev = 0, n = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 148;
+}
+
+template <int DP>
+cudaError_t launch_kb_refine(const QueryPlan* qps, const int2* items, int nitems, uint32_t* claim, int ctas_per_sm,
+                             cudaStream_t s)
+{
+    const int smem = (int)sizeof(refine::RefineSmem<DP>);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(batched::kb_refine<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    int per_sm = ctas_per_sm;
+    if (per_sm <= 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched::kb_refine<DP>, refine::kTQ + 32, smem);
+        if (per_sm < 1) per_sm = 1;
+    }
+    int grid = sm_count() * per_sm;
+    if (grid > nitems) grid = nitems;
+    if (grid < 1) return cudaSuccess;
+    batched::kb_refine<DP><<<grid, refine::kTQ + 32, smem, s>>>(qps, items, nitems, claim);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_batched(const BatchLaunch& b, cudaStream_t s)
+{
+    using namespace batched;
+    cudaMemsetAsync(b.zero_base, 0, b.zero_bytes, s);
+    if (b.chunk_items > 0) {
+        const int grid = (int)std::min<int64_t>(b.chunk_items, (int64_t)sm_count() * 8);
+        kb_map<<<grid, kT, 0, s>>>(b.qps, b.nq, b.pchunk, b.chunk_items);
+        kb_prefix<<<b.nq, 512, (size_t)b.max_words * 4, s>>>(b.qps);
+        kb_survivors<<<(unsigned)b.chunk_items, kT, 0, s>>>(b.qps, b.nq, b.pchunk, b.claims + 0);
+        for (int ps = 0; ps < b.max_passes; ++ps) {
+            kb_radix_hist<<<(unsigned)b.chunk_items, kT, 0, s>>>(b.qps, b.nq, b.pchunk, ps);
+            kb_radix_scan<<<b.nq, 256, 0, s>>>(b.qps, ps);
+            kb_radix_scatter<<<(unsigned)b.chunk_items, kT, 0, s>>>(b.qps, b.nq, b.pchunk, ps);
+        }
+    }
+    if (b.tile_items > 0) kb_gather<<<(unsigned)b.tile_items, kTQ, 0, s>>>(b.qps, b.nq, b.ptile);
+    for (int c = 0; c < 4; ++c) {
+        const int n = b.class_items[c];
+        if (!n) continue;
+        const int2* it = b.items + b.class_begin[c];
+        uint32_t* claim = b.claims + 2 + c;
+        cudaError_t e = cudaSuccess;
+        switch (c) {
+            case 0: e = launch_kb_refine<4>(b.qps, it, n, claim, b.refine_ctas_per_sm, s); break;
+            case 1: e = launch_kb_refine<8>(b.qps, it, n, claim, b.refine_ctas_per_sm, s); break;
+            case 2: e = launch_kb_refine<12>(b.qps, it, n, claim, b.refine_ctas_per_sm, s); break;
+            default: e = launch_kb_refine<16>(b.qps, it, n, claim, b.refine_ctas_per_sm, s); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    if (b.chunk_items > 0) kb_emit<<<(unsigned)b.chunk_items, kT, 0, s>>>(b.qps, b.nq, b.pchunk, b.claims + 1);
+    kb_finish<<<1, 1024, 0, s>>>(b.qps, b.nq, b.capacity, b.offsets, b.status);
+    if (b.chunk_items > 0) {
+        const int grid = (int)std::min<int64_t>(b.chunk_items, (int64_t)sm_count() * 8);
+        kb_copy<<<grid, kT, 0, s>>>(b.qps, b.nq, b.pchunk, b.chunk_items, b.offsets, b.out, b.capacity);
+    }
+    return cudaGetLastError();
+}
+
+int batched_kernel_count(const BatchLaunch& b)
+{
+    int k = 0;
+    if (b.chunk_items > 0) k += 3 + 3 * b.max_passes + 2;  // map, prefix, survivors, sort, emit, copy
+    if (b.tile_items > 0) k += 1;
+    for (int c = 0; c < 4; ++c) k += b.class_items[c] ? 1 : 0;
+    return k + 1;                                           // finish
+}
+
+}  // namespace sky

@@ -361,86 +361,13 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
 }
 
 // ---------------------------------------------------------------------------
-// Inclusive prefix-OR along dimension k of the 2^(log2g*d)-bit grid.
-// Bit stride of dimension k: 2^(log2g*k).
+// One dimension of the prefix-OR over the whole grid (global memory).
 __global__ void __launch_bounds__(kThreads) k_prefix_or_dim(uint32_t* R, int64_t words, int log2g, int k)
 {
-    const int slog = log2g * k;
-    const uint32_t G = 1u << log2g;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-    if (slog >= 5) {
-        // whole words: word stride sw, G words per line
-        const int64_t sw = 1ll << (slog - 5);
-        const int64_t ncol = words / G;
-        for (int64_t c = tid; c < ncol; c += nthr) {
-            const int64_t lo = c % sw, hi = c / sw;
-            uint32_t* p = R + hi * (int64_t)G * sw + lo;
-            uint32_t acc = *p;
-            for (uint32_t j = 1; j < G; ++j) {
-                p += sw;
-                acc |= *p;
-                *p = acc;
-            }
-        }
-    } else if (slog + log2g <= 5) {
-        // every line inside one word: log2(G) doubling steps with masks that
-        // keep each shifted bit inside its own line
-        uint32_t mask[6];
-        int nsteps = 0;
-        for (uint32_t j = 1; j < G; j <<= 1) {
-            uint32_t m = 0;
-            for (int b = 0; b < 32; ++b)
-                if (((uint32_t)(b >> slog) & (G - 1u)) >= j) m |= 1u << b;
-            mask[nsteps++] = m;
-        }
-        for (int64_t w = tid; w < words; w += nthr) {
-            uint32_t x = R[w];
-            int st = 0;
-            for (uint32_t j = 1; j < G; j <<= 1, ++st) x |= (x << (j << slog)) & mask[st];
-            R[w] = x;
-        }
-    } else {
-        // a line spans Lw consecutive words holding e = 32 >> slog of its
-        // elements each (2^slog interleaved lines): scan inside each word, then
-        // carry the last element group from word to word
-        const int64_t Lw = 1ll << (slog + log2g - 5);
-        const int e = 32 >> slog;
-        const int sbits = 1 << slog;
-        uint32_t rep = 0;
-        for (int t = 0; t < e; ++t) rep |= 1u << (t << slog);
-        const int64_t ngroups = words / Lw;
-        for (int64_t g = tid; g < ngroups; g += nthr) {
-            uint32_t* p = R + g * Lw;
-            uint32_t carry = 0;
-            for (int64_t t = 0; t < Lw; ++t) {
-                uint32_t x = p[t];
-                for (int j = 1; j < e; j <<= 1) x |= x << (j << slog);
-                x |= carry;
-                p[t] = x;
-                const uint32_t top = x >> (32 - sbits);
-                carry = top * rep;
-            }
-        }
-    }
+    prefix_or_dim(R, words, log2g, k, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                  (int64_t)gridDim.x * blockDim.x);
 }
 
-__device__ __forceinline__ uint32_t ones_key(int log2g, int d)
-{
-    uint32_t o = 0;
-    for (int k = 0; k < d; ++k) o |= 1u << (log2g * k);
-    return o;
-}
-
-__device__ __forceinline__ bool all_columns_positive(uint32_t key, int log2g, int d)
-{
-    const uint32_t m = (1u << log2g) - 1u;
-    bool ok = true;
-    for (int k = 0; k < d; ++k) ok &= ((key >> (log2g * k)) & m) != 0u;
-    return ok;
-}
-
-// dominated[c] = prefix[c - (1,..,1)] when every column of c is >= 1 (Def. 3).
 __global__ void __launch_bounds__(kThreads) k_dominated(const uint32_t* R, uint32_t* dom, int64_t words,
                                                         int log2g, int d)
 {
@@ -539,31 +466,6 @@ __global__ void k_snap_finalize(const float* __restrict__ pts, int d, int64_t ld
 }
 
 // ---------------------------------------------------------------------------
-// Block-wide exclusive scan of one value per thread (kThreads threads).
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t& total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = (lane < kThreads / 32) ? s_warp[lane] : 0u;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < kThreads / 32) s_warp[lane] = w;
-    }
-    __syncthreads();
-    total = s_warp[kThreads / 32 - 1];
-    const uint32_t before = warp ? s_warp[warp - 1] : 0u;
-    return before + x - v;
-}
-
 // Survivors of step (c), compacted in row order, with their Morton keys
 // (computed by the map pass). Reads only the 8-byte (cell key, Morton key)
 // pairs; a row itself is read only when proposals are in use.

@@ -12,35 +12,19 @@
 
 #include "sky_common.cuh"
 #include "sky_internal.h"
+#include "sky_sort.cuh"
 
 namespace sky {
 
 namespace {
 
-constexpr int kT = kSortThreads;
-constexpr int kI = kSortItems;
-constexpr int kTile = kSortTile;
-constexpr int kWarps = kT / 32;
+using namespace radix;
 
 __global__ void __launch_bounds__(kT) k_radix_hist(const uint32_t* __restrict__ keys, const DevResult* res,
                                                    int shift, uint32_t* hist, int64_t nblk_max,
                                                    uint32_t* digit_total)
 {
-    __shared__ uint32_t s_h[256];
-    const uint32_t m = res->survivors;
-    const int64_t base = (int64_t)blockIdx.x * kTile;
-    if (base >= m) return;
-    s_h[threadIdx.x] = 0;
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kI; ++r) {
-        const int64_t i = base + r * kT + threadIdx.x;
-        if (i < m) atomicAdd(&s_h[(keys[i] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    const uint32_t c = s_h[threadIdx.x];
-    hist[(int64_t)threadIdx.x * nblk_max + blockIdx.x] = c;
-    if (c) atomicAdd(&digit_total[threadIdx.x], c);
+    radix_hist_block(keys, res->survivors, shift, hist, nblk_max, digit_total, blockIdx.x);
 }
 
 // One CTA per digit: exclusive scan of that digit's row of block counts,
@@ -88,83 +72,7 @@ __global__ void __launch_bounds__(kT) k_radix_scatter(const uint32_t* __restrict
                                                       uint32_t* vout, const DevResult* res, int shift,
                                                       const uint32_t* __restrict__ hist, int64_t nblk_max)
 {
-    __shared__ uint32_t s_wcnt[kWarps][256];
-    __shared__ uint32_t s_run[256];
-    __shared__ uint32_t s_start[256];
-    __shared__ uint32_t s_key[kTile];
-    __shared__ uint32_t s_val[kTile];
-    __shared__ uint32_t s_warp[kWarps];
-    const uint32_t m = res->survivors;
-    const int64_t base = (int64_t)blockIdx.x * kTile;
-    if (base >= m) return;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int w = 0; w < kWarps; ++w) s_wcnt[w][tid] = 0;
-    s_run[tid] = 0;
-    __syncthreads();
-
-    uint32_t key[kI], val[kI], rank[kI];
-#pragma unroll
-    for (int r = 0; r < kI; ++r) {
-        const int64_t i = base + r * kT + tid;
-        const bool valid = i < m;
-        key[r] = valid ? kin[i] : 0u;
-        val[r] = valid ? vin[i] : 0u;
-        const uint32_t digit = valid ? ((key[r] >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(kFull, digit);
-        const uint32_t below = __popc(peers & lanemask_lt());
-        const bool leader = (__ffs(peers) - 1) == lane;
-        if (valid && leader) s_wcnt[warp][digit] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            uint32_t pre = s_run[digit];
-            for (int w = 0; w < warp; ++w) pre += s_wcnt[w][digit];
-            rank[r] = pre + below;
-        }
-        __syncthreads();
-        {
-            uint32_t tot = 0;
-            for (int w = 0; w < kWarps; ++w) {
-                tot += s_wcnt[w][tid];
-                s_wcnt[w][tid] = 0;
-            }
-            s_run[tid] += tot;
-        }
-        __syncthreads();
-    }
-    // local digit starts (exclusive scan of the block's digit counts)
-    {
-        const uint32_t c = s_run[tid];
-        uint32_t x = c;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_warp[warp] = x;
-        __syncthreads();
-        uint32_t before = 0;
-        for (int w = 0; w < warp; ++w) before += s_warp[w];
-        s_start[tid] = before + x - c;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kI; ++r) {
-        const int64_t i = base + r * kT + tid;
-        if (i < m) {
-            const uint32_t digit = (key[r] >> shift) & 255u;
-            const uint32_t pos = s_start[digit] + rank[r];
-            s_key[pos] = key[r];
-            s_val[pos] = val[r];
-        }
-    }
-    __syncthreads();
-    const int64_t cnt = (m - base) < kTile ? (m - base) : kTile;
-    for (int j = tid; j < cnt; j += kT) {
-        const uint32_t k = s_key[j];
-        const uint32_t digit = (k >> shift) & 255u;
-        const uint32_t g = hist[(int64_t)digit * nblk_max + blockIdx.x] + (j - s_start[digit]);
-        kout[g] = k;
-        vout[g] = s_val[j];
-    }
+    radix_scatter_block(kin, vin, kout, vout, res->survivors, shift, hist, nblk_max, blockIdx.x);
 }
 
 }  // namespace

@@ -35,6 +35,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t* bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_fence_init()
 {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -191,5 +196,118 @@ __device__ __forceinline__ float ordered_to_float(uint32_t u)
 }
 
 __host__ __device__ constexpr inline int pad4(int d) { return (d + 3) & ~3; }
+
+// ---- cell keys -----------------------------------------------------------
+// Key of the cell one step down the diagonal is key - ones_key (valid when
+// every column of the key is >= 1).
+__device__ __forceinline__ uint32_t ones_key(int log2g, int d)
+{
+    uint32_t o = 0;
+    for (int k = 0; k < d; ++k) o |= 1u << (log2g * k);
+    return o;
+}
+
+__device__ __forceinline__ bool all_columns_positive(uint32_t key, int log2g, int d)
+{
+    const uint32_t m = (1u << log2g) - 1u;
+    bool ok = true;
+    for (int k = 0; k < d; ++k) ok &= ((key >> (log2g * k)) & m) != 0u;
+    return ok;
+}
+
+// Block-wide exclusive scan of one value per thread (NT threads, NT <= 1024).
+template <int NT = 256>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t& total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < NT / 32) ? s_warp[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NT / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    total = s_warp[NT / 32 - 1];
+    const uint32_t before = warp ? s_warp[warp - 1] : 0u;
+    return before + x - v;
+}
+
+// Inclusive prefix-OR along dimension k of the 2^(log2g*d)-bit grid stored in
+// `words` 32-bit words (bit stride of dimension k: 2^(log2g*k)). Threads
+// tid = 0 .. nthr-1 of the caller share the work; the caller orders
+// successive dimensions (grid launches or __syncthreads).
+__device__ __forceinline__ void prefix_or_dim(uint32_t* R, int64_t words, int log2g, int k, int64_t tid,
+                                              int64_t nthr)
+{
+    const int slog = log2g * k;
+    const uint32_t G = 1u << log2g;
+    if (slog >= 5) {
+        // whole words: word stride sw, G words per line
+        const int64_t sw = 1ll << (slog - 5);
+        const int64_t ncol = words / G;
+        for (int64_t c = tid; c < ncol; c += nthr) {
+            const int64_t lo = c % sw, hi = c / sw;
+            uint32_t* p = R + hi * (int64_t)G * sw + lo;
+            uint32_t acc = *p;
+            for (uint32_t j = 1; j < G; ++j) {
+                p += sw;
+                acc |= *p;
+                *p = acc;
+            }
+        }
+    } else if (slog + log2g <= 5) {
+        // every line inside one word: log2(G) doubling steps with masks that
+        // keep each shifted bit inside its own line
+        uint32_t mask[6];
+        int nsteps = 0;
+        for (uint32_t j = 1; j < G; j <<= 1) {
+            uint32_t m = 0;
+            for (int b = 0; b < 32; ++b)
+                if (((uint32_t)(b >> slog) & (G - 1u)) >= j) m |= 1u << b;
+            mask[nsteps++] = m;
+        }
+        for (int64_t w = tid; w < words; w += nthr) {
+            uint32_t x = R[w];
+            int st = 0;
+            for (uint32_t j = 1; j < G; j <<= 1, ++st) x |= (x << (j << slog)) & mask[st];
+            R[w] = x;
+        }
+    } else {
+        // a line spans Lw consecutive words holding e = 32 >> slog of its
+        // elements each (2^slog interleaved lines): scan inside each word, then
+        // carry the last element group from word to word
+        const int64_t Lw = 1ll << (slog + log2g - 5);
+        const int e = 32 >> slog;
+        const int sbits = 1 << slog;
+        uint32_t rep = 0;
+        for (int t = 0; t < e; ++t) rep |= 1u << (t << slog);
+        const int64_t ngroups = words / Lw;
+        for (int64_t g = tid; g < ngroups; g += nthr) {
+            uint32_t* p = R + g * Lw;
+            uint32_t carry = 0;
+            for (int64_t t = 0; t < Lw; ++t) {
+                uint32_t x = p[t];
+                for (int j = 1; j < e; j <<= 1) x |= x << (j << slog);
+                x |= carry;
+                p[t] = x;
+                const uint32_t top = x >> (32 - sbits);
+                carry = top * rep;
+            }
+        }
+    }
+}
+
+// dominated[c] = prefix[c - (1,..,1)] when every column of c is >= 1 (Def. 3).
+
+
 
 }  // namespace sky

@@ -72,6 +72,35 @@ struct Plan {
     const uint32_t* sorted_val = nullptr;
 };
 
+// One query of a batch (device copy; pointers resolved into the workspace).
+struct QueryPlan {
+    const float* base;        // table row row_begin
+    int64_t n;                // rows of the query
+    int64_t rs, cs;           // element (r, k) = base[r * rs + col[k] * cs]
+    int64_t row_begin;
+    int32_t d, dp, log2g, mbits, passes, dpclass;
+    int32_t col[16];
+    int64_t words, chunks, tiles;
+    uint2* keys;
+    uint32_t* occ;
+    uint32_t* pre;
+    unsigned long long* lb_a;
+    unsigned long long* lb_b;
+    uint32_t* surv_key;
+    uint32_t* surv_idx;
+    uint32_t* key2;
+    uint32_t* val2;
+    uint32_t* hist;
+    uint32_t* digit_total;    // [4][256]
+    float* X;
+    uint32_t* C;
+    int32_t* ids;
+    uint32_t* sub;
+    uint8_t* keep;
+    int32_t* stage;
+    DevResult* res;
+};
+
 constexpr int kRefineTile = 128;   // points per refinement tile
 constexpr int kScanItems = 8;      // items per thread in the look-back scans
 constexpr int kScanThreads = 256;
@@ -101,6 +130,31 @@ cudaError_t launch_sort(Plan& p, cudaStream_t s);
 cudaError_t launch_gather(const Plan& p, cudaStream_t s);
 cudaError_t launch_refine(const Plan& p, cudaStream_t s);
 cudaError_t launch_emit(const Plan& p, int32_t* out, int64_t capacity, cudaStream_t s);
+
+// One batched launch (k_batched.cu): device pointers into the workspace.
+struct BatchLaunch {
+    const QueryPlan* qps = nullptr;
+    int nq = 0;
+    const int64_t* pchunk = nullptr;   // [nq+1] exclusive prefix of 2048-row chunks
+    int64_t chunk_items = 0;
+    const int64_t* ptile = nullptr;    // [nq+1] exclusive prefix of 128-point tiles
+    int64_t tile_items = 0;
+    const int2* items = nullptr;       // refinement (query, p-tile) items, grouped by class
+    int class_begin[4] = {0, 0, 0, 0};
+    int class_items[4] = {0, 0, 0, 0};
+    uint32_t* claims = nullptr;        // [6] work counters (zeroed per launch)
+    void* zero_base = nullptr;         // region cleared at the start of every launch
+    size_t zero_bytes = 0;
+    int max_passes = 0;
+    int64_t max_words = 1;
+    int refine_ctas_per_sm = 0;
+    int32_t* out = nullptr;
+    int64_t capacity = 0;
+    int64_t* offsets = nullptr;
+    int32_t* status = nullptr;
+};
+cudaError_t launch_batched(const BatchLaunch& b, cudaStream_t s);
+int batched_kernel_count(const BatchLaunch& b);
 
 int auto_log2g(int64_t n, int d);
 int morton_bits_for(int64_t n, int d);

@@ -1,0 +1,100 @@
+"""Parity of the batched path (one CUDA-graph launch for many queries) with
+the CPU oracle, query by query. Every comparison is exact equality of the
+ascending global row-id arrays."""
+import numpy as np
+import pytest
+
+import oracle
+import skydata
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2107_09993_b300 as sky  # noqa: E402
+
+
+def _table(n_rows=60000, n_cols=12, seed=5):
+    return skydata.mixed_table(n_rows, n_cols, seed)
+
+
+def _check(T, queries, results, status=None):
+    for i, (b, c, mask) in enumerate(queries):
+        want = oracle.skyline_subset(T, int(b), int(c), int(mask))
+        got = results[i]
+        assert got.tolist() == want.tolist(), (i, b, c, bin(mask))
+        if status is not None:
+            assert status[i] == 0
+
+
+@pytest.mark.parametrize("layout", ["row", "col"])
+def test_batched_matches_oracle(layout):
+    T = _table()
+    q = skydata.batched_queries(300, T.shape[0], T.shape[1], seed=3, n_lo=1, n_hi=20000, d_lo=1, d_hi=12)
+    q[0] = (0, 0, 0b101)                 # empty query
+    q[1] = (17, 1, 0b1)                  # one row, one column
+    q[2] = (0, T.shape[0], 0xfff)        # the whole table, all 12 columns
+    q[3] = (T.shape[0] - 5, 5, 0b100000000001)
+    t = torch.from_numpy(T).cuda()
+    if layout == "col":
+        t = t.t().contiguous().t()       # column-major view
+    b = sky.Batch(t, q)
+    b.run()
+    res = b.results()
+    _check(T, q, res, b.query_status())
+    off = b.offsets.cpu().numpy()
+    assert off[0] == 0 and np.all(np.diff(off) >= 0)
+    # a second launch of the same graph gives the same answer
+    b.run()
+    res2 = b.results()
+    assert all(np.array_equal(x, y) for x, y in zip(res, res2))
+    st = b.stats()
+    assert st["n_queries"] == 300 and st["skyline"] == off[-1] and st["graph_launches_per_call"] == 1
+    b.close()
+
+
+def test_batched_explicit_grids_and_agreement_with_plain():
+    T = _table(40000, 12, seed=9)
+    rng = np.random.default_rng(1)
+    q = skydata.batched_queries(64, T.shape[0], T.shape[1], seed=11, n_lo=500, n_hi=30000, d_lo=2, d_hi=12)
+    lg = [int(rng.integers(0, 18 // bin(int(m)).count("1") + 1)) for _, _, m in q]
+    t = torch.from_numpy(T).cuda()
+    b = sky.Batch(t, q, log2g=lg, refine_ctas_per_sm=2)
+    b.run()
+    res = b.results()
+    for i, (r0, c, mask) in enumerate(q):
+        cols = [k for k in range(12) if (int(mask) >> k) & 1]
+        sub = t[int(r0):int(r0) + int(c)][:, cols].contiguous()
+        want = (sky.skyline(sub).cpu().numpy() + int(r0)).tolist()
+        assert res[i].tolist() == want, i
+    b.close()
+
+
+def test_batched_capacity_and_nonfinite():
+    T = _table(20000, 6, seed=2)
+    T[12345, 3] = np.nan
+    q = np.array([(0, 10000, 0b111), (10000, 5000, 0b0011), (12000, 1000, 0b1000), (0, 20000, 0b1)],
+                 dtype=np.int64)
+    t = torch.from_numpy(T).cuda()
+    full = [oracle.skyline_subset(T, *map(int, x)) if i != 2 else None for i, x in enumerate(q)]
+    cap = len(full[0])                                      # query 0 fits exactly, query 1 does not
+    b = sky.Batch(t, q, capacity=cap)
+    b.run()
+    st = b.query_status()
+    assert st[0] == 0 and st[1] == 3
+    assert st[2] == 2                                       # NaN inside rows 12000..12999, column 3
+    assert st[3] == 3
+    off = b.offsets.cpu().numpy()
+    assert off[1] == len(full[0]) and off[2] - off[1] == len(full[1])
+    assert b.results()[0].tolist() == full[0].tolist()
+    b.close()
+
+
+def test_batched_rejects_bad_queries():
+    T = torch.rand((1000, 4), device="cuda")
+    for bad in ([(0, 1001, 1)], [(-1, 5, 1)], [(0, 5, 0)], [(0, 5, 1 << 4)]):
+        with pytest.raises(sky.SkyError) as e:
+            sky.Batch(T, np.array(bad, dtype=np.int64))
+        assert e.value.name == "SKY_ERR_INVALID_ARGUMENT"
+    with pytest.raises(sky.SkyError) as e:
+        sky.Batch(T, np.array([(0, 10, 0b11)], dtype=np.int64), log2g=[10])
+    assert e.value.name == "SKY_ERR_TOO_LARGE"
