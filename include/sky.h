@@ -271,6 +271,58 @@ SKY_API sky_status sky_batch_stats(const sky_batch* batch, void* stream, sky_bat
 SKY_API void sky_batch_destroy(sky_batch* batch);        /* NULL accepted */
 SKY_API const char* sky_batch_last_error(void);          /* thread-local detail */
 
+/* ------------------------------------------------------------------------ */
+/* Learned proposal (a project addition; the paper has no counterpart). A    */
+/* 3-layer perceptron (636 -> 64 -> 64 -> 264, ReLU, bfloat16 weights, fp32  */
+/* accumulation) maps distribution features of a point set to a grid layer   */
+/* and 16 filter points. Parameters are one flat array of SKY_MLP_PARAMS     */
+/* values in the order W1[64][636], b1[64], W2[64][64], b2[64], W3[264][64], */
+/* b3[264]; outputs 0..7 score log2_g = 1..8, outputs 8 + 16 j + k give      */
+/* coordinate k (normalised to the sample's min/max) of filter point j.      */
+/* ------------------------------------------------------------------------ */
+#define SKY_MLP_FEATURES 636
+#define SKY_MLP_OUTPUTS 264
+#define SKY_MLP_PARAMS 62088
+
+/* Features of n x d points (device): d_feat[636] = 16 x 32 histograms of the
+ * min/max-normalised values, the 120 pairwise Pearson correlations (k < l),
+ * d/16, log2(n)/32, 0, 0 -- over a strided sample of at most 65,536 rows.
+ * d_range[32] receives the sample's min[16] and max[16]. Asynchronous. */
+SKY_API sky_status sky_features(const float* d_pts, int64_t n, int32_t d, int64_t ld, float* d_feat,
+                                float* d_range, void* stream);
+
+/* Floats of scratch the forward/backward calls need for a batch. */
+SKY_API size_t sky_mlp_work_floats(int32_t batch);
+
+/* Forward pass for `batch` feature rows: d_out[batch][264]. Asynchronous. */
+SKY_API sky_status sky_mlp_forward(const uint16_t* d_params_bf16, const float* d_feat, int32_t batch,
+                                   float* d_out, float* d_work, void* stream);
+
+/* Mean loss over the batch (cross-entropy of the layer label over the
+ * admissible layers log2_g * d <= 24, plus lam x masked mean squared error of
+ * the filter coordinates) into *d_loss, and its gradient with respect to
+ * every parameter into d_grad[SKY_MLP_PARAMS]. Asynchronous. */
+SKY_API sky_status sky_mlp_backward(const uint16_t* d_params_bf16, const float* d_feat, const int32_t* d_dims,
+                                    const int32_t* d_labels, const float* d_targets, const float* d_masks,
+                                    int32_t batch, float lam, float* d_grad, float* d_work, float* d_loss,
+                                    void* stream);
+
+/* One AdamW step (beta 0.9 / 0.999, eps 1e-8, decoupled decay wd) on the fp32
+ * master parameters; refreshes the bfloat16 copy. `step` counts from 1. */
+SKY_API sky_status sky_mlp_adamw(float* d_master, uint16_t* d_bf16, float* d_m, float* d_v, const float* d_grad,
+                                 int32_t step, float lr, float wd, void* stream);
+
+/* bfloat16 copy (round to nearest even) of `count` fp32 values. */
+SKY_API sky_status sky_mlp_round(const float* d_master, uint16_t* d_bf16, int64_t count, void* stream);
+
+/* Proposal for one point set: *h_log2g (host) and d_prop[16][d] (device)
+ * filter points in data units, each moved up by `inflate` x the sample range
+ * in every dimension. d_work: sky_propose_work_floats() floats. Synchronises. */
+SKY_API sky_status sky_propose(const float* d_pts, int64_t n, int32_t d, int64_t ld, const uint16_t* d_params_bf16,
+                               float inflate, float* d_prop, int32_t* h_log2g, float* d_work, void* stream);
+SKY_API size_t sky_propose_work_floats(void);
+SKY_API const char* sky_mlp_last_error(void);
+
 /* Work counters of the last sky_skyline / sky_skyline_host call made on the
  * calling thread (for measurement; not part of the result). */
 typedef struct sky_run_stats {

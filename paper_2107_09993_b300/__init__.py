@@ -383,3 +383,106 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------- learned proposal --
+MLP_FEATURES, MLP_OUTPUTS, MLP_PARAMS = 636, 264, 62088
+
+
+def _load_mlp():
+    lib = load()
+    if getattr(lib, "_mlp_bound", False):
+        return lib
+    sig = {
+        "sky_features": ([_vp, _i64, _i32, _i64, _vp, _vp, _vp], _i32),
+        "sky_mlp_work_floats": ([_i32], _sz),
+        "sky_mlp_forward": ([_vp, _vp, _i32, _vp, _vp, _vp], _i32),
+        "sky_mlp_backward": ([_vp, _vp, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, _vp, _vp, _vp, _vp], _i32),
+        "sky_mlp_adamw": ([_vp, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float, _vp], _i32),
+        "sky_mlp_round": ([_vp, _vp, _i64, _vp], _i32),
+        "sky_propose": ([_vp, _i64, _i32, _i64, _vp, ctypes.c_float, _vp, ctypes.POINTER(_i32), _vp, _vp], _i32),
+        "sky_propose_work_floats": ([], _sz),
+        "sky_mlp_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    lib._mlp_bound = True
+    return lib
+
+
+def _mcheck(status: int):
+    if status != SKY_OK:
+        raise SkyError(status, _load_mlp().sky_mlp_last_error().decode())
+
+
+def _p(t):
+    return _vp(t.data_ptr())
+
+
+def features(points, stream=None):
+    """sky_features: (features[636], range[32]) float32 CUDA tensors."""
+    torch = _torch()
+    lib = _load_mlp()
+    points, n, d, ld = _points(points)
+    feat = torch.empty(MLP_FEATURES, dtype=torch.float32, device=points.device)
+    rng = torch.empty(32, dtype=torch.float32, device=points.device)
+    _mcheck(lib.sky_features(_p(points), n, d, ld, _p(feat), _p(rng), _stream_ptr(stream)))
+    return feat, rng
+
+
+def mlp_forward(params_bf16, feat, stream=None):
+    """sky_mlp_forward: outputs [B, 264] for features [B, 636] (params: uint16/bf16 CUDA tensor)."""
+    torch = _torch()
+    lib = _load_mlp()
+    feat = feat.reshape(-1, MLP_FEATURES).contiguous()
+    B = feat.shape[0]
+    out = torch.empty((B, MLP_OUTPUTS), dtype=torch.float32, device=feat.device)
+    work = torch.empty(int(lib.sky_mlp_work_floats(B)), dtype=torch.float32, device=feat.device)
+    _mcheck(lib.sky_mlp_forward(_p(params_bf16), _p(feat), B, _p(out), _p(work), _stream_ptr(stream)))
+    return out
+
+
+def mlp_backward(params_bf16, feat, dims, labels, targets, masks, lam, stream=None):
+    """sky_mlp_backward: (mean loss tensor[1], gradient[62088])."""
+    torch = _torch()
+    lib = _load_mlp()
+    B = feat.shape[0]
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=feat.device)
+    loss = torch.zeros(1, dtype=torch.float32, device=feat.device)
+    work = torch.empty(int(lib.sky_mlp_work_floats(B)), dtype=torch.float32, device=feat.device)
+    _mcheck(lib.sky_mlp_backward(_p(params_bf16), _p(feat.contiguous()), _p(dims), _p(labels), _p(targets),
+                                 _p(masks), B, float(lam), _p(grad), _p(work), _p(loss), _stream_ptr(stream)))
+    return loss, grad
+
+
+def mlp_adamw(master, params_bf16, m, v, grad, step, lr, wd, stream=None):
+    _mcheck(_load_mlp().sky_mlp_adamw(_p(master), _p(params_bf16), _p(m), _p(v), _p(grad), int(step), float(lr),
+                                      float(wd), _stream_ptr(stream)))
+
+
+def mlp_round(master, params_bf16, stream=None):
+    _mcheck(_load_mlp().sky_mlp_round(_p(master), _p(params_bf16), master.numel(), _stream_ptr(stream)))
+
+
+def propose(points, params_bf16, inflate=0.02, stream=None):
+    """sky_propose: (log2_g, proposals[16, d] CUDA tensor)."""
+    torch = _torch()
+    lib = _load_mlp()
+    points, n, d, ld = _points(points)
+    prop = torch.empty((16, d), dtype=torch.float32, device=points.device)
+    work = torch.empty(int(lib.sky_propose_work_floats()), dtype=torch.float32, device=points.device)
+    lg = _i32(0)
+    _mcheck(lib.sky_propose(_p(points), n, d, ld, _p(params_bf16), float(inflate), _p(prop), ctypes.byref(lg),
+                            _p(work), _stream_ptr(stream)))
+    return int(lg.value), prop
+
+
+def skyline_learned(points, params_bf16, inflate=0.02, stream=None, out=None):
+    """The learned path: sky_propose, then sky_skyline with the proposed layer
+    and filter points. Same result as skyline(points), by construction."""
+    lg, prop = propose(points, params_bf16, inflate, stream)
+    d = points.shape[1] if points.dim() == 2 else 1
+    lg = max(1, min(lg, 27 // d, 16))
+    return skyline(points, log2_g=lg, filter_points=prop, stream=stream, out=out)

@@ -115,3 +115,22 @@ def batched_queries(n_queries: int, n_rows: int, n_cols: int, seed: int,
         start = int(rng.integers(0, n_rows - cnt + 1))
         q[i] = (start, cnt, mask)
     return q
+
+
+def copula_torch(n: int, d: int, seed: int, rho: float, device="cuda"):
+    """Gaussian copula sample drawn on the GPU with torch (seeded), for the
+    learned proposal's training sets: same recipe as `copula`, float32 in
+    [0, 1). Returns (points tensor [n, d], effective rho)."""
+    import torch
+
+    rho_eff = float(rho)
+    if d > 1:
+        rho_eff = max(rho_eff, -0.95 / (d - 1))
+    cov = torch.full((d, d), rho_eff, dtype=torch.float64)
+    cov.fill_diagonal_(1.0)
+    chol = torch.linalg.cholesky(cov).to(device=device, dtype=torch.float32)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    z = torch.randn((n, d), generator=g, device=device, dtype=torch.float32) @ chol.T
+    u = 0.5 * torch.erfc(-z / math.sqrt(2.0))
+    return torch.clamp(u, max=float(np.nextafter(np.float32(1.0), np.float32(0.0)))).contiguous(), rho_eff

@@ -13,7 +13,7 @@ def _rand_problem(rng, B=3):
     theta = rng.normal(0, 0.3, mlp.n_params())
     F = rng.random((B, mlp.F_IN))
     d = rng.integers(2, 17, size=B)
-    labels = np.array([int(rng.integers(0, 24 // di)) for di in d])
+    labels = np.array([int(rng.integers(0, min(8, 24 // di))) for di in d])
     targets = rng.random((B, mlp.N_FILT * mlp.DMAX))
     masks = np.zeros_like(targets)
     for i, di in enumerate(d):
