@@ -74,9 +74,11 @@ typedef struct sky_options {
      *    floor(x * 2^log2_g), values outside [0,1) clamped to the first or
      *    last column.
      * 2: per-dimension min/max normalisation first (one extra read pass).
-     * 0 (default): automatic -- the map pass uses Eq. 1 and tracks min/max;
-     *    if some dimension leaves [0,1] or spans less than half of it, a
-     *    second map pass with min/max scales replaces the first. */
+     * 0 (default): automatic, decided on the strided sample of rows 0, t,
+     *    2t, ... with t = ceil(n / 4096): Eq. 1 when every sampled dimension
+     *    lies in [0,1] and spans at least half of it, otherwise min/max
+     *    scales from the sample (rows outside its range fall into the edge
+     *    columns). One map pass. */
     int32_t assume_unit;
     /* Optional pre-filter proposals: n_filter points of d floats (device,
      * row-major). Any coordinates are accepted. Each proposal f is replaced by
@@ -86,8 +88,11 @@ typedef struct sky_options {
      * never changes the result, only the work. NULL / 0 = no filter. */
     const float* d_filter_pts;
     int32_t n_filter;             /* 0..16 */
-    /* Refinement tile configuration (0 = default). See sky_tile_configs(). */
-    int32_t tile_cfg;
+    /* 1: stop after step (c) [Corollary 4]; the result is then the ascending
+     * row ids of the points whose cell is not dominated (and that no snapped
+     * proposal dominates) -- a superset of the skyline, the candidates of
+     * step (d). 0 (default): the skyline. */
+    int32_t survivors_only;
 } sky_options;
 
 /* Opaque grid handle: steps (a)-(c) for one point set. Owns its workspace. */
@@ -108,8 +113,7 @@ typedef struct sky_grid_stats_t {
 /* Device views into a grid handle, for inspection and tests. Valid until
  * sky_grid_destroy. All arrays live on the device. */
 typedef struct sky_grid_view {
-    const uint32_t* cell_key;     /* [2n] pairs (cell key, sort key); the cell key of point i,
-                                     sum_k c[k] << (log2_g*k), is cell_key[2*i]               */
+    const uint32_t* cell_key;     /* [n] cell key of point i: sum_k c[k] << (log2_g*k)      */
     const uint32_t* occupied;     /* [words] bit c set when cell c holds a point            */
     const uint32_t* dominated;    /* [words] bit c set when cell c is dominated (Def. 3)    */
     const int32_t* survivors;     /* [surviving_points] row ids after step (c), ascending    */
@@ -286,10 +290,13 @@ SKY_API const char* sky_batch_last_error(void);          /* thread-local detail 
 
 /* Features of n x d points (device): d_feat[636] = 16 x 32 histograms of the
  * min/max-normalised values, the 120 pairwise Pearson correlations (k < l),
- * d/16, log2(n)/32, 0, 0 -- over a strided sample of at most 65,536 rows.
- * d_range[32] receives the sample's min[16] and max[16]. Asynchronous. */
+ * d/16, log2(s)/32, 0, 0 -- over the strided sample of s <= 65,536 rows
+ * (every ceil(n / 65,536)-th row). d_range[32] receives the sample's min[16]
+ * and max[16]. d_work: sky_features_work_floats() floats, 8-byte aligned,
+ * owned by the caller and not read before it is written. Asynchronous. */
 SKY_API sky_status sky_features(const float* d_pts, int64_t n, int32_t d, int64_t ld, float* d_feat,
-                                float* d_range, void* stream);
+                                float* d_range, float* d_work, void* stream);
+SKY_API size_t sky_features_work_floats(void);
 
 /* Floats of scratch the forward/backward calls need for a batch. */
 SKY_API size_t sky_mlp_work_floats(int32_t batch);
@@ -317,9 +324,13 @@ SKY_API sky_status sky_mlp_round(const float* d_master, uint16_t* d_bf16, int64_
 
 /* Proposal for one point set: *h_log2g (host) and d_prop[16][d] (device)
  * filter points in data units, each moved up by `inflate` x the sample range
- * in every dimension. d_work: sky_propose_work_floats() floats. Synchronises. */
+ * in every dimension. n_ref > 0 is the set size the weights were trained at:
+ * the network's layer is then moved by the automatic policy's change from
+ * n_ref to n rows (clamped to 1 .. max(1, 24 / d)); n_ref = 0 keeps it.
+ * d_work: sky_propose_work_floats() floats, 8-byte aligned. Synchronises. */
 SKY_API sky_status sky_propose(const float* d_pts, int64_t n, int32_t d, int64_t ld, const uint16_t* d_params_bf16,
-                               float inflate, float* d_prop, int32_t* h_log2g, float* d_work, void* stream);
+                               float inflate, int64_t n_ref, float* d_prop, int32_t* h_log2g, float* d_work,
+                               void* stream);
 SKY_API size_t sky_propose_work_floats(void);
 SKY_API const char* sky_mlp_last_error(void);
 
@@ -336,6 +347,8 @@ typedef struct sky_run_stats {
     int32_t kernels;              /* kernels of this library the call launched  */
     int64_t tiles;                /* survivor tiles streamed by step (d)        */
     int64_t group_scans;          /* (warp, point-group) scans in step (d)      */
+    int64_t code_hits;            /* pairs whose 7-bit codes allow q <= p       */
+    int64_t exact_tests;          /* pairs that needed the float test           */
 } sky_run_stats;
 
 SKY_API sky_status sky_last_run_stats(sky_run_stats* out);

@@ -140,8 +140,10 @@ def _mode(assume_unit, mode):
 
 def cell_params(P, log2g: int, assume_unit: bool = False, mode: str | None = None):
     """Offsets and scales of the value->column map (float32 arrays of length d).
-    mode: "unit" (Eq. 1 as printed), "minmax" (per-dimension normalisation) or
-    "auto" (Eq. 1 when every dimension lies in [0,1] and spans >= 0.5)."""
+    mode: "unit" (Eq. 1 as printed), "minmax" (per-dimension normalisation
+    over all rows) or "auto" (decided on the rows 0, t, 2t, ... with
+    t = ceil(n / 4096): Eq. 1 when every sampled dimension lies in [0,1] and
+    spans >= 0.5, else normalisation by the sample's min / max)."""
     P, n, d = _pts(P)
     off = np.empty(d, dtype=np.float32)
     sc = np.empty(d, dtype=np.float32)
@@ -179,6 +181,22 @@ def occupancy(keys, d: int, log2g: int) -> np.ndarray:
     occ = np.zeros(1 << (log2g * d), dtype=np.uint8)
     occ[np.asarray(keys, dtype=np.int64)] = 1
     return occ
+
+
+def dominated_cells(occ, d: int, log2g: int) -> np.ndarray:
+    """Definition 3 through the box identity: cell c is dominated iff some
+    occupied cell c' has c'[k] < c[k] in every dimension, i.e. iff the closed
+    box [0, c - (1, ..., 1)] holds an occupied cell. The box indicator is the
+    cumulative OR of the occupancy along every axis (numpy). uint8 array."""
+    G = 1 << log2g
+    occ = np.asarray(occ, dtype=bool)
+    assert occ.size == G ** d
+    box = occ.reshape((G,) * d)              # axis 0 is dimension d-1 (most significant)
+    for ax in range(d):
+        box = np.logical_or.accumulate(box, axis=ax)
+    dom = np.zeros((G,) * d, dtype=np.uint8)
+    dom[(slice(1, None),) * d] = box[(slice(0, -1),) * d]
+    return dom.reshape(-1)
 
 
 def cell_classes(occ, d: int, log2g: int):

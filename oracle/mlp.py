@@ -5,7 +5,7 @@ the CUDA kernels compute, written from the definitions:
 
 * features(P): per-dimension 32-bin histograms of the min/max-normalised
   values and the Pearson correlation of every pair of dimensions, over a
-  strided row sample, plus (d/16, log2(n)/32). Normalised value and bin are
+  strided row sample of s rows, plus (d/16, log2(s)/32). Normalised value and bin are
   binary32 expressions, so the bins are exact; correlations are float64.
 * forward / backward: a 3-layer perceptron 636 -> 64 -> 64 -> 264 with ReLU,
   weights rounded to bfloat16 (round to nearest even), float64 arithmetic.
@@ -87,7 +87,7 @@ def features(P) -> np.ndarray:
             if var[k] > 0 and var[l] > 0:
                 corr[k, l] = C[k, l] / np.sqrt(var[k] * var[l])
     tri = [corr[k, l] for k in range(DMAX) for l in range(k + 1, DMAX)]
-    extra = [d / 16.0, np.log2(max(n, 1)) / 32.0, 0.0, 0.0]
+    extra = [d / 16.0, np.log2(s) / 32.0, 0.0, 0.0]
     return np.concatenate([hist.ravel(), np.array(tri), np.array(extra)])
 
 

@@ -33,8 +33,9 @@
  *     min_k = 0 and s_k = G. Range 0 gives s_k = 0 (every point in column 0);
  *     an infinite range gives s_k = G / FLT_MAX. Every such map is monotone
  *     non-decreasing in x, which is all that cell pruning needs. The
- *     automatic choice keeps Eq. 1 when every dimension lies in [0,1] and
- *     spans at least half of it, and normalises otherwise.
+ *     automatic choice looks at a strided sample of at most 4096 rows: it
+ *     keeps Eq. 1 when every sampled dimension lies in [0,1] and spans at
+ *     least half of it, and normalises by the sample's range otherwise.
  *   - Non-finite inputs are outside the method (they break the order); callers
  *     of the oracle must not pass them.
  *   - Cell keys: key = sum_k column_k << (log2G * k), i.e. dimension d-1 is
@@ -208,12 +209,17 @@ ORC_API int64_t orc_skyline_sfs(const float* P, int64_t n, int d, int64_t ld,
 /* ---------------------------------------------------------------------- */
 /* Value -> column map (Eq. 1 and its min/max reading, see header).       */
 /* mode 1: unit cube, Eq. 1 as printed (offset 0, scale G).               */
-/* mode 2: min/max normalisation of every dimension.                      */
-/* mode 0: automatic -- Eq. 1 when every dimension's values lie in [0,1]  */
-/*         and span at least half of it (max - min >= 0.5 in binary32),   */
-/*         min/max normalisation of every dimension otherwise.            */
+/* mode 2: min/max normalisation of every dimension over all n rows.      */
+/* mode 0: automatic, from the strided sample S of rows 0, t, 2t, ... < n */
+/*         with t = ceil(n / 4096) (at most 4096 rows): Eq. 1 when every  */
+/*         dimension of S lies in [0,1] and spans at least half of it     */
+/*         (max - min >= 0.5 in binary32), otherwise normalisation by S's */
+/*         per-dimension min / max. Rows outside S's range land in the   */
+/*         first / last column; the map is still monotone.                */
 /* `offset` and `scale` receive d floats each.                            */
 /* ---------------------------------------------------------------------- */
+#define ORC_DECIDE_SAMPLE 4096
+
 ORC_API void orc_cell_params(const float* P, int64_t n, int d, int64_t ld,
                              int log2g, int mode, float* offset, float* scale)
 {
@@ -221,10 +227,14 @@ ORC_API void orc_cell_params(const float* P, int64_t n, int d, int64_t ld,
     float mn[64], mx[64];
     int unit = (mode == 1) || n <= 0;
     if (!unit) {
+        /* rows visited: all of them (mode 2) or the sample (mode 0) */
+        int64_t step = 1;
+        if (mode == 0) step = (n + ORC_DECIDE_SAMPLE - 1) / ORC_DECIDE_SAMPLE;
+        if (step < 1) step = 1;
         for (int k = 0; k < d; ++k) {
             mn[k] = P[k];
             mx[k] = P[k];
-            for (int64_t i = 1; i < n; ++i) {
+            for (int64_t i = step; i < n; i += step) {
                 float v = P[i * ld + k];
                 if (v < mn[k]) mn[k] = v;
                 if (v > mx[k]) mx[k] = v;

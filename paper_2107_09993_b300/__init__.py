@@ -40,7 +40,7 @@ class SkyError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("log2_g", _i32), ("assume_unit", _i32), ("d_filter_pts", _vp),
-                ("n_filter", _i32), ("tile_cfg", _i32)]
+                ("n_filter", _i32), ("survivors_only", _i32)]
 
 
 class GridStats(ctypes.Structure):
@@ -52,7 +52,7 @@ class GridStats(ctypes.Structure):
 class RunStats(ctypes.Structure):
     _fields_ = [("n", _i64), ("d", _i32), ("log2_g", _i32), ("survivors", _i64), ("skyline", _i64),
                 ("pairs", _i64), ("n_filter_used", _i32), ("kernels", _i32), ("tiles", _i64),
-                ("group_scans", _i64)]
+                ("group_scans", _i64), ("code_hits", _i64), ("exact_tests", _i64)]
 
 
 class PhaseTimes(ctypes.Structure):
@@ -111,12 +111,12 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _opts(log2_g, assume_unit, filter_points, tile_cfg):
+def _opts(log2_g, assume_unit, filter_points, survivors_only=False):
     o = Options()
     o.log2_g = -1 if log2_g is None else int(log2_g)
     # True -> 1 (Eq. 1 on the unit cube); False/0 -> automatic; 2 -> min/max normalisation
     o.assume_unit = int(assume_unit) if not isinstance(assume_unit, bool) else (1 if assume_unit else 0)
-    o.tile_cfg = int(tile_cfg)
+    o.survivors_only = 1 if survivors_only else 0
     if filter_points is not None and filter_points.numel() > 0:
         assert filter_points.is_cuda and filter_points.dtype == _torch().float32
         assert filter_points.is_contiguous()
@@ -141,8 +141,9 @@ def _points(points, dev=True):
 
 
 def skyline(points, log2_g=None, assume_unit=False, filter_points=None, capacity=None,
-            tile_cfg=0, stream=None, out=None):
-    """Steps (a)-(d) on device-resident points: ascending int32 row ids (cuda)."""
+            survivors_only=False, stream=None, out=None):
+    """Steps (a)-(d) on device-resident points: ascending int32 row ids (cuda).
+    survivors_only=True stops after step (c) and returns the candidates."""
     torch = _torch()
     lib = load()
     points, n, d, ld = _points(points)
@@ -150,7 +151,7 @@ def skyline(points, log2_g=None, assume_unit=False, filter_points=None, capacity
     if out is None:
         out = torch.empty(max(cap, 1), dtype=torch.int32, device=points.device)
     cnt = _i64(0)
-    o = _opts(log2_g, assume_unit, filter_points, tile_cfg)
+    o = _opts(log2_g, assume_unit, filter_points, survivors_only)
     with torch.cuda.device(points.device):
         st = lib.sky_skyline(_vp(points.data_ptr()), n, d, ld, ctypes.byref(o), _vp(out.data_ptr()), cap,
                              ctypes.byref(cnt), _stream_ptr(stream))
@@ -160,7 +161,7 @@ def skyline(points, log2_g=None, assume_unit=False, filter_points=None, capacity
     return out[:cnt.value]
 
 
-def skyline_host(points, log2_g=None, assume_unit=False, capacity=None, tile_cfg=0, stream=None, out=None):
+def skyline_host(points, log2_g=None, assume_unit=False, capacity=None, stream=None, out=None):
     """Same result from host (ideally pinned) memory: copies in, computes, copies out.
     `points` is a CPU float32 torch tensor; returns a CPU int32 tensor."""
     torch = _torch()
@@ -170,7 +171,7 @@ def skyline_host(points, log2_g=None, assume_unit=False, capacity=None, tile_cfg
     if out is None:
         out = torch.empty(max(cap, 1), dtype=torch.int32, pin_memory=points.is_pinned())
     cnt = _i64(0)
-    o = _opts(log2_g, assume_unit, None, tile_cfg)
+    o = _opts(log2_g, assume_unit, None)
     st = lib.sky_skyline_host(_vp(points.data_ptr()), n, d, ld, ctypes.byref(o), _vp(out.data_ptr()), cap,
                               ctypes.byref(cnt), _stream_ptr(stream))
     _check(st)
@@ -394,13 +395,15 @@ def _load_mlp():
     if getattr(lib, "_mlp_bound", False):
         return lib
     sig = {
-        "sky_features": ([_vp, _i64, _i32, _i64, _vp, _vp, _vp], _i32),
+        "sky_features": ([_vp, _i64, _i32, _i64, _vp, _vp, _vp, _vp], _i32),
+        "sky_features_work_floats": ([], _sz),
         "sky_mlp_work_floats": ([_i32], _sz),
         "sky_mlp_forward": ([_vp, _vp, _i32, _vp, _vp, _vp], _i32),
         "sky_mlp_backward": ([_vp, _vp, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, _vp, _vp, _vp, _vp], _i32),
         "sky_mlp_adamw": ([_vp, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float, _vp], _i32),
         "sky_mlp_round": ([_vp, _vp, _i64, _vp], _i32),
-        "sky_propose": ([_vp, _i64, _i32, _i64, _vp, ctypes.c_float, _vp, ctypes.POINTER(_i32), _vp, _vp], _i32),
+        "sky_propose": ([_vp, _i64, _i32, _i64, _vp, ctypes.c_float, _i64, _vp, ctypes.POINTER(_i32), _vp, _vp],
+                        _i32),
         "sky_propose_work_floats": ([], _sz),
         "sky_mlp_last_error": ([], ctypes.c_char_p),
     }
@@ -428,7 +431,8 @@ def features(points, stream=None):
     points, n, d, ld = _points(points)
     feat = torch.empty(MLP_FEATURES, dtype=torch.float32, device=points.device)
     rng = torch.empty(32, dtype=torch.float32, device=points.device)
-    _mcheck(lib.sky_features(_p(points), n, d, ld, _p(feat), _p(rng), _stream_ptr(stream)))
+    work = torch.empty(int(lib.sky_features_work_floats()), dtype=torch.float32, device=points.device)
+    _mcheck(lib.sky_features(_p(points), n, d, ld, _p(feat), _p(rng), _p(work), _stream_ptr(stream)))
     return feat, rng
 
 
@@ -466,23 +470,28 @@ def mlp_round(master, params_bf16, stream=None):
     _mcheck(_load_mlp().sky_mlp_round(_p(master), _p(params_bf16), master.numel(), _stream_ptr(stream)))
 
 
-def propose(points, params_bf16, inflate=0.02, stream=None):
-    """sky_propose: (log2_g, proposals[16, d] CUDA tensor)."""
+def propose(points, params_bf16, inflate=0.02, n_ref=0, stream=None):
+    """sky_propose: (log2_g, proposals[16, d] CUDA tensor). n_ref: the set
+    size the weights were trained at (0: use the network's layer as is)."""
     torch = _torch()
     lib = _load_mlp()
     points, n, d, ld = _points(points)
     prop = torch.empty((16, d), dtype=torch.float32, device=points.device)
     work = torch.empty(int(lib.sky_propose_work_floats()), dtype=torch.float32, device=points.device)
     lg = _i32(0)
-    _mcheck(lib.sky_propose(_p(points), n, d, ld, _p(params_bf16), float(inflate), _p(prop), ctypes.byref(lg),
-                            _p(work), _stream_ptr(stream)))
+    _mcheck(lib.sky_propose(_p(points), n, d, ld, _p(params_bf16), float(inflate), int(n_ref), _p(prop),
+                            ctypes.byref(lg), _p(work), _stream_ptr(stream)))
     return int(lg.value), prop
 
 
-def skyline_learned(points, params_bf16, inflate=0.02, stream=None, out=None):
+# Rows per training set of the shipped weights (learned_weights.npz).
+TRAIN_ROWS = 100_000
+
+
+def skyline_learned(points, params_bf16, inflate=0.02, n_ref=TRAIN_ROWS, stream=None, out=None):
     """The learned path: sky_propose, then sky_skyline with the proposed layer
     and filter points. Same result as skyline(points), by construction."""
-    lg, prop = propose(points, params_bf16, inflate, stream)
+    lg, prop = propose(points, params_bf16, inflate, n_ref=n_ref, stream=stream)
     d = points.shape[1] if points.dim() == 2 else 1
     lg = max(1, min(lg, 27 // d, 16))
     return skyline(points, log2_g=lg, filter_points=prop, stream=stream, out=out)

@@ -15,6 +15,7 @@
 //                   that no snapped proposal dominates), compacted in row
 //                   order by a decoupled look-back scan, with a Morton key
 //                   for the refinement's spatial sort
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
 
@@ -137,131 +138,206 @@ __global__ void k_params(const uint32_t* mm_min, const uint32_t* mm_max, int d, 
     if (k < kMaxDim) write_params(k, d, log2g, mbits, normalise != 0, mm_min, mm_max, params);
 }
 
-// Automatic map: keep the unit-cube map when every dimension's values lie in
-// [0, 1] and span at least half of it; otherwise switch to min/max scales and
-// ask for a second map pass (the first pass tracked min / max).
-__global__ void k_decide(const uint32_t* mm_min, const uint32_t* mm_max, int d, int log2g, int mbits,
-                         float* params, DevResult* res)
+// Automatic map, decided on the strided sample of rows 0, t, 2t, ... < n
+// with t = ceil(n / kDecideSample): the unit-cube map (Eq. 1 as printed) when
+// every sampled dimension lies in [0, 1] and spans at least half of it,
+// otherwise min / max scales from the sample's range. Rows outside that range
+// clamp into the edge columns, so the map stays monotone -- all that pruning
+// and the refinement's codes need. One CTA; the sample's min / max are exact,
+// so the decision does not depend on the reduction order.
+constexpr int kDecideSample = 4096;
+constexpr int kDecideThreads = 1024;
+
+template <int DP>
+__global__ void __launch_bounds__(kDecideThreads) k_sample_params(const float* __restrict__ pts, int64_t n, int d,
+                                                                  int64_t ld, int log2g, int mbits,
+                                                                  uint32_t* mm_min, uint32_t* mm_max,
+                                                                  float* params)
 {
+    __shared__ float s_mn[kDecideThreads / 32][DP], s_mx[kDecideThreads / 32][DP];
     __shared__ int s_bad;
-    const int k = threadIdx.x;
-    if (k == 0) s_bad = 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int64_t t = (n + kDecideSample - 1) / kDecideSample;
+    if (t < 1) t = 1;
+    const int64_t rows = (n + t - 1) / t;
+    constexpr int U = kDecideSample / kDecideThreads;
+    float mn[DP], mx[DP];
+#pragma unroll
+    for (int k = 0; k < DP; ++k) { mn[k] = INFINITY; mx[k] = -INFINITY; }
+    float x[U][DP];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t r = (int64_t)u * kDecideThreads + tid;
+#pragma unroll
+        for (int k = 0; k < DP; ++k) x[u][k] = (r < rows && k < d) ? __ldg(pts + r * t * ld + k) : NAN;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int k = 0; k < DP; ++k) { mn[k] = fminf(mn[k], x[u][k]); mx[k] = fmaxf(mx[k], x[u][k]); }
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[k] = fminf(mn[k], __shfl_xor_sync(kFull, mn[k], o));
+            mx[k] = fmaxf(mx[k], __shfl_xor_sync(kFull, mx[k], o));
+        }
+        if (lane == 0) { s_mn[warp][k] = mn[k]; s_mx[warp][k] = mx[k]; }
+    }
+    if (tid == 0) s_bad = 0;
     __syncthreads();
-    if (k < d) {
-        const float lo = ordered_to_float(mm_min[k]);
-        const float hi = ordered_to_float(mm_max[k]);
+    if (tid < d) {
+        float lo = INFINITY, hi = -INFINITY;
+        for (int w = 0; w < kDecideThreads / 32; ++w) { lo = fminf(lo, s_mn[w][tid]); hi = fmaxf(hi, s_mx[w][tid]); }
+        mm_min[tid] = float_to_ordered(lo);
+        mm_max[tid] = float_to_ordered(hi);
         const bool unit_ok = (lo >= 0.0f) && (hi <= 1.0f) && (__fsub_rn(hi, lo) >= 0.5f);
         if (!unit_ok) atomicOr(&s_bad, 1);
     }
     __syncthreads();
-    const bool redo = s_bad != 0;
-    if (redo && k < kMaxDim) write_params(k, d, log2g, mbits, true, mm_min, mm_max, params);
-    if (k == 0) res->redo = redo ? 1u : 0u;
+    if (tid < kMaxDim) write_params(tid, d, log2g, mbits, s_bad != 0, mm_min, mm_max, params);
 }
-
-__global__ void k_clear_if(uint32_t* words, int64_t n, const DevResult* res)
-{
-    if (!res->redo) return;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        words[i] = 0u;
-}
-
-// Per-thread min / max accumulation, reduced and published once per block.
-template <int DP>
-struct MinMaxAcc {
-    float mn[DP], mx[DP];
-    __device__ __forceinline__ void init()
-    {
-#pragma unroll
-        for (int k = 0; k < DP; ++k) { mn[k] = INFINITY; mx[k] = -INFINITY; }
-    }
-    __device__ __forceinline__ void add(const float (&x)[DP])
-    {
-#pragma unroll
-        for (int k = 0; k < DP; ++k) { mn[k] = fminf(mn[k], x[k]); mx[k] = fmaxf(mx[k], x[k]); }
-    }
-    __device__ __forceinline__ void publish(int d, uint32_t* mm_min, uint32_t* mm_max)
-    {
-#pragma unroll
-        for (int k = 0; k < DP; ++k) {
-            for (int o = 16; o > 0; o >>= 1) {
-                mn[k] = fminf(mn[k], __shfl_xor_sync(kFull, mn[k], o));
-                mx[k] = fmaxf(mx[k], __shfl_xor_sync(kFull, mx[k], o));
-            }
-        }
-        if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-            for (int k = 0; k < DP; ++k) {
-                if (k < d && mn[k] <= mx[k]) {
-                    atomicMin(&mm_min[k], float_to_ordered(mn[k]));
-                    atomicMax(&mm_max[k], float_to_ordered(mx[k]));
-                }
-            }
-        }
-    }
-};
 
 // ---------------------------------------------------------------------------
 // Steps (a)+(b). One point -> (cell key, Morton key) -> bit. The bitmap OR
 // is fire-and-forget; when a whole warp hits one word (hot cells of
 // correlated data) the bits are merged first and one lane issues it.
-template <int DP>
-__device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, int mbits, const float* s_off,
-                                        const float* s_sc, const float* s_ms, int64_t row,
-                                        uint2* __restrict__ keys, uint32_t* occ, bool& bad)
+//
+// Morton key: bit l of dimension k's column goes to bit l * d + k. When
+// d - 1 >= mbits, one multiply spreads all mbits bits of a column at once:
+// q * sum_j 2^(j (d-1)) places bit l at l + j (d-1) for every j < mbits;
+// those positions are distinct (base-(d-1) digits), so nothing carries, and
+// position l * d holds exactly bit l (the j = l term). A mask keeps those.
+struct MortonSpread {
+    uint32_t magic, mask;
+    __device__ __forceinline__ MortonSpread(int d, int mbits) : magic(0u), mask(0u)
+    {
+        if (d - 1 >= mbits) {
+            for (int j = 0; j < mbits; ++j) {
+                magic |= 1u << (j * (d - 1));
+                mask |= 1u << (j * d);
+            }
+        }
+    }
+    __device__ __forceinline__ bool fast() const { return mask != 0u; }
+};
+
+// Where the occupancy bits go. All three keep every bit; they differ in how
+// many global atomics hit one word.
+//   MarkGlobal  fire-and-forget atomicOr on the bitmap
+//   MarkPrivate a block-private copy of a small bitmap in shared memory
+//   MarkCache   a direct-mapped, tagged cache of bitmap words in shared memory
+//               (slot = word mod kCacheSlots): a word claims a free slot and
+//               later bits for it are ORed there; a word whose slot another
+//               word holds goes to the bitmap. The block writes the cached
+//               words out at its end. Clustered data (many rows on few words)
+//               then sends at most one atomic per hot word per block.
+constexpr int kCacheSlots = 1024;
+constexpr uint32_t kCacheEmpty = 0xffffffffu;
+
+struct MarkGlobal {
+    uint32_t* occ;
+    __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const { atomicOr(occ + word, bits); }
+};
+struct MarkPrivate {
+    uint32_t* s_occ;   // shared memory
+    __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const { atomicOr(s_occ + word, bits); }
+};
+struct MarkCache {
+    uint32_t* occ;
+    uint32_t* s_key;   // shared memory [kCacheSlots]
+    uint32_t* s_val;   // shared memory [kCacheSlots]
+    uint32_t* s_claimed;
+    bool on;           // block-uniform: false once the cache stopped paying off
+    __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const
+    {
+        if (on) {
+            const uint32_t slot = word & (kCacheSlots - 1);
+            uint32_t k = s_key[slot];
+            if (k == kCacheEmpty) {
+                k = atomicCAS(s_key + slot, kCacheEmpty, word);
+                if (k == kCacheEmpty) { atomicAdd(s_claimed, 1u); k = word; }
+            }
+            if (k == word) { atomicOr(s_val + slot, bits); return; }
+        }
+        atomicOr(occ + word, bits);
+    }
+};
+
+// The key is built as key * G + c (G a runtime power of two: an integer
+// multiply-add, off the integer ALU pipe that the clamps and masks use).
+// `converged`: every lane of the warp calls together (no activemask query).
+template <int DP, bool converged, class Marker>
+__device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, int mbits, const MortonSpread& ms,
+                                        const float* s_off, const float* s_sc, const float* s_ms, int64_t row,
+                                        uint32_t* __restrict__ ckey, uint32_t* __restrict__ mkey,
+                                        const Marker& marker, bool& bad)
 {
     const uint32_t G = 1u << log2g;
     const uint32_t M = 1u << mbits;
     uint32_t key = 0;
     uint32_t mq[DP];
+    float nanacc = 0.0f;   // x * 0 is NaN exactly when x is infinite or NaN
 #pragma unroll
     for (int k = DP - 1; k >= 0; --k) {
         mq[k] = 0;
         if (k < d) {
-            bad |= !isfinite(x[k]);
+            nanacc = fmaf(x[k], 0.0f, nanacc);
             const uint32_t c = column_of(x[k], s_off[k], s_sc[k], G);
-            key = (key << log2g) | c;
+            key = key * G + c;
             // the Morton map is only for locality: reuse the cell column when
             // it is at least as fine
             mq[k] = (mbits <= log2g) ? (c >> (log2g - mbits)) : column_of(x[k], s_off[k], s_ms[k], M);
         }
     }
+    bad |= nanacc != nanacc;
     uint32_t code = 0;
-    for (int l = mbits - 1; l >= 0; --l)
+    if (ms.fast()) {
 #pragma unroll
-        for (int k = DP - 1; k >= 0; --k)
-            if (k < d) code = (code << 1) | ((mq[k] >> l) & 1u);
-    keys[row] = make_uint2(key, code);
+        for (int k = 0; k < DP; ++k)
+            if (k < d) code += ((mq[k] * ms.magic) & ms.mask) << k;   // disjoint bits: + is |
+    } else {
+        for (int l = mbits - 1; l >= 0; --l)
+#pragma unroll
+            for (int k = DP - 1; k >= 0; --k)
+                if (k < d) code = (code << 1) | ((mq[k] >> l) & 1u);
+    }
+    ckey[row] = key;
+    mkey[row] = code;
     const uint32_t word = key >> 5;
     const uint32_t bit = 1u << (key & 31u);
-    const uint32_t am = __activemask();
-    const int leader = __ffs(am) - 1;
+    const uint32_t am = converged ? kFull : __activemask();
+    const int leader = converged ? 0 : __ffs(am) - 1;
     const uint32_t w0 = __shfl_sync(am, word, leader);
     if (__all_sync(am, word == w0)) {
         const uint32_t bits = __reduce_or_sync(am, bit);
-        if ((int)(threadIdx.x & 31) == leader) atomicOr(occ + word, bits);
+        if ((int)(threadIdx.x & 31) == leader) marker.mark(word, bits);
     } else {
-        atomicOr(occ + word, bit);
+        marker.mark(word, bit);
     }
 }
 
-template <int DP>
+// Small grids (at most kPrivWords words) are marked in a private copy of the
+// bitmap in shared memory -- many rows share few words there, and global
+// atomics on them would serialise -- which each block then writes to its row
+// of `stage`; k_occ_merge ORs the rows into the bitmap.
+template <int DP, bool SMALL>
 __global__ void __launch_bounds__(kThreads) k_map_mark_plain(const float* __restrict__ pts, int64_t n,
                                                              int d, int64_t ld, bool vec4, int log2g, int mbits,
-                                                             const float* params, uint2* keys,
-                                                             uint32_t* occ, uint32_t* err, const DevResult* gate,
-                                                             uint32_t* mm_min, uint32_t* mm_max)
+                                                             const float* params, uint32_t* ckey,
+                                                             uint32_t* mkey, uint32_t* occ, uint32_t* err,
+                                                             uint32_t* stage, int64_t words)
 {
-    if (gate && !gate->redo) return;
+    extern __shared__ __align__(16) uint32_t s_occ[];   // [words] when SMALL
     __shared__ float s_off[kMaxDim], s_sc[kMaxDim], s_ms[kMaxDim];
     if (threadIdx.x < kMaxDim) {
         s_off[threadIdx.x] = params[threadIdx.x];
         s_sc[threadIdx.x] = params[16 + threadIdx.x];
         s_ms[threadIdx.x] = params[48 + threadIdx.x];
     }
+    if (SMALL)
+        for (int64_t w = threadIdx.x; w < words; w += blockDim.x) s_occ[w] = 0u;
     __syncthreads();
-    MinMaxAcc<DP> acc;
-    acc.init();
+    const MortonSpread ms(d, mbits);
     bool bad = false;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n_round = ((n + 31) / 32) * 32;   // whole warps stay in the loop together
@@ -269,40 +345,63 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_plain(const float* __rest
         if (i < n) {
             float x[DP];
             load_row<DP>(pts + i * ld, d, vec4, x);
-            map_one<DP>(x, d, log2g, mbits, s_off, s_sc, s_ms, i, keys, occ, bad);
-            if (mm_min) acc.add(x);
+            if (SMALL)
+                map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkPrivate{s_occ}, bad);
+            else
+                map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkGlobal{occ}, bad);
         }
     }
-    if (mm_min) acc.publish(d, mm_min, mm_max);
     if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, SKY_DEV_ERR_NONFINITE);
+    if (SMALL) {
+        __syncthreads();
+        for (int64_t w = threadIdx.x; w < words; w += blockDim.x) stage[blockIdx.x * words + w] = s_occ[w];
+    }
 }
 
 // Bulk-copy streaming version: rows are contiguous (ld == d) and the base is
 // 16-byte aligned. Chunks of kThreads rows (kThreads*d*4 bytes, a multiple of
 // 16) go through kStages shared-memory buffers; one thread issues the copies.
+// A thread reads its row from shared memory as float4s when d is a multiple
+// of 4 (eight rows per quarter-warp phase: at most 4-way bank conflicts at
+// d = 16 instead of 16-way for scalar reads).
 constexpr int kMapStages = 4;
 
-template <int DP>
+template <int DP, bool SMALL>
 __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restrict__ pts, int64_t n,
                                                            int d, int log2g, int mbits, const float* params,
-                                                           uint2* keys, uint32_t* occ, uint32_t* err,
-                                                           const DevResult* gate, uint32_t* mm_min, uint32_t* mm_max)
+                                                           uint32_t* ckey, uint32_t* mkey, uint32_t* occ,
+                                                           uint32_t* err, uint32_t* stage, int64_t words)
 {
-    if (gate && !gate->redo) return;
-    extern __shared__ __align__(128) float s_buf[];  // [kMapStages][kThreads * d]
+    // [kMapStages][kThreads * d] row stages, then either the private bitmap
+    // [words] (SMALL) or the word cache: tags and values [kCacheSlots] each
+    extern __shared__ __align__(128) float s_buf[];
     __shared__ float s_off[kMaxDim], s_sc[kMaxDim], s_ms[kMaxDim];
     __shared__ __align__(8) uint64_t s_bar[kMapStages];
+    __shared__ uint32_t s_claimed, s_cache_on;
     const int tid = threadIdx.x;
+    uint32_t* s_tail = reinterpret_cast<uint32_t*>(s_buf + kMapStages * kThreads * d);
     if (tid < kMaxDim) {
         s_off[tid] = params[tid];
         s_sc[tid] = params[16 + tid];
         s_ms[tid] = params[48 + tid];
     }
+    if (SMALL) {
+        for (int64_t w = tid; w < words; w += kThreads) s_tail[w] = 0u;
+    } else {
+        for (int t = tid; t < kCacheSlots; t += kThreads) {
+            s_tail[t] = kCacheEmpty;
+            s_tail[kCacheSlots + t] = 0u;
+        }
+    }
     if (tid == 0) {
         for (int s = 0; s < kMapStages; ++s) mbar_init(&s_bar[s], 1);
         mbar_fence_init();
+        s_claimed = 0u;
+        s_cache_on = 1u;
     }
     __syncthreads();
+    const MortonSpread ms(d, mbits);
+    const bool v4 = (d == DP);      // DP is d rounded up to a multiple of 4
 
     const int64_t nfull = n / kThreads;
     const uint32_t chunk_bytes = (uint32_t)(kThreads * d * sizeof(float));
@@ -316,48 +415,98 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
     }
     bool bad = false;
     bool timed_out = false;
-    MinMaxAcc<DP> acc;
-    acc.init();
     for (int64_t i = 0; i < my_chunks; ++i) {
         const int s = (int)(i % kMapStages);
         const uint32_t parity = (uint32_t)((i / kMapStages) & 1);
         if (!mbar_wait(&s_bar[s], parity, err)) { timed_out = true; }
         if (__syncthreads_or(timed_out)) {
-            // Let every copy already issued land before the block exits.
+            // Let every copy already issued land before the block goes on.
             if (tid == 0) {
                 for (int64_t j = i; j < my_chunks && j < i + kMapStages; ++j)
                     mbar_wait(&s_bar[j % kMapStages], (uint32_t)((j / kMapStages) & 1), nullptr);
             }
+            timed_out = true;
             __syncthreads();
-            return;
+            break;
         }
         const int64_t c = blockIdx.x + i * gridDim.x;
         const float* r = s_buf + s * kThreads * d + tid * d;
         float x[DP];
+        if (v4) {
 #pragma unroll
-        for (int k = 0; k < DP; ++k) x[k] = (k < d) ? r[k] : 0.0f;
-        map_one<DP>(x, d, log2g, mbits, s_off, s_sc, s_ms, c * kThreads + tid, keys, occ, bad);
-        if (mm_min) acc.add(x);
+            for (int k = 0; k < DP; k += 4) {
+                const float4 q = *reinterpret_cast<const float4*>(r + k);
+                x[k] = q.x; x[k + 1] = q.y; x[k + 2] = q.z; x[k + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < DP; ++k) x[k] = (k < d) ? r[k] : 0.0f;
+        }
+        if (SMALL)
+            map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, c * kThreads + tid, ckey, mkey,
+                              MarkPrivate{s_tail}, bad);
+        else
+            map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, c * kThreads + tid, ckey, mkey,
+                              MarkCache{occ, s_tail, s_tail + kCacheSlots, &s_claimed, s_cache_on != 0u}, bad);
         __syncthreads();  // every thread is done with stage s
-        if (tid == 0 && i + kMapStages < my_chunks) {
-            const int64_t c2 = blockIdx.x + (i + kMapStages) * gridDim.x;
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&s_bar[s], chunk_bytes);
-            bulk_g2s(s_buf + s * kThreads * d, pts + c2 * kThreads * d, chunk_bytes, &s_bar[s]);
+        if (tid == 0) {
+            // after the first chunk: keep the cache only if rows repeat words
+            // (fewer claimed slots than 3/4 of the rows)
+            if (!SMALL && i == 0 && s_claimed > (uint32_t)(kThreads * 3 / 4)) s_cache_on = 0u;
+            if (i + kMapStages < my_chunks) {
+                const int64_t c2 = blockIdx.x + (i + kMapStages) * gridDim.x;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&s_bar[s], chunk_bytes);
+                bulk_g2s(s_buf + s * kThreads * d, pts + c2 * kThreads * d, chunk_bytes, &s_bar[s]);
+            }
         }
     }
     // Tail rows (fewer than one chunk): the last block loads them directly.
-    if (blockIdx.x == gridDim.x - 1) {
+    if (!timed_out && blockIdx.x == gridDim.x - 1) {
         const int64_t i = nfull * kThreads + tid;
         if (i < n) {
             float x[DP];
             load_row<DP>(pts + i * d, d, false, x);
-            map_one<DP>(x, d, log2g, mbits, s_off, s_sc, s_ms, i, keys, occ, bad);
-            if (mm_min) acc.add(x);
+            if (SMALL)
+                map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkPrivate{s_tail}, bad);
+            else
+                map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkGlobal{occ}, bad);
         }
     }
-    if (mm_min) acc.publish(d, mm_min, mm_max);
     if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(err, SKY_DEV_ERR_NONFINITE);
+    __syncthreads();
+    if (SMALL) {
+        for (int64_t w = tid; w < words; w += kThreads) stage[blockIdx.x * words + w] = s_tail[w];
+    } else {
+        for (int t = tid; t < kCacheSlots; t += kThreads) {
+            const uint32_t k = s_tail[t], v = s_tail[kCacheSlots + t];
+            if (k != kCacheEmpty && v) atomicOr(occ + k, v);
+        }
+    }
+}
+
+// ORs the blocks' private bitmaps (rows of `stage`) into the bitmap: block
+// (c, r) takes 32 words and every kMergeSplit-th row from r on; the bitmap
+// was zeroed before the map pass.
+constexpr int kMergeSplit = 8;
+
+__global__ void __launch_bounds__(kThreads) k_occ_merge(const uint32_t* __restrict__ stage, int rows,
+                                                        int64_t words, uint32_t* occ)
+{
+    __shared__ uint32_t s_acc[kThreads / 32][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t w = (int64_t)(blockIdx.x / kMergeSplit) * 32 + lane;
+    const int r0 = (int)(blockIdx.x % kMergeSplit);
+    uint32_t acc = 0;
+    if (w < words)
+        for (int r = r0 + warp * kMergeSplit; r < rows; r += kMergeSplit * (kThreads / 32))
+            acc |= __ldg(stage + (int64_t)r * words + w);
+    s_acc[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        for (int k = 1; k < kThreads / 32; ++k) acc |= s_acc[k][lane];
+        if (w < words && acc) atomicOr(occ + w, acc);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -366,6 +515,55 @@ __global__ void __launch_bounds__(kThreads) k_prefix_or_dim(uint32_t* R, int64_t
 {
     prefix_or_dim(R, words, log2g, k, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                   (int64_t)gridDim.x * blockDim.x);
+}
+
+// Prefix-OR in two launches. The low kl dimensions (the low S = log2g * kl
+// bits of a cell key, S >= 5) are done per aligned block of 2^S bits in
+// shared memory; the high kh = d - kl dimensions by a second kernel that
+// holds, for a run of wc consecutive words of the low block, all G^kh rows
+// of the high grid in shared memory. Both are the per-dimension prefix-OR of
+// prefix_or_dim applied in dimension order.
+constexpr int kPrefixThreads = 512;
+
+__global__ void __launch_bounds__(kPrefixThreads) k_prefix_low(const uint32_t* __restrict__ occ, uint32_t* pre,
+                                                               int64_t block_words, int log2g, int kl)
+{
+    extern __shared__ uint32_t s_w[];
+    const int64_t base = (int64_t)blockIdx.x * block_words;
+    for (int64_t w = threadIdx.x; w < block_words; w += blockDim.x) s_w[w] = occ[base + w];
+    __syncthreads();
+    for (int k = 0; k < kl; ++k) {
+        prefix_or_dim(s_w, block_words, log2g, k, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
+    for (int64_t w = threadIdx.x; w < block_words; w += blockDim.x) pre[base + w] = s_w[w];
+}
+
+__global__ void __launch_bounds__(kThreads) k_prefix_high(uint32_t* pre, int64_t row_words, int64_t rows, int wc,
+                                                          int log2g, int kh)
+{
+    extern __shared__ uint32_t s_t[];   // [rows][wc]
+    const int64_t c0 = (int64_t)blockIdx.x * wc;
+    const int64_t cells = rows * wc;
+    for (int64_t t = threadIdx.x; t < cells; t += blockDim.x) s_t[t] = pre[(t / wc) * row_words + c0 + t % wc];
+    __syncthreads();
+    const int64_t G = 1ll << log2g;
+    for (int j = 0; j < kh; ++j) {
+        const int64_t sr = 1ll << (log2g * j);    // row stride of high dimension j
+        const int64_t lines = rows / G * wc;
+        for (int64_t L = threadIdx.x; L < lines; L += blockDim.x) {
+            const int64_t w = L % wc, l = L / wc;
+            int64_t r = (l / sr) * G * sr + l % sr;
+            uint32_t acc = s_t[r * wc + w];
+            for (int64_t i = 1; i < G; ++i) {
+                r += sr;
+                acc |= s_t[r * wc + w];
+                s_t[r * wc + w] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    for (int64_t t = threadIdx.x; t < cells; t += blockDim.x) pre[(t / wc) * row_words + c0 + t % wc] = s_t[t];
 }
 
 __global__ void __launch_bounds__(kThreads) k_dominated(const uint32_t* R, uint32_t* dom, int64_t words,
@@ -409,46 +607,59 @@ __global__ void __launch_bounds__(kThreads) k_cell_stats(const uint32_t* occ, co
 // ---------------------------------------------------------------------------
 // Pre-filter proposals. For proposal f_j, the data point q <= f_j (all
 // dimensions) with the smallest binary32 coordinate sum, ties to the lower
-// row, found by a packed 64-bit atomic min.
+// row: the packed (ordered sum, row) minimum. Each thread keeps its running
+// minimum per proposal in registers over its grid-stride rows; the block
+// combines them by warp shuffles and shared-memory atomics and issues one
+// global 64-bit atomic min per proposal, so the global traffic is
+// blocks x proposals however many rows qualify.
 template <int DP>
 __global__ void __launch_bounds__(kThreads) k_snap(const float* __restrict__ pts, int64_t n, int d,
                                                    int64_t ld, bool vec4, const float* __restrict__ prop,
                                                    int n_prop, unsigned long long* snap)
 {
-    __shared__ float s_f[16 * kMaxDim];
+    constexpr int NP = 16;
+    __shared__ float s_f[NP * kMaxDim];
+    __shared__ unsigned long long s_best[NP];
     for (int t = threadIdx.x; t < n_prop * d; t += blockDim.x) s_f[t] = prop[t];
+    if (threadIdx.x < NP) s_best[threadIdx.x] = ~0ull;
     __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n_round = ((n + 31) / 32) * 32;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-        const bool valid = i < n;
-        float x[DP];
-        float sum = 0.0f;
-        if (valid) {
-            load_row<DP>(pts + i * ld, d, vec4, x);
+    unsigned long long best[NP];
 #pragma unroll
-            for (int k = 0; k < DP; ++k)
-                if (k < d) sum = __fadd_rn(sum, x[k]);
-        }
+    for (int j = 0; j < NP; ++j) best[j] = ~0ull;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float x[DP];
+        load_row<DP>(pts + i * ld, d, vec4, x);
+        float sum = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DP; ++k)
+            if (k < d) sum = __fadd_rn(sum, x[k]);
         const unsigned long long packed =
             ((unsigned long long)float_to_ordered(sum) << 32) | (unsigned long long)(uint32_t)i;
-        for (int j = 0; j < n_prop; ++j) {
-            bool le = valid;
-            if (valid) {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            if (j < n_prop) {
+                bool le = true;
 #pragma unroll
                 for (int k = 0; k < DP; ++k)
                     if (k < d) le &= x[k] <= s_f[j * d + k];
-            }
-            if (__any_sync(kFull, le)) {
-                unsigned long long v = le ? packed : ~0ull;
-                for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
-                    v = w < v ? w : v;
-                }
-                if ((threadIdx.x & 31) == 0) atomicMin(&snap[j], v);
+                if (le && packed < best[j]) best[j] = packed;
             }
         }
     }
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        if (j < n_prop) {
+            unsigned long long v = best[j];
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+                v = w < v ? w : v;
+            }
+            if ((threadIdx.x & 31) == 0 && v != ~0ull) atomicMin(&s_best[j], v);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < n_prop && s_best[threadIdx.x] != ~0ull) atomicMin(&snap[threadIdx.x], s_best[threadIdx.x]);
 }
 
 __global__ void k_snap_finalize(const float* __restrict__ pts, int d, int64_t ld,
@@ -466,95 +677,200 @@ __global__ void k_snap_finalize(const float* __restrict__ pts, int d, int64_t ld
 }
 
 // ---------------------------------------------------------------------------
-// Survivors of step (c), compacted in row order, with their Morton keys
-// (computed by the map pass). Reads only the 8-byte (cell key, Morton key)
-// pairs; a row itself is read only when proposals are in use.
-template <int DP>
-__global__ void __launch_bounds__(kThreads) k_survivors(
-    const float* __restrict__ pts, int64_t n, int d, int64_t ld, bool vec4, int log2g,
-    const uint2* __restrict__ keys, const uint32_t* __restrict__ pre,
-    const float* __restrict__ filt, int n_filter_max, DevResult* res, unsigned long long* states,
-    uint32_t* tile_counter, uint32_t* surv_key, uint32_t* surv_idx)
+// Survivors of step (c), compacted in row order with their Morton keys, in
+// two passes over the same fixed split of the rows: block b owns the
+// contiguous tiles [b * tpb, (b + 1) * tpb) of kSurvTile rows.
+//   k_surv_flags    reads the cell keys, probes the prefix-OR bitmap at
+//                   key - (1, ..., 1) (Corollary 4: a cell is dominated iff
+//                   that cell is covered), applies the optional snapped
+//                   proposals, writes one flag bit per row and the block's
+//                   survivor count
+//   k_surv_scatter  sums the counts of the blocks before it, then walks its
+//                   tiles: block scan of the flags, survivors staged in
+//                   shared memory, written out coalesced
+// No look-back chain and no atomics; the second pass reads the flag bits
+// (n / 8 bytes) and the Morton keys of survivors only.
+constexpr int kSurvItems = 8;
+constexpr int kSurvTile = kSurvItems * kThreads;   // 2048 rows
+static_assert(kSurvTile % 32 == 0, "whole flag words per tile");
+
+// True when some lg-bit field of key is zero: (key - ones) borrows into the
+// top bit of a field only below a zero field, and ~key keeps it only there.
+__device__ __forceinline__ bool has_zero_column(uint32_t key, uint32_t ones, uint32_t highs)
 {
-    __shared__ uint32_t s_warp[kThreads / 32];
-    __shared__ uint32_t s_tile, s_prefix;
+    return ((key - ones) & ~key & highs) != 0u;
+}
+
+template <int DP>
+__global__ void __launch_bounds__(kThreads) k_surv_flags(
+    const float* __restrict__ pts, int64_t n, int d, int64_t ld, bool vec4, int log2g,
+    const uint32_t* __restrict__ ckey, const uint32_t* __restrict__ pre, const float* __restrict__ filt,
+    int n_filter_max, const DevResult* res, int64_t tpb, uint32_t* __restrict__ flags, uint32_t* __restrict__ counts)
+{
     __shared__ float s_f[16 * kMaxDim];
-    const int tid = threadIdx.x;
-    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    __shared__ uint32_t s_cnt[kThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31;
     const int nf = n_filter_max ? (int)res->n_filter_used : 0;
     for (int t = tid; t < nf * kMaxDim; t += kThreads) s_f[t] = filt[t];
     __syncthreads();
-    const uint32_t tile = s_tile;
+    // With log2g = 0 the grid is one cell, which nothing dominates (and the
+    // field masks below would be empty): no row probes the bitmap then.
+    const bool can_dominate = log2g > 0;
     const uint32_t ones = ones_key(log2g, d);
-    const int64_t base = (int64_t)tile * kScanTile + (int64_t)tid * kScanItems;
-    uint2 kk[kScanItems];
-    if (base + kScanItems <= n) {
-        const uint4* src = reinterpret_cast<const uint4*>(keys + base);
+    const uint32_t highs = can_dominate ? ones << (log2g - 1) : 0u;
+    const int64_t ntiles = (n + kSurvTile - 1) / kSurvTile;
+    const int64_t t0 = (int64_t)blockIdx.x * tpb;
+    const int64_t t1 = t0 + tpb < ntiles ? t0 + tpb : ntiles;
+    const int64_t nwords = (n + 31) / 32;
+    uint32_t cnt = 0;
+    uint32_t kk[kSurvItems], nx[kSurvItems];
+    auto load_keys = [&](int64_t tile, uint32_t (&dst)[kSurvItems]) {
+        const int64_t base = tile * kSurvTile + (int64_t)tid * kSurvItems;
+        if (base + kSurvItems <= n) {
+            const uint4* src = reinterpret_cast<const uint4*>(ckey + base);
+            const uint4 a = __ldg(src), b = __ldg(src + 1);
+            dst[0] = a.x; dst[1] = a.y; dst[2] = a.z; dst[3] = a.w;
+            dst[4] = b.x; dst[5] = b.y; dst[6] = b.z; dst[7] = b.w;
+        } else {
 #pragma unroll
-        for (int h = 0; h < kScanItems / 2; ++h) {
-            const uint4 v = src[h];
-            kk[2 * h] = make_uint2(v.x, v.y);
-            kk[2 * h + 1] = make_uint2(v.z, v.w);
+            for (int j = 0; j < kSurvItems; ++j) dst[j] = (base + j < n) ? __ldg(ckey + base + j) : 0u;
         }
-    } else {
+    };
+    if (t0 < t1) load_keys(t0, kk);
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        if (tile + 1 < t1) load_keys(tile + 1, nx);      // next tile's keys in flight
+        const int64_t base = tile * kSurvTile + (int64_t)tid * kSurvItems;
+        uint32_t word[kSurvItems];
+        bool probe[kSurvItems];
 #pragma unroll
-        for (int j = 0; j < kScanItems; ++j) kk[j] = (base + j < n) ? keys[base + j] : make_uint2(0u, 0u);
-    }
-    // all bitmap words first (independent loads), then the tests
-    uint32_t word[kScanItems];
-    bool probe[kScanItems];
+        for (int j = 0; j < kSurvItems; ++j) {
+            probe[j] = can_dominate && (base + j < n) && !has_zero_column(kk[j], ones, highs);
+            word[j] = probe[j] ? __ldg(pre + ((kk[j] - ones) >> 5)) : 0u;
+        }
+        uint32_t f = 0;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        probe[j] = (base + j < n) && all_columns_positive(kk[j].x, log2g, d);
-        const uint32_t src = kk[j].x - ones;
-        word[j] = probe[j] ? __ldg(pre + (src >> 5)) : 0u;
-    }
-    uint32_t flags = 0;
+        for (int j = 0; j < kSurvItems; ++j) {
+            const int64_t i = base + j;
+            if (i >= n) continue;
+            if (probe[j] && ((word[j] >> ((kk[j] - ones) & 31u)) & 1u)) continue;
+            if (nf) {
+                float x[DP];
+                load_row<DP>(pts + i * ld, d, vec4, x);
+                bool filtered = false;
+                for (int q = 0; q < nf && !filtered; ++q) {
+                    bool le = true, lt = false;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        const int64_t i = base + j;
-        if (i >= n) continue;
-        const uint32_t src = kk[j].x - ones;
-        const bool dominated = probe[j] && ((word[j] >> (src & 31u)) & 1u);
-        if (dominated) continue;
-        if (nf) {
-            float x[DP];
-            load_row<DP>(pts + i * ld, d, vec4, x);
-            bool filtered = false;
-            for (int f = 0; f < nf && !filtered; ++f) {
-                bool le = true, lt = false;
-#pragma unroll
-                for (int k = 0; k < DP; ++k) {
-                    if (k < d) {
-                        const float q = s_f[f * kMaxDim + k];
-                        le &= q <= x[k];
-                        lt |= q < x[k];
+                    for (int k = 0; k < DP; ++k) {
+                        if (k < d) {
+                            const float v = s_f[q * kMaxDim + k];
+                            le &= v <= x[k];
+                            lt |= v < x[k];
+                        }
                     }
+                    filtered = le && lt;  // Definition 1: the snapped point dominates x
                 }
-                filtered = le && lt;  // Definition 1: the snapped point dominates x
+                if (filtered) continue;
             }
-            if (filtered) continue;
+            f |= 1u << j;
         }
-        flags |= 1u << j;
+        cnt += __popc(f);
+        // lanes 4q .. 4q+3 hold the four bytes of flag word (tile * 64 + tid / 4)
+        uint32_t v = f << (8 * (lane & 3));
+        v |= __shfl_xor_sync(kFull, v, 1);
+        v |= __shfl_xor_sync(kFull, v, 2);
+        const int64_t w = tile * (kSurvTile / 32) + tid / 4;
+        if ((lane & 3) == 0 && w < nwords) flags[w] = v;
+        if (tile + 1 < t1) {
+#pragma unroll
+            for (int j = 0; j < kSurvItems; ++j) kk[j] = nx[j];
+        }
     }
-    uint32_t total;
-    const uint32_t excl = block_excl_scan((uint32_t)__popc(flags), s_warp, total);
-    if (tid < 32) {
-        const uint32_t prefix = lookback_prefix(states, tile, total, &res->err);
-        if (tid == 0) s_prefix = prefix;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+    if (lane == 0) s_cnt[tid >> 5] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) t += s_cnt[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_surv_scatter(int64_t n, const uint32_t* __restrict__ mkey,
+                                                           const uint32_t* __restrict__ flags,
+                                                           const uint32_t* __restrict__ counts, int64_t tpb,
+                                                           DevResult* res, uint32_t* __restrict__ surv_key,
+                                                           uint32_t* __restrict__ surv_idx)
+{
+    __shared__ uint32_t s_warp[kThreads / 32];
+    __shared__ uint32_t s_key[kSurvTile], s_idx[kSurvTile];
+    __shared__ uint32_t s_off;
+    const int tid = threadIdx.x, lane = tid & 31;
+    // rows kept by the blocks before this one
+    uint32_t part = 0;
+    for (int b = tid; b < (int)blockIdx.x; b += kThreads) part += counts[b];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+    if (lane == 0) s_warp[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) t += s_warp[w];
+        s_off = t;
     }
     __syncthreads();
-    uint32_t pos = s_prefix + excl;
+    uint32_t running = s_off;
+    const int64_t ntiles = (n + kSurvTile - 1) / kSurvTile;
+    const int64_t t0 = (int64_t)blockIdx.x * tpb;
+    const int64_t t1 = t0 + tpb < ntiles ? t0 + tpb : ntiles;
+    const int64_t nwords = (n + 31) / 32;
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        const int64_t w = tile * (kSurvTile / 32) + tid / 4;
+        const uint32_t f = (w < nwords) ? (__ldg(flags + w) >> (8 * (tid & 3))) & 0xffu : 0u;
+        const int64_t base = tile * kSurvTile + (int64_t)tid * kSurvItems;
+        uint32_t mk[kSurvItems];
+        if (f) {
+            if (base + kSurvItems <= n) {
+                const uint4* src = reinterpret_cast<const uint4*>(mkey + base);
+                const uint4 a = __ldg(src), b = __ldg(src + 1);
+                mk[0] = a.x; mk[1] = a.y; mk[2] = a.z; mk[3] = a.w;
+                mk[4] = b.x; mk[5] = b.y; mk[6] = b.z; mk[7] = b.w;
+            } else {
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        if (flags & (1u << j)) {
-            surv_key[pos] = kk[j].y;
-            surv_idx[pos] = (uint32_t)(base + j);
-            ++pos;
+                for (int j = 0; j < kSurvItems; ++j) mk[j] = (base + j < n) ? __ldg(mkey + base + j) : 0u;
+            }
         }
+        uint32_t total;
+        uint32_t pos = block_excl_scan<kThreads>((uint32_t)__popc(f), s_warp, total);
+        if (f) {
+#pragma unroll
+            for (int j = 0; j < kSurvItems; ++j) {
+                if (f & (1u << j)) {
+                    s_key[pos] = mk[j];
+                    s_idx[pos] = (uint32_t)(base + j);
+                    ++pos;
+                }
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < total; i += kThreads) {
+            surv_key[running + i] = s_key[i];
+            surv_idx[running + i] = s_idx[i];
+        }
+        running += total;
+        __syncthreads();   // s_key / s_idx / s_warp are reused by the next tile
     }
-    const uint32_t ntiles = (uint32_t)((n + kScanTile - 1) / kScanTile);
-    if (tile == ntiles - 1 && tid == 0) res->survivors = s_prefix + total;
+    if (blockIdx.x == gridDim.x - 1 && tid == 0) res->survivors = running;
+}
+
+// Result of a survivors-only call: the survivor row ids (already ascending)
+// into the caller's buffer; count = survivors, nothing written past capacity.
+__global__ void __launch_bounds__(kThreads) k_copy_survivors(const uint32_t* __restrict__ surv_idx, DevResult* res,
+                                                             int32_t* out, int64_t capacity)
+{
+    const uint32_t m = res->survivors;
+    if (blockIdx.x == 0 && threadIdx.x == 0) res->count = m;
+    if ((int64_t)m > capacity) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)surv_idx[i];
 }
 
 int grid_for(int64_t work, int per_block, int max_blocks)
@@ -592,30 +908,57 @@ static bool vec4_ok(const Plan& p)
     return (p.d % 4 == 0) && (p.ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.pts) & 15u) == 0);
 }
 
-static cudaError_t launch_map(const Plan& p, const DevResult* gate, bool track, cudaStream_t s)
+// Upper bound of the map pass's block count (sizes the private-bitmap rows).
+int map_blocks_bound(int64_t n)
 {
-    uint32_t* mn = track ? p.mm_min : nullptr;
-    uint32_t* mx = track ? p.mm_max : nullptr;
+    int64_t b = (n + kThreads - 1) / kThreads;
+    if (b < 1) b = 1;
+    return (int)std::min<int64_t>(b, kMapMaxBlocks);
+}
+
+static cudaError_t launch_map(const Plan& p, cudaStream_t s)
+{
+    const bool small = p.occ_stage != nullptr;
+    const int64_t pw = small ? p.words : 0;
+    int blocks = 0;
     if (p.tma_ok && p.n >= kThreads) {
-        const size_t smem = (size_t)kMapStages * kThreads * p.d * sizeof(float);
+        const size_t tail = small ? (size_t)pw * sizeof(uint32_t) : 2 * kCacheSlots * sizeof(uint32_t);
+        const size_t smem = (size_t)kMapStages * kThreads * p.d * sizeof(float) + tail;
+        const int smem_max = kMapStages * kThreads * 16 * (int)sizeof(float) +
+                             (int)std::max<int64_t>(kPrivWords, 2 * kCacheSlots) * (int)sizeof(uint32_t);
         const int64_t nchunks = p.n / kThreads;
-        const int blocks = grid_for(nchunks, 1, num_sms() * 4);
+        blocks = grid_for(nchunks, 1, std::min(num_sms() * 4, kMapMaxBlocks));
         SKY_DISPATCH_DP(p.d, {
-            static bool attr_set = false;
-            if (!attr_set) {
-                cudaFuncSetAttribute(k_map_mark_tma<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kMapStages * kThreads * 16 * (int)sizeof(float));
-                attr_set = true;
+            if (small) {
+                cudaFuncSetAttribute(k_map_mark_tma<DP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+                k_map_mark_tma<DP, true><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.log2g, p.morton_bits,
+                                                                        p.params, p.ckey, p.mkey, p.occ,
+                                                                        &p.res->err, p.occ_stage, pw);
+            } else {
+                cudaFuncSetAttribute(k_map_mark_tma<DP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+                k_map_mark_tma<DP, false><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.log2g, p.morton_bits,
+                                                                         p.params, p.ckey, p.mkey, p.occ,
+                                                                         &p.res->err, nullptr, 0);
             }
-            k_map_mark_tma<DP><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.log2g, p.morton_bits, p.params,
-                                                              p.keys, p.occ, &p.res->err, gate, mn, mx);
         });
     } else {
-        const int blocks = grid_for(p.n, kThreads * 4, num_sms() * 8);
+        blocks = grid_for(p.n, kThreads * 4, std::min(num_sms() * 8, kMapMaxBlocks));
         const bool v = vec4_ok(p);
-        SKY_DISPATCH_DP(p.d, k_map_mark_plain<DP><<<blocks, kThreads, 0, s>>>(
-                                 p.pts, p.n, p.d, p.ld, v, p.log2g, p.morton_bits, p.params, p.keys, p.occ,
-                                 &p.res->err, gate, mn, mx));
+        const size_t smem = (size_t)pw * sizeof(uint32_t);
+        SKY_DISPATCH_DP(p.d, {
+            if (small)
+                k_map_mark_plain<DP, true><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.ld, v, p.log2g,
+                                                                          p.morton_bits, p.params, p.ckey, p.mkey,
+                                                                          p.occ, &p.res->err, p.occ_stage, pw);
+            else
+                k_map_mark_plain<DP, false><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, p.log2g,
+                                                                        p.morton_bits, p.params, p.ckey, p.mkey,
+                                                                        p.occ, &p.res->err, nullptr, 0);
+        });
+    }
+    if (small) {
+        const int64_t cols = (p.words + 31) / 32;
+        k_occ_merge<<<(unsigned)(cols * kMergeSplit), kThreads, 0, s>>>(p.occ_stage, blocks, p.words, p.occ);
     }
     return cudaGetLastError();
 }
@@ -623,7 +966,7 @@ static cudaError_t launch_map(const Plan& p, const DevResult* gate, bool track, 
 cudaError_t launch_build(const Plan& p, cudaStream_t s)
 {
     cudaMemsetAsync(p.occ, 0, sizeof(uint32_t) * p.words, s);
-    if (p.map_mode != kMapUnit) {
+    if (p.map_mode == kMapMinMax) {
         cudaMemsetAsync(p.mm_min, 0xff, sizeof(uint32_t) * kMaxDim, s);
         cudaMemsetAsync(p.mm_max, 0x00, sizeof(uint32_t) * kMaxDim, s);
     }
@@ -634,31 +977,87 @@ cudaError_t launch_build(const Plan& p, cudaStream_t s)
         SKY_DISPATCH_DP(p.d, k_minmax<DP><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, p.mm_min,
                                                                        p.mm_max, &p.res->err));
         k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 1, p.params);
-        return launch_map(p, nullptr, false, s);
+    } else if (p.map_mode == kMapUnit) {
+        k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 0, p.params);
+    } else {
+        SKY_DISPATCH_DP(p.d, k_sample_params<DP><<<1, kDecideThreads, 0, s>>>(
+                                 p.pts, p.n, p.d, p.ld, p.log2g, p.morton_bits, p.mm_min, p.mm_max, p.params));
     }
-    k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 0, p.params);
-    if (p.map_mode == kMapUnit) return launch_map(p, nullptr, false, s);
-    // automatic: unit map with min/max tracking, then a gated second pass
-    launch_map(p, nullptr, true, s);
-    k_decide<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, p.params, p.res);
-    k_clear_if<<<grid_for(p.words, kThreads, num_sms() * 4), kThreads, 0, s>>>(p.occ, p.words, p.res);
-    return launch_map(p, p.res, false, s);
+    return launch_map(p, s);
 }
 
 int build_kernel_count(const Plan& p)
 {
     if (p.n == 0) return 0;
-    if (p.map_mode == kMapMinMax) return 3;
-    if (p.map_mode == kMapUnit) return 2;
-    return 5;
+    const int merge = p.occ_stage ? 1 : 0;
+    if (p.map_mode == kMapMinMax) return 3 + merge;
+    return 2 + merge;
+}
+
+// Split of the prefix-OR: kl low dimensions per shared-memory block (at most
+// 2^20 bits, 128 KB), the rest in rows of the high grid (at most 2^14 rows).
+// kl = 0 selects the fallback of one launch per dimension.
+struct PrefixSplit {
+    int kl = 0, kh = 0;
+    int64_t block_words = 0, rows = 0;
+    int wc = 0;
+    int64_t high_blocks = 0, low_blocks = 0;
+};
+
+PrefixSplit prefix_split(const Plan& p)
+{
+    PrefixSplit ps;
+    const int lg = p.log2g, d = p.d, B = lg * d;
+    if (B <= 16) {                       // the whole grid (at most 8 KB) in one block
+        ps.kl = d;
+        ps.block_words = p.words;
+        ps.low_blocks = 1;
+        return ps;
+    }
+    int kl = 0;
+    while (kl + 1 <= d && lg * (kl + 1) <= 15) ++kl;
+    while (kl < d && B - lg * kl > 12 && lg * (kl + 1) <= 20) ++kl;
+    if (kl < 1 || kl >= d || lg * kl < 5 || B - lg * kl > 14) return PrefixSplit{};
+    ps.kl = kl;
+    ps.kh = d - kl;
+    ps.block_words = 1ll << (lg * kl - 5);
+    ps.low_blocks = p.words / ps.block_words;
+    ps.rows = 1ll << (B - lg * kl);
+    int64_t wc = 1024 / ps.rows;          // about 4 KB of shared memory per block, many blocks
+    if (wc < 1) wc = 1;
+    if (wc > ps.block_words) wc = ps.block_words;
+    ps.wc = (int)wc;
+    ps.high_blocks = ps.block_words / wc;
+    return ps;
+}
+
+int prefix_kernel_count(const Plan& p)
+{
+    const PrefixSplit ps = prefix_split(p);
+    if (ps.kl == 0) return p.d;
+    return ps.kh > 0 ? 2 : 1;
 }
 
 cudaError_t launch_prefix_or(const Plan& p, cudaStream_t s)
 {
-    cudaMemcpyAsync(p.pre, p.occ, sizeof(uint32_t) * p.words, cudaMemcpyDeviceToDevice, s);
-    for (int k = 0; k < p.d; ++k) {
-        const int blocks = grid_for(p.words, kThreads, num_sms() * 8);
-        k_prefix_or_dim<<<blocks, kThreads, 0, s>>>(p.pre, p.words, p.log2g, k);
+    const PrefixSplit ps = prefix_split(p);
+    if (ps.kl == 0) {
+        cudaMemcpyAsync(p.pre, p.occ, sizeof(uint32_t) * p.words, cudaMemcpyDeviceToDevice, s);
+        for (int k = 0; k < p.d; ++k) {
+            const int blocks = grid_for(p.words, kThreads, num_sms() * 8);
+            k_prefix_or_dim<<<blocks, kThreads, 0, s>>>(p.pre, p.words, p.log2g, k);
+        }
+        return cudaGetLastError();
+    }
+    const int smem_low = (int)(ps.block_words * sizeof(uint32_t));
+    cudaFuncSetAttribute(k_prefix_low, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_low);
+    k_prefix_low<<<(unsigned)ps.low_blocks, kPrefixThreads, smem_low, s>>>(p.occ, p.pre, ps.block_words, p.log2g,
+                                                                           ps.kl);
+    if (ps.kh > 0) {
+        const int smem_high = (int)(ps.rows * ps.wc * sizeof(uint32_t));
+        cudaFuncSetAttribute(k_prefix_high, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_high);
+        k_prefix_high<<<(unsigned)ps.high_blocks, kThreads, smem_high, s>>>(p.pre, ps.block_words, ps.rows, ps.wc,
+                                                                             p.log2g, ps.kh);
     }
     return cudaGetLastError();
 }
@@ -684,16 +1083,38 @@ cudaError_t launch_snap(const Plan& p, const float* d_prop, int n_prop, cudaStre
     return cudaGetLastError();
 }
 
+void survivor_split(int64_t n, int64_t* tpb, int* blocks)
+{
+    const int64_t ntiles = (n + kSurvTile - 1) / kSurvTile;
+    int64_t target = (int64_t)num_sms() * 4;
+    if (target > kSurvMaxBlocks) target = kSurvMaxBlocks;
+    int64_t t = (ntiles + target - 1) / target;
+    if (t < 1) t = 1;
+    int64_t b = (ntiles + t - 1) / t;
+    if (b < 1) b = 1;
+    *tpb = t;
+    *blocks = (int)b;
+}
+
 cudaError_t launch_survivors(const Plan& p, int n_filter, cudaStream_t s)
 {
     if (p.n == 0) return cudaGetLastError();
-    const int64_t ntiles = (p.n + kScanTile - 1) / kScanTile;
-    cudaMemsetAsync(p.lb_states, 0, sizeof(unsigned long long) * ntiles, s);
-    cudaMemsetAsync(p.lb_counter, 0, sizeof(uint32_t), s);
+    int64_t tpb = 1;
+    int blocks = 1;
+    survivor_split(p.n, &tpb, &blocks);
     const bool v = vec4_ok(p);
-    SKY_DISPATCH_DP(p.d, k_survivors<DP><<<(unsigned)ntiles, kThreads, 0, s>>>(
-                             p.pts, p.n, p.d, p.ld, v, p.log2g, p.keys, p.pre, p.filt, n_filter, p.res,
-                             p.lb_states, p.lb_counter, p.surv_key, p.surv_idx));
+    SKY_DISPATCH_DP(p.d, k_surv_flags<DP><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, p.log2g, p.ckey,
+                                                                       p.pre, p.filt, n_filter, p.res, tpb,
+                                                                       p.sflags, p.scount));
+    k_surv_scatter<<<blocks, kThreads, 0, s>>>(p.n, p.mkey, p.sflags, p.scount, tpb, p.res, p.surv_key,
+                                               p.surv_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_survivors(const Plan& p, int32_t* out, int64_t capacity, cudaStream_t s)
+{
+    const int blocks = grid_for(p.n, kThreads * 4, num_sms() * 4);
+    k_copy_survivors<<<blocks, kThreads, 0, s>>>(p.surv_idx, p.res, out, capacity);
     return cudaGetLastError();
 }
 

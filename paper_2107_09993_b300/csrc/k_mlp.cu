@@ -44,26 +44,49 @@ static_assert(P == SKY_MLP_PARAMS, "parameter count");
 __device__ __forceinline__ bool layer_ok(int c, int d) { return (c + 1) * d <= 24; }
 
 // ------------------------------------------------------------- features ---
-__global__ void __launch_bounds__(1024) k_features(const float* __restrict__ pts, int64_t n, int d, int64_t ld,
-                                                   float* feat, float* range)
+// The sample: every stride-th row, stride = ceil(n / 65,536), so at most
+// 65,536 rows in 64 tiles of 1,024. Three launches:
+//   k_feat_minmax  one CTA per tile: per-dimension min / max of the tile
+//   k_feat_tile    one CTA per tile: reduces the tile minima / maxima (in
+//                  tile order), normalises its rows to [0, 1], and writes
+//                  the tile's 32-bin histogram counts and its first and
+//                  second moment sums (binary32 over the tile's rows, stored
+//                  as binary64)
+//   k_feat_final   one CTA: sums the tiles' counts and moments in tile order
+//                  and writes the 636 features and the sample range
+// The fixed tile decomposition makes the result independent of the GPU's
+// SM count and of scheduling.
+constexpr int kTiles = (int)(SAMPLE / kTileRows);            // 64
+constexpr int kNPair = DMAX * (DMAX + 1) / 2;                 // 136 (k <= l)
+constexpr int kNSum = kNPair + DMAX;                          // 152
+// per-tile partials in the work buffer, in floats
+constexpr int64_t kWorkMM = 0;                                          // [kTiles][2 * DMAX]
+constexpr int64_t kWorkHist = kWorkMM + (int64_t)kTiles * 2 * DMAX;     // [kTiles][DMAX * BINS] u32
+constexpr int64_t kWorkSum = kWorkHist + (int64_t)kTiles * DMAX * BINS; // [kTiles][kNSum] f64
+constexpr int64_t kWorkFeat = kWorkSum + (int64_t)kTiles * kNSum * 2;
+static_assert(kWorkSum % 2 == 0, "f64 partials 8-byte aligned");
+
+__device__ __forceinline__ int64_t sample_stride(int64_t n)
 {
-    extern __shared__ float s_x[];                  // [kTileRows][DMAX]
+    const int64_t t = (n + SAMPLE - 1) / SAMPLE;
+    return t > 1 ? t : 1;
+}
+
+__global__ void __launch_bounds__(kTileRows) k_feat_minmax(const float* __restrict__ pts, int64_t n, int d,
+                                                           int64_t ld, float* __restrict__ mm)
+{
     __shared__ float s_mn[32][DMAX], s_mx[32][DMAX];
-    __shared__ float s_lo[DMAX], s_inv[DMAX];
-    __shared__ uint32_t s_hist[DMAX][BINS];
-    __shared__ double s_sum[DMAX * (DMAX + 1) / 2 + DMAX];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t stride = (n + SAMPLE - 1) / SAMPLE > 1 ? (n + SAMPLE - 1) / SAMPLE : 1;
-    const int64_t s = (n + stride - 1) / stride;
-    // pass 1: min / max of the sample
+    const int64_t stride = sample_stride(n), s = (n + stride - 1) / stride;
+    const int64_t i = (int64_t)blockIdx.x * kTileRows + tid;
     float mn[DMAX], mx[DMAX];
 #pragma unroll
     for (int k = 0; k < DMAX; ++k) { mn[k] = INFINITY; mx[k] = -INFINITY; }
-    for (int64_t i = tid; i < s; i += blockDim.x) {
+    if (i < s) {
         const float* r = pts + i * stride * ld;
 #pragma unroll
         for (int k = 0; k < DMAX; ++k)
-            if (k < d) { const float v = r[k]; mn[k] = fminf(mn[k], v); mx[k] = fmaxf(mx[k], v); }
+            if (k < d) { const float v = __ldg(r + k); mn[k] = v; mx[k] = v; }
     }
 #pragma unroll
     for (int k = 0; k < DMAX; ++k) {
@@ -73,60 +96,86 @@ __global__ void __launch_bounds__(1024) k_features(const float* __restrict__ pts
         }
         if (lane == 0) { s_mn[warp][k] = mn[k]; s_mx[warp][k] = mx[k]; }
     }
-    for (int t = tid; t < DMAX * BINS; t += blockDim.x) s_hist[t / BINS][t % BINS] = 0u;
-    for (int t = tid; t < DMAX * (DMAX + 1) / 2 + DMAX; t += blockDim.x) s_sum[t] = 0.0;
     __syncthreads();
     if (tid < DMAX) {
         float lo = INFINITY, hi = -INFINITY;
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w) { lo = fminf(lo, s_mn[w][tid]); hi = fmaxf(hi, s_mx[w][tid]); }
+        for (int w = 0; w < kTileRows / 32; ++w) { lo = fminf(lo, s_mn[w][tid]); hi = fmaxf(hi, s_mx[w][tid]); }
+        mm[blockIdx.x * 2 * DMAX + tid] = lo;
+        mm[blockIdx.x * 2 * DMAX + DMAX + tid] = hi;
+    }
+}
+
+__global__ void __launch_bounds__(kTileRows) k_feat_tile(const float* __restrict__ pts, int64_t n, int d, int64_t ld,
+                                                         const float* __restrict__ mm, int tiles,
+                                                         uint32_t* __restrict__ hist_out,
+                                                         double* __restrict__ sum_out, float* __restrict__ range)
+{
+    extern __shared__ float s_x[];                  // [kTileRows][DMAX]
+    __shared__ float s_lo[DMAX], s_inv[DMAX];
+    __shared__ uint32_t s_hist[DMAX * BINS];
+    const int tid = threadIdx.x;
+    const int64_t stride = sample_stride(n), s = (n + stride - 1) / stride;
+    if (tid < DMAX) {
+        float lo = INFINITY, hi = -INFINITY;
+        for (int t = 0; t < tiles; ++t) { lo = fminf(lo, mm[t * 2 * DMAX + tid]); hi = fmaxf(hi, mm[t * 2 * DMAX + DMAX + tid]); }
         if (tid >= d) { lo = 0.0f; hi = 0.0f; }
         const float rg = __fsub_rn(hi, lo);
         s_lo[tid] = lo;
         s_inv[tid] = rg > 0.0f ? __fdiv_rn(1.0f, rg) : 0.0f;
-        range[tid] = lo;
-        range[DMAX + tid] = hi;
+        if (blockIdx.x == 0) { range[tid] = lo; range[DMAX + tid] = hi; }
+    }
+    for (int t = tid; t < DMAX * BINS; t += kTileRows) s_hist[t] = 0u;
+    __syncthreads();
+    const int64_t t0 = (int64_t)blockIdx.x * kTileRows;
+    const int rows = (int)((s - t0) < kTileRows ? (s - t0) : kTileRows);
+    if (tid < rows) {
+        const float* r = pts + (t0 + tid) * stride * ld;
+#pragma unroll
+        for (int k = 0; k < DMAX; ++k) {
+            float x = 0.0f;
+            if (k < d) {
+                x = __fmul_rn(__fsub_rn(__ldg(r + k), s_lo[k]), s_inv[k]);
+                x = fminf(fmaxf(x, 0.0f), 1.0f);
+                const int b = min(BINS - 1, (int)floorf(__fmul_rn(x, (float)BINS)));
+                atomicAdd(&s_hist[k * BINS + b], 1u);
+            }
+            s_x[tid * DMAX + k] = x;
+        }
     }
     __syncthreads();
-    // pass 2: tiles of normalised rows -> histograms and moment sums
-    const int npair = DMAX * (DMAX + 1) / 2;
-    int pk = 0, pl = 0;
-    if (tid < npair) {               // pair index -> (k, l), k <= l
-        int t = tid;
+    for (int t = tid; t < DMAX * BINS; t += kTileRows) hist_out[(int64_t)blockIdx.x * DMAX * BINS + t] = s_hist[t];
+    if (tid < kNPair) {               // pair index -> (k, l), k <= l
+        int pk = 0, t = tid;
         while (t >= DMAX - pk) { t -= DMAX - pk; ++pk; }
-        pl = pk + t;
+        const int pl = pk + t;
+        float acc = 0.0f;
+        for (int i = 0; i < rows; ++i) acc = fmaf(s_x[i * DMAX + pk], s_x[i * DMAX + pl], acc);
+        sum_out[(int64_t)blockIdx.x * kNSum + tid] = (double)acc;
+    } else if (tid < kNSum) {
+        const int k = tid - kNPair;
+        float acc = 0.0f;
+        for (int i = 0; i < rows; ++i) acc += s_x[i * DMAX + k];
+        sum_out[(int64_t)blockIdx.x * kNSum + tid] = (double)acc;
     }
-    for (int64_t t0 = 0; t0 < s; t0 += kTileRows) {
-        const int rows = (int)((s - t0) < kTileRows ? (s - t0) : kTileRows);
-        for (int i = tid; i < rows; i += blockDim.x) {
-            const float* r = pts + (t0 + i) * stride * ld;
-#pragma unroll
-            for (int k = 0; k < DMAX; ++k) {
-                float x = 0.0f;
-                if (k < d) {
-                    x = __fmul_rn(__fsub_rn(r[k], s_lo[k]), s_inv[k]);
-                    x = fminf(fmaxf(x, 0.0f), 1.0f);
-                    const int b = min(BINS - 1, (int)floorf(__fmul_rn(x, (float)BINS)));
-                    atomicAdd(&s_hist[k][b], 1u);
-                }
-                s_x[i * DMAX + k] = x;
-            }
-        }
-        __syncthreads();
-        if (tid < npair) {
-            float acc = 0.0f;
-            for (int i = 0; i < rows; ++i) acc = fmaf(s_x[i * DMAX + pk], s_x[i * DMAX + pl], acc);
-            s_sum[tid] += (double)acc;
-        } else if (tid < npair + DMAX) {
-            const int k = tid - npair;
-            float acc = 0.0f;
-            for (int i = 0; i < rows; ++i) acc += s_x[i * DMAX + k];
-            s_sum[tid] += (double)acc;
-        }
-        __syncthreads();
+}
+
+__global__ void __launch_bounds__(512) k_feat_final(int64_t n, int d, int tiles, const uint32_t* __restrict__ hist,
+                                                    const double* __restrict__ sums, float* __restrict__ feat)
+{
+    __shared__ double s_sum[kNSum];
+    const int tid = threadIdx.x;
+    const int64_t stride = sample_stride(n), s = (n + stride - 1) / stride;
+    if (tid < kNSum) {
+        double a = 0.0;
+        for (int t = 0; t < tiles; ++t) a += sums[(int64_t)t * kNSum + tid];
+        s_sum[tid] = a;
     }
-    // outputs
-    for (int t = tid; t < DMAX * BINS; t += blockDim.x)
-        feat[t] = (float)((double)s_hist[t / BINS][t % BINS] / (double)s);
+    for (int b = tid; b < DMAX * BINS; b += blockDim.x) {
+        uint32_t c = 0;
+        for (int t = 0; t < tiles; ++t) c += hist[(int64_t)t * DMAX * BINS + b];
+        feat[b] = (float)((double)c / (double)s);
+    }
+    __syncthreads();
     if (tid < DMAX * (DMAX - 1) / 2) {
         int k = 0, t = tid;
         while (t >= DMAX - 1 - k) { t -= DMAX - 1 - k; ++k; }
@@ -134,7 +183,7 @@ __global__ void __launch_bounds__(1024) k_features(const float* __restrict__ pts
         auto pair = [&](int a, int b) {   // index of (a, b), a <= b, in the pair list
             return a * DMAX - a * (a - 1) / 2 + (b - a);
         };
-        const double ek = s_sum[npair + k] / s, el = s_sum[npair + l] / s;
+        const double ek = s_sum[kNPair + k] / s, el = s_sum[kNPair + l] / s;
         const double vk = s_sum[pair(k, k)] / s - ek * ek;
         const double vl = s_sum[pair(l, l)] / s - el * el;
         const double cv = s_sum[pair(k, l)] / s - ek * el;
@@ -144,7 +193,7 @@ __global__ void __launch_bounds__(1024) k_features(const float* __restrict__ pts
     }
     if (tid == 0) {
         feat[F_IN - 4] = (float)d / 16.0f;
-        feat[F_IN - 3] = (float)(log2((double)(n > 1 ? n : 1)) / 32.0);
+        feat[F_IN - 3] = (float)(log2((double)s) / 32.0);
         feat[F_IN - 2] = 0.0f;
         feat[F_IN - 1] = 0.0f;
     }
@@ -310,18 +359,26 @@ size_t sky_mlp_work_floats(int32_t batch)
     return (size_t)batch * (size_t)(2 * HID + OUT + OUT + 2 * HID) + 64;
 }
 
+size_t sky_features_work_floats(void) { return (size_t)kWorkFeat; }
+
 sky_status sky_features(const float* d_pts, int64_t n, int32_t d, int64_t ld, float* d_feat, float* d_range,
-                        void* stream)
+                        float* d_work, void* stream)
 {
-    if (d < 1 || d > DMAX || n < 1 || ld < d || !d_pts || !d_feat || !d_range)
+    if (d < 1 || d > DMAX || n < 1 || ld < d || !d_pts || !d_feat || !d_range || !d_work)
         return mfail(SKY_ERR_INVALID_ARGUMENT, "bad features arguments");
-    static bool attr = false;
+    if (reinterpret_cast<uintptr_t>(d_work) % 8 != 0) return mfail(SKY_ERR_INVALID_ARGUMENT, "work not 8-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t stride = (n + SAMPLE - 1) / SAMPLE > 1 ? (n + SAMPLE - 1) / SAMPLE : 1;
+    const int64_t s = (n + stride - 1) / stride;
+    const int tiles = (int)((s + kTileRows - 1) / kTileRows);
+    float* mm = d_work + kWorkMM;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(d_work + kWorkHist);
+    double* sums = reinterpret_cast<double*>(d_work + kWorkSum);
+    k_feat_minmax<<<tiles, kTileRows, 0, st>>>(d_pts, n, d, ld, mm);
     const int smem = kTileRows * DMAX * (int)sizeof(float);
-    if (!attr) {
-        cudaFuncSetAttribute(k_features, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
-    k_features<<<1, 1024, smem, static_cast<cudaStream_t>(stream)>>>(d_pts, n, d, ld, d_feat, d_range);
+    cudaFuncSetAttribute(k_feat_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_feat_tile<<<tiles, kTileRows, smem, st>>>(d_pts, n, d, ld, mm, tiles, hist, sums, d_range);
+    k_feat_final<<<1, 512, 0, st>>>(n, d, tiles, hist, sums, d_feat);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SKY_OK : mfail(SKY_ERR_CUDA, "features launch", e);
 }
@@ -391,16 +448,17 @@ sky_status sky_mlp_adamw(float* d_master, uint16_t* d_bf16, float* d_m, float* d
 }
 
 sky_status sky_propose(const float* d_pts, int64_t n, int32_t d, int64_t ld, const uint16_t* d_params_bf16,
-                       float inflate, float* d_prop, int32_t* h_log2g, float* d_work, void* stream)
+                       float inflate, int64_t n_ref, float* d_prop, int32_t* h_log2g, float* d_work, void* stream)
 {
-    if (!d_params_bf16 || !d_prop || !h_log2g || !d_work) return mfail(SKY_ERR_INVALID_ARGUMENT, "bad propose arguments");
+    if (!d_params_bf16 || !d_prop || !h_log2g || !d_work || n_ref < 0)
+        return mfail(SKY_ERR_INVALID_ARGUMENT, "bad propose arguments");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    float* feat = d_work;
+    float* feat = d_work + kWorkFeat;
     float* range = feat + F_IN;
     float* y = range + 2 * DMAX;
     float* act = y + OUT;
     int32_t* layer = reinterpret_cast<int32_t*>(act + 2 * HID);
-    sky_status st = sky_features(d_pts, n, d, ld, feat, range, stream);
+    sky_status st = sky_features(d_pts, n, d, ld, feat, range, d_work, stream);
     if (st != SKY_OK) return st;
     cudaError_t e = forward_impl(reinterpret_cast<const __nv_bfloat16*>(d_params_bf16), feat, 1, y, act, s);
     if (e == cudaSuccess) {
@@ -411,10 +469,18 @@ sky_status sky_propose(const float* d_pts, int64_t n, int32_t d, int64_t ld, con
     if (e == cudaSuccess) e = cudaMemcpyAsync(&lg, layer, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return mfail(SKY_ERR_CUDA, "propose", e);
+    if (n_ref > 0) {
+        // The network's layer is the best layer for a set of n_ref rows with
+        // these features; the automatic policy's change from n_ref to n rows
+        // carries it to this set's size.
+        lg += auto_log2g(n, d) - auto_log2g(n_ref, d);
+        const int top = 24 / d > 1 ? 24 / d : 1;
+        lg = lg < 1 ? 1 : (lg > top ? top : lg);
+    }
     *h_log2g = lg;
     return SKY_OK;
 }
 
-size_t sky_propose_work_floats(void) { return (size_t)(F_IN + 2 * DMAX + OUT + 2 * HID + 8); }
+size_t sky_propose_work_floats(void) { return (size_t)(kWorkFeat + F_IN + 2 * DMAX + OUT + 2 * HID + 8); }
 
 }  // extern "C"

@@ -53,7 +53,9 @@ struct PhaseClock {
 int count_kernels(const Plan& p, int n_prop)
 {
     const int passes = (p.morton_bits * p.d + 7) / 8;
-    return build_kernel_count(p) + (n_prop > 0 ? 1 : 0) + 1 + p.d + 1 + 3 * passes + 1 + 1 + 1;
+    const int through_c = build_kernel_count(p) + (n_prop > 0 ? 1 : 0) + 1 + prefix_kernel_count(p) + 2;
+    if (p.survivors_only) return through_c + 1;
+    return through_c + 3 * passes + 1 + 1 + 1;
 }
 
 sky_status fail(sky_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
@@ -117,9 +119,13 @@ size_t layout(Plan& p, char* base, bool grid_api)
     p.lb_counter = c.take<uint32_t>(4);
     p.lb_states = c.take<unsigned long long>(p.lb_tiles);
     p.occ = c.take<uint32_t>(p.words);
+    p.occ_stage = p.words <= kPrivWords ? c.take<uint32_t>((size_t)map_blocks_bound(n) * p.words) : nullptr;
     p.pre = c.take<uint32_t>(p.words);
     p.dom = grid_api ? c.take<uint32_t>(p.words) : nullptr;
-    p.keys = c.take<uint2>(n);
+    p.ckey = c.take<uint32_t>(n);
+    p.mkey = c.take<uint32_t>(n);
+    p.sflags = c.take<uint32_t>((n + 31) / 32);
+    p.scount = c.take<uint32_t>(kSurvMaxBlocks);
     p.surv_key = c.take<uint32_t>(n);
     p.surv_idx = c.take<uint32_t>(n);
     p.sort_key2 = c.take<uint32_t>(n);
@@ -174,7 +180,9 @@ sky_status make_plan(Plan& p, const float* pts, int64_t n, int32_t d, int64_t ld
     p.log2g = lg;
     p.morton_bits = morton_bits_for(n, d);
     p.tma_ok = (ld == d) && ((reinterpret_cast<uintptr_t>(pts) & 15u) == 0);
-    p.refine_cfg = opt ? opt->tile_cfg : 0;
+    if (opt && (opt->survivors_only < 0 || opt->survivors_only > 1))
+        return fail(SKY_ERR_INVALID_ARGUMENT, "survivors_only = %d outside {0, 1}", opt->survivors_only);
+    p.survivors_only = opt && opt->survivors_only == 1;
     if (opt && (opt->n_filter < 0 || opt->n_filter > 16))
         return fail(SKY_ERR_INVALID_ARGUMENT, "n_filter = %d outside [0, 16]", opt->n_filter);
     if (opt && opt->n_filter > 0 && !opt->d_filter_pts)
@@ -233,6 +241,11 @@ cudaError_t enqueue_pipeline(Plan& p, const float* prop, int n_prop, int32_t* ou
     clk.mark();
     if (e == cudaSuccess) e = launch_survivors(p, n_prop, s);
     clk.mark();
+    if (p.survivors_only) {
+        if (e == cudaSuccess) e = launch_copy_survivors(p, out, capacity, s);
+        clk.mark();
+        return e;
+    }
     if (e == cudaSuccess) e = launch_sort(p, s);
     clk.mark();
     if (e == cudaSuccess) e = launch_gather(p, s);
@@ -253,13 +266,14 @@ struct CacheKey {
     int dev = -1;
     const float* pts = nullptr;
     int64_t n = 0, ld = 0, cap = 0;
-    int d = 0, log2g = 0, mode = 0, n_prop = 0, timing = 0;
+    int d = 0, log2g = 0, mode = 0, n_prop = 0, timing = 0, surv_only = 0;
     const float* prop = nullptr;
     int32_t* out = nullptr;
     bool operator==(const CacheKey& o) const
     {
         return dev == o.dev && pts == o.pts && n == o.n && ld == o.ld && cap == o.cap && d == o.d &&
                log2g == o.log2g && mode == o.mode && n_prop == o.n_prop && timing == o.timing &&
+               surv_only == o.surv_only &&
                prop == o.prop && out == o.out;
     }
 };
@@ -344,6 +358,7 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
     CacheKey key;
     key.dev = dev; key.pts = pts; key.n = n; key.ld = ld; key.cap = capacity; key.d = d;
     key.log2g = p.log2g; key.mode = p.map_mode; key.n_prop = n_prop; key.timing = t_timing ? 1 : 0;
+    key.surv_only = p.survivors_only ? 1 : 0;
     key.prop = prop; key.out = out;
     const size_t bytes = layout(p, nullptr, false);
     CacheEntry* ce = cache_lookup(key, bytes, s, &st);
@@ -395,6 +410,8 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
     t_stats.n_filter_used = (int32_t)r.n_filter_used;
     t_stats.tiles = (int64_t)r.tiles;
     t_stats.group_scans = (int64_t)r.groups;
+    t_stats.code_hits = (int64_t)r.hits;
+    t_stats.exact_tests = (int64_t)r.exact;
     st = status_from_flags(r.err);
     if (st != SKY_OK) return st;
     *count = r.count;
@@ -529,7 +546,7 @@ sky_status sky_grid_stats(const sky_grid* g, sky_grid_stats_t* out)
 sky_status sky_grid_get_view(const sky_grid* g, sky_grid_view* out)
 {
     if (!g || !out) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL argument");
-    out->cell_key = reinterpret_cast<const uint32_t*>(g->plan.keys);
+    out->cell_key = g->plan.ckey;
     out->occupied = g->plan.occ;
     out->dominated = g->plan.dom;
     out->survivors = reinterpret_cast<const int32_t*>(g->plan.surv_idx);
@@ -546,15 +563,7 @@ sky_status sky_grid_copy_out(const sky_grid* g, sky_grid_array which, void* d_ds
     const void* src = nullptr;
     size_t need = 0;
     switch (which) {
-        case SKY_GRID_CELL_KEY: {
-            // the handle stores (cell key, Morton key) pairs: copy the first of each
-            need = sizeof(uint32_t) * (size_t)p.n;
-            if (bytes < need) return fail(SKY_ERR_CAPACITY, "array needs %zu bytes, got %zu", need, bytes);
-            if (p.n) SKY_CUDA(cudaMemcpy2DAsync(d_dst, sizeof(uint32_t), p.keys, sizeof(uint2), sizeof(uint32_t),
-                                                (size_t)p.n, cudaMemcpyDeviceToDevice, g->stream));
-            SKY_CUDA(cudaStreamSynchronize(g->stream));
-            return SKY_OK;
-        }
+        case SKY_GRID_CELL_KEY: src = p.ckey; need = sizeof(uint32_t) * (size_t)p.n; break;
         case SKY_GRID_OCCUPIED: src = p.occ; need = sizeof(uint32_t) * (size_t)p.words; break;
         case SKY_GRID_DOMINATED:
             if (!g->pruned) return fail(SKY_ERR_INVALID_ARGUMENT, "grid not pruned yet");

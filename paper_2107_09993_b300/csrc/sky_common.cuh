@@ -266,15 +266,13 @@ __device__ __forceinline__ void prefix_or_dim(uint32_t* R, int64_t words, int lo
         }
     } else if (slog + log2g <= 5) {
         // every line inside one word: log2(G) doubling steps with masks that
-        // keep each shifted bit inside its own line
+        // keep each shifted bit inside its own line (lane b of each warp
+        // votes for bit b; callers run whole, converged warps here)
+        const uint32_t lane = threadIdx.x & 31u;
         uint32_t mask[6];
         int nsteps = 0;
-        for (uint32_t j = 1; j < G; j <<= 1) {
-            uint32_t m = 0;
-            for (int b = 0; b < 32; ++b)
-                if (((uint32_t)(b >> slog) & (G - 1u)) >= j) m |= 1u << b;
-            mask[nsteps++] = m;
-        }
+        for (uint32_t j = 1; j < G; j <<= 1)
+            mask[nsteps++] = __ballot_sync(kFull, ((lane >> slog) & (G - 1u)) >= j);
         for (int64_t w = tid; w < words; w += nthr) {
             uint32_t x = R[w];
             int st = 0;
@@ -288,8 +286,7 @@ __device__ __forceinline__ void prefix_or_dim(uint32_t* R, int64_t words, int lo
         const int64_t Lw = 1ll << (slog + log2g - 5);
         const int e = 32 >> slog;
         const int sbits = 1 << slog;
-        uint32_t rep = 0;
-        for (int t = 0; t < e; ++t) rep |= 1u << (t << slog);
+        const uint32_t rep = __ballot_sync(kFull, ((threadIdx.x & 31u) & (uint32_t)(sbits - 1)) == 0u);
         const int64_t ngroups = words / Lw;
         for (int64_t g = tid; g < ngroups; g += nthr) {
             uint32_t* p = R + g * Lw;

@@ -16,10 +16,11 @@ struct DevResult {
     unsigned long long pairs;  // candidate pairs examined by the refinement
     uint32_t occupied_cells;   // filled on request (grid statistics)
     uint32_t surviving_cells;
-    uint32_t redo;             // automatic value map: 1 = second map pass with min/max scales
-    uint32_t pad;
+    uint32_t pad[2];
     unsigned long long tiles;  // q-tiles streamed by the refinement (all CTAs)
     unsigned long long groups; // (warp, p-group) list scans in the refinement
+    unsigned long long hits;   // pairs with code(q) <= code(p) in every dimension
+    unsigned long long exact;  // pairs that ran the float test
 };
 
 
@@ -38,14 +39,18 @@ struct Plan {
     int map_mode = kMapAuto;   // MapMode
     bool tma_ok = false;       // 16-byte aligned and ld == d
     int morton_bits = 0;       // bits per dimension of the sort key
-    int refine_cfg = 0;
+    bool survivors_only = false;   // stop after step (c)
 
     // workspace (device)
     uint32_t* mm_min = nullptr;      // [d] ordered-uint min
     uint32_t* mm_max = nullptr;      // [d] ordered-uint max
     float* params = nullptr;         // [4][16]: offset, cell scale, code scale, morton scale
-    uint2* keys = nullptr;           // [n] (cell key, Morton key) per point
+    uint32_t* ckey = nullptr;        // [n] cell key per point (Eq. 1 columns packed)
+    uint32_t* mkey = nullptr;        // [n] Morton key per point (spatial sort key)
+    uint32_t* sflags = nullptr;      // [ceil(n / 32)] survivor flag bits of step (c)
+    uint32_t* scount = nullptr;      // [kSurvMaxBlocks] survivors per block of step (c)
     uint32_t* occ = nullptr;         // [words] occupancy bitmap
+    uint32_t* occ_stage = nullptr;   // [map blocks][words] private bitmaps (grids of <= kPrivWords words)
     uint32_t* pre = nullptr;         // [words] inclusive prefix-OR of occ
     uint32_t* dom = nullptr;         // [words] dominated bitmap (grid API only)
     int64_t words = 0;
@@ -102,6 +107,9 @@ struct QueryPlan {
 };
 
 constexpr int kRefineTile = 128;   // points per refinement tile
+constexpr int kSurvMaxBlocks = 4096;  // blocks of the survivor passes (at most 4 per SM)
+constexpr int kMapMaxBlocks = 1024;   // blocks of the map pass
+constexpr int64_t kPrivWords = 2048;  // grids of at most 2^16 cells are marked in shared memory first
 constexpr int kScanItems = 8;      // items per thread in the look-back scans
 constexpr int kScanThreads = 256;
 constexpr int kScanTile = kScanItems * kScanThreads;
@@ -120,9 +128,12 @@ void plan_carve(Plan& p, void* ws, bool grid_api);
 cudaError_t launch_build(const Plan& p, cudaStream_t s);
 int build_kernel_count(const Plan& p);
 cudaError_t launch_prefix_or(const Plan& p, cudaStream_t s);
+int prefix_kernel_count(const Plan& p);
+int map_blocks_bound(int64_t n);
 cudaError_t launch_dominated(const Plan& p, cudaStream_t s);
 cudaError_t launch_snap(const Plan& p, const float* d_prop, int n_prop, cudaStream_t s);
 cudaError_t launch_survivors(const Plan& p, int n_filter, cudaStream_t s);
+cudaError_t launch_copy_survivors(const Plan& p, int32_t* out, int64_t capacity, cudaStream_t s);
 cudaError_t launch_cell_stats(const Plan& p, cudaStream_t s);
 // k_sort.cu
 cudaError_t launch_sort(Plan& p, cudaStream_t s);

@@ -109,6 +109,9 @@ extern "C" sky_status sky_skyline_noalloc(const float* d_pts, int64_t n, int32_t
     p.log2g = lg;
     p.morton_bits = morton_bits_for(n, d);
     p.tma_ok = (ld == d) && ((reinterpret_cast<uintptr_t>(d_pts) & 15u) == 0);
+    if (opt && (opt->survivors_only < 0 || opt->survivors_only > 1))
+        return noalloc_fail(SKY_ERR_INVALID_ARGUMENT, "survivors_only outside {0, 1}");
+    p.survivors_only = opt && opt->survivors_only == 1;
     if (plan_workspace_bytes(n, d, lg, false) > kScratchBytes)
         return noalloc_fail(SKY_ERR_TOO_LARGE, "workspace exceeds the fixed scratch array");
 
@@ -124,10 +127,14 @@ extern "C" sky_status sky_skyline_noalloc(const float* d_pts, int64_t n, int32_t
     if (e == cudaSuccess) e = launch_snap(p, n_prop ? opt->d_filter_pts : nullptr, n_prop, s);
     if (e == cudaSuccess) e = launch_prefix_or(p, s);
     if (e == cudaSuccess) e = launch_survivors(p, n_prop, s);
-    if (e == cudaSuccess) e = launch_sort(p, s);
-    if (e == cudaSuccess) e = launch_gather(p, s);
-    if (e == cudaSuccess) e = launch_refine(p, s);
-    if (e == cudaSuccess) e = launch_emit(p, d_out_idx, out_capacity, s);
+    if (p.survivors_only) {
+        if (e == cudaSuccess) e = launch_copy_survivors(p, d_out_idx, out_capacity, s);
+    } else {
+        if (e == cudaSuccess) e = launch_sort(p, s);
+        if (e == cudaSuccess) e = launch_gather(p, s);
+        if (e == cudaSuccess) e = launch_refine(p, s);
+        if (e == cudaSuccess) e = launch_emit(p, d_out_idx, out_capacity, s);
+    }
     DevResult r{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, p.res, sizeof(DevResult), cudaMemcpyDeviceToHost, s);
     const cudaError_t es = cudaStreamSynchronize(s);

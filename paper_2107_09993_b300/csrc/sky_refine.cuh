@@ -233,6 +233,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
         // ------------------------------------------------------------ consumers
         const int qi = warp * 32 + lane;
         unsigned long long pairs = 0, gscans = 0;
+        uint32_t hits = 0, exact = 0;   // per lane
         for (uint32_t k = 0;; ++k) {
             const int s = (int)(k % S);
             const bool ok = mbar_wait(&sm.full[s], (k / S) & 1u, err);
@@ -272,11 +273,13 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                             a &= D[w];
                         }
                         if (a == kHigh) {  // code(q) <= code(p) in every dimension
+                            ++hits;
                             uint32_t eq = 0;
 #pragma unroll
                             for (int w = 0; w < DW; ++w) eq |= has_zero_byte(D[w] ^ kHigh);
                             bool dom = true;   // strictly lower code everywhere: q < p everywhere
                             if (eq) {
+                                ++exact;
                                 const float* qx = &sm.qX[s][qi * DP];
                                 const float* px = &sm.pX[pi * DP];
                                 bool le = true, lt = false;
@@ -302,6 +305,9 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
         }
         if (lane == 0 && pairs) atomicAdd(&res->pairs, pairs);  // 32 q-lanes per listed p, per warp
         if (lane == 0 && gscans) atomicAdd(&res->groups, gscans);
+        const uint32_t wh = __reduce_add_sync(kFull, hits), we = __reduce_add_sync(kFull, exact);
+        if (lane == 0 && wh) atomicAdd(&res->hits, (unsigned long long)wh);
+        if (lane == 0 && we) atomicAdd(&res->exact, (unsigned long long)we);
     }
     __syncthreads();
     if (tid < kTQ && pbase + tid < m && !sm.failed && ((sm.livemask[tid >> 5] >> (tid & 31)) & 1u))

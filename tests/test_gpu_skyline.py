@@ -147,6 +147,54 @@ def test_cell_grid_matches_oracle():
         g.close()
 
 
+@pytest.mark.parametrize("d,lg", [(2, 9), (2, 12), (2, 13), (3, 6), (3, 8), (3, 9), (4, 5), (4, 6), (5, 5),
+                                  (6, 4), (7, 3), (8, 3), (9, 3), (10, 2), (12, 2), (13, 2), (16, 1)])
+def test_large_grid_prefix_matches_oracle(d, lg):
+    """Grids of 2^16 .. 2^27 cells, where the prefix-OR splits into blocks
+    of low dimensions and rows of high dimensions: the dominated bitmap and
+    the survivors equal Definition 3 computed by the oracle's box identity."""
+    rng = np.random.default_rng(d * 100 + lg)
+    n = 6000
+    kind = ["independent", "correlated", "anticorrelated"][(d + lg) % 3]
+    P = skydata.generate(kind, n, d, seed=d + lg)
+    # a few points near the low corner and clusters make long dominated runs
+    P[:50] = (rng.random((50, d)) * 0.2).astype(np.float32)
+    g = sky.Grid(dev(P), log2_g=lg, assume_unit=True).prune()
+    want_keys = oracle.cell_keys(P, lg, assume_unit=True)
+    keys = g.cell_keys().cpu().numpy().view(np.uint32).astype(np.uint64)
+    assert np.array_equal(keys, want_keys)
+    ncell = 1 << (lg * d)
+    occ = oracle.occupancy(want_keys, d, lg)
+    want_dom = oracle.dominated_cells(occ, d, lg)
+    dom_bits = np.unpackbits(g.dominated().cpu().numpy().view(np.uint8), bitorder="little")[:ncell]
+    assert np.array_equal(dom_bits, want_dom)
+    surv = g.survivors().cpu().numpy()
+    assert surv.tolist() == np.flatnonzero(want_dom[want_keys.astype(np.int64)] == 0).tolist()
+    g.close()
+    # the full path on the same grid returns the exact skyline
+    assert gpu_sky(P, log2_g=lg, assume_unit=True) == oracle.skyline_sfs(P).tolist()
+
+
+def test_survivors_only_returns_step_c_candidates():
+    """survivors_only stops after step (c): the rows whose cell no occupied
+    cell dominates (Definition 3, the oracle's box identity on the oracle's
+    cell keys), ascending; a superset of the skyline."""
+    for i, (kind, n, d) in enumerate([("independent", 50000, 4), ("correlated", 120000, 6),
+                                      ("anticorrelated", 30000, 3), ("independent", 300000, 8)]):
+        P = skydata.generate(kind, n, d, seed=40 + i)
+        x = dev(P)
+        got = sky.skyline(x, survivors_only=True).cpu().numpy()
+        lg = sky.last_run_stats()["log2_g"]
+        keys = oracle.cell_keys(P, lg, mode="auto")
+        dom = oracle.dominated_cells(oracle.occupancy(keys, d, lg), d, lg)
+        want = np.flatnonzero(dom[keys.astype(np.int64)] == 0)
+        assert got.tolist() == want.tolist(), (kind, n, d)
+        assert set(oracle.skyline_sfs(P).tolist()) <= set(got.tolist())
+        with pytest.raises(sky.SkyError) as e:
+            sky.skyline(x, survivors_only=True, capacity=len(want) - 1)
+        assert e.value.name == "SKY_ERR_CAPACITY"
+
+
 def test_fig1_and_fig2_dominated_cells(golden):
     g1 = golden("fig1_layer4.json")
     G = 1 << g1["log2g"]

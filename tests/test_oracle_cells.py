@@ -86,6 +86,39 @@ def test_automatic_map_choice():
         assert cols[np.argmin(narrow[:, k]), k] == 0 and cols[np.argmax(narrow[:, k]), k] == 15
 
 
+def test_automatic_map_decides_on_a_strided_sample():
+    """Above 4096 rows the automatic map looks at rows 0, t, 2t, ... with
+    t = ceil(n / 4096) only. An outlier off the sample leaves Eq. 1 in place
+    (it is clamped into an edge column); on the sample it switches to the
+    sample's min / max. Either way the map is monotone in every dimension."""
+    rng = np.random.default_rng(9)
+    n = 10_000                                   # t = 3
+    P = rng.random((n, 3), dtype=np.float32)
+    P[0] = 0.0
+    P[3] = 0.999
+    off_row = P.copy()
+    off_row[3 * 1000 + 1, 1] = 7.0               # not a multiple of 3
+    assert np.array_equal(oracle.cell_keys(off_row, 4, mode="auto"), oracle.cell_keys(off_row, 4, mode="unit"))
+    assert oracle.cell_columns(int(oracle.cell_keys(off_row, 4, mode="auto")[3001]), 3, 4)[1] == 15
+    on_row = P.copy()
+    on_row[3 * 1000, 1] = 7.0                    # a sampled row
+    off, sc = oracle.cell_params(on_row, 4, mode="auto")
+    S = on_row[::3]
+    assert np.array_equal(off, S.min(axis=0))
+    assert np.array_equal(sc, (np.float32(16) / (S.max(axis=0) - S.min(axis=0))).astype(np.float32))
+    # rows below the sample's minimum fall into column 0
+    low = on_row.copy()
+    low[5, 0] = -3.0
+    keys = oracle.cell_keys(low, 4, mode="auto")
+    assert oracle.cell_columns(int(keys[5]), 3, 4)[0] == 0
+    # monotone: a componentwise smaller point never gets a larger column
+    for Q in (off_row, on_row, low):
+        cols = np.array([oracle.cell_columns(int(k), 3, 4) for k in oracle.cell_keys(Q, 4, mode="auto")])
+        for k in range(3):
+            o = np.argsort(Q[:, k], kind="stable")
+            assert np.all(np.diff(cols[o, k]) >= 0)
+
+
 # ---------------------------------------------------------- Definitions ---
 
 def _occ_from_cells(cells_c0_first, d, log2g):
@@ -263,3 +296,22 @@ def test_corollaries_3_4_and_soundness(kind):
                 parent = tuple(c // 2 for c in oracle.cell_columns(k, d, L))
                 assert pcand[oracle.cell_key(parent, pL)]
         prev = (key, cand, L)
+
+
+def test_dominated_cells_box_identity_matches_enumeration():
+    """Two computations of Definition 3 agree: enumeration over all cell
+    pairs (C) and the cumulative-OR box identity (numpy)."""
+    rng = np.random.default_rng(21)
+    for d, lg in [(1, 5), (2, 3), (2, 4), (3, 2), (3, 3), (4, 2), (5, 1), (6, 1)]:
+        ncell = 1 << (lg * d)
+        for density in (0.01, 0.1, 0.5):
+            occ = (rng.random(ncell) < density).astype(np.uint8)
+            dom, _, _, _ = oracle.cell_classes(occ, d, lg)
+            assert np.array_equal(oracle.dominated_cells(occ, d, lg), dom), (d, lg, density)
+    # one occupied cell dominates exactly the cells strictly above it
+    d, lg = 3, 2
+    occ = np.zeros(64, np.uint8)
+    occ[oracle.cell_key((1, 0, 2), lg)] = 1
+    dom = oracle.dominated_cells(occ, d, lg)
+    want = [oracle.cell_key((a, b, c), lg) for a in range(2, 4) for b in range(1, 4) for c in range(3, 4)]
+    assert sorted(np.flatnonzero(dom).tolist()) == sorted(want)

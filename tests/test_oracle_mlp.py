@@ -92,6 +92,17 @@ def test_features_of_constructed_data():
     assert abs(tri[idx[(0, 3)]]) < 0.1
     assert np.allclose([tri[idx[(k, l)]] for k in range(16) for l in range(k + 1, 16) if l >= 4], 0)
     assert np.isclose(f[-4], 4 / 16) and np.isclose(f[-3], np.log2(n) / 32)
+    # above 65,536 rows the features see every ceil(n / 65,536)-th row: for
+    # n = 200,001 that is every 4th row, 50,001 rows, and the size feature
+    # is that sample's log2 / 32
+    big = np.tile(P, (63, 1))[:200_001]
+    fb = mlp.features(big)
+    assert np.isclose(fb[-3], np.log2(50_001) / 32)
+    # dimension 0 of row i is (i mod 32 + 0.5) / 32: every 4th row leaves 8
+    # distinct values, 6,251 rows of residue 0 and 6,250 of each other one
+    h0 = fb[:mlp.DMAX * mlp.BINS].reshape(16, 32)[0]
+    assert np.count_nonzero(h0) == 8 and np.isclose(h0.sum(), 1.0)
+    assert np.isclose(h0.max(), 6251 / 50_001) and np.isclose(h0[h0 > 0].min(), 6250 / 50_001)
     # a constant dimension has an empty correlation row
     Q = P.copy()
     Q[:, 1] = 0.3
