@@ -9,6 +9,8 @@ per step. Inputs are resident in HBM when the timed region starts; L2 (126 MB)
 is flushed before every timed step by writing a 512 MB buffer.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sky|reference]
+    python bench.py --case KIND:N:D[:survivors] [--seed S] [--steps K] [--warmup W]   (one input)
+    python bench.py --batched [--steps K] [--warmup W]                  (4,096-query batched workload)
 
 N > 1 runs independent replicas (the skyline of one point set is computed on
 one GPU), launched under torchrun, weak scaling.
@@ -41,8 +43,13 @@ KINDS = ("independent", "correlated", "anticorrelated")
 METRIC = "skyline input points/s (exact)"
 UNIT = "points/s"
 CPU_SAMPLE_ROWS = 100_000
+# the paper's largest run: 3.2e9 correlated points, d = 4, layer 6 (Sec. 7).
+# Drawn with rows outside the unit cube redrawn instead of clipped: clipping
+# piles points onto the faces (x_k = 0), which at 3.2e9 rows gives millions of
+# skyline points; the paper's correlated set has 4,203.
+PAPER_SCALE = ("correlated_inside", 3_200_000_000, 4)
 # pruning pass (steps a-c) measured alone on inputs larger than L2
-PRUNE_N = 10_000_000
+PRUNE_SETS = (("anticorrelated", 10_000_000, 16), ("independent", 10_000_000, 12))
 PRUNE_REPS = 10
 
 
@@ -111,9 +118,12 @@ def measured_peaks():
 
 
 def refine_source_hash():
-    src = os.path.join(ROOT, "paper_2107_09993_b300", "csrc", "k_refine.cu")
-    with open(src, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the refinement's source (kernel file and its device body)."""
+    h = hashlib.sha256()
+    for name in ("k_refine.cu", "sky_refine.cuh"):
+        with open(os.path.join(ROOT, "paper_2107_09993_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel):
@@ -138,16 +148,17 @@ def ops_per_pair(d):
 # ------------------------------------------------------------------ sky arm --
 def prune_roofline(sky, torch, dev, flush, peaks, peak_src):
     """Steps (a)-(c) alone (survivors_only calls, replayed as CUDA graphs)
-    on the three families at n = 10^7, d = 8 (320 MB each, above L2), timed
-    with CUDA events on the calling stream, L2 flushed before every call.
+    on the inputs larger than L2 that the roofline is quoted on: n = 10^7
+    anti-correlated at d = 16 (640 MB) and independent at d = 12 (480 MB),
+    seed 1; CUDA events on the calling stream, L2 flushed before every call.
     Algorithmic bytes per call: 4nd (map read) + 16n (cell and Morton keys
     written and read) + 8m (survivor keys and ids written)."""
     stream = torch.cuda.current_stream(dev)
-    per_kind = {}
+    per_set = {}
     tot_b, tot_ms = 0, 0.0
-    for kind in KINDS:
-        x = torch.from_numpy(skydata.generate(kind, PRUNE_N, DIM, SEED)).to(dev)
-        out = torch.empty(PRUNE_N, dtype=torch.int32, device=dev)
+    for kind, n, d in PRUNE_SETS:
+        x = torch.from_numpy(skydata.generate(kind, n, d, SEED)).to(dev)
+        out = torch.empty(n, dtype=torch.int32, device=dev)
         for _ in range(3):
             sky.skyline(x, survivors_only=True, out=out)
         ms = []
@@ -161,23 +172,56 @@ def prune_roofline(sky, torch, dev, flush, peaks, peak_src):
             torch.cuda.synchronize(dev)
             ms.append(e0.elapsed_time(e1))
         st = sky.last_run_stats()
-        b = 4 * PRUNE_N * DIM + 16 * PRUNE_N + 8 * st["survivors"]
+        b = 4 * n * d + 16 * n + 8 * st["survivors"]
         med = statistics.median(ms)
-        per_kind[kind] = {"ms": round(med, 4), "survivors": st["survivors"], "log2_g": st["log2_g"],
-                          "gbs": round(b / (med / 1e3) / 1e9, 1)}
+        per_set[f"{kind} n={n} d={d}"] = {"ms": round(med, 4), "survivors": st["survivors"],
+                                          "log2_g": st["log2_g"], "gbs": round(b / (med / 1e3) / 1e9, 1)}
         tot_b += b
         tot_ms += med
         del x, out
     gbs = tot_b / (tot_ms / 1e3) / 1e9
-    return {"kernel": "pruning pass: k_sample_params, k_map_mark_tma, k_prefix_low/high, k_surv_flags, "
-                      "k_surv_scatter (+ k_copy_survivors, timed but not counted)",
+    return {"kernel": "pruning pass: k_sample_params, k_map_mark_tma (+ k_occ_merge), k_prefix_low/high, "
+                      "k_surv_flags, k_surv_scatter (+ k_copy_survivors, timed but not counted)",
             "bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": None,
+            "frac": round(gbs / peaks["hbm_gbs"], 4),
+            "frac_of_nominal_8000": round(gbs / 8000.0, 4),
+            "traffic": None,
             "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json)" if peak_src == "measured"
             else "fallback 6.4 TB/s",
-            "workload": f"n={PRUNE_N:,} x d={DIM} float32, {', '.join(KINDS)} (seed {SEED}); median of "
-                        f"{PRUNE_REPS} calls each, L2 flushed before every call",
-            "per_distribution": per_kind}
+            "workload": "; ".join(f"{k} n={n:,} d={d}" for k, n, d in PRUNE_SETS)
+                        + f" (seed {SEED}); median of {PRUNE_REPS} calls each, L2 flushed before every call",
+            "per_set": per_set}
+
+
+def paper_scale(sky, torch, dev):
+    """The paper's largest workload on one B300: 3.2e9 correlated points,
+    d = 4, drawn on the device (skydata.generate_torch, seed 1), skyline by
+    sky_skyline_chunked from device memory (the automatic layer is 6, the
+    paper's rho). Median of 3 calls after one warm-up, CUDA events."""
+    kind, n, d = PAPER_SCALE
+    need = n * d * 4 + (16 << 30)
+    free, _ = torch.cuda.mem_get_info(dev)
+    if free < need:
+        return {"skipped": f"needs about {need / 2**30:.0f} GiB free device memory, {free / 2**30:.0f} GiB free"}
+    x = skydata.generate_torch(kind, n, d, SEED, device=dev)
+    r = sky.skyline_chunked(x)
+    ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = sky.skyline_chunked(x)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    st = sky.last_run_stats()
+    med = statistics.median(ms)
+    del x
+    torch.cuda.empty_cache()
+    return {"workload": f"{kind} n={n:,} d={d}, device-resident, drawn on the GPU (seed {SEED})",
+            "ms": round(med, 2), "points_per_s": round(n / (med / 1e3), 1), "skyline": int(r.numel()),
+            "candidates_after_step_c": st["n"], "log2_g_refine": st["log2_g"],
+            "paper": {"seconds": 0.6, "points_per_s": 5.3e9, "skyline": 4203,
+                      "hardware": "Quadro RTX 6000 (Turing, 24 GB); its generator and timing boundaries differ"}}
 
 
 def run_sky(args):
@@ -334,7 +378,8 @@ def run_sky(args):
         "gpu_launches": launches,
         "roofline": roofline,
         "roofline_prune": roof_prune,
-        "roofline_prune_large": prune_roofline(sky, torch, dev, flush, peaks, peak_src),
+        "roofline_prune_large": None if args.no_extras else prune_roofline(sky, torch, dev, flush, peaks, peak_src),
+        "paper_scale": None if args.no_extras else paper_scale(sky, torch, dev),
         "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in phase_sum.items()},
         "skyline_sizes": sizes,
         "clocks": clk,
@@ -395,6 +440,94 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_case(args):
+    """One named input (for profiling runs): `--case KIND:N:D[:survivors]`
+    runs `warmup` untimed and `steps` timed sky_skyline calls on the seeded
+    set and prints one JSON line with their median time and the run stats."""
+    import torch
+    import paper_2107_09993_b300 as sky
+
+    parts = args.case.split(":")
+    kind, n, d = parts[0], int(parts[1]), int(parts[2])
+    surv = len(parts) > 3 and parts[3] == "survivors"
+    x = torch.from_numpy(skydata.generate(kind, n, d, args.seed)).cuda()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        sky.skyline(x, survivors_only=surv, out=out)
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sky.skyline(x, survivors_only=surv, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"case": args.case, "seed": args.seed, "calls": args.steps,
+                      "ms_median": round(statistics.median(ms), 4) if ms else None,
+                      "stats": sky.last_run_stats()}), flush=True)
+
+
+def run_batched(args):
+    """The batched workload: 4,096 skyline queries (row count log-uniform in
+    [1e3, 1e6], d uniform in {2..12}, random column subsets and row ranges) on
+    a 20M x 12 float32 table, half independent and half anti-correlated
+    (seed 2), stored column-major on the device. One CUDA-graph launch per
+    step; `steps` timed launches after `warmup`. Reference point: the same
+    first 256 queries as plain sky_skyline calls in a loop (columns gathered
+    per query) against one batched launch of those 256. One JSON line."""
+    import torch
+    import paper_2107_09993_b300 as sky
+
+    n_rows, n_cols, nq = 20_000_000, 12, 4096
+    T = skydata.mixed_table(n_rows, n_cols, seed=2)
+    q = skydata.batched_queries(nq, n_rows, n_cols, seed=2)
+    t = torch.from_numpy(T).cuda()
+    tc = t.t().contiguous().t()
+    b = sky.Batch(tc, q)
+    for _ in range(args.warmup):
+        b.run()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    st = b.stats()
+    bad = int((b.query_status() != 0).sum())
+    b.close()
+    sel = q[:256]
+    b2 = sky.Batch(tc, sel)
+    b2.run()
+    ms_b = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b2.run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_b.append(e0.elapsed_time(e1))
+    b2.close()
+    ms_l = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (r0, c, m) in sel:
+            cols = [k for k in range(n_cols) if (int(m) >> k) & 1]
+            sky.skyline(t[int(r0):int(r0) + int(c)][:, cols].contiguous())
+        torch.cuda.synchronize()
+        ms_l.append((time.perf_counter() - t0) * 1e3)
+    med = statistics.median(ms)
+    pts = int(q[:, 1].sum())
+    print(json.dumps({
+        "workload": "batched: 4,096 queries on a 20M x 12 mixed table (seed 2), one graph launch",
+        "points": pts, "ms_per_launch": round(med, 2), "points_per_s": round(pts / (med / 1e3), 1),
+        "skyline": st["skyline"], "survivors": st["survivors"], "query_errors": bad,
+        "first_256": {"batched_ms": round(min(ms_b), 2), "looped_plain_ms": round(min(ms_l), 2),
+                      "speedup": round(min(ms_l) / min(ms_b), 2)}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -403,7 +536,19 @@ def main():
     ap.add_argument("--impl", choices=["sky", "reference"], default="sky")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the large-input pruning roofline and the paper-scale run (launch-list profiling)")
+    ap.add_argument("--batched", action="store_true", help="time the batched workload (4,096 queries) only")
+    ap.add_argument("--seed", type=int, default=SEED, help="seed of the --case input")
+    ap.add_argument("--case", default=None,
+                    help="KIND:N:D[:survivors] -- time one seeded input only (profiling runs)")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
+    if args.batched:
+        run_batched(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -200,12 +200,19 @@ SKY_API sky_status sky_skyline_host(const float* h_pts, int64_t n, int32_t d, in
 /* ------------------------------------------------------------------------ */
 
 /* One query: rows [row_begin, row_begin + row_count) of the table, with the
- * columns whose bits are set in dim_mask (1 to 16 columns) as attributes. */
+ * columns whose bits are set in dim_mask (1 to 16 columns) as attributes.
+ * With SKY_QUERY_QUADRANT in flags it is a quadrant query (the query
+ * experiments of Sec. 7): the point `origin` (one value per selected column,
+ * in column order) becomes the origin and only the rows >= origin in every
+ * selected column take part; their skyline is returned (shifting them by the
+ * origin would not change it). */
+#define SKY_QUERY_QUADRANT 1u
 typedef struct sky_query {
     int64_t row_begin;
     int64_t row_count;
     uint32_t dim_mask;
-    uint32_t reserved;            /* must be 0 */
+    uint32_t flags;               /* 0 or SKY_QUERY_QUADRANT */
+    float origin[16];             /* used with SKY_QUERY_QUADRANT */
 } sky_query;
 
 /* Tuning knobs (zero-initialise; see paper_2107_09993_b300/tune.py). */
@@ -333,6 +340,40 @@ SKY_API sky_status sky_propose(const float* d_pts, int64_t n, int32_t d, int64_t
                                void* stream);
 SKY_API size_t sky_propose_work_floats(void);
 SKY_API const char* sky_mlp_last_error(void);
+
+/*
+ * Skyline of a point set that one sky_skyline call cannot take: up to 2^40
+ * rows, in device memory or in host memory (streamed through the GPU).
+ * Steps (a)-(c) run chunk by chunk against one occupancy bitmap of the whole
+ * set [Eq. 1, Definition 3, Corollary 4]: a first pass marks every chunk's
+ * cells, then (after the prefix-OR) a second pass appends the rows of
+ * non-dominated cells, coordinates and 64-bit row ids, to a candidate
+ * buffer; one in-core refinement of the candidates gives the skyline
+ * [Definition 1]. The value map is decided once for all n rows (the rule of
+ * sky_options.assume_unit over the whole set). Paper: Sec. 7 runs 3.2e9
+ * points, more than one device holds at d >= 2 in the paper's hardware.
+ *
+ *   pts            n x d float32, row stride ld floats; device memory when
+ *                  host_pts = 0, host memory when host_pts = 1 (pinned
+ *                  memory streams fastest; each pass reads it once).
+ *   opt            log2_g, assume_unit and survivors_only as for
+ *                  sky_skyline; filter proposals are not accepted here.
+ *   chunk_rows     rows per chunk, 1 .. 2^30; 0 = 2^28 (device input) or
+ *                  2^26 (host input). Device workspace ~16 B per chunk row
+ *                  (+ two staging chunks of 4d B per row for host input).
+ *   max_candidates capacity of the candidate buffer (4d + 8 B each),
+ *                  1 .. 2^31 - 1; 0 = min(n, 2^28). More candidates after
+ *                  step (c) -> SKY_ERR_CAPACITY, message with the count.
+ *   d_out_ids      device int64[capacity]: ascending row ids of the skyline
+ *                  (of the candidates when survivors_only = 1); *h_count
+ *                  gets their number, also when it exceeds capacity
+ *                  (SKY_ERR_CAPACITY, nothing written).
+ * Synchronises with `stream` before returning; the library's memory is
+ * allocated and released inside the call.
+ */
+SKY_API sky_status sky_skyline_chunked(const float* pts, int32_t host_pts, int64_t n, int32_t d, int64_t ld,
+                                       const sky_options* opt, int64_t chunk_rows, int64_t max_candidates,
+                                       int64_t* d_out_ids, int64_t capacity, int64_t* h_count, void* stream);
 
 /* Work counters of the last sky_skyline / sky_skyline_host call made on the
  * calling thread (for measurement; not part of the result). */

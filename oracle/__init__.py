@@ -213,10 +213,22 @@ def cell_classes(occ, d: int, log2g: int):
 
 
 def skyline_subset(table, row_begin: int, row_count: int, dim_mask: int,
-                   threads: int = 0, method: str = "sfs") -> np.ndarray:
+                   threads: int = 0, method: str = "sfs", origin=None) -> np.ndarray:
     """Skyline of rows [row_begin, row_begin+row_count) over the columns in
-    dim_mask, returned as ascending global row ids (int32)."""
+    dim_mask, returned as ascending global row ids (int32).
+
+    origin (quadrant query, the paper's query experiments in Sec. 7): the
+    query point becomes the origin and only the rows in its upper quadrant
+    (row >= origin in every selected column) take part; since Definition 1
+    compares coordinates pairwise, shifting those rows by the origin leaves
+    their skyline unchanged, so it is the skyline of the kept rows as they
+    are."""
     cols = [k for k in range(table.shape[1]) if (dim_mask >> k) & 1]
     sub = np.ascontiguousarray(table[row_begin:row_begin + row_count][:, cols])
+    keep = np.arange(sub.shape[0])
+    if origin is not None:
+        o = np.asarray(origin, dtype=np.float32)[:len(cols)]
+        keep = np.flatnonzero(np.all(sub >= o, axis=1))
+        sub = np.ascontiguousarray(sub[keep])
     f = skyline_sfs if method == "sfs" else skyline_brute
-    return (f(sub, threads) + row_begin).astype(np.int32)
+    return (keep[f(sub, threads)] + row_begin).astype(np.int32)

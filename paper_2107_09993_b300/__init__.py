@@ -75,6 +75,8 @@ def load():
     sig = {
         "sky_skyline": ([_vp, _i64, _i32, _i64, P(Options), _vp, _i64, P(_i64), _vp], _i32),
         "sky_skyline_host": ([_vp, _i64, _i32, _i64, P(Options), _vp, _i64, P(_i64), _vp], _i32),
+        "sky_skyline_chunked": ([_vp, _i32, _i64, _i32, _i64, P(Options), _i64, _i64, _vp, _i64, P(_i64), _vp],
+                                _i32),
         "sky_build_grid": ([_vp, _i64, _i32, _i64, P(Options), _vp, P(_vp)], _i32),
         "sky_prune_cells": ([_vp, _vp, _i32, _vp], _i32),
         "sky_grid_stats": ([_vp, P(GridStats)], _i32),
@@ -178,6 +180,37 @@ def skyline_host(points, log2_g=None, assume_unit=False, capacity=None, stream=N
     return out[:cnt.value]
 
 
+def skyline_chunked(points, log2_g=None, assume_unit=False, survivors_only=False, chunk_rows=0,
+                    max_candidates=0, capacity=None, stream=None):
+    """sky_skyline_chunked: skyline of a set beyond one in-core call, processed
+    in chunks against one occupancy bitmap. `points` is a float32 [n, d] CUDA
+    tensor (device input) or CPU tensor / numpy array (host input, streamed;
+    pin it for speed). Returns ascending int64 row ids (CUDA tensor)."""
+    torch = _torch()
+    lib = load()
+    if not isinstance(points, torch.Tensor):
+        import numpy as np
+        points = torch.from_numpy(np.ascontiguousarray(points, dtype=np.float32))
+    host = not points.is_cuda
+    if points.dim() == 1:
+        points = points.view(-1, 1)
+    assert points.dtype == torch.float32 and points.stride(1) == 1
+    n, d = int(points.shape[0]), int(points.shape[1])
+    ld = int(points.stride(0)) if n > 1 else d
+    dev = points.device if not host else torch.device("cuda", torch.cuda.current_device())
+    cap = n if capacity is None else int(capacity)
+    out = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+    cnt = _i64(0)
+    o = _opts(log2_g, assume_unit, None, survivors_only)
+    st = lib.sky_skyline_chunked(_vp(points.data_ptr()), 1 if host else 0, n, d, ld, ctypes.byref(o),
+                                 int(chunk_rows), int(max_candidates), _vp(out.data_ptr()), cap,
+                                 ctypes.byref(cnt), _stream_ptr(stream))
+    if st == 3:
+        raise SkyError(st, f"{lib.sky_last_error().decode()} (count={cnt.value})")
+    _check(st)
+    return out[:cnt.value]
+
+
 def last_run_stats() -> dict:
     s = RunStats()
     _check(load().sky_last_run_stats(ctypes.byref(s)))
@@ -263,9 +296,12 @@ def version() -> str:
 
 
 # ---------------------------------------------------------------- batched --
+QUERY_QUADRANT = 1
+
+
 class Query(ctypes.Structure):
     _fields_ = [("row_begin", _i64), ("row_count", _i64), ("dim_mask", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("origin", ctypes.c_float * 16)]
 
 
 class BatchTuning(ctypes.Structure):
@@ -310,9 +346,13 @@ class Batch:
 
     table: 2-D float32 CUDA tensor, row-major (stride (ld, 1)) or column-major
     (stride (1, ld)). queries: int array [n_queries, 3] of (row_begin,
-    row_count, dim_mask). Results: global ascending row ids per query."""
+    row_count, dim_mask). origins (optional): float array [n_queries, 16];
+    a row with any non-NaN value makes that query a quadrant query with that
+    origin (values in the order of its selected columns). Results: global
+    ascending row ids per query."""
 
-    def __init__(self, table, queries, log2g=None, refine_ctas_per_sm=0, capacity=None, stream=None):
+    def __init__(self, table, queries, log2g=None, refine_ctas_per_sm=0, capacity=None, stream=None,
+                 origins=None):
         import numpy as np
         torch = _torch()
         lib = _load_batched()
@@ -322,9 +362,14 @@ class Batch:
         q = np.asarray(queries, dtype=np.int64).reshape(-1, 3)
         self.nq = q.shape[0]
         arr = (Query * max(self.nq, 1))()
+        org = None if origins is None else np.asarray(origins, dtype=np.float32).reshape(self.nq, 16)
         for i in range(self.nq):
-            arr[i].row_begin, arr[i].row_count, arr[i].dim_mask, arr[i].reserved = int(q[i, 0]), int(q[i, 1]), \
-                int(q[i, 2]) & 0xffffffff, 0
+            arr[i].row_begin, arr[i].row_count, arr[i].dim_mask = int(q[i, 0]), int(q[i, 1]), int(q[i, 2]) & 0xffffffff
+            arr[i].flags = 0
+            if org is not None and not np.all(np.isnan(org[i])):
+                arr[i].flags = QUERY_QUADRANT
+                for k in range(16):
+                    arr[i].origin[k] = float(0.0 if np.isnan(org[i, k]) else org[i, k])
         self._queries = arr
         tune = BatchTuning()
         self._lg = None

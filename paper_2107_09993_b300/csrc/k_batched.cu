@@ -45,6 +45,10 @@ __device__ __forceinline__ float elem(const QueryPlan& q, int64_t r, int k)
     return __ldg(q.base + r * q.rs + (int64_t)q.col[k] * q.cs);
 }
 
+// Key of a row outside a quadrant query's quadrant (batched grids have at
+// most 2^18 cells, so no cell key reaches it).
+constexpr uint32_t kOutsideKey = 0xffffffffu;
+
 // ---------------------------------------------------------------- (a)+(b)
 __global__ void __launch_bounds__(kT) kb_map(const QueryPlan* __restrict__ qps, int nq,
                                              const int64_t* __restrict__ pchunk, int64_t nitems)
@@ -58,12 +62,14 @@ __global__ void __launch_bounds__(kT) kb_map(const QueryPlan* __restrict__ qps, 
         bool bad = false;
         for (int64_t r = r0 + threadIdx.x; r < r0 + kChunk && r < q.n; r += kT) {
             uint32_t key = 0, mq[kMaxDim];
+            bool outside = false;   // quadrant query: below the origin in some column
 #pragma unroll
             for (int k = kMaxDim - 1; k >= 0; --k) {
                 mq[k] = 0;
                 if (k < q.d) {
                     const float x = elem(q, r, k);
                     bad |= !isfinite(x);
+                    outside |= q.quadrant && !(x >= q.origin[k]);
                     const uint32_t c = column_of(x, 0.0f, sc, G);
                     key = (key << q.log2g) | c;
                     mq[k] = (q.mbits <= q.log2g) ? (c >> (q.log2g - q.mbits)) : column_of(x, 0.0f, sm, M);
@@ -74,6 +80,11 @@ __global__ void __launch_bounds__(kT) kb_map(const QueryPlan* __restrict__ qps, 
 #pragma unroll
                 for (int k = kMaxDim - 1; k >= 0; --k)
                     if (k < q.d) code = (code << 1) | ((mq[k] >> l) & 1u);
+            if (outside) {
+                // takes no part: marks no cell and never survives step (c)
+                q.keys[r] = make_uint2(kOutsideKey, code);
+                continue;
+            }
             q.keys[r] = make_uint2(key, code);
             atomicOr(q.occ + (key >> 5), 1u << (key & 31u));
         }
@@ -119,6 +130,7 @@ __global__ void __launch_bounds__(kT) kb_survivors(const QueryPlan* __restrict__
         if (i >= q.n) continue;
         const uint2 kk = q.keys[i];
         mk[j] = kk.y;
+        if (kk.x == kOutsideKey) continue;   // outside the query's quadrant
         bool dominated = false;
         if (all_columns_positive(kk.x, q.log2g, q.d)) {
             const uint32_t src = kk.x - ones;

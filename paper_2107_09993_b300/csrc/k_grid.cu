@@ -221,43 +221,47 @@ struct MortonSpread {
     __device__ __forceinline__ bool fast() const { return mask != 0u; }
 };
 
-// Where the occupancy bits go. All three keep every bit; they differ in how
-// many global atomics hit one word.
+// Where the occupancy bits go. All of them keep every bit; they differ in how
+// many atomics hit one word.
 //   MarkGlobal  fire-and-forget atomicOr on the bitmap
 //   MarkPrivate a block-private copy of a small bitmap in shared memory
-//   MarkCache   a direct-mapped, tagged cache of bitmap words in shared memory
-//               (slot = word mod kCacheSlots): a word claims a free slot and
-//               later bits for it are ORed there; a word whose slot another
-//               word holds goes to the bitmap. The block writes the cached
-//               words out at its end. Clustered data (many rows on few words)
-//               then sends at most one atomic per hot word per block.
-constexpr int kCacheSlots = 1024;
-constexpr uint32_t kCacheEmpty = 0xffffffffu;
-
+//   MarkCheck   the bitmap, but a mark whose bits are already set (read
+//               through L1; stale is fine: bits are only ever set) sends no
+//               atomic. Many rows of clustered data land on few cells, whose
+//               words then take no further atomics. `hits` counts this
+//               thread's marks that found their bits set; the block stops
+//               looking after a few chunks when that was rare (spread data,
+//               where the extra load per row only adds latency).
+//   MarkNone    no marking (a pass that only needs the keys again)
+// (A shared-memory cache of bitmap words measured slower on clustered data
+// than both global variants.)
 struct MarkGlobal {
     uint32_t* occ;
     __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const { atomicOr(occ + word, bits); }
 };
+// The private marker looks before it ORs: a bit already set costs one shared
+// load, not a serialised atomic on the same address.
 struct MarkPrivate {
     uint32_t* s_occ;   // shared memory
-    __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const { atomicOr(s_occ + word, bits); }
-};
-struct MarkCache {
-    uint32_t* occ;
-    uint32_t* s_key;   // shared memory [kCacheSlots]
-    uint32_t* s_val;   // shared memory [kCacheSlots]
-    uint32_t* s_claimed;
-    bool on;           // block-uniform: false once the cache stopped paying off
     __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const
     {
-        if (on) {
-            const uint32_t slot = word & (kCacheSlots - 1);
-            uint32_t k = s_key[slot];
-            if (k == kCacheEmpty) {
-                k = atomicCAS(s_key + slot, kCacheEmpty, word);
-                if (k == kCacheEmpty) { atomicAdd(s_claimed, 1u); k = word; }
-            }
-            if (k == word) { atomicOr(s_val + slot, bits); return; }
+        if ((s_occ[word] & bits) != bits) atomicOr(s_occ + word, bits);
+    }
+};
+struct MarkNone {
+    __device__ __forceinline__ void mark(uint32_t, uint32_t) const {}
+};
+constexpr int kCheckChunk = 2;   // the chunk whose hits decide whether a block keeps checking
+
+struct MarkCheck {
+    uint32_t* occ;
+    bool check;        // block-uniform
+    uint32_t* hits;    // per-thread counter (register of the caller)
+    __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const
+    {
+        if (check && (__ldca(occ + word) & bits) == bits) {
+            ++*hits;
+            return;
         }
         atomicOr(occ + word, bits);
     }
@@ -265,13 +269,14 @@ struct MarkCache {
 
 // The key is built as key * G + c (G a runtime power of two: an integer
 // multiply-add, off the integer ALU pipe that the clamps and masks use).
-// `converged`: every lane of the warp calls together (no activemask query).
-template <int DP, bool converged, class Marker>
-__device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, int mbits, const MortonSpread& ms,
-                                        const float* s_off, const float* s_sc, const float* s_ms, int64_t row,
-                                        uint32_t* __restrict__ ckey, uint32_t* __restrict__ mkey,
-                                        const Marker& marker, bool& bad)
+// EXACT: d == DP (no per-dimension guards); COARSE: the Morton grid is no
+// finer than the cell grid, so the Morton column is the cell column shifted.
+template <int DP, bool EXACT, bool COARSE>
+__device__ __forceinline__ void map_keys(const float (&x)[DP], int d, int log2g, int mbits, const MortonSpread& ms,
+                                         const float* s_off, const float* s_sc, const float* s_ms,
+                                         uint32_t& key_out, uint32_t& code_out, bool& bad)
 {
+    const int dd = EXACT ? DP : d;
     const uint32_t G = 1u << log2g;
     const uint32_t M = 1u << mbits;
     uint32_t key = 0;
@@ -280,13 +285,11 @@ __device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, 
 #pragma unroll
     for (int k = DP - 1; k >= 0; --k) {
         mq[k] = 0;
-        if (k < d) {
+        if (k < dd) {
             nanacc = fmaf(x[k], 0.0f, nanacc);
             const uint32_t c = column_of(x[k], s_off[k], s_sc[k], G);
             key = key * G + c;
-            // the Morton map is only for locality: reuse the cell column when
-            // it is at least as fine
-            mq[k] = (mbits <= log2g) ? (c >> (log2g - mbits)) : column_of(x[k], s_off[k], s_ms[k], M);
+            mq[k] = COARSE ? (c >> (log2g - mbits)) : column_of(x[k], s_off[k], s_ms[k], M);
         }
     }
     bad |= nanacc != nanacc;
@@ -294,12 +297,33 @@ __device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, 
     if (ms.fast()) {
 #pragma unroll
         for (int k = 0; k < DP; ++k)
-            if (k < d) code += ((mq[k] * ms.magic) & ms.mask) << k;   // disjoint bits: + is |
+            if (k < dd) code += ((mq[k] * ms.magic) & ms.mask) << k;   // disjoint bits: + is |
     } else {
         for (int l = mbits - 1; l >= 0; --l)
 #pragma unroll
             for (int k = DP - 1; k >= 0; --k)
-                if (k < d) code = (code << 1) | ((mq[k] >> l) & 1u);
+                if (k < dd) code = (code << 1) | ((mq[k] >> l) & 1u);
+    }
+    key_out = key;
+    code_out = code;
+}
+
+// `converged`: every lane of the warp calls together (no activemask query).
+// The two shape tests are uniform across the grid, so each call runs one
+// specialised body.
+template <int DP, bool converged, class Marker>
+__device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, int mbits, const MortonSpread& ms,
+                                        const float* s_off, const float* s_sc, const float* s_ms, int64_t row,
+                                        uint32_t* __restrict__ ckey, uint32_t* __restrict__ mkey,
+                                        Marker marker, bool& bad)
+{
+    uint32_t key, code;
+    if (d == DP) {
+        if (mbits <= log2g) map_keys<DP, true, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, key, code, bad);
+        else map_keys<DP, true, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, key, code, bad);
+    } else {
+        if (mbits <= log2g) map_keys<DP, false, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, key, code, bad);
+        else map_keys<DP, false, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, key, code, bad);
     }
     ckey[row] = key;
     mkey[row] = code;
@@ -320,21 +344,26 @@ __device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, 
 // bitmap in shared memory -- many rows share few words there, and global
 // atomics on them would serialise -- which each block then writes to its row
 // of `stage`; k_occ_merge ORs the rows into the bitmap.
-template <int DP, bool SMALL>
+// Marking modes of the map kernels: the bitmap itself (through the word cache
+// in the streaming kernel), a private shared-memory copy of a small bitmap,
+// or no marking at all (a second pass that only needs the keys again).
+enum MapMark { kMarkCheck = 0, kMarkSmall = 1, kMarkNone = 2 };
+
+template <int DP, int MODE>
 __global__ void __launch_bounds__(kThreads) k_map_mark_plain(const float* __restrict__ pts, int64_t n,
                                                              int d, int64_t ld, bool vec4, int log2g, int mbits,
                                                              const float* params, uint32_t* ckey,
                                                              uint32_t* mkey, uint32_t* occ, uint32_t* err,
                                                              uint32_t* stage, int64_t words)
 {
-    extern __shared__ __align__(16) uint32_t s_occ[];   // [words] when SMALL
+    extern __shared__ __align__(16) uint32_t s_occ[];   // [words] in kMarkSmall mode
     __shared__ float s_off[kMaxDim], s_sc[kMaxDim], s_ms[kMaxDim];
     if (threadIdx.x < kMaxDim) {
         s_off[threadIdx.x] = params[threadIdx.x];
         s_sc[threadIdx.x] = params[16 + threadIdx.x];
         s_ms[threadIdx.x] = params[48 + threadIdx.x];
     }
-    if (SMALL)
+    if (MODE == kMarkSmall)
         for (int64_t w = threadIdx.x; w < words; w += blockDim.x) s_occ[w] = 0u;
     __syncthreads();
     const MortonSpread ms(d, mbits);
@@ -345,14 +374,16 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_plain(const float* __rest
         if (i < n) {
             float x[DP];
             load_row<DP>(pts + i * ld, d, vec4, x);
-            if (SMALL)
+            if (MODE == kMarkSmall)
                 map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkPrivate{s_occ}, bad);
+            else if (MODE == kMarkNone)
+                map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkNone{}, bad);
             else
                 map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkGlobal{occ}, bad);
         }
     }
     if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, SKY_DEV_ERR_NONFINITE);
-    if (SMALL) {
+    if (MODE == kMarkSmall) {
         __syncthreads();
         for (int64_t w = threadIdx.x; w < words; w += blockDim.x) stage[blockIdx.x * words + w] = s_occ[w];
     }
@@ -366,18 +397,18 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_plain(const float* __rest
 // d = 16 instead of 16-way for scalar reads).
 constexpr int kMapStages = 4;
 
-template <int DP, bool SMALL>
+template <int DP, int MODE>
 __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restrict__ pts, int64_t n,
                                                            int d, int log2g, int mbits, const float* params,
                                                            uint32_t* ckey, uint32_t* mkey, uint32_t* occ,
                                                            uint32_t* err, uint32_t* stage, int64_t words)
 {
-    // [kMapStages][kThreads * d] row stages, then either the private bitmap
-    // [words] (SMALL) or the word cache: tags and values [kCacheSlots] each
+    // [kMapStages][kThreads * d] row stages, then the private bitmap [words]
+    // (kMarkSmall)
     extern __shared__ __align__(128) float s_buf[];
     __shared__ float s_off[kMaxDim], s_sc[kMaxDim], s_ms[kMaxDim];
     __shared__ __align__(8) uint64_t s_bar[kMapStages];
-    __shared__ uint32_t s_claimed, s_cache_on;
+    __shared__ uint32_t s_hits, s_check;
     const int tid = threadIdx.x;
     uint32_t* s_tail = reinterpret_cast<uint32_t*>(s_buf + kMapStages * kThreads * d);
     if (tid < kMaxDim) {
@@ -385,19 +416,13 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
         s_sc[tid] = params[16 + tid];
         s_ms[tid] = params[48 + tid];
     }
-    if (SMALL) {
+    if (MODE == kMarkSmall)
         for (int64_t w = tid; w < words; w += kThreads) s_tail[w] = 0u;
-    } else {
-        for (int t = tid; t < kCacheSlots; t += kThreads) {
-            s_tail[t] = kCacheEmpty;
-            s_tail[kCacheSlots + t] = 0u;
-        }
-    }
     if (tid == 0) {
         for (int s = 0; s < kMapStages; ++s) mbar_init(&s_bar[s], 1);
         mbar_fence_init();
-        s_claimed = 0u;
-        s_cache_on = 1u;
+        s_hits = 0u;
+        s_check = 1u;
     }
     __syncthreads();
     const MortonSpread ms(d, mbits);
@@ -415,6 +440,7 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
     }
     bool bad = false;
     bool timed_out = false;
+    uint32_t hits = 0;
     for (int64_t i = 0; i < my_chunks; ++i) {
         const int s = (int)(i % kMapStages);
         const uint32_t parity = (uint32_t)((i / kMapStages) & 1);
@@ -431,6 +457,7 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
         }
         const int64_t c = blockIdx.x + i * gridDim.x;
         const float* r = s_buf + s * kThreads * d + tid * d;
+        if (i == kCheckChunk) hits = 0;
         float x[DP];
         if (v4) {
 #pragma unroll
@@ -442,17 +469,25 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
 #pragma unroll
             for (int k = 0; k < DP; ++k) x[k] = (k < d) ? r[k] : 0.0f;
         }
-        if (SMALL)
+        if (MODE == kMarkSmall)
             map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, c * kThreads + tid, ckey, mkey,
                               MarkPrivate{s_tail}, bad);
+        else if (MODE == kMarkNone)
+            map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, c * kThreads + tid, ckey, mkey,
+                              MarkNone{}, bad);
         else
             map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, c * kThreads + tid, ckey, mkey,
-                              MarkCache{occ, s_tail, s_tail + kCacheSlots, &s_claimed, s_cache_on != 0u}, bad);
+                              MarkCheck{occ, s_check != 0u, &hits}, bad);
+        if (MODE == kMarkCheck && i == kCheckChunk) {
+            const uint32_t h = __reduce_add_sync(kFull, hits);
+            if ((tid & 31) == 0 && h) atomicAdd(&s_hits, h);
+        }
         __syncthreads();  // every thread is done with stage s
         if (tid == 0) {
-            // after the first chunk: keep the cache only if rows repeat words
-            // (fewer claimed slots than 3/4 of the rows)
-            if (!SMALL && i == 0 && s_claimed > (uint32_t)(kThreads * 3 / 4)) s_cache_on = 0u;
+            // keep looking only if at least a quarter of the rows of chunk
+            // kCheckChunk found their bits set (by then every block has
+            // marked a few chunks, so the hot cells of clustered data are set)
+            if (MODE == kMarkCheck && i == kCheckChunk && s_hits < (uint32_t)(kThreads / 4)) s_check = 0u;
             if (i + kMapStages < my_chunks) {
                 const int64_t c2 = blockIdx.x + (i + kMapStages) * gridDim.x;
                 fence_proxy_async_smem();
@@ -467,21 +502,18 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
         if (i < n) {
             float x[DP];
             load_row<DP>(pts + i * d, d, false, x);
-            if (SMALL)
+            if (MODE == kMarkSmall)
                 map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkPrivate{s_tail}, bad);
+            else if (MODE == kMarkNone)
+                map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkNone{}, bad);
             else
                 map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkGlobal{occ}, bad);
         }
     }
     if (__any_sync(kFull, bad) && (tid & 31) == 0) atomicOr(err, SKY_DEV_ERR_NONFINITE);
     __syncthreads();
-    if (SMALL) {
+    if (MODE == kMarkSmall) {
         for (int64_t w = tid; w < words; w += kThreads) stage[blockIdx.x * words + w] = s_tail[w];
-    } else {
-        for (int t = tid; t < kCacheSlots; t += kThreads) {
-            const uint32_t k = s_tail[t], v = s_tail[kCacheSlots + t];
-            if (k != kCacheEmpty && v) atomicOr(occ + k, v);
-        }
     }
 }
 
@@ -916,49 +948,88 @@ int map_blocks_bound(int64_t n)
     return (int)std::min<int64_t>(b, kMapMaxBlocks);
 }
 
-static cudaError_t launch_map(const Plan& p, cudaStream_t s)
+template <int DP, int MODE>
+static void map_tma(const Plan& p, int blocks, size_t smem, int smem_max, int64_t pw, cudaStream_t s)
 {
-    const bool small = p.occ_stage != nullptr;
-    const int64_t pw = small ? p.words : 0;
+    cudaFuncSetAttribute(k_map_mark_tma<DP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    k_map_mark_tma<DP, MODE><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.log2g, p.morton_bits, p.params,
+                                                            p.ckey, p.mkey, p.occ, &p.res->err,
+                                                            MODE == kMarkSmall ? p.occ_stage : nullptr, pw);
+}
+
+template <int DP, int MODE>
+static void map_plain(const Plan& p, int blocks, size_t smem, int64_t pw, bool v, cudaStream_t s)
+{
+    k_map_mark_plain<DP, MODE><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.ld, v, p.log2g, p.morton_bits,
+                                                              p.params, p.ckey, p.mkey, p.occ, &p.res->err,
+                                                              MODE == kMarkSmall ? p.occ_stage : nullptr, pw);
+}
+
+// Steps (a)+(b) over p.pts with the parameters already in p.params. With
+// mark = false only the keys are written (the bitmap is left alone).
+cudaError_t launch_map_pass(const Plan& p, bool mark, cudaStream_t s)
+{
+    if (p.n == 0) return cudaGetLastError();
+    const int mode = !mark ? kMarkNone : (p.occ_stage != nullptr ? kMarkSmall : kMarkCheck);
+    const int64_t pw = mode == kMarkSmall ? p.words : 0;
     int blocks = 0;
     if (p.tma_ok && p.n >= kThreads) {
-        const size_t tail = small ? (size_t)pw * sizeof(uint32_t) : 2 * kCacheSlots * sizeof(uint32_t);
+        const size_t tail = mode == kMarkSmall ? (size_t)pw * sizeof(uint32_t) : 0;
         const size_t smem = (size_t)kMapStages * kThreads * p.d * sizeof(float) + tail;
         const int smem_max = kMapStages * kThreads * 16 * (int)sizeof(float) +
-                             (int)std::max<int64_t>(kPrivWords, 2 * kCacheSlots) * (int)sizeof(uint32_t);
+                             (int)kPrivWords * (int)sizeof(uint32_t);
         const int64_t nchunks = p.n / kThreads;
         blocks = grid_for(nchunks, 1, std::min(num_sms() * 4, kMapMaxBlocks));
         SKY_DISPATCH_DP(p.d, {
-            if (small) {
-                cudaFuncSetAttribute(k_map_mark_tma<DP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
-                k_map_mark_tma<DP, true><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.log2g, p.morton_bits,
-                                                                        p.params, p.ckey, p.mkey, p.occ,
-                                                                        &p.res->err, p.occ_stage, pw);
-            } else {
-                cudaFuncSetAttribute(k_map_mark_tma<DP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
-                k_map_mark_tma<DP, false><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.log2g, p.morton_bits,
-                                                                         p.params, p.ckey, p.mkey, p.occ,
-                                                                         &p.res->err, nullptr, 0);
-            }
+            if (mode == kMarkSmall) map_tma<DP, kMarkSmall>(p, blocks, smem, smem_max, pw, s);
+            else if (mode == kMarkNone) map_tma<DP, kMarkNone>(p, blocks, smem, smem_max, pw, s);
+            else map_tma<DP, kMarkCheck>(p, blocks, smem, smem_max, pw, s);
         });
     } else {
         blocks = grid_for(p.n, kThreads * 4, std::min(num_sms() * 8, kMapMaxBlocks));
         const bool v = vec4_ok(p);
         const size_t smem = (size_t)pw * sizeof(uint32_t);
         SKY_DISPATCH_DP(p.d, {
-            if (small)
-                k_map_mark_plain<DP, true><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.ld, v, p.log2g,
-                                                                          p.morton_bits, p.params, p.ckey, p.mkey,
-                                                                          p.occ, &p.res->err, p.occ_stage, pw);
-            else
-                k_map_mark_plain<DP, false><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, p.log2g,
-                                                                        p.morton_bits, p.params, p.ckey, p.mkey,
-                                                                        p.occ, &p.res->err, nullptr, 0);
+            if (mode == kMarkSmall) map_plain<DP, kMarkSmall>(p, blocks, smem, pw, v, s);
+            else if (mode == kMarkNone) map_plain<DP, kMarkNone>(p, blocks, smem, pw, v, s);
+            else map_plain<DP, kMarkCheck>(p, blocks, smem, pw, v, s);
         });
     }
-    if (small) {
+    if (mode == kMarkSmall) {
         const int64_t cols = (p.words + 31) / 32;
         k_occ_merge<<<(unsigned)(cols * kMergeSplit), kThreads, 0, s>>>(p.occ_stage, blocks, p.words, p.occ);
+    }
+    return cudaGetLastError();
+}
+
+void launch_mm_reset(const Plan& p, cudaStream_t s)
+{
+    cudaMemsetAsync(p.mm_min, 0xff, sizeof(uint32_t) * kMaxDim, s);
+    cudaMemsetAsync(p.mm_max, 0x00, sizeof(uint32_t) * kMaxDim, s);
+}
+
+// Min / max of p's rows folded into p.mm_min / p.mm_max (reset beforehand).
+cudaError_t launch_minmax_accumulate(const Plan& p, cudaStream_t s)
+{
+    if (p.n == 0) return cudaGetLastError();
+    const int blocks = grid_for(p.n, kThreads * 8, num_sms() * 8);
+    const bool v = vec4_ok(p);
+    SKY_DISPATCH_DP(p.d, k_minmax<DP><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, p.mm_min, p.mm_max,
+                                                                   &p.res->err));
+    return cudaGetLastError();
+}
+
+// p.params for p.map_mode: min / max scales from p.mm_* (mode 2), the unit
+// cube (mode 1), or the automatic rule over p's rows (mode 0).
+cudaError_t launch_params(const Plan& p, cudaStream_t s)
+{
+    if (p.map_mode == kMapMinMax) {
+        k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 1, p.params);
+    } else if (p.map_mode == kMapUnit || p.n == 0) {
+        k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 0, p.params);
+    } else {
+        SKY_DISPATCH_DP(p.d, k_sample_params<DP><<<1, kDecideThreads, 0, s>>>(
+                                 p.pts, p.n, p.d, p.ld, p.log2g, p.morton_bits, p.mm_min, p.mm_max, p.params));
     }
     return cudaGetLastError();
 }
@@ -966,24 +1037,11 @@ static cudaError_t launch_map(const Plan& p, cudaStream_t s)
 cudaError_t launch_build(const Plan& p, cudaStream_t s)
 {
     cudaMemsetAsync(p.occ, 0, sizeof(uint32_t) * p.words, s);
-    if (p.map_mode == kMapMinMax) {
-        cudaMemsetAsync(p.mm_min, 0xff, sizeof(uint32_t) * kMaxDim, s);
-        cudaMemsetAsync(p.mm_max, 0x00, sizeof(uint32_t) * kMaxDim, s);
-    }
+    if (p.map_mode == kMapMinMax) launch_mm_reset(p, s);
     if (p.n == 0) return cudaGetLastError();
-    if (p.map_mode == kMapMinMax) {
-        const int blocks = grid_for(p.n, kThreads * 8, num_sms() * 8);
-        const bool v = vec4_ok(p);
-        SKY_DISPATCH_DP(p.d, k_minmax<DP><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, p.mm_min,
-                                                                       p.mm_max, &p.res->err));
-        k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 1, p.params);
-    } else if (p.map_mode == kMapUnit) {
-        k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 0, p.params);
-    } else {
-        SKY_DISPATCH_DP(p.d, k_sample_params<DP><<<1, kDecideThreads, 0, s>>>(
-                                 p.pts, p.n, p.d, p.ld, p.log2g, p.morton_bits, p.mm_min, p.mm_max, p.params));
-    }
-    return launch_map(p, s);
+    if (p.map_mode == kMapMinMax) launch_minmax_accumulate(p, s);
+    launch_params(p, s);
+    return launch_map_pass(p, true, s);
 }
 
 int build_kernel_count(const Plan& p)

@@ -55,7 +55,7 @@ int count_kernels(const Plan& p, int n_prop)
     const int passes = (p.morton_bits * p.d + 7) / 8;
     const int through_c = build_kernel_count(p) + (n_prop > 0 ? 1 : 0) + 1 + prefix_kernel_count(p) + 2;
     if (p.survivors_only) return through_c + 1;
-    return through_c + 3 * passes + 1 + 1 + 1;
+    return through_c + 3 * passes + 1 + 3 + 1;   // sort, gather, cost + order + refine, emit
 }
 
 sky_status fail(sky_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
@@ -135,7 +135,9 @@ size_t layout(Plan& p, char* base, bool grid_api)
     p.X = c.take<float>(n_pad * dp);
     p.C = c.take<uint32_t>(n_pad * (dp / 4));
     p.ids = c.take<int32_t>(n_pad);
-    p.bbox = c.take<float>(tiles * 2 * dp);
+    p.tmax = c.take<uint32_t>(tiles * (dp / 4));
+    p.tile_cost = c.take<uint32_t>(tiles);
+    p.tile_order = c.take<uint32_t>(tiles);
     p.subcode = c.take<uint32_t>(tiles * 5 * (dp / 4));
     p.keep = c.take<uint8_t>(n + 16);
     return c.off;
@@ -437,6 +439,8 @@ void plan_carve(Plan& p, void* ws, bool grid_api)
 {
     layout(p, static_cast<char*>(ws), grid_api);
 }
+
+void set_last_error(const char* msg) { t_err = msg ? msg : ""; }
 
 }  // namespace sky
 

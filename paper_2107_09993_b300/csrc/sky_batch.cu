@@ -98,9 +98,10 @@ sky_status sky_batch_create(const float* d_table, int64_t n_rows, int32_t n_cols
     // -------- per-query plan
     for (int q = 0; q < nq; ++q) {
         const sky_query& Q = h_queries[q];
-        if (Q.reserved != 0 || Q.row_begin < 0 || Q.row_count < 0 || Q.row_begin + Q.row_count > n_rows) {
+        if ((Q.flags & ~SKY_QUERY_QUADRANT) != 0 || Q.row_begin < 0 || Q.row_count < 0 ||
+            Q.row_begin + Q.row_count > n_rows) {
             delete b;
-            return bfail(SKY_ERR_INVALID_ARGUMENT, "query %d: bad row range or reserved field", q);
+            return bfail(SKY_ERR_INVALID_ARGUMENT, "query %d: bad row range or unknown flag", q);
         }
         const uint32_t allowed = n_cols >= 32 ? 0xffffffffu : ((1u << n_cols) - 1u);
         const int d = __builtin_popcount(Q.dim_mask);
@@ -120,6 +121,8 @@ sky_status sky_batch_create(const float* d_table, int64_t n_rows, int32_t n_cols
         int c = 0;
         for (int k = 0; k < 32; ++k)
             if ((Q.dim_mask >> k) & 1u) p.col[c++] = k;
+        p.quadrant = (Q.flags & SKY_QUERY_QUADRANT) ? 1 : 0;
+        for (int k = 0; k < kMaxDim; ++k) p.origin[k] = (p.quadrant && k < d) ? Q.origin[k] : 0.0f;
         int lg = -1;
         if (tuning && tuning->h_log2g) lg = tuning->h_log2g[q];
         if (lg < 0) {

@@ -67,7 +67,9 @@ struct Plan {
     float* X = nullptr;              // [n_pad][dp] sorted survivor coordinates
     uint32_t* C = nullptr;           // [n_pad][dp/4] 7-bit codes
     int32_t* ids = nullptr;          // [n_pad] row id per sorted survivor
-    float* bbox = nullptr;           // [tiles][2][dp]
+    uint32_t* tmax = nullptr;        // [tiles][dp/4] byte-wise max code of each tile
+    uint32_t* tile_cost = nullptr;   // [tiles] cost estimate of each p-tile
+    uint32_t* tile_order = nullptr;  // [tiles] p-tiles, largest cost first
     uint32_t* subcode = nullptr;     // [tiles][5][dp/4] byte-wise min code of each 32-point sub-tile, then of the tile
     uint8_t* keep = nullptr;         // [n] 1 = skyline
     float* filt = nullptr;           // [16][16] snapped filter points
@@ -85,6 +87,8 @@ struct QueryPlan {
     int64_t row_begin;
     int32_t d, dp, log2g, mbits, passes, dpclass;
     int32_t col[16];
+    int32_t quadrant;         // 1: only rows >= origin (every column) take part
+    float origin[16];
     int64_t words, chunks, tiles;
     uint2* keys;
     uint32_t* occ;
@@ -130,6 +134,11 @@ int build_kernel_count(const Plan& p);
 cudaError_t launch_prefix_or(const Plan& p, cudaStream_t s);
 int prefix_kernel_count(const Plan& p);
 int map_blocks_bound(int64_t n);
+void launch_mm_reset(const Plan& p, cudaStream_t s);
+cudaError_t launch_minmax_accumulate(const Plan& p, cudaStream_t s);
+cudaError_t launch_params(const Plan& p, cudaStream_t s);
+cudaError_t launch_map_pass(const Plan& p, bool mark, cudaStream_t s);
+void set_last_error(const char* msg);   // the message sky_last_error() returns
 cudaError_t launch_dominated(const Plan& p, cudaStream_t s);
 cudaError_t launch_snap(const Plan& p, const float* d_prop, int n_prop, cudaStream_t s);
 cudaError_t launch_survivors(const Plan& p, int n_filter, cudaStream_t s);

@@ -25,7 +25,7 @@ import numpy as np
 
 __all__ = [
     "independent", "correlated", "anticorrelated", "copula", "generate",
-    "mixed_table", "batched_queries", "GENERATORS",
+    "mixed_table", "batched_queries", "GENERATORS", "generate_torch",
 ]
 
 
@@ -134,3 +134,41 @@ def copula_torch(n: int, d: int, seed: int, rho: float, device="cuda"):
     z = torch.randn((n, d), generator=g, device=device, dtype=torch.float32) @ chol.T
     u = 0.5 * torch.erfc(-z / math.sqrt(2.0))
     return torch.clamp(u, max=float(np.nextafter(np.float32(1.0), np.float32(0.0)))).contiguous(), rho_eff
+
+
+def generate_torch(kind: str, n: int, d: int, seed: int, device="cuda", block: int = 1 << 26):
+    """The three families drawn on the GPU with torch (float32 arithmetic,
+    seeded per block of rows), for sets too large to draw on the host (the
+    paper's 3.2e9-point runs). Same recipes as the numpy generators, not the
+    same numbers. Returns a [n, d] float32 CUDA tensor."""
+    import torch
+
+    out = torch.empty((n, d), dtype=torch.float32, device=device)
+    g = torch.Generator(device=device)
+    for b, s in enumerate(range(0, n, block)):
+        m = min(block, n - s)
+        g.manual_seed(int(seed) * 1_000_003 + b)
+        if kind == "independent":
+            out[s:s + m] = torch.rand((m, d), generator=g, device=device)
+        elif kind == "correlated":
+            t = torch.rand((m, 1), generator=g, device=device)
+            out[s:s + m] = (t + 0.05 * torch.randn((m, d), generator=g, device=device)).clamp_(0.0, 1.0)
+        elif kind == "correlated_inside":
+            # the correlated recipe with rows outside [0, 1)^d drawn again
+            # instead of clipped (no pile of points on the faces of the cube)
+            x = torch.rand((m, 1), generator=g, device=device) + 0.05 * torch.randn((m, d), generator=g, device=device)
+            bad = ((x < 0) | (x >= 1)).any(dim=1)
+            while bool(bad.any()):
+                k = int(bad.sum())
+                y = torch.rand((k, 1), generator=g, device=device) + 0.05 * torch.randn((k, d), generator=g,
+                                                                                         device=device)
+                x[bad] = y
+                bad = ((x < 0) | (x >= 1)).any(dim=1)
+            out[s:s + m] = x
+        elif kind == "anticorrelated":
+            u = torch.rand((m, d), generator=g, device=device)
+            c = 0.5 + 0.05 * torch.randn((m, 1), generator=g, device=device)
+            out[s:s + m] = (u - u.mean(dim=1, keepdim=True) + c).clamp_(0.0, 1.0)
+        else:
+            raise ValueError(kind)
+    return out

@@ -98,3 +98,27 @@ def test_batched_rejects_bad_queries():
     with pytest.raises(sky.SkyError) as e:
         sky.Batch(T, np.array([(0, 10, 0b11)], dtype=np.int64), log2g=[10])
     assert e.value.name == "SKY_ERR_TOO_LARGE"
+
+
+def test_quadrant_queries_match_oracle():
+    """Quadrant queries (a query point becomes the origin; only rows above it
+    in every selected column take part) mixed with plain ones in one batch."""
+    T = _table(40000, 10, seed=9)
+    q = skydata.batched_queries(200, T.shape[0], T.shape[1], seed=8, n_lo=10, n_hi=20000, d_lo=1, d_hi=10)
+    rng = np.random.default_rng(4)
+    origins = np.full((len(q), 16), np.nan, dtype=np.float32)
+    for i, (b, c, mask) in enumerate(q):
+        if i % 3:
+            d = bin(int(mask)).count("1")
+            origins[i, :d] = rng.random(d).astype(np.float32) * 0.6      # some quadrants are empty-ish
+    origins[5, :1] = 2.0                                                  # nothing in the quadrant
+    b = sky.Batch(torch.from_numpy(T).cuda(), q, origins=origins)
+    b.run()
+    res, st = b.results(), b.query_status()
+    for i, (rb, rc, mask) in enumerate(q):
+        o = None if np.all(np.isnan(origins[i])) else origins[i]
+        want = oracle.skyline_subset(T, int(rb), int(rc), int(mask), origin=o)
+        assert res[i].tolist() == want.tolist(), (i, rb, rc, bin(mask))
+        assert st[i] == 0
+    assert len(res[5]) == 0
+    b.close()

@@ -168,3 +168,27 @@ def test_o5_cross_cell_domination():
     dom, key, cand, _ = oracle.cell_classes(occ, 2, 2)
     assert cand[keys[1]] and not dom[keys[1]]      # b's cell survives cell pruning
     assert oracle.skyline_brute(P).tolist() == [0]  # yet a dominates b
+
+
+def test_quadrant_query_definition():
+    """A quadrant query keeps the rows >= the origin in every selected column;
+    its skyline equals the skyline of those rows shifted to the origin (the
+    comparison of Definition 1 is translation invariant), and a row below the
+    origin in one column never takes part, even when it would dominate."""
+    rng = np.random.default_rng(31)
+    T = rng.random((400, 5)).astype(np.float32)
+    mask = 0b10110                                     # columns 1, 2, 4
+    o = np.array([0.2, 0.35, 0.1], dtype=np.float32)
+    got = oracle.skyline_subset(T, 50, 300, mask, origin=o)
+    sub = T[50:350][:, [1, 2, 4]]
+    inq = np.all(sub >= o, axis=1)
+    shifted = (sub[inq] - o).astype(np.float32)
+    brute = np.flatnonzero(inq)[oracle.skyline_brute(shifted)] + 50
+    assert got.tolist() == brute.tolist()
+    # a dominating row outside the quadrant is ignored
+    U = np.array([[0.5, 0.5], [0.6, 0.6], [0.1, 0.9]], dtype=np.float32)
+    assert oracle.skyline_subset(U, 0, 3, 0b11).tolist() == [0, 2]
+    assert oracle.skyline_subset(U, 0, 3, 0b11, origin=[0.55, 0.0]).tolist() == [1]
+    # an origin below every row changes nothing
+    assert oracle.skyline_subset(T, 0, 400, mask, origin=[-1, -1, -1]).tolist() == \
+        oracle.skyline_subset(T, 0, 400, mask).tolist()
