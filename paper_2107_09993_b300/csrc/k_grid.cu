@@ -228,10 +228,10 @@ struct MortonSpread {
 //   MarkCheck   the bitmap, but a mark whose bits are already set (read
 //               through L1; stale is fine: bits are only ever set) sends no
 //               atomic. Many rows of clustered data land on few cells, whose
-//               words then take no further atomics. `hits` counts this
-//               thread's marks that found their bits set; the block stops
-//               looking after a few chunks when that was rare (spread data,
-//               where the extra load per row only adds latency).
+//               words then take no further atomics. A block looks only when
+//               the rows of its first chunk repeat words inside their warps
+//               (clustered data); for spread data the extra load per row
+//               would only add latency.
 //   MarkNone    no marking (a pass that only needs the keys again)
 // (A shared-memory cache of bitmap words measured slower on clustered data
 // than both global variants.)
@@ -251,18 +251,12 @@ struct MarkPrivate {
 struct MarkNone {
     __device__ __forceinline__ void mark(uint32_t, uint32_t) const {}
 };
-constexpr int kCheckChunk = 2;   // the chunk whose hits decide whether a block keeps checking
-
 struct MarkCheck {
     uint32_t* occ;
     bool check;        // block-uniform
-    uint32_t* hits;    // per-thread counter (register of the caller)
     __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const
     {
-        if (check && (__ldca(occ + word) & bits) == bits) {
-            ++*hits;
-            return;
-        }
+        if (check && (__ldca(occ + word) & bits) == bits) return;
         atomicOr(occ + word, bits);
     }
 };
@@ -311,23 +305,16 @@ __device__ __forceinline__ void map_keys(const float (&x)[DP], int d, int log2g,
 // `converged`: every lane of the warp calls together (no activemask query).
 // The two shape tests are uniform across the grid, so each call runs one
 // specialised body.
-template <int DP, bool converged, class Marker>
-__device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, int mbits, const MortonSpread& ms,
-                                        const float* s_off, const float* s_sc, const float* s_ms, int64_t row,
-                                        uint32_t* __restrict__ ckey, uint32_t* __restrict__ mkey,
-                                        Marker marker, bool& bad)
+// Writes a row's keys and marks its cell.
+template <bool converged, class Marker>
+__device__ __forceinline__ void store_mark(uint32_t key, uint32_t code, int64_t row, uint32_t* __restrict__ ckey,
+                                           uint32_t* __restrict__ mkey, const Marker& marker,
+                                           uint32_t* dups = nullptr)
 {
-    uint32_t key, code;
-    if (d == DP) {
-        if (mbits <= log2g) map_keys<DP, true, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, key, code, bad);
-        else map_keys<DP, true, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, key, code, bad);
-    } else {
-        if (mbits <= log2g) map_keys<DP, false, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, key, code, bad);
-        else map_keys<DP, false, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, key, code, bad);
-    }
     ckey[row] = key;
     mkey[row] = code;
     const uint32_t word = key >> 5;
+    if (dups) *dups += __popc(__match_any_sync(kFull, word)) > 1 ? 1u : 0u;   // converged callers only
     const uint32_t bit = 1u << (key & 31u);
     const uint32_t am = converged ? kFull : __activemask();
     const int leader = converged ? 0 : __ffs(am) - 1;
@@ -338,6 +325,68 @@ __device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, 
     } else {
         marker.mark(word, bit);
     }
+}
+
+template <int DP, bool converged, class Marker>
+__device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, int mbits, const MortonSpread& ms,
+                                        const float* s_off, const float* s_sc, const float* s_ms, int64_t row,
+                                        uint32_t* __restrict__ ckey, uint32_t* __restrict__ mkey,
+                                        Marker marker, bool& bad, uint32_t* dups = nullptr)
+{
+    uint32_t key, code;
+    if (d == DP) {
+        if (mbits <= log2g) map_keys<DP, true, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, key, code, bad);
+        else map_keys<DP, true, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, key, code, bad);
+    } else {
+        if (mbits <= log2g) map_keys<DP, false, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, key, code, bad);
+        else map_keys<DP, false, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, key, code, bad);
+    }
+    store_mark<converged>(key, code, row, ckey, mkey, marker, dups);
+}
+
+// Unit-cube map (offset 0, scale G in every dimension; Eq. 1 as printed),
+// d == DP a multiple of 4, multiply-spread Morton keys: the keys of one row
+// read from its shared-memory stage. The four-float pieces of the row are
+// visited starting at piece `rot`, so that the eight threads of a 128-byte
+// shared-memory phase read eight different bank groups (rows of 32 or 64
+// bytes would otherwise collide 2- or 4-way); the key and the Morton key are
+// ORs of shifted per-dimension values, so the visiting order does not matter.
+// x * G here equals (x - 0) * G of the general map bit for bit.
+template <int DP, bool COARSE>
+__device__ __forceinline__ void map_keys_unit(const float* __restrict__ r, int rot, int log2g, int mbits,
+                                              const MortonSpread& ms, uint32_t& key_out, uint32_t& code_out,
+                                              bool& bad)
+{
+    constexpr int NQ = DP / 4;
+    const uint32_t G = 1u << log2g, M = 1u << mbits;
+    const float Gf = (float)G, Mf = (float)M;
+    uint32_t key = 0, code = 0;
+    float nanacc = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+        const int q = (j + rot) % NQ;
+        const float4 v = *reinterpret_cast<const float4*>(r + 4 * q);
+        const float xs[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = 4 * q + i;
+            nanacc = fmaf(xs[i], 0.0f, nanacc);
+            uint32_t c = __float2uint_rd(__fmul_rn(xs[i], Gf));
+            c = c < G - 1u ? c : G - 1u;
+            key |= c << (log2g * k);
+            uint32_t mq;
+            if (COARSE) {
+                mq = c >> (log2g - mbits);
+            } else {
+                mq = __float2uint_rd(__fmul_rn(xs[i], Mf));
+                mq = mq < M - 1u ? mq : M - 1u;
+            }
+            code |= ((mq * ms.magic) & ms.mask) << k;
+        }
+    }
+    bad |= nanacc != nanacc;
+    key_out = key;
+    code_out = code;
 }
 
 // Small grids (at most kPrivWords words) are marked in a private copy of the
@@ -408,7 +457,7 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
     extern __shared__ __align__(128) float s_buf[];
     __shared__ float s_off[kMaxDim], s_sc[kMaxDim], s_ms[kMaxDim];
     __shared__ __align__(8) uint64_t s_bar[kMapStages];
-    __shared__ uint32_t s_hits, s_check;
+    __shared__ uint32_t s_dups, s_check;
     const int tid = threadIdx.x;
     uint32_t* s_tail = reinterpret_cast<uint32_t*>(s_buf + kMapStages * kThreads * d);
     if (tid < kMaxDim) {
@@ -421,12 +470,19 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
     if (tid == 0) {
         for (int s = 0; s < kMapStages; ++s) mbar_init(&s_bar[s], 1);
         mbar_fence_init();
-        s_hits = 0u;
-        s_check = 1u;
+        s_dups = 0u;
+        s_check = 0u;
     }
     __syncthreads();
     const MortonSpread ms(d, mbits);
     const bool v4 = (d == DP);      // DP is d rounded up to a multiple of 4
+    // the unit-cube map with whole float4 rows: the piece-rotated fast path
+    bool unit = v4 && ms.fast();
+    for (int k = 0; k < d && unit; ++k)
+        unit = s_off[k] == 0.0f && s_sc[k] == (float)(1u << log2g) &&
+               (mbits <= log2g || s_ms[k] == (float)(1u << mbits));
+    constexpr int NQ = DP / 4;
+    const int rot = NQ == 4 ? (tid >> 1) & 3 : (NQ == 2 ? (tid >> 2) & 1 : 0);
 
     const int64_t nfull = n / kThreads;
     const uint32_t chunk_bytes = (uint32_t)(kThreads * d * sizeof(float));
@@ -440,7 +496,7 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
     }
     bool bad = false;
     bool timed_out = false;
-    uint32_t hits = 0;
+    uint32_t dups = 0;   // rows of the first chunk whose word another lane of the warp has too
     for (int64_t i = 0; i < my_chunks; ++i) {
         const int s = (int)(i % kMapStages);
         const uint32_t parity = (uint32_t)((i / kMapStages) & 1);
@@ -457,37 +513,44 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
         }
         const int64_t c = blockIdx.x + i * gridDim.x;
         const float* r = s_buf + s * kThreads * d + tid * d;
-        if (i == kCheckChunk) hits = 0;
-        float x[DP];
-        if (v4) {
-#pragma unroll
-            for (int k = 0; k < DP; k += 4) {
-                const float4 q = *reinterpret_cast<const float4*>(r + k);
-                x[k] = q.x; x[k + 1] = q.y; x[k + 2] = q.z; x[k + 3] = q.w;
-            }
+        if (unit) {
+            uint32_t key, code;
+            if (mbits <= log2g) map_keys_unit<DP, true>(r, rot, log2g, mbits, ms, key, code, bad);
+            else map_keys_unit<DP, false>(r, rot, log2g, mbits, ms, key, code, bad);
+            const int64_t row = c * kThreads + tid;
+            if (MODE == kMarkSmall) store_mark<true>(key, code, row, ckey, mkey, MarkPrivate{s_tail});
+            else if (MODE == kMarkNone) store_mark<true>(key, code, row, ckey, mkey, MarkNone{});
+            else store_mark<true>(key, code, row, ckey, mkey, MarkCheck{occ, s_check != 0u}, i == 0 ? &dups : nullptr);
         } else {
+            float x[DP];
+            if (v4) {
 #pragma unroll
-            for (int k = 0; k < DP; ++k) x[k] = (k < d) ? r[k] : 0.0f;
+                for (int k = 0; k < DP; k += 4) {
+                    const float4 q = *reinterpret_cast<const float4*>(r + k);
+                    x[k] = q.x; x[k + 1] = q.y; x[k + 2] = q.z; x[k + 3] = q.w;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < DP; ++k) x[k] = (k < d) ? r[k] : 0.0f;
+            }
+            const int64_t row = c * kThreads + tid;
+            if (MODE == kMarkSmall)
+                map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, row, ckey, mkey, MarkPrivate{s_tail}, bad);
+            else if (MODE == kMarkNone)
+                map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, row, ckey, mkey, MarkNone{}, bad);
+            else
+                map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, row, ckey, mkey,
+                                  MarkCheck{occ, s_check != 0u}, bad, i == 0 ? &dups : nullptr);
         }
-        if (MODE == kMarkSmall)
-            map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, c * kThreads + tid, ckey, mkey,
-                              MarkPrivate{s_tail}, bad);
-        else if (MODE == kMarkNone)
-            map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, c * kThreads + tid, ckey, mkey,
-                              MarkNone{}, bad);
-        else
-            map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, c * kThreads + tid, ckey, mkey,
-                              MarkCheck{occ, s_check != 0u, &hits}, bad);
-        if (MODE == kMarkCheck && i == kCheckChunk) {
-            const uint32_t h = __reduce_add_sync(kFull, hits);
-            if ((tid & 31) == 0 && h) atomicAdd(&s_hits, h);
+        if (MODE == kMarkCheck && i == 0) {
+            const uint32_t h = __reduce_add_sync(kFull, dups);
+            if ((tid & 31) == 0 && h) atomicAdd(&s_dups, h);
         }
         __syncthreads();  // every thread is done with stage s
         if (tid == 0) {
-            // keep looking only if at least a quarter of the rows of chunk
-            // kCheckChunk found their bits set (by then every block has
-            // marked a few chunks, so the hot cells of clustered data are set)
-            if (MODE == kMarkCheck && i == kCheckChunk && s_hits < (uint32_t)(kThreads / 4)) s_check = 0u;
+            // look before marking from the second chunk on when at least
+            // 1/16 of the first chunk's rows shared their word inside a warp
+            if (MODE == kMarkCheck && i == 0 && s_dups >= (uint32_t)(kThreads / 16)) s_check = 1u;
             if (i + kMapStages < my_chunks) {
                 const int64_t c2 = blockIdx.x + (i + kMapStages) * gridDim.x;
                 fence_proxy_async_smem();
