@@ -394,9 +394,17 @@ typedef struct sky_run_stats {
 
 SKY_API sky_status sky_last_run_stats(sky_run_stats* out);
 
-/* Per-phase device times of the last sky_skyline call on the calling thread,
- * taken with CUDA events recorded on the call's stream between the phases.
- * Recording is off until sky_set_phase_timing(1) is called on that thread. */
+/* Device times of the last sky_skyline call on the calling thread, taken with
+ * CUDA events recorded on the call's stream. Off until sky_set_phase_timing()
+ * selects a mode on that thread:
+ *   1  events between the phases; the kernels are launched one by one (no
+ *      CUDA-graph replay), which adds host launch gaps; fills the *_ms phase
+ *      fields, call_ms = 0;
+ *   2  two events around the call's whole kernel sequence, graph replay kept;
+ *      a bounded device-side delay (50 us) precedes the first event so that
+ *      the host has enqueued everything before the device reaches it; fills
+ *      call_ms only.
+ * 0 turns recording off; other values return SKY_ERR_INVALID_ARGUMENT. */
 typedef struct sky_phase_times {
     float normalize_ms;           /* min/max pass + map parameters             */
     float map_mark_ms;            /* steps (a)+(b)                             */
@@ -406,6 +414,7 @@ typedef struct sky_phase_times {
     float gather_ms;              /* survivor layout + tile boxes              */
     float refine_ms;              /* step (d): dominance tests                 */
     float emit_ms;                /* step (d): index compaction                */
+    float call_ms;                /* mode 2: the whole kernel sequence         */
 } sky_phase_times;
 
 SKY_API sky_status sky_set_phase_timing(int32_t enable);

@@ -57,7 +57,7 @@ class RunStats(ctypes.Structure):
 
 class PhaseTimes(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in ("normalize_ms", "map_mark_ms", "prune_ms", "survivors_ms",
-                                               "sort_ms", "gather_ms", "refine_ms", "emit_ms")]
+                                               "sort_ms", "gather_ms", "refine_ms", "emit_ms", "call_ms")]
 
 
 _lib = None
@@ -217,9 +217,13 @@ def last_run_stats() -> dict:
     return {f: getattr(s, f) for f, _ in RunStats._fields_}
 
 
-def set_phase_timing(enable: bool = True):
-    """Record CUDA events between the phases of later skyline calls on this thread."""
-    _check(load().sky_set_phase_timing(1 if enable else 0))
+def set_phase_timing(enable=True):
+    """Device timing of later skyline calls on this thread: True or 1 = events
+    between the phases (kernels launched one by one), 2 = events around the
+    whole kernel sequence (graph replay kept; last_phase_times()["call_ms"]),
+    False or 0 = off."""
+    mode = 1 if enable is True else (0 if enable is False else int(enable))
+    _check(load().sky_set_phase_timing(mode))
 
 
 def last_phase_times() -> dict:

@@ -19,10 +19,14 @@
 #include <cfloat>
 #include <cstdint>
 
+#include <cooperative_groups.h>
+
 #include "sky_common.cuh"
 #include "sky_internal.h"
 
 namespace sky {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -138,45 +142,68 @@ __global__ void k_params(const uint32_t* mm_min, const uint32_t* mm_max, int d, 
     if (k < kMaxDim) write_params(k, d, log2g, mbits, normalise != 0, mm_min, mm_max, params);
 }
 
+// Clears the call's result block and the occupancy bitmap in one launch (two
+// memset nodes in a CUDA graph cost several microseconds of scheduling each).
+// Both start 256-byte aligned; the bitmap is cleared in 16-byte stores.
+__global__ void __launch_bounds__(kThreads) k_clear(DevResult* res, uint32_t* occ, int64_t words)
+{
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    constexpr int kResWords = (int)(sizeof(DevResult) / sizeof(uint32_t));
+    if (tid < kResWords) reinterpret_cast<uint32_t*>(res)[tid] = 0u;
+    const int64_t q = words / 4;
+    uint4* o4 = reinterpret_cast<uint4*>(occ);
+    for (int64_t i = tid; i < q; i += nthr) o4[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t i = q * 4 + tid; i < words; i += nthr) occ[i] = 0u;
+}
+
 // Automatic map, decided on the strided sample of rows 0, t, 2t, ... < n
 // with t = ceil(n / kDecideSample): the unit-cube map (Eq. 1 as printed) when
 // every sampled dimension lies in [0, 1] and spans at least half of it,
 // otherwise min / max scales from the sample's range. Rows outside that range
 // clamp into the edge columns, so the map stays monotone -- all that pruning
-// and the refinement's codes need. One CTA; the sample's min / max are exact,
-// so the decision does not depend on the reduction order.
+// and the refinement's codes need. The sample's min / max are exact, so the
+// decision does not depend on the reduction order.
+//
+// One cluster of kDecideCluster CTAs, one sampled row per thread: CTA r reads
+// the r-th contiguous slice of the sample (its rows span 1/kDecideCluster of
+// the input, so each SM walks fewer pages), reduces it in shared memory, and
+// CTA 0 combines the slices through distributed shared memory. (A single CTA
+// walking all 4,096 rows was latency-bound: 40 us on a 640 MB input.)
 constexpr int kDecideSample = 4096;
-constexpr int kDecideThreads = 1024;
+constexpr int kDecideCluster = 8;
+constexpr int kDecideThreads = kDecideSample / kDecideCluster;   // 512
 
 template <int DP>
-__global__ void __launch_bounds__(kDecideThreads) k_sample_params(const float* __restrict__ pts, int64_t n, int d,
-                                                                  int64_t ld, int log2g, int mbits,
-                                                                  uint32_t* mm_min, uint32_t* mm_max,
-                                                                  float* params)
+__global__ void __cluster_dims__(kDecideCluster, 1, 1) __launch_bounds__(kDecideThreads)
+    k_sample_params(const float* __restrict__ pts, int64_t n, int d, int64_t ld, bool vec4, int log2g, int mbits,
+                    uint32_t* mm_min, uint32_t* mm_max, float* params)
 {
     __shared__ float s_mn[kDecideThreads / 32][DP], s_mx[kDecideThreads / 32][DP];
+    __shared__ float c_mn[DP], c_mx[DP];   // this CTA's slice; read by CTA 0 of the cluster
     __shared__ int s_bad;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int64_t t = (n + kDecideSample - 1) / kDecideSample;
     if (t < 1) t = 1;
     const int64_t rows = (n + t - 1) / t;
-    constexpr int U = kDecideSample / kDecideThreads;
+    const int64_t r = (int64_t)rank * kDecideThreads + tid;
+    float x[DP];
+    if (r < rows) {
+        load_row<DP>(pts + r * t * ld, d, vec4, x);
+#pragma unroll
+        for (int k = 0; k < DP; ++k)
+            if (k >= d) x[k] = NAN;
+    } else {
+#pragma unroll
+        for (int k = 0; k < DP; ++k) x[k] = NAN;   // fminf / fmaxf ignore NaN
+    }
     float mn[DP], mx[DP];
 #pragma unroll
-    for (int k = 0; k < DP; ++k) { mn[k] = INFINITY; mx[k] = -INFINITY; }
-    float x[U][DP];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int64_t r = (int64_t)u * kDecideThreads + tid;
-#pragma unroll
-        for (int k = 0; k < DP; ++k) x[u][k] = (r < rows && k < d) ? __ldg(pts + r * t * ld + k) : NAN;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int k = 0; k < DP; ++k) { mn[k] = fminf(mn[k], x[u][k]); mx[k] = fmaxf(mx[k], x[u][k]); }
-#pragma unroll
     for (int k = 0; k < DP; ++k) {
+        mn[k] = x[k];
+        mx[k] = x[k];
         for (int o = 16; o > 0; o >>= 1) {
             mn[k] = fminf(mn[k], __shfl_xor_sync(kFull, mn[k], o));
             mx[k] = fmaxf(mx[k], __shfl_xor_sync(kFull, mx[k], o));
@@ -185,16 +212,31 @@ __global__ void __launch_bounds__(kDecideThreads) k_sample_params(const float* _
     }
     if (tid == 0) s_bad = 0;
     __syncthreads();
-    if (tid < d) {
-        float lo = INFINITY, hi = -INFINITY;
+    if (tid < DP) {
+        float lo = NAN, hi = NAN;
         for (int w = 0; w < kDecideThreads / 32; ++w) { lo = fminf(lo, s_mn[w][tid]); hi = fmaxf(hi, s_mx[w][tid]); }
-        mm_min[tid] = float_to_ordered(lo);
-        mm_max[tid] = float_to_ordered(hi);
-        const bool unit_ok = (lo >= 0.0f) && (hi <= 1.0f) && (__fsub_rn(hi, lo) >= 0.5f);
-        if (!unit_ok) atomicOr(&s_bad, 1);
+        c_mn[tid] = lo;
+        c_mx[tid] = hi;
     }
-    __syncthreads();
-    if (tid < kMaxDim) write_params(tid, d, log2g, mbits, s_bad != 0, mm_min, mm_max, params);
+    cluster.sync();   // every slice is in its CTA's shared memory
+    if (rank == 0) {
+        if (tid < d) {
+            float lo = INFINITY, hi = -INFINITY;
+            for (int q = 0; q < kDecideCluster; ++q) {
+                lo = fminf(lo, *cluster.map_shared_rank(&c_mn[tid], q));
+                hi = fmaxf(hi, *cluster.map_shared_rank(&c_mx[tid], q));
+            }
+            mm_min[tid] = float_to_ordered(lo);
+            mm_max[tid] = float_to_ordered(hi);
+            const bool unit_ok = (lo >= 0.0f) && (hi <= 1.0f) && (__fsub_rn(hi, lo) >= 0.5f);
+            if (!unit_ok) atomicOr(&s_bad, 1);
+        }
+    }
+    cluster.sync();   // CTA 0 has read every slice; the other CTAs may exit
+    if (rank == 0) {
+        __syncthreads();
+        if (tid < kMaxDim) write_params(tid, d, log2g, mbits, s_bad != 0, mm_min, mm_max, params);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -350,39 +392,50 @@ __device__ __forceinline__ void map_one(const float (&x)[DP], int d, int log2g, 
 // visited starting at piece `rot`, so that the eight threads of a 128-byte
 // shared-memory phase read eight different bank groups (rows of 32 or 64
 // bytes would otherwise collide 2- or 4-way); the key and the Morton key are
-// ORs of shifted per-dimension values, so the visiting order does not matter.
+// ORs of shifted per-piece values, so the visiting order does not matter.
 // x * G here equals (x - 0) * G of the general map bit for bit.
+//
+// One conversion per dimension: the column in the finer of the two grids
+// (2^fb columns, fb = max(log2g, mbits)), clamped to 2^fb - 1; the column in
+// the coarser grid is that column shifted right by the difference s. Exact:
+// x * 2^fb and x * 2^(fb-s) are both exact products (power-of-two scales),
+// so floor(x * 2^fb) >> s == floor(x * 2^(fb-s)); clamping commutes with the
+// shift (2^fb - 1 >> s == 2^(fb-s) - 1); negative, NaN and overflowing
+// values convert to 0 or saturate in both grids alike.
 template <int DP, bool COARSE>
 __device__ __forceinline__ void map_keys_unit(const float* __restrict__ r, int rot, int log2g, int mbits,
                                               const MortonSpread& ms, uint32_t& key_out, uint32_t& code_out,
                                               bool& bad)
 {
     constexpr int NQ = DP / 4;
-    const uint32_t G = 1u << log2g, M = 1u << mbits;
-    const float Gf = (float)G, Mf = (float)M;
+    const int fbits = COARSE ? log2g : mbits;
+    const int sh = COARSE ? log2g - mbits : mbits - log2g;
+    const float F = (float)(1u << fbits);
+    const uint32_t Fm1 = (1u << fbits) - 1u;
+    const uint32_t G = 1u << log2g;
+    // Morton spread of dimension 4q + i: (mq * (magic << i)) & (mask << i)
+    const uint32_t mg[4] = {ms.magic, ms.magic << 1, ms.magic << 2, ms.magic << 3};
+    const uint32_t mk[4] = {ms.mask, ms.mask << 1, ms.mask << 2, ms.mask << 3};
     uint32_t key = 0, code = 0;
-    float nanacc = 0.0f;
+    float nanacc = 0.0f;   // x * 0 is NaN exactly when x is infinite or NaN
 #pragma unroll
     for (int j = 0; j < NQ; ++j) {
         const int q = (j + rot) % NQ;
         const float4 v = *reinterpret_cast<const float4*>(r + 4 * q);
         const float xs[4] = {v.x, v.y, v.z, v.w};
+        uint32_t kq = 0, cq = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int k = 4 * q + i;
+        for (int i = 3; i >= 0; --i) {
             nanacc = fmaf(xs[i], 0.0f, nanacc);
-            uint32_t c = __float2uint_rd(__fmul_rn(xs[i], Gf));
-            c = c < G - 1u ? c : G - 1u;
-            key |= c << (log2g * k);
-            uint32_t mq;
-            if (COARSE) {
-                mq = c >> (log2g - mbits);
-            } else {
-                mq = __float2uint_rd(__fmul_rn(xs[i], Mf));
-                mq = mq < M - 1u ? mq : M - 1u;
-            }
-            code |= ((mq * ms.magic) & ms.mask) << k;
+            uint32_t f = __float2uint_rd(__fmul_rn(xs[i], F));
+            f = f < Fm1 ? f : Fm1;
+            const uint32_t c = COARSE ? f : f >> sh;
+            const uint32_t mq = COARSE ? f >> sh : f;
+            kq = kq * G + c;                      // dimension 4q + 3 most significant
+            cq |= (mq * mg[i]) & mk[i];
         }
+        key |= kq << (log2g * 4 * q);
+        code |= cq << (4 * q);
     }
     bad |= nanacc != nanacc;
     key_out = key;
@@ -500,7 +553,9 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
     for (int64_t i = 0; i < my_chunks; ++i) {
         const int s = (int)(i % kMapStages);
         const uint32_t parity = (uint32_t)((i / kMapStages) & 1);
-        if (!mbar_wait(&s_bar[s], parity, err)) { timed_out = true; }
+        // one thread waits on the stage (the TMA writes become visible to it),
+        // the block barrier passes them on to the others
+        if (tid == 0 && !mbar_wait(&s_bar[s], parity, err)) timed_out = true;
         if (__syncthreads_or(timed_out)) {
             // Let every copy already issued land before the block goes on.
             if (tid == 0) {
@@ -618,47 +673,91 @@ __global__ void __launch_bounds__(kThreads) k_prefix_or_dim(uint32_t* R, int64_t
 // holds, for a run of wc consecutive words of the low block, all G^kh rows
 // of the high grid in shared memory. Both are the per-dimension prefix-OR of
 // prefix_or_dim applied in dimension order.
-constexpr int kPrefixThreads = 512;
+constexpr int kPrefixThreads = 1024;   // bound of k_prefix_low's launch
+// Tiling of the two-launch prefix-OR (see prefix_split)
+#ifndef SKY_PREFIX_LOW_BITS
+#define SKY_PREFIX_LOW_BITS 16
+#endif
+#ifndef SKY_PREFIX_LOW_THREADS
+#define SKY_PREFIX_LOW_THREADS 512
+#endif
+#ifndef SKY_PREFIX_WORDS_PER_THREAD
+#define SKY_PREFIX_WORDS_PER_THREAD 4
+#endif
+#ifndef SKY_PREFIX_HIGH_WORDS
+#define SKY_PREFIX_HIGH_WORDS 2048
+#endif
+constexpr int kPrefixLowBits = SKY_PREFIX_LOW_BITS;            // bits per low block
+constexpr int kPrefixLowThreads = SKY_PREFIX_LOW_THREADS;      // at most, per low block
+constexpr int kPrefixWordsPerThread = SKY_PREFIX_WORDS_PER_THREAD;
+constexpr int kPrefixHighWords = SKY_PREFIX_HIGH_WORDS;        // shared words per high block
+static_assert(kPrefixLowBits >= 5 && kPrefixLowBits <= 20, "low blocks of whole words, at most 128 KB");
 
 __global__ void __launch_bounds__(kPrefixThreads) k_prefix_low(const uint32_t* __restrict__ occ, uint32_t* pre,
                                                                int64_t block_words, int log2g, int kl)
 {
-    extern __shared__ uint32_t s_w[];
+    extern __shared__ uint4 s_w4[];
+    uint32_t* s_w = reinterpret_cast<uint32_t*>(s_w4);
     const int64_t base = (int64_t)blockIdx.x * block_words;
-    for (int64_t w = threadIdx.x; w < block_words; w += blockDim.x) s_w[w] = occ[base + w];
+    const uint32_t bw = (uint32_t)block_words;
+    if ((bw & 3u) == 0u) {   // 16-byte pieces (blocks of >= 128 cells)
+        for (uint32_t w = threadIdx.x; w < bw / 4u; w += blockDim.x) cp_async16(s_w4 + w, occ + base + 4 * w);
+    } else {
+        for (uint32_t w = threadIdx.x; w < bw; w += blockDim.x) cp_async4(s_w + w, occ + base + w);
+    }
+    cp_async_wait_all();
     __syncthreads();
-    for (int k = 0; k < kl; ++k) {
+    // the dimensions inside one word in one pass, the others one pass each
+    int kin = 0;
+    while (kin < kl && log2g * (kin + 1) <= 5) ++kin;
+    if (kin > 0) {
+        prefix_or_inword(s_w, block_words, log2g, kin, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
+    for (int k = kin; k < kl; ++k) {
         prefix_or_dim(s_w, block_words, log2g, k, threadIdx.x, blockDim.x);
         __syncthreads();
     }
-    for (int64_t w = threadIdx.x; w < block_words; w += blockDim.x) pre[base + w] = s_w[w];
+    if ((bw & 3u) == 0u) {
+        uint4* dst = reinterpret_cast<uint4*>(pre + base);
+        for (uint32_t w = threadIdx.x; w < bw / 4u; w += blockDim.x) dst[w] = s_w4[w];
+    } else {
+        for (uint32_t w = threadIdx.x; w < bw; w += blockDim.x) pre[base + w] = s_w[w];
+    }
 }
 
-__global__ void __launch_bounds__(kThreads) k_prefix_high(uint32_t* pre, int64_t row_words, int64_t rows, int wc,
+// rows, wc and every stride are powers of two (log2: lrows, lwc); indices
+// fit in 32 bits (at most 2^22 words).
+__global__ void __launch_bounds__(kThreads) k_prefix_high(uint32_t* pre, int64_t row_words, int lrows, int lwc,
                                                           int log2g, int kh)
 {
-    extern __shared__ uint32_t s_t[];   // [rows][wc]
-    const int64_t c0 = (int64_t)blockIdx.x * wc;
-    const int64_t cells = rows * wc;
-    for (int64_t t = threadIdx.x; t < cells; t += blockDim.x) s_t[t] = pre[(t / wc) * row_words + c0 + t % wc];
+    extern __shared__ __align__(16) uint32_t s_t[];   // [rows][wc]
+    const uint32_t wc = 1u << lwc;
+    const uint32_t c0 = blockIdx.x << lwc;
+    const uint32_t cells = 1u << (lrows + lwc);
+    const uint32_t rw = (uint32_t)row_words;
+    if (lwc >= 2) {   // rows of >= 4 words: 16-byte pieces (row starts are 16-byte aligned)
+        for (uint32_t t = 4 * threadIdx.x; t < cells; t += 4 * blockDim.x)
+            cp_async16(s_t + t, pre + (t >> lwc) * rw + c0 + (t & (wc - 1u)));
+    } else {
+        for (uint32_t t = threadIdx.x; t < cells; t += blockDim.x)
+            cp_async4(s_t + t, pre + (t >> lwc) * rw + c0 + (t & (wc - 1u)));
+    }
+    cp_async_wait_all();
     __syncthreads();
-    const int64_t G = 1ll << log2g;
+    const uint32_t G = 1u << log2g;
     for (int j = 0; j < kh; ++j) {
-        const int64_t sr = 1ll << (log2g * j);    // row stride of high dimension j
-        const int64_t lines = rows / G * wc;
-        for (int64_t L = threadIdx.x; L < lines; L += blockDim.x) {
-            const int64_t w = L % wc, l = L / wc;
-            int64_t r = (l / sr) * G * sr + l % sr;
-            uint32_t acc = s_t[r * wc + w];
-            for (int64_t i = 1; i < G; ++i) {
-                r += sr;
-                acc |= s_t[r * wc + w];
-                s_t[r * wc + w] = acc;
-            }
+        const int lsr = log2g * j;                          // row stride of high dimension j: 2^lsr
+        const uint32_t lines = 1u << (lrows - log2g + lwc);
+        for (uint32_t L = threadIdx.x; L < lines; L += blockDim.x) {
+            const uint32_t w = L & (wc - 1u), l = L >> lwc;
+            const uint32_t r = ((l >> lsr) << (lsr + log2g)) + (l & ((1u << lsr) - 1u));
+            or_scan_strided(s_t + (r << lwc) + w, G, (1u << lsr) << lwc, 0u);
         }
         __syncthreads();
     }
-    for (int64_t t = threadIdx.x; t < cells; t += blockDim.x) pre[(t / wc) * row_words + c0 + t % wc] = s_t[t];
+    for (uint32_t t = threadIdx.x; t < cells; t += blockDim.x)
+        pre[(t >> lwc) * rw + c0 + (t & (wc - 1u))] = s_t[t];
 }
 
 __global__ void __launch_bounds__(kThreads) k_dominated(const uint32_t* R, uint32_t* dom, int64_t words,
@@ -774,20 +873,28 @@ __global__ void k_snap_finalize(const float* __restrict__ pts, int d, int64_t ld
 // ---------------------------------------------------------------------------
 // Survivors of step (c), compacted in row order with their Morton keys, in
 // two passes over the same fixed split of the rows: block b owns the
-// contiguous tiles [b * tpb, (b + 1) * tpb) of kSurvTile rows.
-//   k_surv_flags    reads the cell keys, probes the prefix-OR bitmap at
-//                   key - (1, ..., 1) (Corollary 4: a cell is dominated iff
-//                   that cell is covered), applies the optional snapped
-//                   proposals, writes one flag bit per row and the block's
-//                   survivor count
-//   k_surv_scatter  sums the counts of the blocks before it, then walks its
-//                   tiles: block scan of the flags, survivors staged in
-//                   shared memory, written out coalesced
-// No look-back chain and no atomics; the second pass reads the flag bits
-// (n / 8 bytes) and the Morton keys of survivors only.
+// contiguous tiles [b * tpb, (b + 1) * tpb) of kSurvTile rows. Row
+// tile * kSurvTile + j * kThreads + tid is item j of thread tid, so the warp
+// ballot of item j is exactly flag word row / 32.
+//   k_surv_flags    streams the cell keys of its tiles through a ring of
+//                   shared-memory stages (1-D bulk copies), probes the
+//                   prefix-OR bitmap at key - (1, ..., 1) (Corollary 4: a cell
+//                   is dominated iff that cell is covered), applies the
+//                   optional snapped proposals, writes the flag words and the
+//                   block's survivor count
+//   k_surv_scatter  sums the counts of the blocks before it, counts the
+//                   survivors of each of its tiles from the flag words and
+//                   scans them (every tile's output offset is known before
+//                   its keys arrive), then streams the Morton keys of the
+//                   tiles that keep a row through the same kind of ring and
+//                   writes (Morton key, row) pairs, coalesced per warp
+// No look-back chain and no global atomics.
 constexpr int kSurvItems = 8;
 constexpr int kSurvTile = kSurvItems * kThreads;   // 2048 rows
-static_assert(kSurvTile % 32 == 0, "whole flag words per tile");
+constexpr int kSurvStages = 4;
+constexpr int kSurvMaxTpb = 2048;                  // tiles per block (n < 2^31 needs at most 1,772)
+constexpr int kTileWords = kSurvTile / 32;         // flag words per tile
+static_assert(kTileWords == 64, "one warp scans a tile's flag words two per lane");
 
 // True when some lg-bit field of key is zero: (key - ones) borrows into the
 // top bit of a field only below a zero field, and ~key keeps it only there.
@@ -796,92 +903,149 @@ __device__ __forceinline__ bool has_zero_column(uint32_t key, uint32_t ones, uin
     return ((key - ones) & ~key & highs) != 0u;
 }
 
+// Bytes of tile `tile`'s 32-bit words (the last tile may be short), rounded
+// up to the 16-byte granule of a bulk copy; the key arrays carry at least 16
+// bytes of slack past row n.
+__device__ __forceinline__ uint32_t surv_tile_bytes(int64_t tile, int64_t n)
+{
+    int64_t rows = n - tile * kSurvTile;
+    if (rows > kSurvTile) rows = kSurvTile;
+    return (uint32_t)((rows * 4 + 15) & ~int64_t(15));
+}
+
+__device__ __forceinline__ void surv_issue(uint32_t* stage, const uint32_t* src, int64_t tile, int64_t n,
+                                           uint64_t* bar)
+{
+    const uint32_t bytes = surv_tile_bytes(tile, n);
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(stage, src + tile * kSurvTile, bytes, bar);
+}
+
+// Four consecutive rows per thread and step (one 16-byte shared-memory
+// read); a tile is two steps of 1,024 rows. The eight lanes 8q .. 8q+7 of a
+// warp hold the 32 rows of one flag word as nibbles, OR-ed together in three
+// shuffles. The bitmap is probed only when some lane of the warp needs it.
 template <int DP>
 __global__ void __launch_bounds__(kThreads) k_surv_flags(
     const float* __restrict__ pts, int64_t n, int d, int64_t ld, bool vec4, int log2g,
     const uint32_t* __restrict__ ckey, const uint32_t* __restrict__ pre, const float* __restrict__ filt,
-    int n_filter_max, const DevResult* res, int64_t tpb, uint32_t* __restrict__ flags, uint32_t* __restrict__ counts)
+    int n_filter_max, DevResult* res, int64_t tpb, uint32_t* __restrict__ flags, uint32_t* __restrict__ counts)
 {
+    extern __shared__ __align__(128) uint32_t s_ring[];   // [kSurvStages][kSurvTile] cell keys
+    __shared__ __align__(8) uint64_t s_bar[kSurvStages];
     __shared__ float s_f[16 * kMaxDim];
     __shared__ uint32_t s_cnt[kThreads / 32];
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nf = n_filter_max ? (int)res->n_filter_used : 0;
     for (int t = tid; t < nf * kMaxDim; t += kThreads) s_f[t] = filt[t];
+    const int64_t ntiles = (n + kSurvTile - 1) / kSurvTile;
+    const int64_t t0 = (int64_t)blockIdx.x * tpb;
+    const int64_t my = (t0 + tpb < ntiles ? t0 + tpb : ntiles) - t0;
+    if (tid == 0) {
+        for (int s = 0; s < kSurvStages; ++s) mbar_init(&s_bar[s], 1);
+        mbar_fence_init();
+        for (int64_t i = 0; i < my && i < kSurvStages; ++i)
+            surv_issue(s_ring + i * kSurvTile, ckey, t0 + i, n, &s_bar[i]);
+    }
     __syncthreads();
     // With log2g = 0 the grid is one cell, which nothing dominates (and the
     // field masks below would be empty): no row probes the bitmap then.
     const bool can_dominate = log2g > 0;
     const uint32_t ones = ones_key(log2g, d);
     const uint32_t highs = can_dominate ? ones << (log2g - 1) : 0u;
-    const int64_t ntiles = (n + kSurvTile - 1) / kSurvTile;
-    const int64_t t0 = (int64_t)blockIdx.x * tpb;
-    const int64_t t1 = t0 + tpb < ntiles ? t0 + tpb : ntiles;
-    const int64_t nwords = (n + 31) / 32;
-    uint32_t cnt = 0;
-    uint32_t kk[kSurvItems], nx[kSurvItems];
-    auto load_keys = [&](int64_t tile, uint32_t (&dst)[kSurvItems]) {
-        const int64_t base = tile * kSurvTile + (int64_t)tid * kSurvItems;
-        if (base + kSurvItems <= n) {
-            const uint4* src = reinterpret_cast<const uint4*>(ckey + base);
-            const uint4 a = __ldg(src), b = __ldg(src + 1);
-            dst[0] = a.x; dst[1] = a.y; dst[2] = a.z; dst[3] = a.w;
-            dst[4] = b.x; dst[5] = b.y; dst[6] = b.z; dst[7] = b.w;
-        } else {
-#pragma unroll
-            for (int j = 0; j < kSurvItems; ++j) dst[j] = (base + j < n) ? __ldg(ckey + base + j) : 0u;
+    const int sub = lane & 7;                  // nibble of this lane in its flag word
+    uint32_t cnt = 0;                          // rows kept by this thread
+    bool timed_out = false;
+    for (int64_t i = 0; i < my; ++i) {
+        const int s = (int)(i % kSurvStages);
+        if (tid == 0 && !mbar_wait(&s_bar[s], (uint32_t)((i / kSurvStages) & 1), &res->err)) timed_out = true;
+        if (__syncthreads_or(timed_out)) {
+            if (tid == 0)   // let the copies already issued land before the block exits
+                for (int64_t j = i; j < my && j < i + kSurvStages; ++j)
+                    mbar_wait(&s_bar[j % kSurvStages], (uint32_t)((j / kSurvStages) & 1), nullptr);
+            break;
         }
-    };
-    if (t0 < t1) load_keys(t0, kk);
-    for (int64_t tile = t0; tile < t1; ++tile) {
-        if (tile + 1 < t1) load_keys(tile + 1, nx);      // next tile's keys in flight
-        const int64_t base = tile * kSurvTile + (int64_t)tid * kSurvItems;
-        uint32_t word[kSurvItems];
-        bool probe[kSurvItems];
+        const int64_t tile = t0 + i;
+        const int64_t row0 = tile * kSurvTile;
+        // rows of this tile: all kSurvTile but in the last tile
+        const uint32_t valid = (uint32_t)(n - row0 < kSurvTile ? n - row0 : kSurvTile);
+        const uint4* sk4 = reinterpret_cast<const uint4*>(s_ring + s * kSurvTile);
+        uint32_t* fl = flags + tile * kTileWords;
+        constexpr int H = kSurvTile / (4 * kThreads);   // steps per tile
+        static_assert(H == 2, "two steps of four rows per thread");
+        uint32_t ks[H][4], keep[H], need[H];
 #pragma unroll
-        for (int j = 0; j < kSurvItems; ++j) {
-            probe[j] = can_dominate && (base + j < n) && !has_zero_column(kk[j], ones, highs);
-            word[j] = probe[j] ? __ldg(pre + ((kk[j] - ones) >> 5)) : 0u;
-        }
-        uint32_t f = 0;
+        for (int h = 0; h < H; ++h) {
+            const uint32_t r = (uint32_t)(h * 4 * kThreads + 4 * tid);   // first of this thread's 4 rows
+            const uint4 k4 = sk4[h * kThreads + tid];
+            ks[h][0] = k4.x; ks[h][1] = k4.y; ks[h][2] = k4.z; ks[h][3] = k4.w;
+            keep[h] = 0u;
+            need[h] = 0u;
 #pragma unroll
-        for (int j = 0; j < kSurvItems; ++j) {
-            const int64_t i = base + j;
-            if (i >= n) continue;
-            if (probe[j] && ((word[j] >> ((kk[j] - ones) & 31u)) & 1u)) continue;
-            if (nf) {
-                float x[DP];
-                load_row<DP>(pts + i * ld, d, vec4, x);
-                bool filtered = false;
-                for (int q = 0; q < nf && !filtered; ++q) {
-                    bool le = true, lt = false;
-#pragma unroll
-                    for (int k = 0; k < DP; ++k) {
-                        if (k < d) {
-                            const float v = s_f[q * kMaxDim + k];
-                            le &= v <= x[k];
-                            lt |= v < x[k];
-                        }
-                    }
-                    filtered = le && lt;  // Definition 1: the snapped point dominates x
+            for (int e = 0; e < 4; ++e) {
+                if (r + e < valid) {
+                    if (can_dominate && !has_zero_column(ks[h][e], ones, highs)) need[h] |= 1u << e;
+                    else keep[h] |= 1u << e;
                 }
-                if (filtered) continue;
             }
-            f |= 1u << j;
         }
-        cnt += __popc(f);
-        // lanes 4q .. 4q+3 hold the four bytes of flag word (tile * 64 + tid / 4)
-        uint32_t v = f << (8 * (lane & 3));
-        v |= __shfl_xor_sync(kFull, v, 1);
-        v |= __shfl_xor_sync(kFull, v, 2);
-        const int64_t w = tile * (kSurvTile / 32) + tid / 4;
-        if ((lane & 3) == 0 && w < nwords) flags[w] = v;
-        if (tile + 1 < t1) {
+        // every bitmap probe of the tile in flight at once
+        if (__any_sync(kFull, (need[0] | need[1]) != 0u)) {
+            uint32_t wd[H][4];
 #pragma unroll
-            for (int j = 0; j < kSurvItems; ++j) kk[j] = nx[j];
+            for (int h = 0; h < H; ++h)
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    wd[h][e] = ((need[h] >> e) & 1u) ? __ldg(pre + ((ks[h][e] - ones) >> 5)) : 0u;
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (((need[h] >> e) & 1u) && !((wd[h][e] >> ((ks[h][e] - ones) & 31u)) & 1u))
+                        keep[h] |= 1u << e;
+        }
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const uint32_t r = (uint32_t)(h * 4 * kThreads + 4 * tid);
+            if (nf && keep[h]) {
+#pragma unroll 1
+                for (int e = 0; e < 4; ++e) {
+                    if (!((keep[h] >> e) & 1u)) continue;
+                    float x[DP];
+                    load_row<DP>(pts + (row0 + r + e) * ld, d, vec4, x);
+                    bool filtered = false;
+                    for (int q = 0; q < nf && !filtered; ++q) {
+                        bool le = true, lt = false;
+#pragma unroll
+                        for (int k = 0; k < DP; ++k) {
+                            if (k < d) {
+                                const float v = s_f[q * kMaxDim + k];
+                                le &= v <= x[k];
+                                lt |= v < x[k];
+                            }
+                        }
+                        filtered = le && lt;  // Definition 1: the snapped point dominates x
+                    }
+                    if (filtered) keep[h] &= ~(1u << e);
+                }
+            }
+            cnt += (uint32_t)__popc(keep[h]);
+            uint32_t v = keep[h] << (4 * sub);
+            v |= __shfl_xor_sync(kFull, v, 1);
+            v |= __shfl_xor_sync(kFull, v, 2);
+            v |= __shfl_xor_sync(kFull, v, 4);
+            // words past the end of the flag array only hold rows >= n
+            const uint32_t wr = r - 4u * (uint32_t)sub;   // first row of this lane's flag word
+            if (sub == 0 && wr < valid) fl[wr >> 5] = v;
+        }
+        __syncthreads();   // stage s consumed by every thread
+        if (tid == 0 && i + kSurvStages < my) {
+            fence_proxy_async_smem();
+            surv_issue(s_ring + s * kSurvTile, ckey, t0 + i + kSurvStages, n, &s_bar[s]);
         }
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
-    if (lane == 0) s_cnt[tid >> 5] = cnt;
+    if (lane == 0) s_cnt[warp] = cnt;
     __syncthreads();
     if (tid == 0) {
         uint32_t t = 0;
@@ -890,70 +1054,132 @@ __global__ void __launch_bounds__(kThreads) k_surv_flags(
     }
 }
 
+// The first kSurvStages tiles of the block are requested before anything
+// else (their keys arrive while the block computes its offsets); later tiles
+// are requested only when they keep a row.
 __global__ void __launch_bounds__(kThreads) k_surv_scatter(int64_t n, const uint32_t* __restrict__ mkey,
                                                            const uint32_t* __restrict__ flags,
                                                            const uint32_t* __restrict__ counts, int64_t tpb,
                                                            DevResult* res, uint32_t* __restrict__ surv_key,
                                                            uint32_t* __restrict__ surv_idx)
 {
+    // [kSurvStages][kSurvTile] Morton keys, then per tile of this block its
+    // survivor count [tpb] and its exclusive offset [tpb]
+    extern __shared__ __align__(128) uint32_t s_ring[];
+    uint32_t* s_tc = s_ring + kSurvStages * kSurvTile;
+    uint32_t* s_to = s_tc + tpb;
+    __shared__ __align__(8) uint64_t s_bar[kSurvStages];
     __shared__ uint32_t s_warp[kThreads / 32];
-    __shared__ uint32_t s_key[kSurvTile], s_idx[kSurvTile];
     __shared__ uint32_t s_off;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t ntiles = (n + kSurvTile - 1) / kSurvTile;
+    const int64_t t0 = (int64_t)blockIdx.x * tpb;
+    const int my = (int)((t0 + tpb < ntiles ? t0 + tpb : ntiles) - t0);
+    const int64_t nwords = (n + 31) / 32;
+    int nxt = 0;            // thread 0: next tile of the block to request
+    int issued = 0;         // thread 0: copies requested
+    if (tid == 0) {
+        for (int st = 0; st < kSurvStages; ++st) mbar_init(&s_bar[st], 1);
+        mbar_fence_init();
+        for (; nxt < my && nxt < kSurvStages; ++nxt, ++issued)
+            surv_issue(s_ring + nxt * kSurvTile, mkey, t0 + nxt, n, &s_bar[nxt]);
+    }
     // rows kept by the blocks before this one
     uint32_t part = 0;
     for (int b = tid; b < (int)blockIdx.x; b += kThreads) part += counts[b];
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
-    if (lane == 0) s_warp[tid >> 5] = part;
+    part = __reduce_add_sync(kFull, part);
+    if (lane == 0) s_warp[warp] = part;
+    for (int i = tid; i < my; i += kThreads) s_tc[i] = 0u;
     __syncthreads();
     if (tid == 0) {
         uint32_t t = 0;
         for (int w = 0; w < kThreads / 32; ++w) t += s_warp[w];
         s_off = t;
     }
+    // survivors per tile: the 32 lanes of a warp read 32 words of one tile
+    for (int w = tid; w < my * kTileWords; w += kThreads) {
+        const int64_t gw = t0 * kTileWords + w;
+        uint32_t c = gw < nwords ? (uint32_t)__popc(__ldg(flags + gw)) : 0u;
+        c = __reduce_add_sync(kFull, c);
+        if (lane == 0) atomicAdd(&s_tc[w / kTileWords], c);
+    }
     __syncthreads();
-    uint32_t running = s_off;
-    const int64_t ntiles = (n + kSurvTile - 1) / kSurvTile;
-    const int64_t t0 = (int64_t)blockIdx.x * tpb;
-    const int64_t t1 = t0 + tpb < ntiles ? t0 + tpb : ntiles;
-    const int64_t nwords = (n + 31) / 32;
-    for (int64_t tile = t0; tile < t1; ++tile) {
-        const int64_t w = tile * (kSurvTile / 32) + tid / 4;
-        const uint32_t f = (w < nwords) ? (__ldg(flags + w) >> (8 * (tid & 3))) & 0xffu : 0u;
-        const int64_t base = tile * kSurvTile + (int64_t)tid * kSurvItems;
-        uint32_t mk[kSurvItems];
-        if (f) {
-            if (base + kSurvItems <= n) {
-                const uint4* src = reinterpret_cast<const uint4*>(mkey + base);
-                const uint4 a = __ldg(src), b = __ldg(src + 1);
-                mk[0] = a.x; mk[1] = a.y; mk[2] = a.z; mk[3] = a.w;
-                mk[4] = b.x; mk[5] = b.y; mk[6] = b.z; mk[7] = b.w;
-            } else {
+    // exclusive offsets of the tiles: each thread scans a contiguous run
+    const int per = (my + kThreads - 1) / kThreads;
+    const int i0 = tid * per;
+    uint32_t run = 0;
+    for (int i = i0; i < i0 + per && i < my; ++i) run += s_tc[i];
+    uint32_t total;
+    uint32_t before = block_excl_scan<kThreads>(run, s_warp, total);
+    for (int i = i0; i < i0 + per && i < my; ++i) {
+        s_to[i] = before;
+        before += s_tc[i];
+    }
+    __syncthreads();
+    const uint32_t base_off = s_off;
+    const uint32_t below = lanemask_lt();
+    int c = 0;              // stages consumed so far
+    bool timed_out = false;
+    for (int i = 0; i < my; ++i) {
+        const uint32_t cnt = s_tc[i];
+        if (i >= kSurvStages && cnt == 0u) continue;   // never requested (block-uniform)
+        const int s = c % kSurvStages;
+        const int64_t tile = t0 + i;
+        uint32_t fa = 0, fb = 0, oa = 0, ob = 0;
+        if (cnt) {
+            // every warp scans the tile's 64 flag words itself (lane l: words
+            // l and 32 + l) while thread 0 waits for the keys
+            const int64_t gw = tile * kTileWords + lane;
+            fa = gw < nwords ? __ldg(flags + gw) : 0u;
+            fb = gw + 32 < nwords ? __ldg(flags + gw + 32) : 0u;
+            const uint32_t pa = (uint32_t)__popc(fa), pb = (uint32_t)__popc(fb);
+            uint32_t xa = pa, xb = pb;
 #pragma unroll
-                for (int j = 0; j < kSurvItems; ++j) mk[j] = (base + j < n) ? __ldg(mkey + base + j) : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t ya = __shfl_up_sync(kFull, xa, o), yb = __shfl_up_sync(kFull, xb, o);
+                if (lane >= o) { xa += ya; xb += yb; }
             }
+            const uint32_t ta = __shfl_sync(kFull, xa, 31);
+            oa = xa - pa;
+            ob = ta + xb - pb;   // exclusive offsets of words l and 32 + l
         }
-        uint32_t total;
-        uint32_t pos = block_excl_scan<kThreads>((uint32_t)__popc(f), s_warp, total);
-        if (f) {
+        if (tid == 0 && !mbar_wait(&s_bar[s], (uint32_t)((c / kSurvStages) & 1), &res->err)) timed_out = true;
+        if (__syncthreads_or(timed_out)) {
+            if (tid == 0)
+                for (int k = c; k < issued; ++k)
+                    mbar_wait(&s_bar[k % kSurvStages], (uint32_t)((k / kSurvStages) & 1), nullptr);
+            break;
+        }
+        ++c;
+        if (cnt) {
+            const uint32_t* sk = s_ring + s * kSurvTile;
+            const uint32_t tile_base = base_off + s_to[i];
+            const uint32_t row0 = (uint32_t)(tile * kSurvTile);
 #pragma unroll
             for (int j = 0; j < kSurvItems; ++j) {
-                if (f & (1u << j)) {
-                    s_key[pos] = mk[j];
-                    s_idx[pos] = (uint32_t)(base + j);
-                    ++pos;
+                const int wi = j * (kThreads / 32) + warp;   // flag word of item j of this warp
+                const uint32_t fw = __shfl_sync(kFull, wi < 32 ? fa : fb, wi & 31);
+                const uint32_t ow = __shfl_sync(kFull, wi < 32 ? oa : ob, wi & 31);
+                if ((fw >> lane) & 1u) {
+                    const uint32_t pos = tile_base + ow + (uint32_t)__popc(fw & below);
+                    const uint32_t r = (uint32_t)(j * kThreads + tid);
+                    surv_key[pos] = sk[r];
+                    surv_idx[pos] = row0 + r;
                 }
             }
         }
-        __syncthreads();
-        for (uint32_t i = tid; i < total; i += kThreads) {
-            surv_key[running + i] = s_key[i];
-            surv_idx[running + i] = s_idx[i];
+        __syncthreads();   // stage s consumed
+        if (tid == 0) {
+            while (nxt < my && !s_tc[nxt]) ++nxt;
+            if (nxt < my) {
+                fence_proxy_async_smem();
+                surv_issue(s_ring + s * kSurvTile, mkey, t0 + nxt, n, &s_bar[s]);
+                ++issued;
+                ++nxt;
+            }
         }
-        running += total;
-        __syncthreads();   // s_key / s_idx / s_warp are reused by the next tile
     }
-    if (blockIdx.x == gridDim.x - 1 && tid == 0) res->survivors = running;
+    if (blockIdx.x == gridDim.x - 1 && tid == 0) res->survivors = base_off + total;
 }
 
 // Result of a survivors-only call: the survivor row ids (already ascending)
@@ -1091,32 +1317,42 @@ cudaError_t launch_params(const Plan& p, cudaStream_t s)
     } else if (p.map_mode == kMapUnit || p.n == 0) {
         k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 0, p.params);
     } else {
-        SKY_DISPATCH_DP(p.d, k_sample_params<DP><<<1, kDecideThreads, 0, s>>>(
-                                 p.pts, p.n, p.d, p.ld, p.log2g, p.morton_bits, p.mm_min, p.mm_max, p.params));
+        const bool v = vec4_ok(p);
+        SKY_DISPATCH_DP(p.d, k_sample_params<DP><<<kDecideCluster, kDecideThreads, 0, s>>>(
+                                 p.pts, p.n, p.d, p.ld, v, p.log2g, p.morton_bits, p.mm_min, p.mm_max, p.params));
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_build(const Plan& p, cudaStream_t s)
+// Cleared result block and bitmap, and the value map's parameters (min / max
+// pass in mode 2).
+cudaError_t launch_build_params(const Plan& p, cudaStream_t s)
 {
-    cudaMemsetAsync(p.occ, 0, sizeof(uint32_t) * p.words, s);
+    k_clear<<<grid_for(p.words, kThreads * 16, num_sms() * 4), kThreads, 0, s>>>(p.res, p.occ, p.words);
     if (p.map_mode == kMapMinMax) launch_mm_reset(p, s);
     if (p.n == 0) return cudaGetLastError();
     if (p.map_mode == kMapMinMax) launch_minmax_accumulate(p, s);
-    launch_params(p, s);
+    return launch_params(p, s);
+}
+
+cudaError_t launch_build(const Plan& p, cudaStream_t s)
+{
+    const cudaError_t e = launch_build_params(p, s);
+    if (e != cudaSuccess || p.n == 0) return e;
     return launch_map_pass(p, true, s);
 }
 
 int build_kernel_count(const Plan& p)
 {
-    if (p.n == 0) return 0;
+    if (p.n == 0) return 1;
     const int merge = p.occ_stage ? 1 : 0;
-    if (p.map_mode == kMapMinMax) return 3 + merge;
-    return 2 + merge;
+    if (p.map_mode == kMapMinMax) return 4 + merge;
+    return 3 + merge;   // clear, parameters, map pass (+ merge)
 }
 
 // Split of the prefix-OR: kl low dimensions per shared-memory block (at most
-// 2^20 bits, 128 KB), the rest in rows of the high grid (at most 2^14 rows).
+// 2^kPrefixLowBits bits, as many dimensions as fit), the rest in rows of the
+// high grid (at most 2^14 rows). Grids of at most 2^16 bits are one block.
 // kl = 0 selects the fallback of one launch per dimension.
 struct PrefixSplit {
     int kl = 0, kh = 0;
@@ -1136,16 +1372,17 @@ PrefixSplit prefix_split(const Plan& p)
         return ps;
     }
     int kl = 0;
-    while (kl + 1 <= d && lg * (kl + 1) <= 15) ++kl;
-    while (kl < d && B - lg * kl > 12 && lg * (kl + 1) <= 20) ++kl;
-    if (kl < 1 || kl >= d || lg * kl < 5 || B - lg * kl > 14) return PrefixSplit{};
+    while (kl + 1 < d && lg * (kl + 1) <= kPrefixLowBits) ++kl;
+    if (kl < 1 || lg * kl < 5 || B - lg * kl > 14) return PrefixSplit{};
     ps.kl = kl;
     ps.kh = d - kl;
     ps.block_words = 1ll << (lg * kl - 5);
     ps.low_blocks = p.words / ps.block_words;
     ps.rows = 1ll << (B - lg * kl);
-    int64_t wc = 1024 / ps.rows;          // about 4 KB of shared memory per block, many blocks
+    int64_t wc = kPrefixHighWords / ps.rows;   // words of shared memory per block: coalesced rows
     if (wc < 1) wc = 1;
+    // long lines leave few lines per block: widen the block (up to 64 KB)
+    while ((ps.rows >> lg) * wc < 32 && ps.rows * wc * 2 <= 16384 && wc * 2 <= ps.block_words) wc *= 2;
     if (wc > ps.block_words) wc = ps.block_words;
     ps.wc = (int)wc;
     ps.high_blocks = ps.block_words / wc;
@@ -1171,13 +1408,18 @@ cudaError_t launch_prefix_or(const Plan& p, cudaStream_t s)
         return cudaGetLastError();
     }
     const int smem_low = (int)(ps.block_words * sizeof(uint32_t));
+    // about two words per thread, whole warps
+    const int thr = (int)std::min<int64_t>(kPrefixLowThreads,
+                                           std::max<int64_t>(64, ps.block_words / kPrefixWordsPerThread));
     cudaFuncSetAttribute(k_prefix_low, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_low);
-    k_prefix_low<<<(unsigned)ps.low_blocks, kPrefixThreads, smem_low, s>>>(p.occ, p.pre, ps.block_words, p.log2g,
-                                                                           ps.kl);
+    k_prefix_low<<<(unsigned)ps.low_blocks, thr, smem_low, s>>>(p.occ, p.pre, ps.block_words, p.log2g, ps.kl);
     if (ps.kh > 0) {
         const int smem_high = (int)(ps.rows * ps.wc * sizeof(uint32_t));
+        int lrows = 0, lwc = 0;
+        while ((1ll << lrows) < ps.rows) ++lrows;
+        while ((1 << lwc) < ps.wc) ++lwc;
         cudaFuncSetAttribute(k_prefix_high, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_high);
-        k_prefix_high<<<(unsigned)ps.high_blocks, kThreads, smem_high, s>>>(p.pre, ps.block_words, ps.rows, ps.wc,
+        k_prefix_high<<<(unsigned)ps.high_blocks, kThreads, smem_high, s>>>(p.pre, ps.block_words, lrows, lwc,
                                                                              p.log2g, ps.kh);
     }
     return cudaGetLastError();
@@ -1207,28 +1449,34 @@ cudaError_t launch_snap(const Plan& p, const float* d_prop, int n_prop, cudaStre
 void survivor_split(int64_t n, int64_t* tpb, int* blocks)
 {
     const int64_t ntiles = (n + kSurvTile - 1) / kSurvTile;
-    int64_t target = (int64_t)num_sms() * 4;
+    int64_t target = (int64_t)num_sms() * 6;   // six 33 KB rings per SM
     if (target > kSurvMaxBlocks) target = kSurvMaxBlocks;
     int64_t t = (ntiles + target - 1) / target;
     if (t < 1) t = 1;
+    if (t > kSurvMaxTpb) t = kSurvMaxTpb;
     int64_t b = (ntiles + t - 1) / t;
     if (b < 1) b = 1;
     *tpb = t;
     *blocks = (int)b;
 }
 
-cudaError_t launch_survivors(const Plan& p, int n_filter, cudaStream_t s)
+cudaError_t launch_survivors(const Plan& p, int n_filter, cudaStream_t s, uint32_t* idx_out)
 {
     if (p.n == 0) return cudaGetLastError();
     int64_t tpb = 1;
     int blocks = 1;
     survivor_split(p.n, &tpb, &blocks);
     const bool v = vec4_ok(p);
-    SKY_DISPATCH_DP(p.d, k_surv_flags<DP><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, p.log2g, p.ckey,
-                                                                       p.pre, p.filt, n_filter, p.res, tpb,
-                                                                       p.sflags, p.scount));
-    k_surv_scatter<<<blocks, kThreads, 0, s>>>(p.n, p.mkey, p.sflags, p.scount, tpb, p.res, p.surv_key,
-                                               p.surv_idx);
+    const int ring = kSurvStages * kSurvTile * (int)sizeof(uint32_t);
+    SKY_DISPATCH_DP(p.d, {
+        cudaFuncSetAttribute(k_surv_flags<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ring);
+        k_surv_flags<DP><<<blocks, kThreads, ring, s>>>(p.pts, p.n, p.d, p.ld, v, p.log2g, p.ckey, p.pre, p.filt,
+                                                        n_filter, p.res, tpb, p.sflags, p.scount);
+    });
+    const int smem = ring + 2 * (int)tpb * (int)sizeof(uint32_t);
+    cudaFuncSetAttribute(k_surv_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_surv_scatter<<<blocks, kThreads, smem, s>>>(p.n, p.mkey, p.sflags, p.scount, tpb, p.res, p.surv_key,
+                                                  idx_out ? idx_out : p.surv_idx);
     return cudaGetLastError();
 }
 
@@ -1244,11 +1492,15 @@ cudaError_t launch_cell_stats(const Plan& p, cudaStream_t s)
     return launch_dominated(p, s);
 }
 
+// Automatic layer: the largest log2_g <= min(8, 24 / d) with 2^(log2_g d)
+// <= 32 n. At most 256 columns per dimension (the paper's default layer is
+// 6): finer layers of 2- and 3-dimensional sets prune little more and make
+// every line of the prefix-OR long.
 int auto_log2g(int64_t n, int d)
 {
     int r = 24 / d;
     if (r < 1) r = 1;
-    if (r > 16) r = 16;
+    if (r > kMaxAutoLayer) r = kMaxAutoLayer;
     while (r > 1 && (double)(1ull << (r * d)) > 32.0 * (double)(n > 1 ? n : 1)) --r;
     return r;
 }

@@ -474,7 +474,8 @@ sky_status sky_propose(const float* d_pts, int64_t n, int32_t d, int64_t ld, con
         // these features; the automatic policy's change from n_ref to n rows
         // carries it to this set's size.
         lg += auto_log2g(n, d) - auto_log2g(n_ref, d);
-        const int top = 24 / d > 1 ? 24 / d : 1;
+        int top = 24 / d > 1 ? 24 / d : 1;
+        if (top > kMaxAutoLayer) top = kMaxAutoLayer;
         lg = lg < 1 ? 1 : (lg > top ? top : lg);
     }
     *h_log2g = lg;

@@ -20,7 +20,9 @@ namespace {
 thread_local std::string t_err;
 thread_local sky_run_stats t_stats = {};
 thread_local sky_phase_times t_phase = {};
-thread_local bool t_timing = false;
+// 0: off; 1: events between the phases (direct launches, no graph);
+// 2: events around the whole kernel sequence of the call (graph replay kept)
+thread_local int t_timing = 0;
 thread_local cudaEvent_t t_ev[9] = {};
 
 // Optional per-phase events on the call's stream.
@@ -28,7 +30,7 @@ struct PhaseClock {
     cudaStream_t s;
     bool on;
     int next = 0;
-    explicit PhaseClock(cudaStream_t st) : s(st), on(t_timing)
+    explicit PhaseClock(cudaStream_t st) : s(st), on(t_timing == 1)
     {
         if (!on) return;
         for (auto& e : t_ev)
@@ -46,15 +48,37 @@ struct PhaseClock {
         for (int i = 0; i + 1 < next; ++i)
             if (cudaEventElapsedTime(&ms[i], t_ev[i], t_ev[i + 1]) != cudaSuccess) ms[i] = 0.0f;
         cudaGetLastError();   // leave no error behind for the caller
-        t_phase = {ms[0], ms[1], ms[2], ms[3], ms[4], ms[5], ms[6], ms[7]};
+        t_phase = {ms[0], ms[1], ms[2], ms[3], ms[4], ms[5], ms[6], ms[7], 0.0f};
     }
 };
 
-int count_kernels(const Plan& p, int n_prop)
+// Whole-call timing (mode 2): two events per thread and a bounded delay
+// kernel (it sleeps until the global timer has advanced by `ns`).
+thread_local cudaEvent_t t_span[2] = {};
+constexpr uint32_t kSpanDelayNs = 50000;
+
+bool span_events()
+{
+    for (auto& e : t_span)
+        if (!e && cudaEventCreate(&e) != cudaSuccess) return false;
+    return true;
+}
+
+__global__ void k_delay(uint32_t ns)
+{
+    uint64_t t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    do {
+        __nanosleep(1000);
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    } while (t - t0 < ns);
+}
+
+int count_kernels(const Plan& p, int n_prop, int64_t capacity)
 {
     const int passes = (p.morton_bits * p.d + 7) / 8;
-    const int through_c = build_kernel_count(p) + (n_prop > 0 ? 1 : 0) + 1 + prefix_kernel_count(p) + 2;
-    if (p.survivors_only) return through_c + 1;
+    const int through_c = build_kernel_count(p) + (n_prop > 0 ? 2 : 0) + prefix_kernel_count(p) + 2;
+    if (p.survivors_only) return through_c + (capacity >= p.n ? 0 : 1);   // + the id copy
     return through_c + 3 * passes + 1 + 3 + 1;   // sort, gather, cost + order + refine, emit
 }
 
@@ -234,17 +258,21 @@ DevResult* host_result()
 cudaError_t enqueue_pipeline(Plan& p, const float* prop, int n_prop, int32_t* out, int64_t capacity,
                              cudaStream_t s, PhaseClock& clk)
 {
-    cudaError_t e = cudaMemsetAsync(p.res, 0, sizeof(DevResult), s);
+    cudaError_t e = launch_build_params(p, s);   // clears the result block first
     clk.mark();
-    if (e == cudaSuccess) e = launch_build(p, s);
+    if (e == cudaSuccess) e = launch_map_pass(p, true, s);
     clk.mark();
-    if (e == cudaSuccess) e = launch_snap(p, prop, n_prop, s);
+    // without proposals the snap is skipped: n_filter_used stays 0 from the
+    // cleared result block, and the survivor pass then reads no filter
+    if (e == cudaSuccess && n_prop > 0) e = launch_snap(p, prop, n_prop, s);
     if (e == cudaSuccess) e = launch_prefix_or(p, s);
     clk.mark();
-    if (e == cudaSuccess) e = launch_survivors(p, n_prop, s);
+    // a survivors-only call whose buffer holds n ids receives them directly
+    const bool direct = p.survivors_only && capacity >= p.n;
+    if (e == cudaSuccess) e = launch_survivors(p, n_prop, s, direct ? reinterpret_cast<uint32_t*>(out) : nullptr);
     clk.mark();
     if (p.survivors_only) {
-        if (e == cudaSuccess) e = launch_copy_survivors(p, out, capacity, s);
+        if (e == cudaSuccess && !direct) e = launch_copy_survivors(p, out, capacity, s);
         clk.mark();
         return e;
     }
@@ -359,7 +387,7 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
     const float* prop = n_prop ? opt->d_filter_pts : nullptr;
     CacheKey key;
     key.dev = dev; key.pts = pts; key.n = n; key.ld = ld; key.cap = capacity; key.d = d;
-    key.log2g = p.log2g; key.mode = p.map_mode; key.n_prop = n_prop; key.timing = t_timing ? 1 : 0;
+    key.log2g = p.log2g; key.mode = p.map_mode; key.n_prop = n_prop; key.timing = t_timing == 1 ? 1 : 0;
     key.surv_only = p.survivors_only ? 1 : 0;
     key.prop = prop; key.out = out;
     const size_t bytes = layout(p, nullptr, false);
@@ -372,7 +400,7 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
     cudaError_t e = cudaSuccess;
     // graphs only when no phase events are requested (the events time the
     // direct launches)
-    if (ce->calls >= 2 && !ce->exec && !t_timing) {
+    if (ce->calls >= 2 && !ce->exec && t_timing != 1) {
         // second call with these arguments: capture the sequence once
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
@@ -388,13 +416,22 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
         cudaGetLastError();   // a failed capture falls back to direct launches
         e = cudaSuccess;
     }
-    if (ce->exec && !t_timing) {
+    // whole-call timing: a short device-side delay first, so that the host
+    // has enqueued the start event and the kernel sequence before the device
+    // reaches them; the two events then bracket device work only
+    const bool span = t_timing == 2 && span_events();
+    if (span) {
+        k_delay<<<1, 32, 0, s>>>(kSpanDelayNs);
+        cudaEventRecord(t_span[0], s);
+    }
+    if (ce->exec && t_timing != 1) {
         e = cudaGraphLaunch(ce->exec, s);
     } else {
         e = enqueue_pipeline(p, prop, n_prop, out, capacity, s, clk);
     }
+    if (span) cudaEventRecord(t_span[1], s);
     if (e != cudaSuccess) st = cuda_fail(e, "kernel launch");
-    t_stats.kernels = count_kernels(p, n_prop);
+    t_stats.kernels = count_kernels(p, n_prop, capacity);
     DevResult* h = host_result();
     DevResult local{};
     if (st == SKY_OK) {
@@ -406,6 +443,12 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
     const DevResult r = h ? *h : local;
     clk.collect();
+    if (span) {
+        float ms = 0.0f;
+        t_phase = {};
+        if (cudaEventElapsedTime(&ms, t_span[0], t_span[1]) == cudaSuccess) t_phase.call_ms = ms;
+        cudaGetLastError();
+    }
     t_stats.survivors = r.survivors;
     t_stats.skyline = r.count;
     t_stats.pairs = (int64_t)r.pairs;
@@ -416,6 +459,11 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
     t_stats.exact_tests = (int64_t)r.exact;
     st = status_from_flags(r.err);
     if (st != SKY_OK) return st;
+    if (p.survivors_only && capacity >= n) {   // ids written by the survivor pass itself
+        t_stats.skyline = r.survivors;
+        *count = r.survivors;
+        return SKY_OK;
+    }
     *count = r.count;
     if ((int64_t)r.count > capacity)
         return fail(SKY_ERR_CAPACITY, "skyline has %u points, capacity %lld", r.count, (long long)capacity);
@@ -483,7 +531,8 @@ sky_status sky_last_run_stats(sky_run_stats* out)
 
 sky_status sky_set_phase_timing(int32_t enable)
 {
-    t_timing = enable != 0;
+    if (enable < 0 || enable > 2) return fail(SKY_ERR_INVALID_ARGUMENT, "timing mode %d outside {0, 1, 2}", enable);
+    t_timing = enable;
     return SKY_OK;
 }
 

@@ -98,6 +98,23 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// ---- per-thread asynchronous copies global -> shared ------------------------
+// Fire-and-forget (the thread does not wait for each load); cp_async_wait_all
+// then waits for every copy the thread issued. The 16-byte form needs both
+// addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // ---- release / acquire flags ----------------------------------------------
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
 {
@@ -241,28 +258,47 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp
     return before + x - v;
 }
 
+// Inclusive OR-scan of the len words p[0], p[stride], ... (after OR-ing
+// `init` into the first); the loads of a batch are issued before its stores,
+// so a long line is not one load -> store chain.
+constexpr int kScanBatch = 8;
+
+__device__ __forceinline__ void or_scan_strided(uint32_t* p, uint32_t len, uint32_t stride, uint32_t init)
+{
+    uint32_t acc = init;
+    for (uint32_t j0 = 0; j0 < len; j0 += kScanBatch) {
+        uint32_t v[kScanBatch];
+#pragma unroll
+        for (int u = 0; u < kScanBatch; ++u) v[u] = (j0 + u < len) ? p[(j0 + u) * stride] : 0u;
+#pragma unroll
+        for (int u = 0; u < kScanBatch; ++u) {
+            acc |= v[u];
+            if (j0 + u < len) p[(j0 + u) * stride] = acc;
+        }
+    }
+}
+
 // Inclusive prefix-OR along dimension k of the 2^(log2g*d)-bit grid stored in
 // `words` 32-bit words (bit stride of dimension k: 2^(log2g*k)). Threads
 // tid = 0 .. nthr-1 of the caller share the work; the caller orders
-// successive dimensions (grid launches or __syncthreads).
+// successive dimensions (grid launches or __syncthreads). Grids hold at most
+// 2^27 bits, so word indices fit in 32 bits; every stride and line length is
+// a power of two, so indices are split with shifts and masks.
 __device__ __forceinline__ void prefix_or_dim(uint32_t* R, int64_t words, int log2g, int k, int64_t tid,
                                               int64_t nthr)
 {
     const int slog = log2g * k;
     const uint32_t G = 1u << log2g;
+    const uint32_t nw = (uint32_t)words;
+    const uint32_t t0 = (uint32_t)tid, nt = (uint32_t)nthr;
     if (slog >= 5) {
-        // whole words: word stride sw, G words per line
-        const int64_t sw = 1ll << (slog - 5);
-        const int64_t ncol = words / G;
-        for (int64_t c = tid; c < ncol; c += nthr) {
-            const int64_t lo = c % sw, hi = c / sw;
-            uint32_t* p = R + hi * (int64_t)G * sw + lo;
-            uint32_t acc = *p;
-            for (uint32_t j = 1; j < G; ++j) {
-                p += sw;
-                acc |= *p;
-                *p = acc;
-            }
+        // whole words: word stride sw = 2^ls, G words per line
+        const int ls = slog - 5;
+        const uint32_t sw = 1u << ls;
+        const uint32_t ncol = nw >> log2g;
+        for (uint32_t c = t0; c < ncol; c += nt) {
+            const uint32_t lo = c & (sw - 1u), hi = c >> ls;
+            or_scan_strided(R + ((hi << log2g) << ls) + lo, G, sw, 0u);
         }
     } else if (slog + log2g <= 5) {
         // every line inside one word: log2(G) doubling steps with masks that
@@ -273,33 +309,73 @@ __device__ __forceinline__ void prefix_or_dim(uint32_t* R, int64_t words, int lo
         int nsteps = 0;
         for (uint32_t j = 1; j < G; j <<= 1)
             mask[nsteps++] = __ballot_sync(kFull, ((lane >> slog) & (G - 1u)) >= j);
-        for (int64_t w = tid; w < words; w += nthr) {
+        for (uint32_t w = t0; w < nw; w += nt) {
             uint32_t x = R[w];
             int st = 0;
             for (uint32_t j = 1; j < G; j <<= 1, ++st) x |= (x << (j << slog)) & mask[st];
             R[w] = x;
         }
     } else {
-        // a line spans Lw consecutive words holding e = 32 >> slog of its
-        // elements each (2^slog interleaved lines): scan inside each word, then
-        // carry the last element group from word to word
-        const int64_t Lw = 1ll << (slog + log2g - 5);
+        // a line spans Lw = 2^(slog + log2g - 5) consecutive words holding
+        // e = 32 >> slog of its elements each (2^slog interleaved lines): scan
+        // inside each word, then carry the last element group from word to word
+        const int lw = slog + log2g - 5;
+        const uint32_t Lw = 1u << lw;
         const int e = 32 >> slog;
         const int sbits = 1 << slog;
         const uint32_t rep = __ballot_sync(kFull, ((threadIdx.x & 31u) & (uint32_t)(sbits - 1)) == 0u);
-        const int64_t ngroups = words / Lw;
-        for (int64_t g = tid; g < ngroups; g += nthr) {
-            uint32_t* p = R + g * Lw;
+        const uint32_t ngroups = nw >> lw;
+        for (uint32_t g = t0; g < ngroups; g += nt) {
+            uint32_t* p = R + (g << lw);
             uint32_t carry = 0;
-            for (int64_t t = 0; t < Lw; ++t) {
-                uint32_t x = p[t];
-                for (int j = 1; j < e; j <<= 1) x |= x << (j << slog);
-                x |= carry;
-                p[t] = x;
-                const uint32_t top = x >> (32 - sbits);
-                carry = top * rep;
+            for (uint32_t t0w = 0; t0w < Lw; t0w += kScanBatch) {
+                uint32_t v[kScanBatch];
+#pragma unroll
+                for (int u = 0; u < kScanBatch; ++u) v[u] = (t0w + u < Lw) ? p[t0w + u] : 0u;
+#pragma unroll
+                for (int u = 0; u < kScanBatch; ++u) {
+                    uint32_t x = v[u];
+                    for (int j = 1; j < e; j <<= 1) x |= x << (j << slog);
+                    x |= carry;
+                    if (t0w + u < Lw) p[t0w + u] = x;
+                    const uint32_t top = x >> (32 - sbits);
+                    carry = top * rep;
+                }
             }
         }
+    }
+}
+
+// Dimensions 0 .. kin-1 at once, all of them lying inside one word
+// (log2g * kin <= 5): the per-dimension prefix-ORs commute, so applying them
+// one after the other to each word in registers equals kin passes of
+// prefix_or_dim. Whole, converged warps only (the masks are lane votes).
+__device__ __forceinline__ void prefix_or_inword(uint32_t* R, int64_t words, int log2g, int kin, int64_t tid,
+                                                 int64_t nthr)
+{
+    if (kin <= 0) return;
+    const uint32_t G = 1u << log2g;
+    const uint32_t lane = threadIdx.x & 31u;
+    int nst = 0;
+    for (uint32_t j = 1; j < G; j <<= 1) ++nst;
+    // [dimension][doubling step], at most 5 x 5, fully unrolled so that the
+    // masks stay in registers
+    uint32_t mask[5][5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int st = 0; st < 5; ++st)
+            mask[k][st] = __ballot_sync(kFull, k < kin && st < nst &&
+                                                   ((lane >> (log2g * k)) & (G - 1u)) >= (1u << st));
+    const uint32_t nw = (uint32_t)words;
+    for (uint32_t w = (uint32_t)tid; w < nw; w += (uint32_t)nthr) {
+        uint32_t x = R[w];
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+            for (int st = 0; st < 5; ++st)
+                if (k < kin && st < nst) x |= (x << ((1u << st) << (log2g * k))) & mask[k][st];
+        R[w] = x;
     }
 }
 

@@ -111,7 +111,7 @@ struct QueryPlan {
 };
 
 constexpr int kRefineTile = 128;   // points per refinement tile
-constexpr int kSurvMaxBlocks = 4096;  // blocks of the survivor passes (at most 4 per SM)
+constexpr int kSurvMaxBlocks = 4096;  // blocks of the survivor passes (at most 6 per SM)
 constexpr int kMapMaxBlocks = 1024;   // blocks of the map pass
 constexpr int64_t kPrivWords = 2048;  // grids of at most 2^16 cells are marked in shared memory first
 constexpr int kScanItems = 8;      // items per thread in the look-back scans
@@ -130,6 +130,7 @@ void plan_carve(Plan& p, void* ws, bool grid_api);
 // Steps (a)+(b) in the plan's map mode (min/max pass, parameters, map pass,
 // and in automatic mode the decision and the gated second map pass).
 cudaError_t launch_build(const Plan& p, cudaStream_t s);
+cudaError_t launch_build_params(const Plan& p, cudaStream_t s);   // launch_build without the map pass
 int build_kernel_count(const Plan& p);
 cudaError_t launch_prefix_or(const Plan& p, cudaStream_t s);
 int prefix_kernel_count(const Plan& p);
@@ -141,7 +142,9 @@ cudaError_t launch_map_pass(const Plan& p, bool mark, cudaStream_t s);
 void set_last_error(const char* msg);   // the message sky_last_error() returns
 cudaError_t launch_dominated(const Plan& p, cudaStream_t s);
 cudaError_t launch_snap(const Plan& p, const float* d_prop, int n_prop, cudaStream_t s);
-cudaError_t launch_survivors(const Plan& p, int n_filter, cudaStream_t s);
+// idx_out: where the survivor row ids go (default: p.surv_idx; the caller's
+// buffer of a survivors-only call that can hold n ids)
+cudaError_t launch_survivors(const Plan& p, int n_filter, cudaStream_t s, uint32_t* idx_out = nullptr);
 cudaError_t launch_copy_survivors(const Plan& p, int32_t* out, int64_t capacity, cudaStream_t s);
 cudaError_t launch_cell_stats(const Plan& p, cudaStream_t s);
 // k_sort.cu
@@ -176,6 +179,7 @@ struct BatchLaunch {
 cudaError_t launch_batched(const BatchLaunch& b, cudaStream_t s);
 int batched_kernel_count(const BatchLaunch& b);
 
+constexpr int kMaxAutoLayer = 8;   // the automatic layer never exceeds 8 (256 columns per dimension)
 int auto_log2g(int64_t n, int d);
 int morton_bits_for(int64_t n, int d);
 

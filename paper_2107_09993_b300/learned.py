@@ -41,8 +41,9 @@ def directions(seed: int = 7) -> np.ndarray:
 
 def auto_layer(n: int, d: int) -> int:
     """The plain path's automatic layer for n rows in d dimensions (the
-    library's rule: the largest log2_g <= 24 / d with 2^(log2_g d) <= 32 n)."""
-    r = max(1, min(16, 24 // d))
+    library's rule: the largest log2_g <= min(8, 24 / d) with
+    2^(log2_g d) <= 32 n)."""
+    r = max(1, min(8, 24 // d))
     while r > 1 and (1 << (r * d)) > 32.0 * max(n, 1):
         r -= 1
     return r

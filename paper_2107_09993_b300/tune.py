@@ -25,11 +25,12 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "tuning.json")
 MAX_GRID_BITS = 18  # batched grids hold at most 2^18 cells
+MAX_AUTO_LAYER = 8  # the automatic layer never exceeds 8 (256 columns per dimension)
 
 
 def auto_log2g(n: int, d: int) -> int:
     """The library's automatic layer for a batched query (mirrors the C++ rule)."""
-    r = max(1, min(16, 24 // d))
+    r = max(1, min(MAX_AUTO_LAYER, 24 // d))
     while r > 1 and (1 << (r * d)) > 32.0 * max(n, 1):
         r -= 1
     while r > 1 and r * d > MAX_GRID_BITS:

@@ -190,9 +190,36 @@ def test_survivors_only_returns_step_c_candidates():
         want = np.flatnonzero(dom[keys.astype(np.int64)] == 0)
         assert got.tolist() == want.tolist(), (kind, n, d)
         assert set(oracle.skyline_sfs(P).tolist()) <= set(got.tolist())
+        # a buffer shorter than n takes the copy path; same ids
+        got2 = sky.skyline(x, survivors_only=True, capacity=len(want)).cpu().numpy()
+        assert got2.tolist() == want.tolist()
         with pytest.raises(sky.SkyError) as e:
             sky.skyline(x, survivors_only=True, capacity=len(want) - 1)
         assert e.value.name == "SKY_ERR_CAPACITY"
+
+
+def test_device_timing_modes():
+    """Mode 1 times the phases (kernels launched one by one), mode 2 the whole
+    kernel sequence of a call (graph replay kept); neither changes the result,
+    and other modes are rejected."""
+    P = skydata.generate("independent", 200000, 6, seed=9)
+    x = dev(P)
+    want = gpu_sky(P)
+    try:
+        for mode in (1, 2):
+            sky.set_phase_timing(mode)
+            for _ in range(3):   # first call direct, later calls replay the captured graph
+                assert sky.skyline(x).cpu().numpy().tolist() == want
+                t = sky.last_phase_times()
+                if mode == 1:
+                    assert t["map_mark_ms"] > 0 and t["refine_ms"] > 0 and t["call_ms"] == 0
+                else:
+                    assert t["call_ms"] > 0 and t["map_mark_ms"] == 0
+        with pytest.raises(sky.SkyError) as e:
+            sky.set_phase_timing(3)
+        assert e.value.name == "SKY_ERR_INVALID_ARGUMENT"
+    finally:
+        sky.set_phase_timing(False)
 
 
 def test_fig1_and_fig2_dominated_cells(golden):

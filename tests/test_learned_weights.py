@@ -22,12 +22,12 @@ def test_shipped_weights_file():
 
 
 def test_automatic_layer_rule():
-    # largest log2_g <= 24 / d with 2^(log2_g * d) <= 32 n
-    assert [learned.auto_layer(100_000, d) for d in (2, 3, 4, 8, 16)] == [10, 7, 5, 2, 1]
-    assert [learned.auto_layer(10_000_000, d) for d in (2, 3, 4, 8, 16)] == [12, 8, 6, 3, 1]
+    # largest log2_g <= min(8, 24 / d) with 2^(log2_g * d) <= 32 n
+    assert [learned.auto_layer(100_000, d) for d in (2, 3, 4, 8, 16)] == [8, 7, 5, 2, 1]
+    assert [learned.auto_layer(10_000_000, d) for d in (2, 3, 4, 8, 16)] == [8, 8, 6, 3, 1]
     for n in (1, 1000, 10**6, 10**9):
         for d in range(1, 17):
             r = learned.auto_layer(n, d)
-            assert 1 <= r <= max(1, 24 // d)
+            assert 1 <= r <= max(1, min(8, 24 // d))
             assert r == 1 or (1 << (r * d)) <= 32 * n
-            assert r == min(16, 24 // d) or (1 << ((r + 1) * d)) > 32 * n
+            assert r == min(8, 24 // d) or (1 << ((r + 1) * d)) > 32 * n

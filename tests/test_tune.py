@@ -12,7 +12,8 @@ def test_auto_layer_rule_and_limits():
             lg = tune.auto_log2g(n, d)
             assert lg >= 1 and lg * d <= max(tune.MAX_GRID_BITS, d)
     assert tune.auto_log2g(10 ** 6, 8) == 2         # 24 bits would exceed the batched 2^18 cells
-    assert tune.auto_log2g(10 ** 6, 2) == 9
+    assert tune.auto_log2g(10 ** 6, 2) == 8         # the automatic layer stops at 8 (256 columns)
+    assert tune.auto_log2g(10 ** 6, 3) == 6         # 18 bits: the batched limit
 
 
 def test_settings_apply_cache_offsets(tmp_path, monkeypatch):
