@@ -36,9 +36,11 @@ using namespace refine;
 
 template <int DP>
 __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, int d, int64_t ld, bool vec4,
-                                                const uint32_t* __restrict__ sorted_idx, const DevResult* res,
+                                                const uint32_t* __restrict__ sorted_idx,
+                                                const uint32_t* __restrict__ sorted_key, const DevResult* res,
                                                 const float* __restrict__ params, float* X, uint32_t* C,
-                                                int32_t* ids, uint32_t* tmax, uint32_t* subcode)
+                                                int32_t* ids, uint32_t* tmax, uint32_t* subcode,
+                                                uint32_t* tile_end)
 {
     constexpr int DW = DP / 4;
     const uint32_t m = res->survivors;
@@ -112,6 +114,16 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
         subcode[((int64_t)blockIdx.x * kSubSlots + kTQ / 32) * DW + tid] = c;
         tmax[(int64_t)blockIdx.x * DW + tid] = t;
     }
+    // The last q-tile that can hold a dominator of a point of this tile: a
+    // dominator's Morton key is <= its victim's (monotone columns), so only
+    // tiles whose first key is <= this tile's last key qualify. Ties across
+    // tile boundaries are the only reason to look past this tile.
+    if (tid == 0) {
+        const uint32_t last = sorted_key[min((int64_t)m, ((int64_t)blockIdx.x + 1) * kTQ) - 1];
+        uint32_t e = blockIdx.x;
+        while (e + 1 < T && sorted_key[(int64_t)(e + 1) * kTQ] <= last) ++e;
+        tile_end[blockIdx.x] = e;
+    }
 }
 
 // Cost estimate of each p-tile for the launch order of the refinement: how
@@ -125,13 +137,27 @@ constexpr int kCostSamples = 1024;
 
 template <int DW>
 __global__ void __launch_bounds__(256) k_tile_cost(const uint32_t* __restrict__ SUB, const uint32_t* __restrict__ tmax,
-                                                   const DevResult* res, uint32_t* cost)
+                                                   const DevResult* res, uint32_t* cost, uint32_t* supmin)
 {
     // the sampled q-tiles' minimum codes, shared by the block's eight warps
     // (one p-tile each)
     __shared__ uint32_t s_qmin[kCostSamples][DW];
     const uint32_t T = (res->survivors + kTQ - 1) / kTQ;
     if (blockIdx.x * 8 >= T) return;
+    {
+        // warp w of block b: byte-wise minimum code of super-tile 8b + w (32
+        // tiles, one per lane; tiles past the end count as the largest code)
+        const uint32_t sx = blockIdx.x * 8 + (threadIdx.x >> 5);
+        const uint32_t tq = sx * 32 + (threadIdx.x & 31);
+        if (sx * 32 < T) {
+#pragma unroll
+            for (int w = 0; w < DW; ++w) {
+                uint32_t c = tq < T ? __ldg(SUB + ((int64_t)tq * kSubSlots + kTQ / 32) * DW + w) : 0x7f7f7f7fu;
+                for (int o = 16; o > 0; o >>= 1) c = __vminu4(c, __shfl_xor_sync(kFull, c, o));
+                if ((threadIdx.x & 31) == 0) supmin[(int64_t)sx * DW + w] = c;
+            }
+        }
+    }
     const uint32_t step = (T + kCostSamples - 1) / kCostSamples;   // ns <= kCostSamples
     const uint32_t ns = (T + step - 1) / step;
     for (uint32_t i = threadIdx.x; i < ns; i += blockDim.x) {
@@ -190,6 +216,8 @@ template <int DP>
 __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X, const uint32_t* __restrict__ C,
                                                      const int32_t* __restrict__ ids,
                                                      const uint32_t* __restrict__ SUB,
+                                                     const uint32_t* __restrict__ tend,
+                                                     const uint32_t* __restrict__ supmin,
                                                      const uint32_t* __restrict__ order, DevResult* res,
                                                      uint8_t* keep)
 {
@@ -197,7 +225,7 @@ __global__ void __launch_bounds__(kTQ + 32) k_refine(const float* __restrict__ X
     RefineSmem<DP>& sm = *reinterpret_cast<RefineSmem<DP>*>(smem_raw);
     const uint32_t m = res->survivors;
     if (blockIdx.x >= (m + kTQ - 1) / kTQ) return;
-    refine_ptile<DP>(sm, X, C, ids, SUB, m, order[blockIdx.x], res, keep);
+    refine_ptile<DP>(sm, X, C, ids, SUB, tend, supmin, m, order[blockIdx.x], res, keep);
 }
 
 // Ascending row ids of the kept rows (decoupled look-back over 8 rows per
@@ -270,9 +298,9 @@ cudaError_t launch_gather(const Plan& p, cudaStream_t s)
     const int64_t tiles = (p.n + kTQ - 1) / kTQ;
     if (tiles == 0) return cudaGetLastError();
     const bool v = (p.d % 4 == 0) && (p.ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.pts) & 15u) == 0);
-    SKY_DISPATCH_DP(p.d, k_gather<DP><<<(unsigned)tiles, kTQ, 0, s>>>(p.pts, p.d, p.ld, v, p.sorted_val, p.res,
-                                                                       p.params, p.X, p.C, p.ids, p.tmax,
-                                                                       p.subcode));
+    SKY_DISPATCH_DP(p.d, k_gather<DP><<<(unsigned)tiles, kTQ, 0, s>>>(p.pts, p.d, p.ld, v, p.sorted_val,
+                                                                       p.sorted_key, p.res, p.params, p.X, p.C,
+                                                                       p.ids, p.tmax, p.subcode, p.tile_end));
     return cudaGetLastError();
 }
 
@@ -283,12 +311,13 @@ cudaError_t launch_refine(const Plan& p, cudaStream_t s)
     if (tiles == 0) return cudaGetLastError();
     SKY_DISPATCH_DP(p.d, {
         constexpr int DW = DP / 4;
-        k_tile_cost<DW><<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(p.subcode, p.tmax, p.res, p.tile_cost);
+        k_tile_cost<DW><<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(p.subcode, p.tmax, p.res, p.tile_cost,
+                                                                   p.supmin);
         k_cost_order<<<1, 1024, 0, s>>>(p.tile_cost, p.res, p.tile_order);
         const int smem = (int)sizeof(RefineSmem<DP>);
         cudaFuncSetAttribute(k_refine<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_refine<DP><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, p.tile_order, p.res,
-                                                              p.keep);
+        k_refine<DP><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, p.tile_end, p.supmin,
+                                                              p.tile_order, p.res, p.keep);
     });
     return cudaGetLastError();
 }

@@ -102,6 +102,7 @@ cudaError_t launch_sort(Plan& p, cudaStream_t s)
         vin = tv;
     }
     p.sorted_val = vin;
+    p.sorted_key = kin;
     return cudaGetLastError();
 }
 

@@ -163,6 +163,8 @@ size_t layout(Plan& p, char* base, bool grid_api)
     p.tile_cost = c.take<uint32_t>(tiles);
     p.tile_order = c.take<uint32_t>(tiles);
     p.subcode = c.take<uint32_t>(tiles * 5 * (dp / 4));
+    p.tile_end = c.take<uint32_t>(tiles);
+    p.supmin = c.take<uint32_t>(((tiles + 31) / 32) * (dp / 4));
     p.keep = c.take<uint8_t>(n + 16);
     return c.off;
 }

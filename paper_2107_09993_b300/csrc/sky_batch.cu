@@ -197,7 +197,7 @@ sky_status sky_batch_create(const float* d_table, int64_t n_rows, int32_t n_cols
         o.X = at;     at = a256(at + 4 * npad * (size_t)p.dp);
         o.C = at;     at = a256(at + npad * (size_t)p.dp);
         o.ids = at;   at = a256(at + 4 * npad);
-        o.sub = at;   at = a256(at + 4 * (size_t)std::max<int64_t>(p.tiles, 1) * 5 * (size_t)(p.dp / 4));
+        o.sub = at;   at = a256(at + 4 * (size_t)std::max<int64_t>(p.tiles, 1) * 5 * (size_t)(p.dp / 4) + 16);
         o.stage = at; at = a256(at + 4 * n);
     }
     b->total = at;

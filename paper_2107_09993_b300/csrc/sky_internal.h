@@ -71,12 +71,15 @@ struct Plan {
     uint32_t* tile_cost = nullptr;   // [tiles] cost estimate of each p-tile
     uint32_t* tile_order = nullptr;  // [tiles] p-tiles, largest cost first
     uint32_t* subcode = nullptr;     // [tiles][5][dp/4] byte-wise min code of each 32-point sub-tile, then of the tile
+    uint32_t* tile_end = nullptr;    // [tiles] last q-tile whose first Morton key <= the tile's last key
+    uint32_t* supmin = nullptr;      // [ceil(tiles / 32)][dp/4] byte-wise min code of each run of 32 tiles
     uint8_t* keep = nullptr;         // [n] 1 = skyline
     float* filt = nullptr;           // [16][16] snapped filter points
     unsigned long long* snap = nullptr;  // [16] packed (sum, row) argmin
     DevResult* res = nullptr;
     // last sort output
     const uint32_t* sorted_val = nullptr;
+    const uint32_t* sorted_key = nullptr;
 };
 
 // One query of a batch (device copy; pointers resolved into the workspace).

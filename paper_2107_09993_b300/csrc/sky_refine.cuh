@@ -16,8 +16,10 @@ constexpr int kSubSlots = kTQ / 32 + 1;   // sub-tile minima + the whole-tile mi
 constexpr uint32_t kHigh = 0x80808080u;
 
 // One CTA per p-tile of 128 survivors (Morton neighbours), split in 4 groups
-// of 32, plus a producer warp. The producer scans the q-tiles in Morton
-// order, keeps those whose byte-wise minimum code is <= the byte-wise maximum
+// of 32, plus a producer warp. The producer scans the q-tiles up to the last
+// one that can hold a dominator (the p-tile itself first, then the rest in
+// ascending Morton order), keeps those whose byte-wise minimum code is <= the
+// byte-wise maximum
 // code of the live p's of some group (no other tile can hold a dominator of
 // a live p), and streams them into a ring of shared-memory stages by bulk
 // (TMA) copies, gated by full/empty mbarriers. Consumer warp w owns the 32
@@ -28,14 +30,17 @@ constexpr uint32_t kHigh = 0x80808080u;
 // floats; only pairs with some equal code need the exact Definition 1 test.
 // A dominated p is flagged; when none is left the producer stops issuing and
 // the consumers drain the ring. No block-wide barrier in the steady state.
-constexpr int kRingStages = 4;
+// Only the codes of a q-tile are streamed (1-2 KB a tile); the rare exact
+// test reads q's coordinates from global memory (the survivor layout is
+// L2-resident). Small stages allow a deep ring: the tile stream, not the
+// tests, bounds sets whose points die early.
+constexpr int kRingStages = 16;
 constexpr uint32_t kEndTile = 0xffffffffu;
 
 template <int DP>
 struct RefineSmem {
     static constexpr int DW = DP / 4;
-    float qX[kRingStages][kTQ * DP];     // streamed q-tiles
-    uint32_t qC[kRingStages][kTQ * DW];
+    uint32_t qC[kRingStages][kTQ * DW];  // streamed q-tiles (codes)
     float pX[kTQ * DP];                  // own p coordinates (exact tests)
     uint32_t pP[kTQ * DW];               // own p codes | 0x80 per byte
     uint32_t livemask[kTQ / 32];         // bit l of word g: p g*32+l is still undominated
@@ -46,6 +51,8 @@ struct RefineSmem {
     uint32_t stage_sub[kRingStages][kTQ / 32][DW];   // sub-tile minimum codes of the staged tile
     uint64_t full[kRingStages];
     uint64_t empty[kRingStages];
+    uint32_t stc[2][32 * kSubSlots * DW];   // producer: codes of the 32 tiles of a super-tile (double buffer)
+    uint64_t cbar[2];                        // producer: their bulk copies
     uint32_t live;                       // live p's of the CTA
     uint32_t failed;
 };
@@ -68,16 +75,23 @@ __device__ __forceinline__ bool bytes_le(const uint32_t* lo, const uint32_t* hi)
 // Refines p-tile `ptile` (< ceil(m / 128)) of one point set. Called by all
 // kTQ + 32 threads of the CTA with the CTA's shared memory; leaves the
 // shared memory free for the next call (barriers invalidated).
+// TEND (optional): per p-tile, the last q-tile that can hold a dominator of
+// one of its points (the tiles are in Morton order, and a dominator's Morton
+// key is never above its victim's: the column maps are monotone), so the
+// scan stops there; NULL scans every tile. SUPMIN (optional): byte-wise
+// minimum code of each run of 32 q-tiles ("super-tile"); a super-tile whose
+// minimum exceeds every live group's maximum in some byte is skipped whole;
+// NULL examines every super-tile.
 template <int DP>
 __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __restrict__ X,
                                              const uint32_t* __restrict__ C, const int32_t* __restrict__ ids,
-                                             const uint32_t* __restrict__ SUB, uint32_t m, uint32_t ptile,
+                                             const uint32_t* __restrict__ SUB, const uint32_t* __restrict__ TEND,
+                                             const uint32_t* __restrict__ SUPMIN, uint32_t m, uint32_t ptile,
                                              DevResult* res, uint8_t* keep)
 {
     constexpr int DW = DP / 4;
     constexpr int NG = kTQ / 32;
     constexpr int S = kRingStages;
-    constexpr uint32_t kBytesX = kTQ * DP * sizeof(float);
     constexpr uint32_t kBytesC = kTQ * DW * sizeof(uint32_t);
     const uint32_t T = (m + kTQ - 1) / kTQ;
     uint32_t* err = &res->err;
@@ -99,6 +113,8 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
             mbar_init(&sm.full[s], 1);
             mbar_init(&sm.empty[s], NG);
         }
+        mbar_init(&sm.cbar[0], 1);
+        mbar_init(&sm.cbar[1], 1);
         mbar_fence_init();
         sm.live = (m - pbase) < (uint32_t)kTQ ? (m - (uint32_t)pbase) : (uint32_t)kTQ;
         sm.failed = 0;
@@ -140,32 +156,97 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
         auto all_dead = [&]() -> bool {
             return __shfl_sync(kFull, (sm.live == 0u || sm.failed != 0u) ? 1 : 0, 0) != 0;
         };
-        // codes of the next 32 tiles are fetched one batch ahead
-        uint32_t tm[DW], sc[NG][DW];
-        auto fetch = [&](uint32_t t) {
+        const uint32_t E = TEND ? min(TEND[ptile], T - 1u) : T - 1u;   // last q-tile to scan
+        const uint32_t SL = E / 32u;                                     // last super-tile
+        // Streaming order: the p-tile itself first (its own points kill each
+        // other early in anti-correlated sets), then the super-tiles in
+        // ascending Morton order (tiles near the origin, whose points
+        // dominate most, early). Relevant super-tiles are found 32 at a time
+        // (lane = super-tile).
+        uint32_t win = 0, smask = 0;
+        auto next_super = [&]() -> int {
+            while (true) {
+                if (smask) {
+                    const int b = __ffs(smask) - 1;
+                    smask &= smask - 1;
+                    return (int)(win - 32u) + b;
+                }
+                if (win > SL) return -1;
+                const uint32_t sx = win + lane;
+                bool rel = sx <= SL;
+                if (rel && SUPMIN) {
+                    uint32_t mn[DW];
 #pragma unroll
-            for (int w = 0; w < DW; ++w) tm[w] = t < T ? __ldg(SUB + ((int64_t)t * kSubSlots + NG) * DW + w) : 0u;
+                    for (int w = 0; w < DW; ++w) mn[w] = __ldg(SUPMIN + (int64_t)sx * DW + w);
+                    rel = false;
 #pragma unroll
-            for (int q = 0; q < NG; ++q)
-#pragma unroll
-                for (int w = 0; w < DW; ++w) sc[q][w] = t < T ? __ldg(SUB + ((int64_t)t * kSubSlots + q) * DW + w) : 0u;
+                    for (int g = 0; g < NG; ++g) rel |= (sm.glive[g] != 0u) && bytes_le<DW>(mn, sm.gmax[g]);
+                }
+                smask = __ballot_sync(kFull, rel);
+                win += 32u;
+            }
         };
-        fetch(lane);
-        for (uint32_t t0 = 0; t0 < T && !stop; t0 += 32) {
+        // the p-tile itself: every (sub-tile, group) pair whose sub-tile
+        // minimum is within the group's reach
+        {
+            const int q = lane / NG, g = lane % NG;
+            bool rel = false;
+            if (lane < NG * NG && sm.glive[g] != 0u) {
+                uint32_t mn[DW];
+#pragma unroll
+                for (int w = 0; w < DW; ++w) mn[w] = __ldg(SUB + ((int64_t)ptile * kSubSlots + q) * DW + w);
+                rel = bytes_le<DW>(mn, sm.gmax[g]);
+            }
+            if (lane < NG * DW) sm.stage_sub[0][lane / DW][lane % DW] = __ldg(SUB + (int64_t)ptile * kSubSlots * DW + lane);
+            const uint32_t bmask = __ballot_sync(kFull, rel);
+            __syncwarp();   // the lanes' writes before lane 0's arrive on the slot
+            if (lane == 0 && bmask) {
+                sm.stage_tile[0] = ptile;
+                sm.stage_mask[0] = bmask;
+                mbar_arrive_expect_tx(&sm.full[0], kBytesC);
+                bulk_g2s(sm.qC[0], C + (int64_t)ptile * kTQ * DW, kBytesC, &sm.full[0]);
+            }
+            __syncwarp();
+            if (bmask) { ++issued; ++since; }
+        }
+        // the codes of the 32 tiles of a super-tile: one bulk copy (the code
+        // arrays carry 16 bytes of slack past their end); copy k goes to
+        // buffer k & 1 and is that buffer's (k >> 1)-th use
+        uint32_t kiss = 0, kcons = 0;   // copies issued / consumed
+        auto fetch_super = [&](int sx) {
+            const uint32_t t0 = (uint32_t)sx * 32u;
+            const uint32_t nt = min(32u, T - t0);
+            const uint32_t bytes = (nt * kSubSlots * DW * 4u + 15u) & ~15u;
+            const int bb = (int)(kiss & 1u);
+            __syncwarp();
+            if (lane == 0) {
+                fence_proxy_async_smem();   // generic reads of this buffer are done
+                mbar_arrive_expect_tx(&sm.cbar[bb], bytes);
+                bulk_g2s(sm.stc[bb], SUB + (int64_t)t0 * kSubSlots * DW, bytes, &sm.cbar[bb]);
+            }
+            ++kiss;
+        };
+        int cur = next_super();
+        if (cur >= 0) fetch_super(cur);
+        while (cur >= 0 && !stop) {
             if (all_dead()) break;
+            const int nx = next_super();
+            if (nx >= 0) fetch_super(nx);
+            const int bf = (int)(kcons & 1u);
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(&sm.cbar[bf], (kcons >> 1) & 1u, err);
+            if (!__shfl_sync(kFull, ok ? 1 : 0, 0)) { if (lane == 0) sm.failed = 1u; stop = true; break; }
+            ++kcons;
             if (since >= 32) { summarise(); since = 0; }
+            const uint32_t t0 = (uint32_t)cur * 32u;
             const uint32_t t = t0 + lane;
-            uint32_t ctm[DW], csc[NG][DW];
-#pragma unroll
-            for (int w = 0; w < DW; ++w) ctm[w] = tm[w];
-#pragma unroll
-            for (int q = 0; q < NG; ++q)
-#pragma unroll
-                for (int w = 0; w < DW; ++w) csc[q][w] = sc[q][w];
-            fetch(t + 32);
+            const uint32_t* tc = &sm.stc[bf][lane * kSubSlots * DW];
             // relevance of each (sub-tile, group) pair of this q-tile
             uint32_t rmask = 0;
-            if (t < T) {
+            if (t <= E && t != ptile) {   // the p-tile itself went first
+                uint32_t ctm[DW];
+#pragma unroll
+                for (int w = 0; w < DW; ++w) ctm[w] = tc[NG * DW + w];
                 bool any = false;
 #pragma unroll
                 for (int g = 0; g < NG; ++g) any |= (sm.glive[g] != 0u) && bytes_le<DW>(ctm, sm.gmax[g]);
@@ -174,7 +255,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                     for (int q = 0; q < NG; ++q)
 #pragma unroll
                         for (int g = 0; g < NG; ++g)
-                            if (sm.glive[g] != 0u && bytes_le<DW>(csc[q], sm.gmax[g])) rmask |= 1u << (q * NG + g);
+                            if (sm.glive[g] != 0u && bytes_le<DW>(tc + q * DW, sm.gmax[g])) rmask |= 1u << (q * NG + g);
                 }
             }
             uint32_t mask = __ballot_sync(kFull, rmask != 0u);
@@ -184,22 +265,15 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                 const uint32_t bmask = __shfl_sync(kFull, rmask, b);
                 int s;
                 if (!claim(s)) { if (lane == 0) sm.failed = 1u; stop = true; break; }
-                {
-                    // every lane holds its own tile's codes; move tile b's to the slot
-#pragma unroll
-                    for (int q = 0; q < NG; ++q)
-#pragma unroll
-                        for (int w = 0; w < DW; ++w) {
-                            const uint32_t v = __shfl_sync(kFull, csc[q][w], b);
-                            if (lane == 0) sm.stage_sub[s][q][w] = v;
-                        }
-                }
+                // tile b's sub-tile minima to the slot; the warp barrier orders
+                // these writes before lane 0's arrive on the slot
+                if (lane < NG * DW) sm.stage_sub[s][lane / DW][lane % DW] = sm.stc[bf][b * kSubSlots * DW + lane];
+                __syncwarp();
                 if (lane == 0) {
                     const uint32_t tt = t0 + b;
                     sm.stage_tile[s] = tt;
                     sm.stage_mask[s] = bmask;
-                    mbar_arrive_expect_tx(&sm.full[s], kBytesX + kBytesC);
-                    bulk_g2s(sm.qX[s], X + (int64_t)tt * kTQ * DP, kBytesX, &sm.full[s]);
+                    mbar_arrive_expect_tx(&sm.full[s], kBytesC);
                     bulk_g2s(sm.qC[s], C + (int64_t)tt * kTQ * DW, kBytesC, &sm.full[s]);
                 }
                 __syncwarp();
@@ -207,7 +281,11 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                 ++since;
                 if (all_dead()) { stop = true; break; }
             }
+            cur = nx;
         }
+        // code copies that were not consumed land before the exit
+        if (lane == 0)
+            for (uint32_t k = kcons; k < kiss; ++k) mbar_wait(&sm.cbar[k & 1u], (k >> 1) & 1u, nullptr);
         if (lane == 0 && issued) atomicAdd(&res->tiles, (unsigned long long)issued);
         // end-of-stream marker
         int s;
@@ -280,12 +358,12 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                             bool dom = true;   // strictly lower code everywhere: q < p everywhere
                             if (eq) {
                                 ++exact;
-                                const float* qx = &sm.qX[s][qi * DP];
+                                const float* qx = X + ((int64_t)tt * kTQ + qi) * DP;
                                 const float* px = &sm.pX[pi * DP];
                                 bool le = true, lt = false;
 #pragma unroll
                                 for (int kk = 0; kk < DP; kk += 4) {
-                                    const float4 u = *reinterpret_cast<const float4*>(qx + kk);
+                                    const float4 u = __ldg(reinterpret_cast<const float4*>(qx + kk));
                                     const float4 v = *reinterpret_cast<const float4*>(px + kk);
                                     le &= (u.x <= v.x) & (u.y <= v.y) & (u.z <= v.z) & (u.w <= v.w);
                                     lt |= (u.x < v.x) | (u.y < v.y) | (u.z < v.z) | (u.w < v.w);
