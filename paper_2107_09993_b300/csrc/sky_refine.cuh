@@ -34,14 +34,27 @@ constexpr uint32_t kHigh = 0x80808080u;
 // test reads q's coordinates from global memory (the survivor layout is
 // L2-resident). Small stages allow a deep ring: the tile stream, not the
 // tests, bounds sets whose points die early.
-constexpr int kRingStages = 16;
+#ifndef SKY_REFINE_STAGES
+#define SKY_REFINE_STAGES 8
+#endif
+#ifndef SKY_REFINE_SUMMARY
+#define SKY_REFINE_SUMMARY 32
+#endif
+#ifndef SKY_REFINE_UNROLL
+#define SKY_REFINE_UNROLL 1
+#endif
+constexpr int kRingStages = SKY_REFINE_STAGES;
+constexpr uint32_t kSummaryEvery = SKY_REFINE_SUMMARY;   // issued tiles between refreshes of the group maxima
+constexpr int kPUnroll = SKY_REFINE_UNROLL;              // listed p's tested per loop step (1 or 2)
+static_assert(kPUnroll == 1 || kPUnroll == 2, "one or two p's per step");
 constexpr uint32_t kEndTile = 0xffffffffu;
 
 template <int DP>
 struct RefineSmem {
     static constexpr int DW = DP / 4;
-    uint32_t qC[kRingStages][kTQ * DW];  // streamed q-tiles (codes)
-    float pX[kTQ * DP];                  // own p coordinates (exact tests)
+    // bulk-copy destinations: 16-byte aligned whatever the ring depth
+    alignas(16) uint32_t qC[kRingStages][kTQ * DW];  // streamed q-tiles (codes)
+    alignas(16) float pX[kTQ * DP];      // own p coordinates (exact tests)
     uint32_t pP[kTQ * DW];               // own p codes | 0x80 per byte
     uint32_t livemask[kTQ / 32];         // bit l of word g: p g*32+l is still undominated
     uint32_t gmax[kTQ / 32][DW];         // byte-wise max code of each group's live p's (producer)
@@ -51,7 +64,7 @@ struct RefineSmem {
     uint32_t stage_sub[kRingStages][kTQ / 32][DW];   // sub-tile minimum codes of the staged tile
     uint64_t full[kRingStages];
     uint64_t empty[kRingStages];
-    uint32_t stc[2][32 * kSubSlots * DW];   // producer: codes of the 32 tiles of a super-tile (double buffer)
+    alignas(16) uint32_t stc[2][32 * kSubSlots * DW];   // producer: codes of the 32 tiles of a super-tile
     uint64_t cbar[2];                        // producer: their bulk copies
     uint32_t live;                       // live p's of the CTA
     uint32_t failed;
@@ -237,7 +250,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
             if (lane == 0) ok = mbar_wait(&sm.cbar[bf], (kcons >> 1) & 1u, err);
             if (!__shfl_sync(kFull, ok ? 1 : 0, 0)) { if (lane == 0) sm.failed = 1u; stop = true; break; }
             ++kcons;
-            if (since >= 32) { summarise(); since = 0; }
+            if (since >= kSummaryEvery) { summarise(); since = 0; }
             const uint32_t t0 = (uint32_t)cur * 32u;
             const uint32_t t = t0 + lane;
             const uint32_t* tc = &sm.stc[bf][lane * kSubSlots * DW];
@@ -340,9 +353,8 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                     for (int w = 0; w < DW; ++w) r &= sm.pP[pg * DW + w] - Mw[w];
                     uint32_t mask = __ballot_sync(kFull, r == kHigh) & sm.livemask[g];
                     pairs += 32ull * __popc(mask);
-                    while (mask) {
-                        const int pi = g * 32 + __ffs(mask) - 1;
-                        mask &= mask - 1;
+                    // q (this lane) against listed p pi
+                    auto probe = [&](int pi) {
                         uint32_t D[DW];
                         uint32_t a = kHigh;
 #pragma unroll
@@ -374,6 +386,18 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                                 const uint32_t bit = 1u << (pi & 31);
                                 if (atomicAnd(&sm.livemask[pi >> 5], ~bit) & bit) atomicSub(&sm.live, 1u);
                             }
+                        }
+                    };
+                    while (mask) {
+                        const int pa = g * 32 + __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        if (kPUnroll == 2 && mask) {
+                            const int pb = g * 32 + __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            probe(pa);
+                            probe(pb);
+                        } else {
+                            probe(pa);
                         }
                     }
                 }
