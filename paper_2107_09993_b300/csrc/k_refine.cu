@@ -118,11 +118,20 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
     // dominator's Morton key is <= its victim's (monotone columns), so only
     // tiles whose first key is <= this tile's last key qualify. Ties across
     // tile boundaries are the only reason to look past this tile.
-    if (tid == 0) {
+    // Warp 0 checks the first keys of the next 32 tiles at once (one round of
+    // loads; ties spanning more tiles take further rounds).
+    if (warp == 0) {
         const uint32_t last = sorted_key[min((int64_t)m, ((int64_t)blockIdx.x + 1) * kTQ) - 1];
         uint32_t e = blockIdx.x;
-        while (e + 1 < T && sorted_key[(int64_t)(e + 1) * kTQ] <= last) ++e;
-        tile_end[blockIdx.x] = e;
+        while (true) {
+            const uint32_t t = e + 1 + lane;
+            const bool tie = t < T && sorted_key[(int64_t)t * kTQ] <= last;
+            const uint32_t run = __ballot_sync(kFull, !tie);   // first lane that is not a tie ends the run
+            const uint32_t k = run ? (uint32_t)(__ffs(run) - 1) : 32u;
+            e += k;
+            if (k < 32u) break;
+        }
+        if (lane == 0) tile_end[blockIdx.x] = e;
     }
 }
 
