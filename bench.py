@@ -15,7 +15,8 @@ is flushed before every timed step by writing a 512 MB buffer.
 N > 1 runs independent replicas (the skyline of one point set is computed on
 one GPU), launched under torchrun, weak scaling.
 `--impl reference` times the CPU oracle (sort-first skyline) on the host cores
-on a bounded row sample of the same workload.
+on a bounded row sample of the same workload. The sky arm's line also carries
+the paper's own sequential SkyCell (host, one thread) on a smaller sample.
 """
 from __future__ import annotations
 
@@ -436,6 +437,7 @@ def run_sky(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(host, args.cpu_seconds)
+        line["cpu_baseline_sequential"] = seq_baseline(host, args.cpu_seconds / 2)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -461,6 +463,26 @@ def cpu_baseline(host, seconds):
     return {"value": round(value, 1), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"sort-first skyline oracle on the first {rows:,} rows of each of the 3 datasets, "
                       f"{reps} repetition(s), {spent:.1f} s"}
+
+
+SEQ_SAMPLE_ROWS = 20_000
+
+
+def seq_baseline(host, seconds):
+    """The paper's sequential SkyCell on the host (one thread), on the first
+    SEQ_SAMPLE_ROWS rows of each dataset, repeated for about `seconds`."""
+    import paper_2107_09993_b300 as sky
+    rows = SEQ_SAMPLE_ROWS
+    spent, reps = 0.0, 0
+    while spent < seconds or reps == 0:
+        t0 = time.perf_counter()
+        for P in host:
+            sky.baseline_sequential(P[:rows])
+        spent += time.perf_counter() - t0
+        reps += 1
+    value = reps * rows * len(host) / spent
+    return {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "paper's sequential SkyCell (Alg. 1 + 2)",
+            "sample": f"first {rows:,} rows of each of the 3 datasets, {reps} repetition(s), {spent:.1f} s"}
 
 
 # -------------------------------------------------------------- reference --

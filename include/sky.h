@@ -447,6 +447,43 @@ SKY_API sky_status sky_skyline_noalloc(const float* d_pts, int64_t n, int32_t d,
                                        int64_t* h_out_count, void* stream);
 SKY_API const char* sky_noalloc_last_error(void);
 
+/* ------------------------------------------------------------------------ */
+/* CPU baseline: the paper's sequential SkyCell (Alg. 1 driving the          */
+/* sequential ShrinkKeyCells of Alg. 2, Sec. 4) on the host. It is the      */
+/* comparison the GPU path is timed against, not part of the GPU path: no   */
+/* GPU entry point calls it. Host pointers only; no CUDA call.              */
+/*                                                                          */
+/* Layers 0 .. log2_g are built from the points' Layer-log2_g cells (Eq. 1  */
+/* on the unit cube with assume_unit = 1, otherwise after the min / max of  */
+/* all rows). Layer by layer the cells are enumerated slice by slice        */
+/* ([cl_{d-1} .. cl_1], dimension d-1 outermost) between a start bound       */
+/* doubled from the previous layer (step (a) of Alg. 2) and an end bound     */
+/* from the lower slices (MinGE); the first non-empty cell of a slice below  */
+/* its end bound is a key cell (Def. 4). Points of cells that no non-empty   */
+/* cell dominates (Def. 3) are refined by a sort-first skyline across cells. */
+/* ------------------------------------------------------------------------ */
+
+/* h_pts: n x d float32, row stride ld >= d (floats), finite values (else
+ * SKY_ERR_NONFINITE); 1 <= d <= 16, 0 <= n < 2^31. log2_g: the layer rho
+ * (-1: the GPU path's automatic rule); rho * d <= 24 (SKY_ERR_TOO_LARGE
+ * otherwise). assume_unit: 1 = Eq. 1 on [0,1)^d, 0 = min / max scaling.
+ * Writes the ascending skyline row ids to h_out (capacity entries; a larger
+ * skyline returns SKY_ERR_CAPACITY with *h_count set), *h_count = |S|, and
+ * *h_candidates (optional) = the points refined after the cell pruning. */
+SKY_API sky_status sky_baseline_sequential(const float* h_pts, int64_t n, int32_t d, int64_t ld, int32_t log2_g,
+                                           int32_t assume_unit, int32_t* h_out, int64_t capacity,
+                                           int64_t* h_count, int64_t* h_candidates);
+
+/* The key cells (Def. 4) of Layer log2_g (>= 0) found by the baseline's
+ * enumeration, as cell keys sum_k c[k] 2^(log2_g k), ascending. Same input
+ * conventions as sky_baseline_sequential. */
+SKY_API sky_status sky_baseline_key_cells(const float* h_pts, int64_t n, int32_t d, int64_t ld, int32_t log2_g,
+                                          int32_t assume_unit, int64_t* h_keys, int64_t capacity,
+                                          int64_t* h_count);
+
+/* Thread-local detail of the last error of the two baseline calls. */
+SKY_API const char* sky_baseline_last_error(void);
+
 /* Static text for a status code. */
 SKY_API const char* sky_status_string(sky_status status);
 

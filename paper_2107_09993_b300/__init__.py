@@ -88,6 +88,9 @@ def load():
         "sky_status_string": ([_i32], ctypes.c_char_p),
         "sky_last_error": ([], ctypes.c_char_p),
         "sky_version": ([], ctypes.c_char_p),
+        "sky_baseline_sequential": ([_vp, _i64, _i32, _i64, _i32, _i32, _vp, _i64, P(_i64), P(_i64)], _i32),
+        "sky_baseline_key_cells": ([_vp, _i64, _i32, _i64, _i32, _i32, _vp, _i64, P(_i64)], _i32),
+        "sky_baseline_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -544,3 +547,51 @@ def skyline_learned(points, params_bf16, inflate=0.02, n_ref=TRAIN_ROWS, stream=
     d = points.shape[1] if points.dim() == 2 else 1
     lg = max(1, min(lg, 27 // d, 16))
     return skyline(points, log2_g=lg, filter_points=prop, stream=stream, out=out)
+
+
+# ------------------------------------------------------------ CPU baseline --
+def _baseline_points(points):
+    import numpy as np
+    P = np.ascontiguousarray(points, dtype=np.float32)
+    if P.ndim != 2:
+        raise ValueError("points must be an n x d array")
+    return P
+
+
+def _baseline_check(status: int):
+    if status != SKY_OK:
+        raise SkyError(status, load().sky_baseline_last_error().decode())
+
+
+def baseline_sequential(points, log2_g=None, assume_unit=False):
+    """The paper's sequential SkyCell on the host (sky_baseline_sequential):
+    a CPU comparison for the GPU path, not part of it. numpy n x d float32 in,
+    (ascending int32 skyline row ids, candidates refined after the cell
+    pruning) out."""
+    import numpy as np
+    lib = load()
+    P = _baseline_points(points)
+    n, d = P.shape
+    out = np.empty(max(n, 1), dtype=np.int32)
+    cnt, cand = _i64(0), _i64(0)
+    st = lib.sky_baseline_sequential(_vp(P.ctypes.data), n, d, d, -1 if log2_g is None else int(log2_g),
+                                     1 if assume_unit else 0, _vp(out.ctypes.data), out.size, ctypes.byref(cnt),
+                                     ctypes.byref(cand))
+    _baseline_check(st)
+    return out[:cnt.value].copy(), int(cand.value)
+
+
+def baseline_key_cells(points, log2_g, assume_unit=False):
+    """Key cells (Def. 4) of Layer log2_g found by the sequential baseline's
+    slice enumeration: ascending int64 cell keys."""
+    import numpy as np
+    lib = load()
+    P = _baseline_points(points)
+    n, d = P.shape
+    cap = max(n, 1)
+    out = np.empty(cap, dtype=np.int64)
+    cnt = _i64(0)
+    st = lib.sky_baseline_key_cells(_vp(P.ctypes.data), n, d, d, int(log2_g), 1 if assume_unit else 0,
+                                    _vp(out.ctypes.data), cap, ctypes.byref(cnt))
+    _baseline_check(st)
+    return out[:cnt.value].copy()
