@@ -278,12 +278,14 @@ struct MortonSpread {
 // (A shared-memory cache of bitmap words measured slower on clustered data
 // than both global variants.)
 struct MarkGlobal {
+    static constexpr bool kNone = false;
     uint32_t* occ;
     __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const { atomicOr(occ + word, bits); }
 };
 // The private marker looks before it ORs: a bit already set costs one shared
 // load, not a serialised atomic on the same address.
 struct MarkPrivate {
+    static constexpr bool kNone = false;
     uint32_t* s_occ;   // shared memory
     __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const
     {
@@ -291,9 +293,11 @@ struct MarkPrivate {
     }
 };
 struct MarkNone {
+    static constexpr bool kNone = true;
     __device__ __forceinline__ void mark(uint32_t, uint32_t) const {}
 };
 struct MarkCheck {
+    static constexpr bool kNone = false;
     uint32_t* occ;
     bool check;        // block-uniform
     __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const
@@ -348,13 +352,11 @@ __device__ __forceinline__ void map_keys(const float (&x)[DP], int d, int log2g,
 // The two shape tests are uniform across the grid, so each call runs one
 // specialised body.
 // Writes a row's keys and marks its cell.
+// Marks a row's cell; when a whole warp hits one word the bits are merged
+// first and one lane issues the mark.
 template <bool converged, class Marker>
-__device__ __forceinline__ void store_mark(uint32_t key, uint32_t code, int64_t row, uint32_t* __restrict__ ckey,
-                                           uint32_t* __restrict__ mkey, const Marker& marker,
-                                           uint32_t* dups = nullptr)
+__device__ __forceinline__ void mark_cell(uint32_t key, const Marker& marker, uint32_t* dups = nullptr)
 {
-    ckey[row] = key;
-    mkey[row] = code;
     const uint32_t word = key >> 5;
     if (dups) *dups += __popc(__match_any_sync(kFull, word)) > 1 ? 1u : 0u;   // converged callers only
     const uint32_t bit = 1u << (key & 31u);
@@ -367,6 +369,19 @@ __device__ __forceinline__ void store_mark(uint32_t key, uint32_t code, int64_t 
     } else {
         marker.mark(word, bit);
     }
+}
+
+// Writes a row's keys (when the pass keeps keys) and marks its cell.
+template <bool converged, class Marker>
+__device__ __forceinline__ void store_mark(uint32_t key, uint32_t code, int64_t row, uint32_t* __restrict__ ckey,
+                                           uint32_t* __restrict__ mkey, const Marker& marker,
+                                           uint32_t* dups = nullptr)
+{
+    if (ckey) {   // a marking pass that needs no keys passes none
+        ckey[row] = key;
+        mkey[row] = code;
+    }
+    if (!Marker::kNone) mark_cell<converged>(key, marker, dups);
 }
 
 template <int DP, bool converged, class Marker>
@@ -499,20 +514,26 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_plain(const float* __rest
 // d = 16 instead of 16-way for scalar reads).
 constexpr int kMapStages = 4;
 
+// Rows per thread and stage: a stage holds kThreads * map_rpt(DP) rows, at
+// most 16 KB (four rows of four floats per thread at d <= 4, two at d <= 8),
+// so that small rows keep as many bytes in flight as 16-float rows.
+__host__ __device__ constexpr int map_rpt(int DP) { return DP >= 16 ? 1 : 16 / DP; }
+
 template <int DP, int MODE>
 __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restrict__ pts, int64_t n,
                                                            int d, int log2g, int mbits, const float* params,
                                                            uint32_t* ckey, uint32_t* mkey, uint32_t* occ,
-                                                           uint32_t* err, uint32_t* stage, int64_t words)
+                                                           uint32_t* err, uint32_t* stage, int64_t words,
+                                                           bool look)
 {
-    // [kMapStages][kThreads * d] row stages, then the private bitmap [words]
-    // (kMarkSmall)
+    // [kMapStages][kThreads * map_rpt(DP) * d] row stages, then the private
+    // bitmap [words] (kMarkSmall)
     extern __shared__ __align__(128) float s_buf[];
     __shared__ float s_off[kMaxDim], s_sc[kMaxDim], s_ms[kMaxDim];
     __shared__ __align__(8) uint64_t s_bar[kMapStages];
     __shared__ uint32_t s_dups, s_check;
     const int tid = threadIdx.x;
-    uint32_t* s_tail = reinterpret_cast<uint32_t*>(s_buf + kMapStages * kThreads * d);
+    uint32_t* s_tail = reinterpret_cast<uint32_t*>(s_buf + kMapStages * kThreads * map_rpt(DP) * d);
     if (tid < kMaxDim) {
         s_off[tid] = params[tid];
         s_sc[tid] = params[16 + tid];
@@ -524,7 +545,7 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
         for (int s = 0; s < kMapStages; ++s) mbar_init(&s_bar[s], 1);
         mbar_fence_init();
         s_dups = 0u;
-        s_check = 0u;
+        s_check = look ? 1u : 0u;
     }
     __syncthreads();
     const MortonSpread ms(d, mbits);
@@ -537,14 +558,16 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
     constexpr int NQ = DP / 4;
     const int rot = NQ == 4 ? (tid >> 1) & 3 : (NQ == 2 ? (tid >> 2) & 1 : 0);
 
-    const int64_t nfull = n / kThreads;
-    const uint32_t chunk_bytes = (uint32_t)(kThreads * d * sizeof(float));
+    constexpr int RPT = map_rpt(DP);
+    constexpr int CR = kThreads * RPT;             // rows per stage
+    const int64_t nfull = n / CR;
+    const uint32_t chunk_bytes = (uint32_t)(CR * d * sizeof(float));
     const int64_t my_chunks = (nfull > blockIdx.x) ? (nfull - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     if (tid == 0) {
         for (int64_t i = 0; i < my_chunks && i < kMapStages; ++i) {
             const int64_t c = blockIdx.x + i * gridDim.x;
             mbar_arrive_expect_tx(&s_bar[i], chunk_bytes);
-            bulk_g2s(s_buf + i * kThreads * d, pts + c * kThreads * d, chunk_bytes, &s_bar[i]);
+            bulk_g2s(s_buf + i * CR * d, pts + c * CR * d, chunk_bytes, &s_bar[i]);
         }
     }
     bool bad = false;
@@ -567,35 +590,70 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
             break;
         }
         const int64_t c = blockIdx.x + i * gridDim.x;
-        const float* r = s_buf + s * kThreads * d + tid * d;
         if (unit) {
-            uint32_t key, code;
-            if (mbits <= log2g) map_keys_unit<DP, true>(r, rot, log2g, mbits, ms, key, code, bad);
-            else map_keys_unit<DP, false>(r, rot, log2g, mbits, ms, key, code, bad);
-            const int64_t row = c * kThreads + tid;
-            if (MODE == kMarkSmall) store_mark<true>(key, code, row, ckey, mkey, MarkPrivate{s_tail});
-            else if (MODE == kMarkNone) store_mark<true>(key, code, row, ckey, mkey, MarkNone{});
-            else store_mark<true>(key, code, row, ckey, mkey, MarkCheck{occ, s_check != 0u}, i == 0 ? &dups : nullptr);
-        } else {
-            float x[DP];
-            if (v4) {
+            // the stage's rows of this thread: keys first, then the marks
+            uint32_t key[RPT], code[RPT];
 #pragma unroll
-                for (int k = 0; k < DP; k += 4) {
-                    const float4 q = *reinterpret_cast<const float4*>(r + k);
-                    x[k] = q.x; x[k + 1] = q.y; x[k + 2] = q.z; x[k + 3] = q.w;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < DP; ++k) x[k] = (k < d) ? r[k] : 0.0f;
+            for (int j = 0; j < RPT; ++j) {
+                const float* r = s_buf + s * CR * d + (j * kThreads + tid) * d;
+                if (mbits <= log2g) map_keys_unit<DP, true>(r, rot, log2g, mbits, ms, key[j], code[j], bad);
+                else map_keys_unit<DP, false>(r, rot, log2g, mbits, ms, key[j], code[j], bad);
             }
-            const int64_t row = c * kThreads + tid;
-            if (MODE == kMarkSmall)
-                map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, row, ckey, mkey, MarkPrivate{s_tail}, bad);
-            else if (MODE == kMarkNone)
-                map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, row, ckey, mkey, MarkNone{}, bad);
-            else
-                map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, row, ckey, mkey,
-                                  MarkCheck{occ, s_check != 0u}, bad, i == 0 ? &dups : nullptr);
+            if (ckey) {
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    const int64_t row = c * CR + j * kThreads + tid;
+                    ckey[row] = key[j];
+                    mkey[row] = code[j];
+                }
+            }
+            if (MODE == kMarkSmall) {
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) mark_cell<true>(key[j], MarkPrivate{s_tail});
+            } else if (MODE == kMarkCheck) {
+                if (s_check != 0u && i > 0) {
+                    // looking: every bitmap read of the thread in flight at
+                    // once; a mark is sent only when its bit is not set yet
+                    uint32_t w[RPT];
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j) w[j] = __ldca(occ + (key[j] >> 5));
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j)
+                        if (!((w[j] >> (key[j] & 31u)) & 1u)) atomicOr(occ + (key[j] >> 5), 1u << (key[j] & 31u));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j)
+                        mark_cell<true>(key[j], MarkCheck{occ, s_check != 0u}, (i == 0 && j == 0) ? &dups : nullptr);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < RPT && !unit; ++j) {
+            const int rr = j * kThreads + tid;          // row of the stage
+            const float* r = s_buf + s * CR * d + rr * d;
+            const int64_t row = c * CR + rr;
+            uint32_t* dp = (i == 0 && j == 0) ? &dups : nullptr;
+            {
+                float x[DP];
+                if (v4) {
+#pragma unroll
+                    for (int k = 0; k < DP; k += 4) {
+                        const float4 q = *reinterpret_cast<const float4*>(r + k);
+                        x[k] = q.x; x[k + 1] = q.y; x[k + 2] = q.z; x[k + 3] = q.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < DP; ++k) x[k] = (k < d) ? r[k] : 0.0f;
+                }
+                if (MODE == kMarkSmall)
+                    map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, row, ckey, mkey, MarkPrivate{s_tail},
+                                      bad);
+                else if (MODE == kMarkNone)
+                    map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, row, ckey, mkey, MarkNone{}, bad);
+                else
+                    map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, row, ckey, mkey,
+                                      MarkCheck{occ, s_check != 0u}, bad, dp);
+            }
         }
         if (MODE == kMarkCheck && i == 0) {
             const uint32_t h = __reduce_add_sync(kFull, dups);
@@ -604,20 +662,19 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
         __syncthreads();  // every thread is done with stage s
         if (tid == 0) {
             // look before marking from the second chunk on when at least
-            // 1/16 of the first chunk's rows shared their word inside a warp
+            // 1/16 of the first chunk's first rows shared their word inside a warp
             if (MODE == kMarkCheck && i == 0 && s_dups >= (uint32_t)(kThreads / 16)) s_check = 1u;
             if (i + kMapStages < my_chunks) {
                 const int64_t c2 = blockIdx.x + (i + kMapStages) * gridDim.x;
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&s_bar[s], chunk_bytes);
-                bulk_g2s(s_buf + s * kThreads * d, pts + c2 * kThreads * d, chunk_bytes, &s_bar[s]);
+                bulk_g2s(s_buf + s * CR * d, pts + c2 * CR * d, chunk_bytes, &s_bar[s]);
             }
         }
     }
-    // Tail rows (fewer than one chunk): the last block loads them directly.
+    // Tail rows (fewer than one stage): the last block loads them directly.
     if (!timed_out && blockIdx.x == gridDim.x - 1) {
-        const int64_t i = nfull * kThreads + tid;
-        if (i < n) {
+        for (int64_t i = nfull * CR + tid; i < n; i += kThreads) {
             float x[DP];
             load_row<DP>(pts + i * d, d, false, x);
             if (MODE == kMarkSmall)
@@ -935,6 +992,7 @@ __global__ void __launch_bounds__(kThreads) k_surv_flags(
     __shared__ __align__(8) uint64_t s_bar[kSurvStages];
     __shared__ float s_f[16 * kMaxDim];
     __shared__ uint32_t s_cnt[kThreads / 32];
+    __shared__ uint32_t s_diag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nf = n_filter_max ? (int)res->n_filter_used : 0;
     for (int t = tid; t < nf * kMaxDim; t += kThreads) s_f[t] = filt[t];
@@ -954,6 +1012,28 @@ __global__ void __launch_bounds__(kThreads) k_surv_flags(
     const uint32_t ones = ones_key(log2g, d);
     const uint32_t highs = can_dominate ? ones << (log2g - 1) : 0u;
     const int sub = lane & 7;                  // nibble of this lane in its flag word
+    // D = the first t whose diagonal cell (t, .., t) has its prefix-OR bit
+    // set: some occupied cell lies in [0, t]^d, so every cell whose columns
+    // all exceed D is dominated (Def. 3) without a probe. D = 0 (the origin
+    // cell is occupied) settles every row that would probe.
+    if (warp == 0) {
+        const uint32_t G = 1u << log2g;
+        uint32_t first = G;
+        for (uint32_t t0 = 0; t0 < G && can_dominate; t0 += 32) {
+            const uint32_t t = t0 + lane;
+            bool set = false;
+            if (t < G) {
+                const uint32_t c = t * ones;
+                set = (__ldg(pre + (c >> 5)) >> (c & 31u)) & 1u;
+            }
+            const uint32_t b = __ballot_sync(kFull, set);
+            if (b) { first = t0 + (uint32_t)(__ffs(b) - 1); break; }
+        }
+        if (lane == 0) s_diag = first;
+    }
+    __syncthreads();
+    const uint32_t D = s_diag;
+    const uint32_t cmask = (1u << log2g) - 1u;
     uint32_t cnt = 0;                          // rows kept by this thread
     bool timed_out = false;
     for (int64_t i = 0; i < my; ++i) {
@@ -984,8 +1064,20 @@ __global__ void __launch_bounds__(kThreads) k_surv_flags(
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (r + e < valid) {
-                    if (can_dominate && !has_zero_column(ks[h][e], ones, highs)) need[h] |= 1u << e;
-                    else keep[h] |= 1u << e;
+                    if (can_dominate && !has_zero_column(ks[h][e], ones, highs)) {
+                        // every column >= 1; dominated outright when every
+                        // column exceeds D, else the bitmap decides
+                        bool above = D == 0u;
+                        if (!above && DP <= 8) {
+                            above = true;
+#pragma unroll
+                            for (int k = 0; k < DP; ++k)
+                                if (k < d) above &= ((ks[h][e] >> (log2g * k)) & cmask) > D;
+                        }
+                        if (!above) need[h] |= 1u << e;
+                    } else {
+                        keep[h] |= 1u << e;
+                    }
                 }
             }
         }
@@ -1238,12 +1330,31 @@ int map_blocks_bound(int64_t n)
 }
 
 template <int DP, int MODE>
-static void map_tma(const Plan& p, int blocks, size_t smem, int smem_max, int64_t pw, cudaStream_t s)
+static void map_tma(const Plan& p, int& blocks, size_t smem, int smem_max, int64_t pw, cudaStream_t s)
 {
+    // look before marking from the start when the rows outnumber the cells
+    // four to one: most marks then find their bit set already
+    const bool look = p.n >= 4 * (int64_t(1) << (p.log2g * p.d));
     cudaFuncSetAttribute(k_map_mark_tma<DP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    // one wave: as many blocks as fit on the SMs at once (a partial second
+    // wave would run its blocks at a fraction of the occupancy)
+    // (asked once per kernel instance and shared-memory size)
+    static thread_local size_t cached_smem = ~size_t(0);
+    static thread_local int cached_per_sm = 0;
+    if (cached_smem != smem) {
+        cached_per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_per_sm, k_map_mark_tma<DP, MODE>, kThreads, smem) !=
+                cudaSuccess || cached_per_sm < 1) {
+            cudaGetLastError();
+            cached_per_sm = 1;
+        }
+        cached_smem = smem;
+    }
+    const int per_sm = cached_per_sm;
+    blocks = std::min(blocks, per_sm * num_sms());
     k_map_mark_tma<DP, MODE><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.log2g, p.morton_bits, p.params,
                                                             p.ckey, p.mkey, p.occ, &p.res->err,
-                                                            MODE == kMarkSmall ? p.occ_stage : nullptr, pw);
+                                                            MODE == kMarkSmall ? p.occ_stage : nullptr, pw, look);
 }
 
 template <int DP, int MODE>
@@ -1262,13 +1373,14 @@ cudaError_t launch_map_pass(const Plan& p, bool mark, cudaStream_t s)
     const int mode = !mark ? kMarkNone : (p.occ_stage != nullptr ? kMarkSmall : kMarkCheck);
     const int64_t pw = mode == kMarkSmall ? p.words : 0;
     int blocks = 0;
-    if (p.tma_ok && p.n >= kThreads) {
+    const int rpt = map_rpt(pad4(p.d));
+    if (p.tma_ok && p.n >= (int64_t)kThreads * rpt) {
         const size_t tail = mode == kMarkSmall ? (size_t)pw * sizeof(uint32_t) : 0;
-        const size_t smem = (size_t)kMapStages * kThreads * p.d * sizeof(float) + tail;
+        const size_t smem = (size_t)kMapStages * kThreads * rpt * p.d * sizeof(float) + tail;
         const int smem_max = kMapStages * kThreads * 16 * (int)sizeof(float) +
                              (int)kPrivWords * (int)sizeof(uint32_t);
-        const int64_t nchunks = p.n / kThreads;
-        blocks = grid_for(nchunks, 1, std::min(num_sms() * 4, kMapMaxBlocks));
+        const int64_t nchunks = p.n / ((int64_t)kThreads * rpt);
+        blocks = grid_for(nchunks, 1, kMapMaxBlocks);   // capped at one wave by map_tma
         SKY_DISPATCH_DP(p.d, {
             if (mode == kMarkSmall) map_tma<DP, kMarkSmall>(p, blocks, smem, smem_max, pw, s);
             else if (mode == kMarkNone) map_tma<DP, kMarkNone>(p, blocks, smem, smem_max, pw, s);

@@ -312,6 +312,7 @@ sky_status sky_skyline_chunked(const float* pts, int32_t host_pts, int64_t n, in
     for (int64_t c = 0; c < nchunks; ++c) {
         Plan q;
         if ((e = chunk(c, q)) != cudaSuccess) return cfail(SKY_ERR_CUDA, "chunk copy", e);
+        q.ckey = q.mkey = nullptr;   // this pass only marks: no keys are written
         if ((e = launch_map_pass(q, true, s)) != cudaSuccess) return cfail(SKY_ERR_CUDA, "map pass", e);
         chunk_done(c);
     }
