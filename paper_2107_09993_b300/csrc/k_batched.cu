@@ -273,6 +273,23 @@ __global__ void __launch_bounds__(kTQ) kb_gather(const QueryPlan* __restrict__ q
         for (int w = 1; w < kTQ / 32; ++w) c = __vminu4(c, s_sub[w][tid]);
         q.sub[((int64_t)t * kSubSlots + kTQ / 32) * dw + tid] = c;
     }
+    // the last q-tile whose first Morton key is <= this tile's last key (a
+    // dominator never sorts after its victim); warp 0, ties in rounds of 32
+    if (warp == 0) {
+        const uint32_t* skeys = (q.passes & 1) ? q.key2 : q.surv_key;
+        const uint32_t T = (m + kTQ - 1) / kTQ;
+        const uint32_t last = skeys[min((int64_t)m, ((int64_t)t + 1) * kTQ) - 1];
+        uint32_t e = t;
+        while (true) {
+            const uint32_t tn = e + 1 + lane;
+            const bool tie = tn < T && skeys[(int64_t)tn * kTQ] <= last;
+            const uint32_t run = __ballot_sync(kFull, !tie);
+            const uint32_t k = run ? (uint32_t)(__ffs(run) - 1) : 32u;
+            e += k;
+            if (k < 32u) break;
+        }
+        if (lane == 0) q.tend[t] = e;
+    }
 }
 
 // -------------------------------------------------------------------- (d)
@@ -293,7 +310,7 @@ __global__ void __launch_bounds__(kTQ + 32) kb_refine(const QueryPlan* __restric
         const QueryPlan& q = qps[w.x];
         const uint32_t m = q.res->survivors;
         if ((uint32_t)w.y < (m + kTQ - 1) / kTQ)
-            refine::refine_ptile<DP>(sm, q.X, q.C, q.ids, q.sub, nullptr, nullptr, m, (uint32_t)w.y, q.res, q.keep);
+            refine::refine_ptile<DP>(sm, q.X, q.C, q.ids, q.sub, q.tend, nullptr, m, (uint32_t)w.y, q.res, q.keep);
     }
 }
 

@@ -108,6 +108,7 @@ struct QueryPlan {
     uint32_t* C;
     int32_t* ids;
     uint32_t* sub;
+    uint32_t* tend;           // [tiles] last q-tile whose first Morton key <= the tile's last key
     uint8_t* keep;
     int32_t* stage;
     DevResult* res;
