@@ -192,6 +192,56 @@ SKY_API sky_status sky_skyline_host(const float* h_pts, int64_t n, int32_t d, in
                             int64_t* h_out_count, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Many independent point sets in one call (a project addition: the paper    */
+/* computes one skyline at a time). Each set is steps (a)-(d) exactly as     */
+/* sky_skyline computes it; the sets run concurrently on up to four          */
+/* library-internal streams, so that one set's small phases overlap another  */
+/* set's large ones.                                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct sky_set {
+    const float* pts;             /* in: n*ld floats, row-major (device or host, per entry point) */
+    int64_t n;                    /* in: rows, [0, 2^31)                        */
+    int32_t d;                    /* in: attributes, [1, 16]                    */
+    int32_t reserved0;
+    int64_t ld;                   /* in: row stride in floats, >= d             */
+    int32_t* out_idx;             /* in: buffer of `capacity` ints (device or host) */
+    int64_t capacity;             /* in: entries of out_idx                     */
+    int64_t count;                /* out: skyline size (the size needed when status is
+                                   * SKY_ERR_CAPACITY); -1 when the set did not complete */
+    int32_t status;               /* out: sky_status of this set                */
+    int32_t reserved1;
+} sky_set;
+
+/*
+ * Device-resident sets: for every sets[i], the ascending row ids of its
+ * skyline go to sets[i].out_idx and the size to sets[i].count, as sky_skyline
+ * would write them. `opt` applies to every set; proposals (n_filter > 0)
+ * belong to one set and are rejected here. Arguments of every set are checked
+ * before any work starts (SKY_ERR_INVALID_ARGUMENT / SKY_ERR_TOO_LARGE name
+ * the set in sky_last_error()). A run-time failure of one set (capacity,
+ * non-finite input, timeout) is recorded in its status and does not stop the
+ * others. Returns SKY_OK when every set succeeded, else the status of the
+ * first failing set (in index order), described by sky_last_error(). Work
+ * starts after the work already queued on `stream`; the call returns when
+ * every set has completed. sky_last_run_stats() then reports the sums over
+ * the sets (d and log2_g of the last set); sky_last_phase_times() is not
+ * updated. Workspaces and graphs are cached per set as for sky_skyline.
+ */
+SKY_API sky_status sky_skyline_sets(sky_set* sets, int32_t count, const sky_options* opt, void* stream);
+
+/*
+ * Host-resident sets: pts and out_idx are host memory (page-locked memory
+ * makes the copies asynchronous). The inputs are copied to per-slot device
+ * buffers in set order on one copy stream, so the copy of set i+1 overlaps
+ * the kernels of set i; the ids of a set are copied back as soon as its count
+ * is known (at most `capacity` of them; SKY_ERR_CAPACITY with count = the
+ * size needed when they do not fit). Same checks, statuses and return value
+ * as sky_skyline_sets. The staging buffers grow to the largest set seen and
+ * are kept for later calls on the same thread.
+ */
+SKY_API sky_status sky_skyline_host_sets(sky_set* sets, int32_t count, const sky_options* opt, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Batched skylines (a project addition; the paper has no batched form).     */
 /* Many skyline queries over row ranges and attribute subsets of one table   */
 /* run as one CUDA-graph launch: every phase of steps (a)-(d) is one kernel  */

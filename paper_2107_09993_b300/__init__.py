@@ -9,7 +9,8 @@ library or a CUDA device is missing, every call raises.
     idx = sky.skyline(points_cuda_f32)          # ascending int32 row ids
 
 Names follow the C ABI: ``skyline`` (sky_skyline), ``skyline_host``
-(sky_skyline_host), ``Grid`` (sky_build_grid / sky_prune_cells /
+(sky_skyline_host), ``skyline_sets`` / ``skyline_host_sets``
+(sky_skyline_sets / sky_skyline_host_sets), ``Grid`` (sky_build_grid / sky_prune_cells /
 sky_grid_stats / sky_grid_copy_out / sky_grid_destroy).
 """
 from __future__ import annotations
@@ -60,6 +61,12 @@ class PhaseTimes(ctypes.Structure):
                                                "sort_ms", "gather_ms", "refine_ms", "emit_ms", "call_ms")]
 
 
+class SkySet(ctypes.Structure):
+    """struct sky_set: one point set of sky_skyline_sets / sky_skyline_host_sets."""
+    _fields_ = [("pts", _vp), ("n", _i64), ("d", _i32), ("reserved0", _i32), ("ld", _i64),
+                ("out_idx", _vp), ("capacity", _i64), ("count", _i64), ("status", _i32), ("reserved1", _i32)]
+
+
 _lib = None
 
 
@@ -75,6 +82,8 @@ def load():
     sig = {
         "sky_skyline": ([_vp, _i64, _i32, _i64, P(Options), _vp, _i64, P(_i64), _vp], _i32),
         "sky_skyline_host": ([_vp, _i64, _i32, _i64, P(Options), _vp, _i64, P(_i64), _vp], _i32),
+        "sky_skyline_sets": ([P(SkySet), _i32, P(Options), _vp], _i32),
+        "sky_skyline_host_sets": ([P(SkySet), _i32, P(Options), _vp], _i32),
         "sky_skyline_chunked": ([_vp, _i32, _i64, _i32, _i64, P(Options), _i64, _i64, _vp, _i64, P(_i64), _vp],
                                 _i32),
         "sky_build_grid": ([_vp, _i64, _i32, _i64, P(Options), _vp, P(_vp)], _i32),
@@ -138,9 +147,9 @@ def _points(points, dev=True):
         raise ValueError("points must be a 2-D float32 tensor")
     if dev and not points.is_cuda:
         raise ValueError("points must live on a CUDA device")
-    if points.stride(1) != 1:
-        raise ValueError("points must have unit column stride")
     n, d = points.shape
+    if n > 0 and d > 1 and points.stride(1) != 1:
+        raise ValueError("points must have unit column stride")
     ld = points.stride(0) if n > 1 else d
     return points, n, d, ld
 
@@ -181,6 +190,54 @@ def skyline_host(points, log2_g=None, assume_unit=False, capacity=None, stream=N
                               ctypes.byref(cnt), _stream_ptr(stream))
     _check(st)
     return out[:cnt.value]
+
+
+def _run_sets(fn, sets_pts, outs, capacity, o, stream, dev):
+    torch = _torch()
+    arr = (SkySet * max(1, len(sets_pts)))()
+    keep = []
+    for i, pts in enumerate(sets_pts):
+        pts, n, d, ld = _points(pts, dev=dev)
+        cap = n if capacity is None else int(capacity)
+        out = outs[i] if outs is not None else None
+        if out is None:
+            out = (torch.empty(max(cap, 1), dtype=torch.int32, device=pts.device) if dev else
+                   torch.empty(max(cap, 1), dtype=torch.int32, pin_memory=pts.is_pinned()))
+        assert out.dtype == torch.int32 and out.is_contiguous() and out.numel() >= cap
+        arr[i].pts, arr[i].n, arr[i].d, arr[i].ld = pts.data_ptr(), n, d, ld
+        arr[i].out_idx, arr[i].capacity = out.data_ptr(), cap
+        keep.append((pts, out))
+    st = fn(arr, len(sets_pts), ctypes.byref(o), stream)
+    if st == 3:
+        raise SkyError(st, load().sky_last_error().decode())
+    _check(st)
+    return [out[:arr[i].count] for i, (_, out) in enumerate(keep)]
+
+
+def skyline_sets(sets, log2_g=None, assume_unit=False, capacity=None, survivors_only=False, stream=None,
+                 outs=None):
+    """sky_skyline_sets: the skylines of several device-resident point sets
+    (a list of float32 [n_i, d_i] CUDA tensors), run concurrently. Returns a
+    list of ascending int32 row-id tensors (cuda), one per set."""
+    torch = _torch()
+    lib = load()
+    o = _opts(log2_g, assume_unit, None, survivors_only)
+    if not sets:
+        return []
+    with torch.cuda.device(sets[0].device):
+        return _run_sets(lib.sky_skyline_sets, sets, outs, capacity, o, _stream_ptr(stream), True)
+
+
+def skyline_host_sets(sets, log2_g=None, assume_unit=False, capacity=None, survivors_only=False, stream=None,
+                      outs=None):
+    """sky_skyline_host_sets: the same from host (ideally pinned) CPU tensors;
+    the copy of one set's points overlaps the kernels of the previous set.
+    Returns a list of CPU int32 row-id tensors."""
+    lib = load()
+    o = _opts(log2_g, assume_unit, None, survivors_only)
+    if not sets:
+        return []
+    return _run_sets(lib.sky_skyline_host_sets, sets, outs, capacity, o, _stream_ptr(stream), False)
 
 
 def skyline_chunked(points, log2_g=None, assume_unit=False, survivors_only=False, chunk_rows=0,

@@ -30,7 +30,7 @@ struct PhaseClock {
     cudaStream_t s;
     bool on;
     int next = 0;
-    explicit PhaseClock(cudaStream_t st) : s(st), on(t_timing == 1)
+    explicit PhaseClock(cudaStream_t st, bool allow = true) : s(st), on(allow && t_timing == 1)
     {
         if (!on) return;
         for (auto& e : t_ev)
@@ -356,40 +356,42 @@ CacheEntry* cache_lookup(const CacheKey& k, size_t bytes, cudaStream_t s, sky_st
     return lru;
 }
 
-// Whole path on device-resident points. The work runs on a library-internal
-// stream that first waits for the caller's stream; the call returns after it
-// completes, so the caller sees the usual stream order.
-sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, const sky_options* opt,
-                          int32_t* out, int64_t capacity, int64_t* count, cudaStream_t user_s)
-{
+// One call between its enqueue and the read of its result block.
+struct Inflight {
     Plan p;
+    int64_t capacity = 0;
+    int n_prop = 0;
+    DevResult* h = nullptr;   // page-locked copy of the result block (NULL: `local`)
+    DevResult local{};
+    bool span = false;
+    bool empty = false;       // n == 0: nothing enqueued
+};
+
+// Enqueues steps (a)-(d) of one point set on `s` and the copy of its result
+// block to the host; returns without waiting. From the second repeat of the
+// same arguments the kernel sequence is one CUDA-graph replay.
+sky_status skyline_enqueue(const float* pts, int64_t n, int32_t d, int64_t ld, const sky_options* opt,
+                           int32_t* out, int64_t capacity, cudaStream_t s, DevResult* hres, int timing,
+                           PhaseClock& clk, Inflight& f)
+{
+    Plan& p = f.p;
     sky_status st = make_plan(p, pts, n, d, ld, opt);
     if (st != SKY_OK) return st;
-    t_stats = {};
-    t_stats.n = n;
-    t_stats.d = d;
-    t_stats.log2_g = p.log2g;
+    f.capacity = capacity;
+    f.h = hres;
     if (n == 0) {
-        *count = 0;
+        f.empty = true;
         return SKY_OK;
     }
     enable_pool_cache();
     int dev = 0;
     SKY_CUDA(cudaGetDevice(&dev));
-    if (!t_stream || t_stream_dev != dev) {
-        SKY_CUDA(cudaStreamCreateWithFlags(&t_stream, cudaStreamNonBlocking));
-        SKY_CUDA(cudaEventCreateWithFlags(&t_join, cudaEventDisableTiming));
-        t_stream_dev = dev;
-    }
-    cudaStream_t s = t_stream;
-    SKY_CUDA(cudaEventRecord(t_join, user_s));
-    SKY_CUDA(cudaStreamWaitEvent(s, t_join, 0));
-
     const int n_prop = opt ? opt->n_filter : 0;
     const float* prop = n_prop ? opt->d_filter_pts : nullptr;
+    f.n_prop = n_prop;
     CacheKey key;
     key.dev = dev; key.pts = pts; key.n = n; key.ld = ld; key.cap = capacity; key.d = d;
-    key.log2g = p.log2g; key.mode = p.map_mode; key.n_prop = n_prop; key.timing = t_timing == 1 ? 1 : 0;
+    key.log2g = p.log2g; key.mode = p.map_mode; key.n_prop = n_prop; key.timing = timing == 1 ? 1 : 0;
     key.surv_only = p.survivors_only ? 1 : 0;
     key.prop = prop; key.out = out;
     const size_t bytes = layout(p, nullptr, false);
@@ -398,16 +400,15 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
     layout(p, static_cast<char*>(ce->ws), false);
     ++ce->calls;
 
-    PhaseClock clk(s);
     cudaError_t e = cudaSuccess;
     // graphs only when no phase events are requested (the events time the
     // direct launches)
-    if (ce->calls >= 2 && !ce->exec && t_timing != 1) {
+    if (ce->calls >= 2 && !ce->exec && timing != 1) {
         // second call with these arguments: capture the sequence once
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            PhaseClock cap_clk(s);
+            PhaseClock cap_clk(s, false);
             const cudaError_t e1 = enqueue_pipeline(p, prop, n_prop, out, capacity, s, cap_clk);
             const cudaError_t e2 = cudaStreamEndCapture(s, &g);
             if (e1 == cudaSuccess && e2 == cudaSuccess && g) {
@@ -421,55 +422,278 @@ sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, co
     // whole-call timing: a short device-side delay first, so that the host
     // has enqueued the start event and the kernel sequence before the device
     // reaches them; the two events then bracket device work only
-    const bool span = t_timing == 2 && span_events();
-    if (span) {
+    f.span = timing == 2 && span_events();
+    if (f.span) {
         k_delay<<<1, 32, 0, s>>>(kSpanDelayNs);
         cudaEventRecord(t_span[0], s);
     }
-    if (ce->exec && t_timing != 1) {
+    if (ce->exec && timing != 1) {
         e = cudaGraphLaunch(ce->exec, s);
     } else {
         e = enqueue_pipeline(p, prop, n_prop, out, capacity, s, clk);
     }
-    if (span) cudaEventRecord(t_span[1], s);
-    if (e != cudaSuccess) st = cuda_fail(e, "kernel launch");
-    t_stats.kernels = count_kernels(p, n_prop, capacity);
-    DevResult* h = host_result();
-    DevResult local{};
-    if (st == SKY_OK) {
-        e = cudaMemcpyAsync(h ? h : &local, p.res, sizeof(DevResult), cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) st = cuda_fail(e, "result copy");
+    if (f.span) cudaEventRecord(t_span[1], s);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    e = cudaMemcpyAsync(f.h ? f.h : &f.local, p.res, sizeof(DevResult), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "result copy");
+    return SKY_OK;
+}
+
+// Reads the result block of an enqueued call whose stream has completed.
+sky_status skyline_finish(Inflight& f, int64_t* count, sky_run_stats& rs)
+{
+    rs = {};
+    rs.n = f.p.n;
+    rs.d = f.p.d;
+    rs.log2_g = f.p.log2g;
+    if (f.empty) {
+        *count = 0;
+        return SKY_OK;
     }
-    e = cudaStreamSynchronize(s);
-    if (st != SKY_OK) return st;
-    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
-    const DevResult r = h ? *h : local;
-    clk.collect();
-    if (span) {
+    rs.kernels = count_kernels(f.p, f.n_prop, f.capacity);
+    const DevResult r = f.h ? *f.h : f.local;
+    if (f.span) {
         float ms = 0.0f;
         t_phase = {};
         if (cudaEventElapsedTime(&ms, t_span[0], t_span[1]) == cudaSuccess) t_phase.call_ms = ms;
         cudaGetLastError();
     }
-    t_stats.survivors = r.survivors;
-    t_stats.skyline = r.count;
-    t_stats.pairs = (int64_t)r.pairs;
-    t_stats.n_filter_used = (int32_t)r.n_filter_used;
-    t_stats.tiles = (int64_t)r.tiles;
-    t_stats.group_scans = (int64_t)r.groups;
-    t_stats.code_hits = (int64_t)r.hits;
-    t_stats.exact_tests = (int64_t)r.exact;
-    st = status_from_flags(r.err);
+    rs.survivors = r.survivors;
+    rs.skyline = r.count;
+    rs.pairs = (int64_t)r.pairs;
+    rs.n_filter_used = (int32_t)r.n_filter_used;
+    rs.tiles = (int64_t)r.tiles;
+    rs.group_scans = (int64_t)r.groups;
+    rs.code_hits = (int64_t)r.hits;
+    rs.exact_tests = (int64_t)r.exact;
+    const sky_status st = status_from_flags(r.err);
     if (st != SKY_OK) return st;
-    if (p.survivors_only && capacity >= n) {   // ids written by the survivor pass itself
-        t_stats.skyline = r.survivors;
+    if (f.p.survivors_only && f.capacity >= f.p.n) {   // ids written by the survivor pass itself
+        rs.skyline = r.survivors;
         *count = r.survivors;
         return SKY_OK;
     }
     *count = r.count;
-    if ((int64_t)r.count > capacity)
-        return fail(SKY_ERR_CAPACITY, "skyline has %u points, capacity %lld", r.count, (long long)capacity);
+    if ((int64_t)r.count > f.capacity)
+        return fail(SKY_ERR_CAPACITY, "skyline has %u points, capacity %lld", r.count, (long long)f.capacity);
     return SKY_OK;
+}
+
+// The library-internal stream of this thread, ordered after `user_s`.
+sky_status internal_stream(cudaStream_t user_s, cudaStream_t* s)
+{
+    int dev = 0;
+    SKY_CUDA(cudaGetDevice(&dev));
+    if (!t_stream || t_stream_dev != dev) {
+        SKY_CUDA(cudaStreamCreateWithFlags(&t_stream, cudaStreamNonBlocking));
+        SKY_CUDA(cudaEventCreateWithFlags(&t_join, cudaEventDisableTiming));
+        t_stream_dev = dev;
+    }
+    SKY_CUDA(cudaEventRecord(t_join, user_s));
+    SKY_CUDA(cudaStreamWaitEvent(t_stream, t_join, 0));
+    *s = t_stream;
+    return SKY_OK;
+}
+
+// Whole path on device-resident points. The work runs on a library-internal
+// stream that first waits for the caller's stream; the call returns after it
+// completes, so the caller sees the usual stream order.
+sky_status skyline_device(const float* pts, int64_t n, int32_t d, int64_t ld, const sky_options* opt,
+                          int32_t* out, int64_t capacity, int64_t* count, cudaStream_t user_s)
+{
+    t_stats = {};
+    cudaStream_t s = nullptr;
+    sky_status st = internal_stream(user_s, &s);
+    if (st != SKY_OK) return st;
+    Inflight f;
+    PhaseClock clk(s);
+    st = skyline_enqueue(pts, n, d, ld, opt, out, capacity, s, host_result(), t_timing, clk, f);
+    const cudaError_t e = f.empty ? cudaSuccess : cudaStreamSynchronize(s);
+    if (st != SKY_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    clk.collect();
+    return skyline_finish(f, count, t_stats);
+}
+
+// ---------------------------------------------------------------- many sets
+// Sets of one sky_skyline_sets / sky_skyline_host_sets call run on up to
+// kSetSlots internal streams at once; set i takes slot i % kSetSlots, after
+// set i - kSetSlots has completed there.
+constexpr int kSetSlots = 4;
+
+struct SetSlots {
+    int dev = -1;
+    cudaStream_t s[kSetSlots] = {};
+    cudaStream_t h2d = nullptr;              // host sets: the input copies, in set order
+    cudaEvent_t join = nullptr;
+    cudaEvent_t copied[kSetSlots] = {};
+    DevResult* res = nullptr;                // page-locked [kSetSlots]
+    float* in[kSetSlots] = {};               // host sets: device staging (grow-only)
+    int32_t* out[kSetSlots] = {};
+    size_t in_cap[kSetSlots] = {}, out_cap[kSetSlots] = {};
+};
+thread_local SetSlots t_slots;
+
+sky_status set_slots(cudaStream_t user_s, bool host)
+{
+    SetSlots& S = t_slots;
+    int dev = 0;
+    SKY_CUDA(cudaGetDevice(&dev));
+    if (S.dev != dev) {
+        S = SetSlots{};   // streams of another device are abandoned, not reused
+        for (int i = 0; i < kSetSlots; ++i) {
+            SKY_CUDA(cudaStreamCreateWithFlags(&S.s[i], cudaStreamNonBlocking));
+            SKY_CUDA(cudaEventCreateWithFlags(&S.copied[i], cudaEventDisableTiming));
+        }
+        SKY_CUDA(cudaStreamCreateWithFlags(&S.h2d, cudaStreamNonBlocking));
+        SKY_CUDA(cudaEventCreateWithFlags(&S.join, cudaEventDisableTiming));
+        SKY_CUDA(cudaMallocHost(&S.res, sizeof(DevResult) * kSetSlots));
+        S.dev = dev;
+    }
+    SKY_CUDA(cudaEventRecord(S.join, user_s));
+    for (int i = 0; i < kSetSlots; ++i) SKY_CUDA(cudaStreamWaitEvent(S.s[i], S.join, 0));
+    if (host) SKY_CUDA(cudaStreamWaitEvent(S.h2d, S.join, 0));
+    return SKY_OK;
+}
+
+sky_status grow(void** p, size_t* cap, size_t bytes)
+{
+    if (bytes <= *cap) return SKY_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    SKY_CUDA(cudaMalloc(p, align256(bytes)));
+    *cap = align256(bytes);
+    return SKY_OK;
+}
+
+sky_status check_sets(const sky_set* sets, int32_t count, const sky_options* opt)
+{
+    if (count < 0 || (count > 0 && !sets)) return fail(SKY_ERR_INVALID_ARGUMENT, "bad set array");
+    if (opt && opt->n_filter != 0)
+        return fail(SKY_ERR_INVALID_ARGUMENT, "proposals (n_filter) belong to one set; not accepted here");
+    for (int32_t i = 0; i < count; ++i) {
+        const sky_set& q = sets[i];
+        if (q.capacity < 0 || (q.capacity > 0 && !q.out_idx))
+            return fail(SKY_ERR_INVALID_ARGUMENT, "set %d: bad output buffer", i);
+        const sky_status st = check_points(q.pts, q.n, q.d, q.ld);
+        if (st != SKY_OK) return fail(st, "set %d: %s", i, t_err.c_str());
+        Plan p;
+        const sky_status sp = make_plan(p, q.pts, q.n, q.d, q.ld, opt);
+        if (sp != SKY_OK) return fail(sp, "set %d: %s", i, t_err.c_str());
+    }
+    return SKY_OK;
+}
+
+// Device or host sets. For host sets every input goes to a per-slot device
+// staging buffer by one copy on the copy stream (in set order, so the copy
+// of set i+1 overlaps the kernels of set i), and the ids come back by one
+// copy of `count` entries once the set's count is known.
+sky_status run_sets(sky_set* sets, int32_t count, const sky_options* opt, cudaStream_t user_s, bool host)
+{
+    t_stats = {};
+    sky_status st = check_sets(sets, count, opt);
+    if (st != SKY_OK) return st;
+    for (int32_t i = 0; i < count; ++i) {
+        sets[i].count = -1;
+        sets[i].status = SKY_OK;
+    }
+    if (count == 0) return SKY_OK;
+    st = set_slots(user_s, host);
+    if (st != SKY_OK) return st;
+    SetSlots& S = t_slots;
+    Inflight fl[kSetSlots];
+    int32_t at[kSetSlots];   // set held by each slot, -1: none
+    for (int k = 0; k < kSetSlots; ++k) at[k] = -1;
+    sky_status first = SKY_OK;
+    std::string first_err;
+    auto note = [&](int32_t i, sky_status s) {
+        sets[i].status = s;
+        if (s != SKY_OK && first == SKY_OK) {
+            first = s;
+            first_err = "set " + std::to_string(i) + ": " + t_err;
+        }
+    };
+    // completes the set that holds slot k (its stream is synchronised)
+    auto complete = [&](int k) {
+        const int32_t i = at[k];
+        if (i < 0) return;
+        at[k] = -1;
+        const cudaError_t e = cudaStreamSynchronize(S.s[k]);
+        if (sets[i].status != SKY_OK) return;   // failed while enqueueing
+        if (e != cudaSuccess) { note(i, cuda_fail(e, "stream synchronize")); return; }
+        int64_t cnt = -1;   // stays -1 when the set fails before its count is known
+        sky_run_stats rs;
+        const sky_status fs = skyline_finish(fl[k], &cnt, rs);
+        sets[i].count = cnt;
+        t_stats.n += rs.n;
+        t_stats.d = rs.d;
+        t_stats.log2_g = rs.log2_g;
+        t_stats.survivors += rs.survivors;
+        t_stats.skyline += rs.skyline;
+        t_stats.pairs += rs.pairs;
+        t_stats.n_filter_used += rs.n_filter_used;
+        t_stats.kernels += rs.kernels;
+        t_stats.tiles += rs.tiles;
+        t_stats.group_scans += rs.group_scans;
+        t_stats.code_hits += rs.code_hits;
+        t_stats.exact_tests += rs.exact_tests;
+        if (fs != SKY_OK || !host) { note(i, fs); return; }
+        // host set: the staging buffer holds all cnt ids; the caller's
+        // buffer receives at most its capacity
+        const int64_t ncopy = std::min(cnt, sets[i].capacity);
+        if (ncopy > 0) {
+            const cudaError_t ec = cudaMemcpyAsync(sets[i].out_idx, S.out[k], sizeof(int32_t) * (size_t)ncopy,
+                                                   cudaMemcpyDeviceToHost, S.s[k]);
+            if (ec != cudaSuccess) { note(i, cuda_fail(ec, "device-to-host copy")); return; }
+        }
+        if (cnt > sets[i].capacity) {
+            note(i, fail(SKY_ERR_CAPACITY, "skyline has %lld points, capacity %lld", (long long)cnt,
+                         (long long)sets[i].capacity));
+            return;
+        }
+        note(i, SKY_OK);
+    };
+    for (int32_t i = 0; i < count; ++i) {
+        const int k = i % kSetSlots;
+        complete(k);   // set i - kSetSlots
+        sky_set& q = sets[i];
+        fl[k] = Inflight{};
+        at[k] = i;
+        const float* pts = q.pts;
+        int32_t* out = q.out_idx;
+        int64_t cap = q.capacity;
+        if (host && q.n > 0) {
+            // the device buffers hold all n ids, so the count is always known
+            const size_t in_bytes = (size_t)((q.n - 1) * q.ld + q.d) * sizeof(float);
+            sky_status gs = grow(reinterpret_cast<void**>(&S.in[k]), &S.in_cap[k], in_bytes);
+            if (gs == SKY_OK)
+                gs = grow(reinterpret_cast<void**>(&S.out[k]), &S.out_cap[k], sizeof(int32_t) * (size_t)q.n);
+            if (gs != SKY_OK) { note(i, gs); continue; }
+            cudaError_t e = cudaMemcpyAsync(S.in[k], q.pts, in_bytes, cudaMemcpyHostToDevice, S.h2d);
+            if (e == cudaSuccess) e = cudaEventRecord(S.copied[k], S.h2d);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(S.s[k], S.copied[k], 0);
+            if (e != cudaSuccess) { note(i, cuda_fail(e, "host-to-device copy")); continue; }
+            pts = S.in[k];
+            out = S.out[k];
+            cap = q.n;
+        }
+        PhaseClock clk(S.s[k], false);   // sets take no phase times
+        const sky_status es =
+            skyline_enqueue(pts, q.n, q.d, q.ld, opt, out, cap, S.s[k], S.res + k, 0, clk, fl[k]);
+        if (es != SKY_OK) note(i, es);
+    }
+    for (int32_t j = 0; j < kSetSlots; ++j) complete((count + j) % kSetSlots);
+    // drain every slot (host sets: the copies of the ids)
+    for (int k = 0; k < kSetSlots; ++k) {
+        const cudaError_t e = cudaStreamSynchronize(S.s[k]);
+        if (e != cudaSuccess && first == SKY_OK) {
+            first = cuda_fail(e, "stream synchronize");
+            first_err = t_err;
+        }
+    }
+    if (first != SKY_OK) t_err = first_err;
+    return first;
 }
 
 }  // namespace
@@ -659,6 +883,16 @@ sky_status sky_skyline(const float* d_pts, int64_t n, int32_t d, int64_t ld, con
     if (st != SKY_OK) return st;
     return skyline_device(d_pts, n, d, ld, opt, d_out_idx, out_capacity, h_out_count,
                           static_cast<cudaStream_t>(stream));
+}
+
+sky_status sky_skyline_sets(sky_set* sets, int32_t count, const sky_options* opt, void* stream)
+{
+    return run_sets(sets, count, opt, static_cast<cudaStream_t>(stream), false);
+}
+
+sky_status sky_skyline_host_sets(sky_set* sets, int32_t count, const sky_options* opt, void* stream)
+{
+    return run_sets(sets, count, opt, static_cast<cudaStream_t>(stream), true);
 }
 
 sky_status sky_skyline_host(const float* h_pts, int64_t n, int32_t d, int64_t ld, const sky_options* opt,
