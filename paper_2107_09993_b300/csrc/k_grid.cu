@@ -145,16 +145,20 @@ __global__ void k_params(const uint32_t* mm_min, const uint32_t* mm_max, int d, 
 // Clears the call's result block and the occupancy bitmap in one launch (two
 // memset nodes in a CUDA graph cost several microseconds of scheduling each).
 // Both start 256-byte aligned; the bitmap is cleared in 16-byte stores.
-__global__ void __launch_bounds__(kThreads) k_clear(DevResult* res, uint32_t* occ, int64_t words)
+// Zeroes the result block and the bitmap; thread tid of nthr.
+__device__ __forceinline__ void clear_res_occ(DevResult* res, uint32_t* occ, int64_t words, int64_t tid, int64_t nthr)
 {
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     constexpr int kResWords = (int)(sizeof(DevResult) / sizeof(uint32_t));
     if (tid < kResWords) reinterpret_cast<uint32_t*>(res)[tid] = 0u;
     const int64_t q = words / 4;
     uint4* o4 = reinterpret_cast<uint4*>(occ);
     for (int64_t i = tid; i < q; i += nthr) o4[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int64_t i = q * 4 + tid; i < words; i += nthr) occ[i] = 0u;
+}
+
+__global__ void __launch_bounds__(kThreads) k_clear(DevResult* res, uint32_t* occ, int64_t words)
+{
+    clear_res_occ(res, occ, words, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 // Automatic map, decided on the strided sample of rows 0, t, 2t, ... < n
@@ -177,7 +181,8 @@ constexpr int kDecideThreads = kDecideSample / kDecideCluster;   // 512
 template <int DP>
 __global__ void __cluster_dims__(kDecideCluster, 1, 1) __launch_bounds__(kDecideThreads)
     k_sample_params(const float* __restrict__ pts, int64_t n, int d, int64_t ld, bool vec4, int log2g, int mbits,
-                    uint32_t* mm_min, uint32_t* mm_max, float* params)
+                    uint32_t* mm_min, uint32_t* mm_max, float* params, DevResult* res, uint32_t* occ,
+                    int64_t clear_words)
 {
     __shared__ float s_mn[kDecideThreads / 32][DP], s_mx[kDecideThreads / 32][DP];
     __shared__ float c_mn[DP], c_mx[DP];   // this CTA's slice; read by CTA 0 of the cluster
@@ -211,6 +216,8 @@ __global__ void __cluster_dims__(kDecideCluster, 1, 1) __launch_bounds__(kDecide
         if (lane == 0) { s_mn[warp][k] = mn[k]; s_mx[warp][k] = mx[k]; }
     }
     if (tid == 0) s_bad = 0;
+    // the cleared result block and bitmap, when this launch replaces k_clear
+    if (res) clear_res_occ(res, occ, clear_words, r, (int64_t)kDecideSample);
     __syncthreads();
     if (tid < DP) {
         float lo = NAN, hi = NAN;
@@ -933,22 +940,22 @@ __global__ void k_snap_finalize(const float* __restrict__ pts, int d, int64_t ld
 // contiguous tiles [b * tpb, (b + 1) * tpb) of kSurvTile rows. Row
 // tile * kSurvTile + j * kThreads + tid is item j of thread tid, so the warp
 // ballot of item j is exactly flag word row / 32.
-//   k_surv_flags    streams the cell keys of its tiles through a ring of
-//                   shared-memory stages (1-D bulk copies), probes the
-//                   prefix-OR bitmap at key - (1, ..., 1) (Corollary 4: a cell
-//                   is dominated iff that cell is covered), applies the
-//                   optional snapped proposals, writes the flag words and the
-//                   block's survivor count
+//   k_surv_flags    reads the cell keys of its tiles (16-byte streaming
+//                   loads, the next tile's in flight while a tile is
+//                   decided), probes the prefix-OR bitmap at key - (1, ..., 1)
+//                   (Corollary 4: a cell is dominated iff that cell is
+//                   covered), applies the optional snapped proposals, writes
+//                   the flag words and the block's survivor count
 //   k_surv_scatter  sums the counts of the blocks before it, counts the
 //                   survivors of each of its tiles from the flag words and
-//                   scans them (every tile's output offset is known before
-//                   its keys arrive), then streams the Morton keys of the
-//                   tiles that keep a row through the same kind of ring and
-//                   writes (Morton key, row) pairs, coalesced per warp
-// No look-back chain and no global atomics.
+//                   scans them, then for the tiles that keep a row loads the
+//                   Morton keys of the set rows and writes (Morton key, row)
+//                   pairs, coalesced per warp
+// No look-back chain and no global atomics. (Staging the keys through a
+// shared-memory ring of 1-D bulk copies measured no faster: these passes are
+// short and bound by the latency of their first loads, not by issue.)
 constexpr int kSurvItems = 8;
 constexpr int kSurvTile = kSurvItems * kThreads;   // 2048 rows
-constexpr int kSurvStages = 4;
 constexpr int kSurvMaxTpb = 2048;                  // tiles per block (n < 2^31 needs at most 1,772)
 constexpr int kTileWords = kSurvTile / 32;         // flag words per tile
 static_assert(kTileWords == 64, "one warp scans a tile's flag words two per lane");
@@ -960,26 +967,22 @@ __device__ __forceinline__ bool has_zero_column(uint32_t key, uint32_t ones, uin
     return ((key - ones) & ~key & highs) != 0u;
 }
 
-// Bytes of tile `tile`'s 32-bit words (the last tile may be short), rounded
-// up to the 16-byte granule of a bulk copy; the key arrays carry at least 16
-// bytes of slack past row n.
-__device__ __forceinline__ uint32_t surv_tile_bytes(int64_t tile, int64_t n)
+// Keys of rows tile * kSurvTile + h * 4 * kThreads + 4 * tid + (0..3) into
+// k[h], one 16-byte streaming load each (rows past n read the arrays' slack
+// and are ignored by the caller; steps starting past n load nothing).
+template <int H>
+__device__ __forceinline__ void surv_load_keys(const uint32_t* __restrict__ keys, int64_t tile, int64_t n, int tid,
+                                               uint4 (&k)[H])
 {
-    int64_t rows = n - tile * kSurvTile;
-    if (rows > kSurvTile) rows = kSurvTile;
-    return (uint32_t)((rows * 4 + 15) & ~int64_t(15));
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int64_t r = tile * kSurvTile + (int64_t)h * 4 * kThreads + 4 * tid;
+        k[h] = r < n ? __ldcs(reinterpret_cast<const uint4*>(keys + r)) : make_uint4(0u, 0u, 0u, 0u);
+    }
 }
 
-__device__ __forceinline__ void surv_issue(uint32_t* stage, const uint32_t* src, int64_t tile, int64_t n,
-                                           uint64_t* bar)
-{
-    const uint32_t bytes = surv_tile_bytes(tile, n);
-    mbar_arrive_expect_tx(bar, bytes);
-    bulk_g2s(stage, src + tile * kSurvTile, bytes, bar);
-}
-
-// Four consecutive rows per thread and step (one 16-byte shared-memory
-// read); a tile is two steps of 1,024 rows. The eight lanes 8q .. 8q+7 of a
+// Four consecutive rows per thread and step (one 16-byte load); a tile is
+// two steps of 1,024 rows. The eight lanes 8q .. 8q+7 of a
 // warp hold the 32 rows of one flag word as nibbles, OR-ed together in three
 // shuffles. The bitmap is probed only when some lane of the warp needs it.
 template <int DP>
@@ -988,24 +991,21 @@ __global__ void __launch_bounds__(kThreads) k_surv_flags(
     const uint32_t* __restrict__ ckey, const uint32_t* __restrict__ pre, const float* __restrict__ filt,
     int n_filter_max, DevResult* res, int64_t tpb, uint32_t* __restrict__ flags, uint32_t* __restrict__ counts)
 {
-    extern __shared__ __align__(128) uint32_t s_ring[];   // [kSurvStages][kSurvTile] cell keys
-    __shared__ __align__(8) uint64_t s_bar[kSurvStages];
     __shared__ float s_f[16 * kMaxDim];
     __shared__ uint32_t s_cnt[kThreads / 32];
     __shared__ uint32_t s_diag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nf = n_filter_max ? (int)res->n_filter_used : 0;
-    for (int t = tid; t < nf * kMaxDim; t += kThreads) s_f[t] = filt[t];
     const int64_t ntiles = (n + kSurvTile - 1) / kSurvTile;
     const int64_t t0 = (int64_t)blockIdx.x * tpb;
     const int64_t my = (t0 + tpb < ntiles ? t0 + tpb : ntiles) - t0;
-    if (tid == 0) {
-        for (int s = 0; s < kSurvStages; ++s) mbar_init(&s_bar[s], 1);
-        mbar_fence_init();
-        for (int64_t i = 0; i < my && i < kSurvStages; ++i)
-            surv_issue(s_ring + i * kSurvTile, ckey, t0 + i, n, &s_bar[i]);
-    }
-    __syncthreads();
+    constexpr int H = kSurvTile / (4 * kThreads);   // steps per tile
+    static_assert(H == 2, "two steps of four rows per thread");
+    // this thread's keys of the block's first tile, in flight while the
+    // block looks for D
+    uint4 nk[H];
+    surv_load_keys<H>(ckey, t0, n, tid, nk);
+    const int nf = n_filter_max ? (int)res->n_filter_used : 0;
+    for (int t = tid; t < nf * kMaxDim; t += kThreads) s_f[t] = filt[t];
     // With log2g = 0 the grid is one cell, which nothing dominates (and the
     // field masks below would be empty): no row probes the bitmap then.
     const bool can_dominate = log2g > 0;
@@ -1035,30 +1035,23 @@ __global__ void __launch_bounds__(kThreads) k_surv_flags(
     const uint32_t D = s_diag;
     const uint32_t cmask = (1u << log2g) - 1u;
     uint32_t cnt = 0;                          // rows kept by this thread
-    bool timed_out = false;
     for (int64_t i = 0; i < my; ++i) {
-        const int s = (int)(i % kSurvStages);
-        if (tid == 0 && !mbar_wait(&s_bar[s], (uint32_t)((i / kSurvStages) & 1), &res->err)) timed_out = true;
-        if (__syncthreads_or(timed_out)) {
-            if (tid == 0)   // let the copies already issued land before the block exits
-                for (int64_t j = i; j < my && j < i + kSurvStages; ++j)
-                    mbar_wait(&s_bar[j % kSurvStages], (uint32_t)((j / kSurvStages) & 1), nullptr);
-            break;
-        }
         const int64_t tile = t0 + i;
         const int64_t row0 = tile * kSurvTile;
         // rows of this tile: all kSurvTile but in the last tile
         const uint32_t valid = (uint32_t)(n - row0 < kSurvTile ? n - row0 : kSurvTile);
-        const uint4* sk4 = reinterpret_cast<const uint4*>(s_ring + s * kSurvTile);
         uint32_t* fl = flags + tile * kTileWords;
-        constexpr int H = kSurvTile / (4 * kThreads);   // steps per tile
-        static_assert(H == 2, "two steps of four rows per thread");
         uint32_t ks[H][4], keep[H], need[H];
 #pragma unroll
         for (int h = 0; h < H; ++h) {
+            ks[h][0] = nk[h].x; ks[h][1] = nk[h].y; ks[h][2] = nk[h].z; ks[h][3] = nk[h].w;
+        }
+        // the next tile's keys in flight (a deeper register ring of three
+        // tiles measured no faster)
+        if (i + 1 < my) surv_load_keys<H>(ckey, tile + 1, n, tid, nk);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
             const uint32_t r = (uint32_t)(h * 4 * kThreads + 4 * tid);   // first of this thread's 4 rows
-            const uint4 k4 = sk4[h * kThreads + tid];
-            ks[h][0] = k4.x; ks[h][1] = k4.y; ks[h][2] = k4.z; ks[h][3] = k4.w;
             keep[h] = 0u;
             need[h] = 0u;
 #pragma unroll
@@ -1130,11 +1123,6 @@ __global__ void __launch_bounds__(kThreads) k_surv_flags(
             const uint32_t wr = r - 4u * (uint32_t)sub;   // first row of this lane's flag word
             if (sub == 0 && wr < valid) fl[wr >> 5] = v;
         }
-        __syncthreads();   // stage s consumed by every thread
-        if (tid == 0 && i + kSurvStages < my) {
-            fence_proxy_async_smem();
-            surv_issue(s_ring + s * kSurvTile, ckey, t0 + i + kSurvStages, n, &s_bar[s]);
-        }
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
     if (lane == 0) s_cnt[warp] = cnt;
@@ -1146,21 +1134,20 @@ __global__ void __launch_bounds__(kThreads) k_surv_flags(
     }
 }
 
-// The first kSurvStages tiles of the block are requested before anything
-// else (their keys arrive while the block computes its offsets); later tiles
-// are requested only when they keep a row.
+// The block's output offset and every tile's offset come from the counts and
+// flag words first; then each warp loads the Morton keys of its set rows (all
+// eight items' loads in flight together) and writes (key, row) pairs,
+// coalesced per warp. Tiles that keep no row are skipped.
 __global__ void __launch_bounds__(kThreads) k_surv_scatter(int64_t n, const uint32_t* __restrict__ mkey,
                                                            const uint32_t* __restrict__ flags,
                                                            const uint32_t* __restrict__ counts, int64_t tpb,
                                                            DevResult* res, uint32_t* __restrict__ surv_key,
                                                            uint32_t* __restrict__ surv_idx)
 {
-    // [kSurvStages][kSurvTile] Morton keys, then per tile of this block its
-    // survivor count [tpb] and its exclusive offset [tpb]
-    extern __shared__ __align__(128) uint32_t s_ring[];
-    uint32_t* s_tc = s_ring + kSurvStages * kSurvTile;
+    // per tile of this block: its survivor count [tpb] and exclusive offset [tpb]
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    uint32_t* s_tc = s_dyn;
     uint32_t* s_to = s_tc + tpb;
-    __shared__ __align__(8) uint64_t s_bar[kSurvStages];
     __shared__ uint32_t s_warp[kThreads / 32];
     __shared__ uint32_t s_off;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1168,14 +1155,6 @@ __global__ void __launch_bounds__(kThreads) k_surv_scatter(int64_t n, const uint
     const int64_t t0 = (int64_t)blockIdx.x * tpb;
     const int my = (int)((t0 + tpb < ntiles ? t0 + tpb : ntiles) - t0);
     const int64_t nwords = (n + 31) / 32;
-    int nxt = 0;            // thread 0: next tile of the block to request
-    int issued = 0;         // thread 0: copies requested
-    if (tid == 0) {
-        for (int st = 0; st < kSurvStages; ++st) mbar_init(&s_bar[st], 1);
-        mbar_fence_init();
-        for (; nxt < my && nxt < kSurvStages; ++nxt, ++issued)
-            surv_issue(s_ring + nxt * kSurvTile, mkey, t0 + nxt, n, &s_bar[nxt]);
-    }
     // rows kept by the blocks before this one
     uint32_t part = 0;
     for (int b = tid; b < (int)blockIdx.x; b += kThreads) part += counts[b];
@@ -1210,64 +1189,41 @@ __global__ void __launch_bounds__(kThreads) k_surv_scatter(int64_t n, const uint
     __syncthreads();
     const uint32_t base_off = s_off;
     const uint32_t below = lanemask_lt();
-    int c = 0;              // stages consumed so far
-    bool timed_out = false;
     for (int i = 0; i < my; ++i) {
-        const uint32_t cnt = s_tc[i];
-        if (i >= kSurvStages && cnt == 0u) continue;   // never requested (block-uniform)
-        const int s = c % kSurvStages;
+        if (s_tc[i] == 0u) continue;   // block-uniform
         const int64_t tile = t0 + i;
-        uint32_t fa = 0, fb = 0, oa = 0, ob = 0;
-        if (cnt) {
-            // every warp scans the tile's 64 flag words itself (lane l: words
-            // l and 32 + l) while thread 0 waits for the keys
-            const int64_t gw = tile * kTileWords + lane;
-            fa = gw < nwords ? __ldg(flags + gw) : 0u;
-            fb = gw + 32 < nwords ? __ldg(flags + gw + 32) : 0u;
-            const uint32_t pa = (uint32_t)__popc(fa), pb = (uint32_t)__popc(fb);
-            uint32_t xa = pa, xb = pb;
+        // every warp scans the tile's 64 flag words itself (lane l: words l
+        // and 32 + l)
+        const int64_t gw = tile * kTileWords + lane;
+        const uint32_t fa = gw < nwords ? __ldg(flags + gw) : 0u;
+        const uint32_t fb = gw + 32 < nwords ? __ldg(flags + gw + 32) : 0u;
+        const uint32_t pa = (uint32_t)__popc(fa), pb = (uint32_t)__popc(fb);
+        uint32_t xa = pa, xb = pb;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t ya = __shfl_up_sync(kFull, xa, o), yb = __shfl_up_sync(kFull, xb, o);
-                if (lane >= o) { xa += ya; xb += yb; }
-            }
-            const uint32_t ta = __shfl_sync(kFull, xa, 31);
-            oa = xa - pa;
-            ob = ta + xb - pb;   // exclusive offsets of words l and 32 + l
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t ya = __shfl_up_sync(kFull, xa, o), yb = __shfl_up_sync(kFull, xb, o);
+            if (lane >= o) { xa += ya; xb += yb; }
         }
-        if (tid == 0 && !mbar_wait(&s_bar[s], (uint32_t)((c / kSurvStages) & 1), &res->err)) timed_out = true;
-        if (__syncthreads_or(timed_out)) {
-            if (tid == 0)
-                for (int k = c; k < issued; ++k)
-                    mbar_wait(&s_bar[k % kSurvStages], (uint32_t)((k / kSurvStages) & 1), nullptr);
-            break;
-        }
-        ++c;
-        if (cnt) {
-            const uint32_t* sk = s_ring + s * kSurvTile;
-            const uint32_t tile_base = base_off + s_to[i];
-            const uint32_t row0 = (uint32_t)(tile * kSurvTile);
+        const uint32_t ta = __shfl_sync(kFull, xa, 31);
+        const uint32_t oa = xa - pa, ob = ta + xb - pb;   // exclusive offsets of words l and 32 + l
+        const uint32_t tile_base = base_off + s_to[i];
+        const uint32_t row0 = (uint32_t)(tile * kSurvTile);
+        uint32_t fw[kSurvItems], ow[kSurvItems], key[kSurvItems];
 #pragma unroll
-            for (int j = 0; j < kSurvItems; ++j) {
-                const int wi = j * (kThreads / 32) + warp;   // flag word of item j of this warp
-                const uint32_t fw = __shfl_sync(kFull, wi < 32 ? fa : fb, wi & 31);
-                const uint32_t ow = __shfl_sync(kFull, wi < 32 ? oa : ob, wi & 31);
-                if ((fw >> lane) & 1u) {
-                    const uint32_t pos = tile_base + ow + (uint32_t)__popc(fw & below);
-                    const uint32_t r = (uint32_t)(j * kThreads + tid);
-                    surv_key[pos] = sk[r];
-                    surv_idx[pos] = row0 + r;
-                }
-            }
+        for (int j = 0; j < kSurvItems; ++j) {
+            const int wi = j * (kThreads / 32) + warp;   // flag word of item j of this warp
+            fw[j] = __shfl_sync(kFull, wi < 32 ? fa : fb, wi & 31);
+            ow[j] = __shfl_sync(kFull, wi < 32 ? oa : ob, wi & 31);
         }
-        __syncthreads();   // stage s consumed
-        if (tid == 0) {
-            while (nxt < my && !s_tc[nxt]) ++nxt;
-            if (nxt < my) {
-                fence_proxy_async_smem();
-                surv_issue(s_ring + s * kSurvTile, mkey, t0 + nxt, n, &s_bar[s]);
-                ++issued;
-                ++nxt;
+#pragma unroll
+        for (int j = 0; j < kSurvItems; ++j)
+            key[j] = ((fw[j] >> lane) & 1u) ? __ldcs(mkey + row0 + j * kThreads + tid) : 0u;
+#pragma unroll
+        for (int j = 0; j < kSurvItems; ++j) {
+            if ((fw[j] >> lane) & 1u) {
+                const uint32_t pos = tile_base + ow[j] + (uint32_t)__popc(fw[j] & below);
+                surv_key[pos] = key[j];
+                surv_idx[pos] = row0 + (uint32_t)(j * kThreads + tid);
             }
         }
     }
@@ -1422,7 +1378,18 @@ cudaError_t launch_minmax_accumulate(const Plan& p, cudaStream_t s)
 
 // p.params for p.map_mode: min / max scales from p.mm_* (mode 2), the unit
 // cube (mode 1), or the automatic rule over p's rows (mode 0).
-cudaError_t launch_params(const Plan& p, cudaStream_t s)
+// The automatic map's sample kernel (eight CTAs) also zeroes the result
+// block and a bitmap of at most this many words (32 KB), saving the k_clear
+// launch; a 2 MB bitmap cleared by those eight CTAs measured slower than a
+// separate wide k_clear.
+constexpr int64_t kFoldClearWords = int64_t(1) << 13;
+
+bool clear_folded(const Plan& p)
+{
+    return p.map_mode == kMapAuto && p.n > 0 && p.words <= kFoldClearWords;
+}
+
+cudaError_t launch_params(const Plan& p, cudaStream_t s, bool clear)
 {
     if (p.map_mode == kMapMinMax) {
         k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 1, p.params);
@@ -1430,8 +1397,10 @@ cudaError_t launch_params(const Plan& p, cudaStream_t s)
         k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 0, p.params);
     } else {
         const bool v = vec4_ok(p);
+        const bool fold = clear && clear_folded(p);
         SKY_DISPATCH_DP(p.d, k_sample_params<DP><<<kDecideCluster, kDecideThreads, 0, s>>>(
-                                 p.pts, p.n, p.d, p.ld, v, p.log2g, p.morton_bits, p.mm_min, p.mm_max, p.params));
+                                 p.pts, p.n, p.d, p.ld, v, p.log2g, p.morton_bits, p.mm_min, p.mm_max, p.params,
+                                 fold ? p.res : nullptr, p.occ, p.words));
     }
     return cudaGetLastError();
 }
@@ -1440,11 +1409,12 @@ cudaError_t launch_params(const Plan& p, cudaStream_t s)
 // pass in mode 2).
 cudaError_t launch_build_params(const Plan& p, cudaStream_t s)
 {
-    k_clear<<<grid_for(p.words, kThreads * 16, num_sms() * 4), kThreads, 0, s>>>(p.res, p.occ, p.words);
+    if (!clear_folded(p))
+        k_clear<<<grid_for(p.words, kThreads * 16, num_sms() * 4), kThreads, 0, s>>>(p.res, p.occ, p.words);
     if (p.map_mode == kMapMinMax) launch_mm_reset(p, s);
     if (p.n == 0) return cudaGetLastError();
     if (p.map_mode == kMapMinMax) launch_minmax_accumulate(p, s);
-    return launch_params(p, s);
+    return launch_params(p, s, true);
 }
 
 cudaError_t launch_build(const Plan& p, cudaStream_t s)
@@ -1459,7 +1429,7 @@ int build_kernel_count(const Plan& p)
     if (p.n == 0) return 1;
     const int merge = p.occ_stage ? 1 : 0;
     if (p.map_mode == kMapMinMax) return 4 + merge;
-    return 3 + merge;   // clear, parameters, map pass (+ merge)
+    return (clear_folded(p) ? 2 : 3) + merge;   // (clear,) parameters, map pass (+ merge)
 }
 
 // Split of the prefix-OR: kl low dimensions per shared-memory block (at most
@@ -1499,6 +1469,19 @@ PrefixSplit prefix_split(const Plan& p)
     ps.wc = (int)wc;
     ps.high_blocks = ps.block_words / wc;
     return ps;
+}
+
+// At most two columns per dimension the survivor pass needs no prefix-OR:
+// a cell with no zero column is then the all-ones cell, whose one-down
+// neighbour is the origin, and the inclusive prefix-OR at the origin is the
+// origin's occupancy bit. The pass's diagonal shortcut also reads the
+// all-ones cell; with the occupancy bit there (not the OR of the whole grid)
+// its threshold only moves between values >= 1, for which every such row
+// still probes the origin. So the survivor pass reads the bitmap itself
+// (log2g = 0: one cell, nothing is dominated and nothing is read).
+bool prefix_trivial(const Plan& p)
+{
+    return p.log2g <= 1;
 }
 
 int prefix_kernel_count(const Plan& p)
@@ -1579,14 +1562,11 @@ cudaError_t launch_survivors(const Plan& p, int n_filter, cudaStream_t s, uint32
     int blocks = 1;
     survivor_split(p.n, &tpb, &blocks);
     const bool v = vec4_ok(p);
-    const int ring = kSurvStages * kSurvTile * (int)sizeof(uint32_t);
-    SKY_DISPATCH_DP(p.d, {
-        cudaFuncSetAttribute(k_surv_flags<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ring);
-        k_surv_flags<DP><<<blocks, kThreads, ring, s>>>(p.pts, p.n, p.d, p.ld, v, p.log2g, p.ckey, p.pre, p.filt,
-                                                        n_filter, p.res, tpb, p.sflags, p.scount);
-    });
-    const int smem = ring + 2 * (int)tpb * (int)sizeof(uint32_t);
-    cudaFuncSetAttribute(k_surv_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    SKY_DISPATCH_DP(p.d, k_surv_flags<DP><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, p.log2g, p.ckey,
+                                                                        p.pre, p.filt, n_filter, p.res, tpb,
+                                                                        p.sflags, p.scount));
+    const int smem = 2 * (int)tpb * (int)sizeof(uint32_t);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_surv_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_surv_scatter<<<blocks, kThreads, smem, s>>>(p.n, p.mkey, p.sflags, p.scount, tpb, p.res, p.surv_key,
                                                   idx_out ? idx_out : p.surv_idx);
     return cudaGetLastError();

@@ -77,7 +77,8 @@ __global__ void k_delay(uint32_t ns)
 int count_kernels(const Plan& p, int n_prop, int64_t capacity)
 {
     const int passes = (p.morton_bits * p.d + 7) / 8;
-    const int through_c = build_kernel_count(p) + (n_prop > 0 ? 2 : 0) + prefix_kernel_count(p) + 2;
+    const int through_c =
+        build_kernel_count(p) + (n_prop > 0 ? 2 : 0) + (prefix_trivial(p) ? 0 : prefix_kernel_count(p)) + 2;
     if (p.survivors_only) return through_c + (capacity >= p.n ? 0 : 1);   // + the id copy
     return through_c + 3 * passes + 1 + 3 + 1;   // sort, gather, cost + order + refine, emit
 }
@@ -267,7 +268,8 @@ cudaError_t enqueue_pipeline(Plan& p, const float* prop, int n_prop, int32_t* ou
     // without proposals the snap is skipped: n_filter_used stays 0 from the
     // cleared result block, and the survivor pass then reads no filter
     if (e == cudaSuccess && n_prop > 0) e = launch_snap(p, prop, n_prop, s);
-    if (e == cudaSuccess) e = launch_prefix_or(p, s);
+    if (prefix_trivial(p)) p.pre = p.occ;   // the survivor pass reads the bitmap itself
+    else if (e == cudaSuccess) e = launch_prefix_or(p, s);
     clk.mark();
     // a survivors-only call whose buffer holds n ids receives them directly
     const bool direct = p.survivors_only && capacity >= p.n;

@@ -138,10 +138,13 @@ cudaError_t launch_build_params(const Plan& p, cudaStream_t s);   // launch_buil
 int build_kernel_count(const Plan& p);
 cudaError_t launch_prefix_or(const Plan& p, cudaStream_t s);
 int prefix_kernel_count(const Plan& p);
+bool prefix_trivial(const Plan& p);   // log2g <= 1: the survivor pass reads the bitmap itself
 int map_blocks_bound(int64_t n);
 void launch_mm_reset(const Plan& p, cudaStream_t s);
 cudaError_t launch_minmax_accumulate(const Plan& p, cudaStream_t s);
-cudaError_t launch_params(const Plan& p, cudaStream_t s);
+// the value map's parameters; with `clear` (the first launch of a call) the
+// automatic map's sample kernel also zeroes the result block and a small bitmap
+cudaError_t launch_params(const Plan& p, cudaStream_t s, bool clear = false);
 cudaError_t launch_map_pass(const Plan& p, bool mark, cudaStream_t s);
 void set_last_error(const char* msg);   // the message sky_last_error() returns
 cudaError_t launch_dominated(const Plan& p, cudaStream_t s);
