@@ -47,11 +47,19 @@ constexpr int kRingStages = SKY_REFINE_STAGES;
 constexpr uint32_t kSummaryEvery = SKY_REFINE_SUMMARY;   // issued tiles between refreshes of the group maxima
 constexpr int kPUnroll = SKY_REFINE_UNROLL;              // listed p's tested per loop step (1 or 2)
 static_assert(kPUnroll == 1 || kPUnroll == 2, "one or two p's per step");
+// 1: the listed p's of a group are compacted into a per-warp list in shared
+// memory and tested branch-free four at a time (hits collected as bits and
+// resolved afterwards); 0: a bit-scan loop over the ballot, one branch per p
+#ifndef SKY_REFINE_LIST
+#define SKY_REFINE_LIST 1
+#endif
+constexpr bool kListProbe = SKY_REFINE_LIST != 0;
 constexpr uint32_t kEndTile = 0xffffffffu;
 
 template <int DP>
 struct RefineSmem {
     static constexpr int DW = DP / 4;
+    static constexpr int DWL = DW == 3 ? 4 : DW;   // list entry words (vector loads)
     // bulk-copy destinations: 16-byte aligned whatever the ring depth
     alignas(16) uint32_t qC[kRingStages][kTQ * DW];  // streamed q-tiles (codes)
     alignas(16) float pX[kTQ * DP];      // own p coordinates (exact tests)
@@ -66,9 +74,27 @@ struct RefineSmem {
     uint64_t empty[kRingStages];
     alignas(16) uint32_t stc[2][32 * kSubSlots * DW];   // producer: codes of the 32 tiles of a super-tile
     uint64_t cbar[2];                        // producer: their bulk copies
+    alignas(16) uint32_t plist[kTQ / 32][32 * DWL];   // consumer warp w: codes of the listed p's
+    uint8_t pidx[kTQ / 32][32];                        // and their indices in the tile
     uint32_t live;                       // live p's of the CTA
     uint32_t failed;
 };
+
+// Listed p entry j of a warp's list, DW words into c (16- or 8-byte loads).
+template <int DW>
+__device__ __forceinline__ void load_entry(const uint32_t* e, uint32_t (&c)[DW])
+{
+    if constexpr (DW == 4 || DW == 3) {
+        const uint4 v = *reinterpret_cast<const uint4*>(e);
+        c[0] = v.x; c[1] = v.y; c[2] = v.z;
+        if constexpr (DW == 4) c[3] = v.w;
+    } else if constexpr (DW == 2) {
+        const uint2 v = *reinterpret_cast<const uint2*>(e);
+        c[0] = v.x; c[1] = v.y;
+    } else {
+        c[0] = e[0];
+    }
+}
 
 __device__ __forceinline__ uint32_t has_zero_byte(uint32_t x)
 {
@@ -353,6 +379,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                     for (int w = 0; w < DW; ++w) r &= sm.pP[pg * DW + w] - Mw[w];
                     uint32_t mask = __ballot_sync(kFull, r == kHigh) & sm.livemask[g];
                     pairs += 32ull * __popc(mask);
+
                     // q (this lane) against listed p pi
                     auto probe = [&](int pi) {
                         uint32_t D[DW];
@@ -388,6 +415,47 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                             }
                         }
                     };
+                    if (kListProbe) {
+                        if (!mask) continue;
+                        // the listed p's of the group, in lane order, into
+                        // this warp's list
+                        constexpr int DWL = RefineSmem<DP>::DWL;
+                        uint32_t* L = sm.plist[warp];
+                        if ((mask >> lane) & 1u) {
+                            const int rank = __popc(mask & ((1u << lane) - 1u));
+#pragma unroll
+                            for (int w = 0; w < DW; ++w) L[rank * DWL + w] = sm.pP[pg * DW + w];
+                            sm.pidx[warp][rank] = (uint8_t)pg;
+                        }
+                        __syncwarp();
+                        const int k = __popc(mask);
+                        // q (this lane) against every listed p, four per
+                        // step; entries past k hold stale codes and their
+                        // bits are dropped below
+                        uint32_t hb = 0;
+                        for (int j0 = 0; j0 < k; j0 += 4) {
+                            uint32_t nb = 0;   // hit bits of entries j0 .. j0 + 3
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                uint32_t c[DW];
+                                load_entry<DW>(L + (j0 + u) * DWL, c);
+                                uint32_t a = kHigh;
+#pragma unroll
+                                for (int w = 0; w < DW; ++w) a &= c[w] - Q[w];
+                                if (a == kHigh) nb |= 1u << u;
+                            }
+                            hb |= nb << j0;
+                        }
+                        if (k < 32) hb &= (1u << k) - 1u;
+                        // rare: code(q) <= code(p) in every dimension
+                        while (hb) {
+                            const int j = __ffs(hb) - 1;
+                            hb &= hb - 1u;
+                            probe((int)sm.pidx[warp][j]);
+                        }
+                        __syncwarp();   // the list is rewritten by the next group
+                        continue;
+                    }
                     while (mask) {
                         const int pa = g * 32 + __ffs(mask) - 1;
                         mask &= mask - 1;
