@@ -415,57 +415,58 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                             }
                         }
                     };
-                    if (kListProbe) {
-                        if (!mask) continue;
-                        // the listed p's of the group, in lane order, into
-                        // this warp's list
-                        constexpr int DWL = RefineSmem<DP>::DWL;
-                        uint32_t* L = sm.plist[warp];
-                        if ((mask >> lane) & 1u) {
-                            const int rank = __popc(mask & ((1u << lane) - 1u));
+                    if constexpr (kListProbe) {
+                        if (mask) {
+                            // the listed p's of the group, in lane order, into
+                            // this warp's list
+                            constexpr int DWL = RefineSmem<DP>::DWL;
+                            uint32_t* L = sm.plist[warp];
+                            if ((mask >> lane) & 1u) {
+                                const int rank = __popc(mask & ((1u << lane) - 1u));
 #pragma unroll
-                            for (int w = 0; w < DW; ++w) L[rank * DWL + w] = sm.pP[pg * DW + w];
-                            sm.pidx[warp][rank] = (uint8_t)pg;
-                        }
-                        __syncwarp();
-                        const int k = __popc(mask);
-                        // q (this lane) against every listed p, four per
-                        // step; entries past k hold stale codes and their
-                        // bits are dropped below
-                        uint32_t hb = 0;
-                        for (int j0 = 0; j0 < k; j0 += 4) {
-                            uint32_t nb = 0;   // hit bits of entries j0 .. j0 + 3
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                uint32_t c[DW];
-                                load_entry<DW>(L + (j0 + u) * DWL, c);
-                                uint32_t a = kHigh;
-#pragma unroll
-                                for (int w = 0; w < DW; ++w) a &= c[w] - Q[w];
-                                if (a == kHigh) nb |= 1u << u;
+                                for (int w = 0; w < DW; ++w) L[rank * DWL + w] = sm.pP[pg * DW + w];
+                                sm.pidx[warp][rank] = (uint8_t)pg;
                             }
-                            hb |= nb << j0;
+                            __syncwarp();
+                            const int k = __popc(mask);
+                            // q (this lane) against every listed p, four per
+                            // step; entries past k hold stale codes and their
+                            // bits are dropped below
+                            uint32_t hb = 0;
+                            for (int j0 = 0; j0 < k; j0 += 4) {
+                                uint32_t nb = 0;   // hit bits of entries j0 .. j0 + 3
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    uint32_t c[DW];
+                                    load_entry<DW>(L + (j0 + u) * DWL, c);
+                                    uint32_t a = kHigh;
+#pragma unroll
+                                    for (int w = 0; w < DW; ++w) a &= c[w] - Q[w];
+                                    if (a == kHigh) nb |= 1u << u;
+                                }
+                                hb |= nb << j0;
+                            }
+                            if (k < 32) hb &= (1u << k) - 1u;
+                            // rare: code(q) <= code(p) in every dimension
+                            while (hb) {
+                                const int j = __ffs(hb) - 1;
+                                hb &= hb - 1u;
+                                probe((int)sm.pidx[warp][j]);
+                            }
+                            __syncwarp();   // the list is rewritten by the next group
                         }
-                        if (k < 32) hb &= (1u << k) - 1u;
-                        // rare: code(q) <= code(p) in every dimension
-                        while (hb) {
-                            const int j = __ffs(hb) - 1;
-                            hb &= hb - 1u;
-                            probe((int)sm.pidx[warp][j]);
-                        }
-                        __syncwarp();   // the list is rewritten by the next group
-                        continue;
-                    }
-                    while (mask) {
-                        const int pa = g * 32 + __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        if (kPUnroll == 2 && mask) {
-                            const int pb = g * 32 + __ffs(mask) - 1;
+                    } else {
+                        while (mask) {
+                            const int pa = g * 32 + __ffs(mask) - 1;
                             mask &= mask - 1;
-                            probe(pa);
-                            probe(pb);
-                        } else {
-                            probe(pa);
+                            if (kPUnroll == 2 && mask) {
+                                const int pb = g * 32 + __ffs(mask) - 1;
+                                mask &= mask - 1;
+                                probe(pa);
+                                probe(pb);
+                            } else {
+                                probe(pa);
+                            }
                         }
                     }
                 }
