@@ -292,6 +292,32 @@ __global__ void __launch_bounds__(kTQ) kb_gather(const QueryPlan* __restrict__ q
     }
 }
 
+// Super-tile minima: the byte-wise minimum code of each run of 32 q-tiles of
+// a query (the refinement skips a super-tile whose minimum is out of every
+// live group's reach). One warp per tile item; the warps of the first tile of
+// each run do the work.
+__global__ void __launch_bounds__(256) kb_supmin(const QueryPlan* __restrict__ qps, int nq,
+                                                 const int64_t* __restrict__ ptile, int64_t items)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (item >= items) return;
+    const int qi = find_query(ptile, nq, item);
+    const QueryPlan& q = qps[qi];
+    const uint32_t t0 = (uint32_t)(item - ptile[qi]);
+    if (t0 & 31u) return;
+    const uint32_t m = q.res->survivors;
+    const uint32_t T = (m + kTQ - 1) / kTQ;
+    if (t0 >= T) return;
+    const int dw = q.dp / 4;
+    for (int w = 0; w < dw; ++w) {
+        const uint32_t t = t0 + (uint32_t)lane;
+        uint32_t c = t < T ? q.sub[((int64_t)t * kSubSlots + kTQ / 32) * dw + w] : 0x7f7f7f7fu;
+        for (int o = 16; o > 0; o >>= 1) c = __vminu4(c, __shfl_xor_sync(kFull, c, o));
+        if (lane == 0) q.supmin[(int64_t)(t0 / 32u) * dw + w] = c;
+    }
+}
+
 // -------------------------------------------------------------------- (d)
 template <int DP>
 __global__ void __launch_bounds__(kTQ + 32) kb_refine(const QueryPlan* __restrict__ qps,
@@ -310,7 +336,7 @@ __global__ void __launch_bounds__(kTQ + 32) kb_refine(const QueryPlan* __restric
         const QueryPlan& q = qps[w.x];
         const uint32_t m = q.res->survivors;
         if ((uint32_t)w.y < (m + kTQ - 1) / kTQ)
-            refine::refine_ptile<DP>(sm, q.X, q.C, q.ids, q.sub, q.tend, nullptr, m, (uint32_t)w.y, q.res, q.keep);
+            refine::refine_ptile<DP>(sm, q.X, q.C, q.ids, q.sub, q.tend, q.supmin, m, (uint32_t)w.y, q.res, q.keep);
     }
 }
 
@@ -445,7 +471,10 @@ cudaError_t launch_batched(const BatchLaunch& b, cudaStream_t s)
             kb_radix_scatter<<<(unsigned)b.chunk_items, kT, 0, s>>>(b.qps, b.nq, b.pchunk, ps);
         }
     }
-    if (b.tile_items > 0) kb_gather<<<(unsigned)b.tile_items, kTQ, 0, s>>>(b.qps, b.nq, b.ptile);
+    if (b.tile_items > 0) {
+        kb_gather<<<(unsigned)b.tile_items, kTQ, 0, s>>>(b.qps, b.nq, b.ptile);
+        kb_supmin<<<(unsigned)((b.tile_items + 7) / 8), 256, 0, s>>>(b.qps, b.nq, b.ptile, b.tile_items);
+    }
     for (int c = 0; c < 4; ++c) {
         const int n = b.class_items[c];
         if (!n) continue;
@@ -473,7 +502,7 @@ int batched_kernel_count(const BatchLaunch& b)
 {
     int k = 0;
     if (b.chunk_items > 0) k += 3 + 3 * b.max_passes + 2;  // map, prefix, survivors, sort, emit, copy
-    if (b.tile_items > 0) k += 1;
+    if (b.tile_items > 0) k += 2;   // gather, super-tile minima
     for (int c = 0; c < 4; ++c) k += b.class_items[c] ? 1 : 0;
     return k + 1;                                           // finish
 }

@@ -109,6 +109,7 @@ struct QueryPlan {
     int32_t* ids;
     uint32_t* sub;
     uint32_t* tend;           // [tiles] last q-tile whose first Morton key <= the tile's last key
+    uint32_t* supmin;         // [ceil(tiles / 32)][dp / 4] byte-wise minimum code of each run of 32 tiles
     uint8_t* keep;
     int32_t* stage;
     DevResult* res;
