@@ -349,7 +349,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
     } else {
         // ------------------------------------------------------------ consumers
         const int qi = warp * 32 + lane;
-        unsigned long long pairs = 0, gscans = 0;
+        uint32_t listed = 0, gscans = 0;   // per warp (32-bit: a CTA lists far fewer than 2^32)
         uint32_t hits = 0, exact = 0;   // per lane
         for (uint32_t k = 0;; ++k) {
             const int s = (int)(k % S);
@@ -378,7 +378,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
 #pragma unroll
                     for (int w = 0; w < DW; ++w) r &= sm.pP[pg * DW + w] - Mw[w];
                     uint32_t mask = __ballot_sync(kFull, r == kHigh) & sm.livemask[g];
-                    pairs += 32ull * __popc(mask);
+                    listed += __popc(mask);
 
                     // q (this lane) against listed p pi
                     auto probe = [&](int pi) {
@@ -474,8 +474,8 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.empty[s]);
         }
-        if (lane == 0 && pairs) atomicAdd(&res->pairs, pairs);  // 32 q-lanes per listed p, per warp
-        if (lane == 0 && gscans) atomicAdd(&res->groups, gscans);
+        if (lane == 0 && listed) atomicAdd(&res->pairs, 32ull * listed);  // 32 q-lanes per listed p
+        if (lane == 0 && gscans) atomicAdd(&res->groups, (unsigned long long)gscans);
         const uint32_t wh = __reduce_add_sync(kFull, hits), we = __reduce_add_sync(kFull, exact);
         if (lane == 0 && wh) atomicAdd(&res->hits, (unsigned long long)wh);
         if (lane == 0 && we) atomicAdd(&res->exact, (unsigned long long)we);
