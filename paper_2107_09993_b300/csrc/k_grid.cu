@@ -145,20 +145,38 @@ __global__ void k_params(const uint32_t* mm_min, const uint32_t* mm_max, int d, 
 // Clears the call's result block and the occupancy bitmap in one launch (two
 // memset nodes in a CUDA graph cost several microseconds of scheduling each).
 // Both start 256-byte aligned; the bitmap is cleared in 16-byte stores.
-// Zeroes the result block and the bitmap; thread tid of nthr.
-__device__ __forceinline__ void clear_res_occ(DevResult* res, uint32_t* occ, int64_t words, int64_t tid, int64_t nthr)
+// What a call zeroes before its first step: the result block, the bitmap
+// and, when the plan has them, the sort's digit totals and the compaction's
+// look-back state (these would otherwise be memset nodes of their own, a few
+// microseconds each in a graph). Thread tid of nthr.
+struct ClearSet {
+    DevResult* res = nullptr;
+    uint32_t* occ = nullptr;
+    int64_t words = 0;
+    uint32_t* digit_total = nullptr;           // [4][256]
+    uint32_t* lb_counter = nullptr;            // [4]
+    unsigned long long* lb_states = nullptr;   // [lb_tiles]
+    int64_t lb_tiles = 0;
+};
+
+__device__ __forceinline__ void clear_set(const ClearSet& c, int64_t tid, int64_t nthr)
 {
     constexpr int kResWords = (int)(sizeof(DevResult) / sizeof(uint32_t));
-    if (tid < kResWords) reinterpret_cast<uint32_t*>(res)[tid] = 0u;
-    const int64_t q = words / 4;
-    uint4* o4 = reinterpret_cast<uint4*>(occ);
+    if (tid < kResWords) reinterpret_cast<uint32_t*>(c.res)[tid] = 0u;
+    if (c.digit_total)
+        for (int64_t i = tid; i < 4 * 256; i += nthr) c.digit_total[i] = 0u;
+    if (c.lb_counter && tid < 4) c.lb_counter[tid] = 0u;
+    if (c.lb_states)
+        for (int64_t i = tid; i < c.lb_tiles; i += nthr) c.lb_states[i] = 0ull;
+    const int64_t q = c.words / 4;
+    uint4* o4 = reinterpret_cast<uint4*>(c.occ);
     for (int64_t i = tid; i < q; i += nthr) o4[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int64_t i = q * 4 + tid; i < words; i += nthr) occ[i] = 0u;
+    for (int64_t i = q * 4 + tid; i < c.words; i += nthr) c.occ[i] = 0u;
 }
 
-__global__ void __launch_bounds__(kThreads) k_clear(DevResult* res, uint32_t* occ, int64_t words)
+__global__ void __launch_bounds__(kThreads) k_clear(ClearSet c)
 {
-    clear_res_occ(res, occ, words, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+    clear_set(c, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 // Automatic map, decided on the strided sample of rows 0, t, 2t, ... < n
@@ -181,8 +199,7 @@ constexpr int kDecideThreads = kDecideSample / kDecideCluster;   // 512
 template <int DP>
 __global__ void __cluster_dims__(kDecideCluster, 1, 1) __launch_bounds__(kDecideThreads)
     k_sample_params(const float* __restrict__ pts, int64_t n, int d, int64_t ld, bool vec4, int log2g, int mbits,
-                    uint32_t* mm_min, uint32_t* mm_max, float* params, DevResult* res, uint32_t* occ,
-                    int64_t clear_words)
+                    uint32_t* mm_min, uint32_t* mm_max, float* params, ClearSet clear)
 {
     __shared__ float s_mn[kDecideThreads / 32][DP], s_mx[kDecideThreads / 32][DP];
     __shared__ float c_mn[DP], c_mx[DP];   // this CTA's slice; read by CTA 0 of the cluster
@@ -216,8 +233,8 @@ __global__ void __cluster_dims__(kDecideCluster, 1, 1) __launch_bounds__(kDecide
         if (lane == 0) { s_mn[warp][k] = mn[k]; s_mx[warp][k] = mx[k]; }
     }
     if (tid == 0) s_bad = 0;
-    // the cleared result block and bitmap, when this launch replaces k_clear
-    if (res) clear_res_occ(res, occ, clear_words, r, (int64_t)kDecideSample);
+    // what k_clear would zero, when this launch replaces it (res != NULL)
+    if (clear.res) clear_set(clear, r, (int64_t)kDecideSample);
     __syncthreads();
     if (tid < DP) {
         float lo = NAN, hi = NAN;
@@ -1389,6 +1406,19 @@ bool clear_folded(const Plan& p)
     return p.map_mode == kMapAuto && p.n > 0 && p.words <= kFoldClearWords;
 }
 
+ClearSet clear_of(const Plan& p)
+{
+    ClearSet c;
+    c.res = p.res;
+    c.occ = p.occ;
+    c.words = p.words;
+    c.digit_total = p.digit_total;
+    c.lb_counter = p.lb_counter;
+    c.lb_states = p.lb_states;
+    c.lb_tiles = p.lb_states ? p.lb_tiles : 0;
+    return c;
+}
+
 cudaError_t launch_params(const Plan& p, cudaStream_t s, bool clear)
 {
     if (p.map_mode == kMapMinMax) {
@@ -1397,10 +1427,10 @@ cudaError_t launch_params(const Plan& p, cudaStream_t s, bool clear)
         k_params<<<1, 32, 0, s>>>(p.mm_min, p.mm_max, p.d, p.log2g, p.morton_bits, 0, p.params);
     } else {
         const bool v = vec4_ok(p);
-        const bool fold = clear && clear_folded(p);
+        const ClearSet cs = clear && clear_folded(p) ? clear_of(p) : ClearSet{};
         SKY_DISPATCH_DP(p.d, k_sample_params<DP><<<kDecideCluster, kDecideThreads, 0, s>>>(
                                  p.pts, p.n, p.d, p.ld, v, p.log2g, p.morton_bits, p.mm_min, p.mm_max, p.params,
-                                 fold ? p.res : nullptr, p.occ, p.words));
+                                 cs));
     }
     return cudaGetLastError();
 }
@@ -1410,7 +1440,7 @@ cudaError_t launch_params(const Plan& p, cudaStream_t s, bool clear)
 cudaError_t launch_build_params(const Plan& p, cudaStream_t s)
 {
     if (!clear_folded(p))
-        k_clear<<<grid_for(p.words, kThreads * 16, num_sms() * 4), kThreads, 0, s>>>(p.res, p.occ, p.words);
+        k_clear<<<grid_for(p.words, kThreads * 16, num_sms() * 4), kThreads, 0, s>>>(clear_of(p));
     if (p.map_mode == kMapMinMax) launch_mm_reset(p, s);
     if (p.n == 0) return cudaGetLastError();
     if (p.map_mode == kMapMinMax) launch_minmax_accumulate(p, s);

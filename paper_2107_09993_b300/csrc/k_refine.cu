@@ -335,8 +335,7 @@ cudaError_t launch_emit(const Plan& p, int32_t* out, int64_t capacity, cudaStrea
 {
     if (p.n == 0) return cudaGetLastError();
     const int64_t ntiles = (p.n + kScanTile - 1) / kScanTile;
-    cudaMemsetAsync(p.lb_states, 0, sizeof(unsigned long long) * ntiles, s);
-    cudaMemsetAsync(p.lb_counter + 1, 0, sizeof(uint32_t), s);
+    // p.lb_states and p.lb_counter were zeroed by the call's first kernel (k_clear)
     k_emit<<<(unsigned)ntiles, kScanThreads, 0, s>>>(p.keep, p.n, out, capacity, p.res, p.lb_states,
                                                      p.lb_counter + 1);
     return cudaGetLastError();

@@ -86,7 +86,7 @@ cudaError_t launch_sort(Plan& p, cudaStream_t s)
     uint32_t* kout = p.sort_key2;
     uint32_t* vout = p.sort_val2;
     const unsigned nblk = (unsigned)p.sort_blocks;
-    cudaMemsetAsync(p.digit_total, 0, sizeof(uint32_t) * 256 * 4, s);
+    // p.digit_total was zeroed by the call's first kernel (k_clear)
     for (int ps = 0; ps < passes; ++ps) {
         const int shift = ps * 8;
         uint32_t* tot = p.digit_total + 256 * ps;
