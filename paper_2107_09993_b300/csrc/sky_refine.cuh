@@ -65,7 +65,7 @@ struct RefineSmem {
     alignas(16) float pX[kTQ * DP];      // own p coordinates (exact tests)
     uint32_t pP[kTQ * DW];               // own p codes | 0x80 per byte
     uint32_t livemask[kTQ / 32];         // bit l of word g: p g*32+l is still undominated
-    uint32_t gmax[kTQ / 32][DW];         // byte-wise max code of each group's live p's (producer)
+    uint32_t gmax[kTQ / 32][DW];         // byte-wise max code of each group's live p's | 0x80 per byte (producer)
     uint32_t glive[kTQ / 32];            // live p's per group (producer)
     uint32_t stage_tile[kRingStages];
     uint32_t stage_mask[kRingStages];    // bit 4w+g: sub-tile w may dominate a live p of group g
@@ -101,13 +101,14 @@ __device__ __forceinline__ uint32_t has_zero_byte(uint32_t x)
     return (x - 0x01010101u) & ~x & 0x80808080u;
 }
 
-// every byte of lo <= the matching byte of hi (both 7-bit codes)
+// every byte of lo <= the matching byte of hi (7-bit codes; hi with its
+// guard bits 0x80 already set)
 template <int DW>
 __device__ __forceinline__ bool bytes_le(const uint32_t* lo, const uint32_t* hi)
 {
     uint32_t r = kHigh;
 #pragma unroll
-    for (int w = 0; w < DW; ++w) r &= (hi[w] | kHigh) - lo[w];
+    for (int w = 0; w < DW; ++w) r &= hi[w] - lo[w];
     return r == kHigh;
 }
 
@@ -174,7 +175,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                 for (int w = 0; w < DW; ++w) {
                     uint32_t c = live ? (sm.pP[pi * DW + w] & 0x7f7f7f7fu) : 0u;
                     for (int o = 16; o > 0; o >>= 1) c = __vmaxu4(c, __shfl_xor_sync(kFull, c, o));
-                    if (lane == 0) sm.gmax[g][w] = c;
+                    if (lane == 0) sm.gmax[g][w] = c | kHigh;   // guard bits set for the box tests
                 }
                 if (lane == 0) sm.glive[g] = nl;
             }
@@ -280,21 +281,36 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
             const uint32_t t0 = (uint32_t)cur * 32u;
             const uint32_t t = t0 + lane;
             const uint32_t* tc = &sm.stc[bf][lane * kSubSlots * DW];
-            // relevance of each (sub-tile, group) pair of this q-tile
+            // relevance of each (sub-tile, group) pair of this q-tile; the
+            // group maxima and the live groups in registers for the 4 + 16
+            // box tests of a lane
+            uint32_t gm[NG][DW];
+            uint32_t gl = 0;
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                if (sm.glive[g] != 0u) gl |= 1u << g;
+#pragma unroll
+                for (int w = 0; w < DW; ++w) gm[g][w] = sm.gmax[g][w];
+            }
+            auto le_g = [&](const uint32_t* lo, int g) -> bool {
+                return ((gl >> g) & 1u) && bytes_le<DW>(lo, gm[g]);
+            };
             uint32_t rmask = 0;
             if (t <= E && t != ptile) {   // the p-tile itself went first
-                uint32_t ctm[DW];
+                uint32_t cw[NG + 1][DW];   // sub-tile minima, then the tile minimum
 #pragma unroll
-                for (int w = 0; w < DW; ++w) ctm[w] = tc[NG * DW + w];
+                for (int q = 0; q <= NG; ++q)
+#pragma unroll
+                    for (int w = 0; w < DW; ++w) cw[q][w] = tc[q * DW + w];
                 bool any = false;
 #pragma unroll
-                for (int g = 0; g < NG; ++g) any |= (sm.glive[g] != 0u) && bytes_le<DW>(ctm, sm.gmax[g]);
+                for (int g = 0; g < NG; ++g) any |= le_g(cw[NG], g);
                 if (any) {
 #pragma unroll
                     for (int q = 0; q < NG; ++q)
 #pragma unroll
                         for (int g = 0; g < NG; ++g)
-                            if (sm.glive[g] != 0u && bytes_le<DW>(tc + q * DW, sm.gmax[g])) rmask |= 1u << (q * NG + g);
+                            if (le_g(cw[q], g)) rmask |= 1u << (q * NG + g);
                 }
             }
             uint32_t mask = __ballot_sync(kFull, rmask != 0u);
