@@ -334,7 +334,9 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                 __syncwarp();
                 ++issued;
                 ++since;
-                if (all_dead()) { stop = true; break; }
+                // every fourth tile: has every p died? (a few stages issued
+                // after the last death cost the consumers one check each)
+                if ((issued & 3u) == 0u && all_dead()) { stop = true; break; }
             }
             cur = nx;
         }
