@@ -50,6 +50,17 @@ static_assert(kPUnroll == 1 || kPUnroll == 2, "one or two p's per step");
 // 1: the listed p's of a group are compacted into a per-warp list in shared
 // memory and tested branch-free four at a time (hits collected as bits and
 // resolved afterwards); 0: a bit-scan loop over the ballot, one branch per p
+// When at most this many p's of a CTA are still live at the start of a
+// super-tile, the ring stops and the rest of the scan runs in sparse mode:
+// all five warps walk the remaining q-tiles themselves, 32 tiles at a time
+// (one lane per tile tests the tile's minimum code against each live p),
+// and test each relevant tile's 128 q's, four per lane, against only the
+// live p's that tile can reach -- no producer, no stage handshakes. 0: off.
+#ifndef SKY_REFINE_SPARSE
+#define SKY_REFINE_SPARSE 6
+#endif
+constexpr uint32_t kSparseLive = SKY_REFINE_SPARSE;
+static_assert(kSparseLive <= 32, "the sparse list is one lane mask wide");
 #ifndef SKY_REFINE_LIST
 #define SKY_REFINE_LIST 1
 #endif
@@ -77,6 +88,10 @@ struct RefineSmem {
     alignas(16) uint32_t plist[kTQ / 32][32 * DWL];   // consumer warp w: codes of the listed p's
     uint8_t pidx[kTQ / 32][32];                        // and their indices in the tile
     uint32_t live;                       // live p's of the CTA
+    uint32_t sparse;                     // 1: the scan continues in sparse mode
+    uint32_t resume;                     // first q-tile of the sparse scan
+    uint32_t scan_end;                   // last q-tile to scan
+    uint32_t nlist;                      // live p's listed for the sparse scan
     uint32_t failed;
 };
 
@@ -158,6 +173,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
         mbar_fence_init();
         sm.live = (m - pbase) < (uint32_t)kTQ ? (m - (uint32_t)pbase) : (uint32_t)kTQ;
         sm.failed = 0;
+        sm.sparse = 0;
     }
     __syncthreads();
 
@@ -197,6 +213,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
             return __shfl_sync(kFull, (sm.live == 0u || sm.failed != 0u) ? 1 : 0, 0) != 0;
         };
         const uint32_t E = TEND ? min(TEND[ptile], T - 1u) : T - 1u;   // last q-tile to scan
+        if (lane == 0) sm.scan_end = E;
         const uint32_t SL = E / 32u;                                     // last super-tile
         // Streaming order: the p-tile itself first (its own points kill each
         // other early in anti-correlated sets), then the super-tiles in
@@ -270,6 +287,15 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
         if (cur >= 0) fetch_super(cur);
         while (cur >= 0 && !stop) {
             if (all_dead()) break;
+            if (kSparseLive > 0 && __shfl_sync(kFull, sm.live, 0) <= kSparseLive) {
+                // few p's left: the rest of the scan runs in sparse mode,
+                // from this (fetched, not yet examined) super-tile on
+                if (lane == 0) {
+                    sm.sparse = 1u;
+                    sm.resume = (uint32_t)cur * 32u;
+                }
+                break;
+            }
             const int nx = next_super();
             if (nx >= 0) fetch_super(nx);
             const int bf = (int)(kcons & 1u);
@@ -499,6 +525,116 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
         if (lane == 0 && we) atomicAdd(&res->exact, (unsigned long long)we);
     }
     __syncthreads();
+    if (kSparseLive > 0 && sm.sparse && !sm.failed && sm.live != 0u) {
+        // ---------------------------------------------------------- sparse mode
+        constexpr int NW = NG + 1;                        // all five warps
+        constexpr int DWL = RefineSmem<DP>::DWL;
+        uint32_t* LC = sm.plist[0];                       // the consumers' lists are free now
+        uint8_t* LI = sm.pidx[0];
+        if (warp == 0) {
+            uint32_t nl = 0;
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const uint32_t lm = sm.livemask[g];
+                if ((lm >> lane) & 1u) {
+                    const uint32_t r = nl + __popc(lm & ((1u << lane) - 1u));
+                    if (r < 32u) {
+#pragma unroll
+                        for (int w = 0; w < DW; ++w) LC[r * DWL + w] = sm.pP[(g * 32 + lane) * DW + w];
+                        LI[r] = (uint8_t)(g * 32 + lane);
+                    }
+                }
+                nl += __popc(lm);
+            }
+            if (lane == 0) sm.nlist = nl < 32u ? nl : 32u;
+        }
+        __syncthreads();
+        const int nl = (int)sm.nlist;
+        const uint32_t E = sm.scan_end;
+        unsigned long long spairs = 0;
+        uint32_t shits = 0, sexact = 0;
+        // windows of 32 consecutive q-tiles, dealt to the warps in turn
+        for (uint32_t wbase = sm.resume + (uint32_t)warp * 32u; wbase <= E; wbase += NW * 32u) {
+            if (__shfl_sync(kFull, sm.live, 0) == 0u) break;
+            const uint32_t t = wbase + (uint32_t)lane;
+            uint32_t rm = 0;   // listed p's whose codes reach this tile's minimum
+            if (t <= E && t != ptile) {
+                uint32_t mn[DW];
+#pragma unroll
+                for (int w = 0; w < DW; ++w) mn[w] = __ldg(SUB + ((int64_t)t * kSubSlots + NG) * DW + w);
+                for (int i = 0; i < nl; ++i) {
+                    uint32_t pc[DW];
+                    load_entry<DW>(LC + i * DWL, pc);
+                    uint32_t r = kHigh;
+#pragma unroll
+                    for (int w = 0; w < DW; ++w) r &= pc[w] - mn[w];
+                    if (r == kHigh) rm |= 1u << i;
+                }
+            }
+            uint32_t tiles = __ballot_sync(kFull, rm != 0u);
+            while (tiles) {
+                const int b = __ffs(tiles) - 1;
+                tiles &= tiles - 1;
+                const uint32_t tt = wbase + (uint32_t)b;
+                uint32_t em = __shfl_sync(kFull, rm, b);
+                uint32_t qc[4][DW];   // q's j * 32 + lane of tile tt
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int w = 0; w < DW; ++w) qc[j][w] = __ldg(C + ((int64_t)tt * kTQ + j * 32 + lane) * DW + w);
+                while (em) {
+                    const int i = __ffs(em) - 1;
+                    em &= em - 1;
+                    const int pi = (int)LI[i];
+                    const bool alive = __shfl_sync(kFull, (sm.livemask[pi >> 5] >> (pi & 31)) & 1u, 0) != 0u;
+                    if (!alive) continue;
+                    spairs += 128;
+                    uint32_t pc[DW];
+                    load_entry<DW>(LC + i * DWL, pc);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        uint32_t D[DW];
+                        uint32_t a = kHigh;
+#pragma unroll
+                        for (int w = 0; w < DW; ++w) {
+                            D[w] = pc[w] - qc[j][w];
+                            a &= D[w];
+                        }
+                        if (a == kHigh) {   // code(q) <= code(p) in every dimension (rare)
+                            ++shits;
+                            uint32_t eq = 0;
+#pragma unroll
+                            for (int w = 0; w < DW; ++w) eq |= has_zero_byte(D[w] ^ kHigh);
+                            bool dom = true;
+                            if (eq) {
+                                ++sexact;
+                                const float* qx = X + ((int64_t)tt * kTQ + j * 32 + lane) * DP;
+                                const float* px = &sm.pX[pi * DP];
+                                bool le = true, lt = false;
+#pragma unroll
+                                for (int kk = 0; kk < DP; kk += 4) {
+                                    const float4 u = __ldg(reinterpret_cast<const float4*>(qx + kk));
+                                    const float4 v = *reinterpret_cast<const float4*>(px + kk);
+                                    le &= (u.x <= v.x) & (u.y <= v.y) & (u.z <= v.z) & (u.w <= v.w);
+                                    lt |= (u.x < v.x) | (u.y < v.y) | (u.z < v.z) | (u.w < v.w);
+                                }
+                                dom = le && lt;
+                            }
+                            if (dom) {
+                                const uint32_t bit = 1u << (pi & 31);
+                                if (atomicAnd(&sm.livemask[pi >> 5], ~bit) & bit) atomicSub(&sm.live, 1u);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (lane == 0 && spairs) atomicAdd(&res->pairs, spairs);
+        const uint32_t wh = __reduce_add_sync(kFull, shits), we = __reduce_add_sync(kFull, sexact);
+        if (lane == 0 && wh) atomicAdd(&res->hits, (unsigned long long)wh);
+        if (lane == 0 && we) atomicAdd(&res->exact, (unsigned long long)we);
+        __syncthreads();
+    }
     if (tid < kTQ && pbase + tid < m && !sm.failed && ((sm.livemask[tid >> 5] >> (tid & 31)) & 1u))
         keep[ids[pbase + tid]] = 1;
     if (tid == 0) {
