@@ -582,6 +582,12 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                 for (int j = 0; j < 4; ++j)
 #pragma unroll
                     for (int w = 0; w < DW; ++w) qc[j][w] = __ldg(C + ((int64_t)tt * kTQ + j * 32 + lane) * DW + w);
+                if (tiles) {   // the next relevant tile's codes on their way into L1 while this one is tested
+                    const uint32_t tn = wbase + (uint32_t)(__ffs(tiles) - 1);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        asm volatile("prefetch.global.L1 [%0];" ::"l"(C + ((int64_t)tn * kTQ + j * 32 + lane) * DW));
+                }
                 while (em) {
                     const int i = __ffs(em) - 1;
                     em &= em - 1;
