@@ -360,9 +360,20 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                 __syncwarp();
                 ++issued;
                 ++since;
-                // every fourth tile: has every p died? (a few stages issued
-                // after the last death cost the consumers one check each)
-                if ((issued & 3u) == 0u && all_dead()) { stop = true; break; }
+                // every fourth tile: has every p died (a few stages issued
+                // after the last death cost the consumers one check each),
+                // or are few enough left for sparse mode, from the next tile?
+                if ((issued & 3u) == 0u) {
+                    if (all_dead()) { stop = true; break; }
+                    if (kSparseLive > 0 && __shfl_sync(kFull, sm.live, 0) <= kSparseLive) {
+                        if (lane == 0) {
+                            sm.sparse = 1u;
+                            sm.resume = t0 + (uint32_t)b + 1u;
+                        }
+                        stop = true;
+                        break;
+                    }
+                }
             }
             cur = nx;
         }
