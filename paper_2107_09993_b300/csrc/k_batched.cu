@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(kTQ + 32) kb_refine(const QueryPlan* __restric
         const QueryPlan& q = qps[w.x];
         const uint32_t m = q.res->survivors;
         if ((uint32_t)w.y < (m + kTQ - 1) / kTQ)
-            refine::refine_ptile<DP>(sm, q.X, q.C, q.ids, q.sub, q.tend, q.supmin, m, (uint32_t)w.y, q.res, q.keep);
+            refine::refine_ptile<DP, false>(sm, q.X, q.C, q.ids, q.sub, q.tend, q.supmin, m, (uint32_t)w.y, q.res,
+                                            q.keep);
     }
 }
 

@@ -137,7 +137,12 @@ __device__ __forceinline__ bool bytes_le(const uint32_t* lo, const uint32_t* hi)
 // minimum code of each run of 32 q-tiles ("super-tile"); a super-tile whose
 // minimum exceeds every live group's maximum in some byte is skipped whole;
 // NULL examines every super-tile.
-template <int DP>
+// SPARSE (the single-set kernel): a p-tile whose live points drop to
+// kSparseLive finishes in sparse mode, and the producer tests relevance
+// against register copies of the group maxima. The batched persistent kernel
+// keeps the ring to the end and the maxima in shared memory (fewer registers:
+// measured faster there).
+template <int DP, bool SPARSE = true>
 __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __restrict__ X,
                                              const uint32_t* __restrict__ C, const int32_t* __restrict__ ids,
                                              const uint32_t* __restrict__ SUB, const uint32_t* __restrict__ TEND,
@@ -287,7 +292,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
         if (cur >= 0) fetch_super(cur);
         while (cur >= 0 && !stop) {
             if (all_dead()) break;
-            if (kSparseLive > 0 && __shfl_sync(kFull, sm.live, 0) <= kSparseLive) {
+            if (SPARSE && kSparseLive > 0 && __shfl_sync(kFull, sm.live, 0) <= kSparseLive) {
                 // few p's left: the rest of the scan runs in sparse mode,
                 // from this (fetched, not yet examined) super-tile on
                 if (lane == 0) {
@@ -307,19 +312,22 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
             const uint32_t t0 = (uint32_t)cur * 32u;
             const uint32_t t = t0 + lane;
             const uint32_t* tc = &sm.stc[bf][lane * kSubSlots * DW];
-            // relevance of each (sub-tile, group) pair of this q-tile; the
-            // group maxima and the live groups in registers for the 4 + 16
-            // box tests of a lane
+            // relevance of each (sub-tile, group) pair of this q-tile; in the
+            // single-set kernel the group maxima and the live groups are read
+            // into registers once for the 4 + 16 box tests of a lane
             uint32_t gm[NG][DW];
             uint32_t gl = 0;
+            if constexpr (SPARSE) {
 #pragma unroll
-            for (int g = 0; g < NG; ++g) {
-                if (sm.glive[g] != 0u) gl |= 1u << g;
+                for (int g = 0; g < NG; ++g) {
+                    if (sm.glive[g] != 0u) gl |= 1u << g;
 #pragma unroll
-                for (int w = 0; w < DW; ++w) gm[g][w] = sm.gmax[g][w];
+                    for (int w = 0; w < DW; ++w) gm[g][w] = sm.gmax[g][w];
+                }
             }
             auto le_g = [&](const uint32_t* lo, int g) -> bool {
-                return ((gl >> g) & 1u) && bytes_le<DW>(lo, gm[g]);
+                if constexpr (SPARSE) return ((gl >> g) & 1u) && bytes_le<DW>(lo, gm[g]);
+                else return (sm.glive[g] != 0u) && bytes_le<DW>(lo, sm.gmax[g]);
             };
             uint32_t rmask = 0;
             if (t <= E && t != ptile) {   // the p-tile itself went first
@@ -365,7 +373,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                 // or are few enough left for sparse mode, from the next tile?
                 if ((issued & 3u) == 0u) {
                     if (all_dead()) { stop = true; break; }
-                    if (kSparseLive > 0 && __shfl_sync(kFull, sm.live, 0) <= kSparseLive) {
+                    if (SPARSE && kSparseLive > 0 && __shfl_sync(kFull, sm.live, 0) <= kSparseLive) {
                         if (lane == 0) {
                             sm.sparse = 1u;
                             sm.resume = t0 + (uint32_t)b + 1u;
@@ -536,7 +544,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
         if (lane == 0 && we) atomicAdd(&res->exact, (unsigned long long)we);
     }
     __syncthreads();
-    if (kSparseLive > 0 && sm.sparse && !sm.failed && sm.live != 0u) {
+    if (SPARSE && kSparseLive > 0 && sm.sparse && !sm.failed && sm.live != 0u) {
         // ---------------------------------------------------------- sparse mode
         constexpr int NW = NG + 1;                        // all five warps
         constexpr int DWL = RefineSmem<DP>::DWL;
