@@ -1006,7 +1006,8 @@ template <int DP>
 __global__ void __launch_bounds__(kThreads) k_surv_flags(
     const float* __restrict__ pts, int64_t n, int d, int64_t ld, bool vec4, int log2g,
     const uint32_t* __restrict__ ckey, const uint32_t* __restrict__ pre, const float* __restrict__ filt,
-    int n_filter_max, DevResult* res, int64_t tpb, uint32_t* __restrict__ flags, uint32_t* __restrict__ counts)
+    int n_filter_max, DevResult* res, int64_t tpb, uint32_t* __restrict__ flags, uint32_t* __restrict__ counts,
+    uint8_t* __restrict__ keep_bytes)
 {
     __shared__ float s_f[16 * kMaxDim];
     __shared__ uint32_t s_cnt[kThreads / 32];
@@ -1058,6 +1059,13 @@ __global__ void __launch_bounds__(kThreads) k_surv_flags(
         // rows of this tile: all kSurvTile but in the last tile
         const uint32_t valid = (uint32_t)(n - row0 < kSurvTile ? n - row0 : kSurvTile);
         uint32_t* fl = flags + tile * kTileWords;
+        if (keep_bytes) {   // the refinement's keep bytes start at zero (4 rows a store; the array has slack)
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const uint32_t r = (uint32_t)(h * 4 * kThreads + 4 * tid);
+                if (r < valid) *reinterpret_cast<uint32_t*>(keep_bytes + row0 + r) = 0u;
+            }
+        }
         uint32_t ks[H][4], keep[H], need[H];
 #pragma unroll
         for (int h = 0; h < H; ++h) {
@@ -1595,7 +1603,8 @@ cudaError_t launch_survivors(const Plan& p, int n_filter, cudaStream_t s, uint32
     const bool v = vec4_ok(p);
     SKY_DISPATCH_DP(p.d, k_surv_flags<DP><<<blocks, kThreads, 0, s>>>(p.pts, p.n, p.d, p.ld, v, p.log2g, p.ckey,
                                                                         p.pre, p.filt, n_filter, p.res, tpb,
-                                                                        p.sflags, p.scount));
+                                                                        p.sflags, p.scount,
+                                                                        p.survivors_only ? nullptr : p.keep));
     const int smem = 2 * (int)tpb * (int)sizeof(uint32_t);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_surv_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_surv_scatter<<<blocks, kThreads, smem, s>>>(p.n, p.mkey, p.sflags, p.scount, tpb, p.res, p.surv_key,

@@ -317,7 +317,7 @@ cudaError_t launch_gather(const Plan& p, cudaStream_t s)
 
 cudaError_t launch_refine(const Plan& p, cudaStream_t s)
 {
-    cudaMemsetAsync(p.keep, 0, (size_t)p.n, s);
+    // p.keep was zeroed by the survivor pass (k_surv_flags)
     const int64_t tiles = (p.n + kTQ - 1) / kTQ;
     if (tiles == 0) return cudaGetLastError();
     SKY_DISPATCH_DP(p.d, {
