@@ -13,7 +13,7 @@ is flushed before every timed step by writing a 512 MB buffer.
     python bench.py --batched [--steps K] [--warmup W]                  (4,096-query batched workload)
 
 N > 1 runs independent replicas (the skyline of one point set is computed on
-one GPU; see DESIGN.md "multi-GPU"), launched under torchrun, weak scaling.
+one GPU), launched under torchrun, weak scaling.
 `--impl reference` times the CPU oracle (sort-first skyline) on the host cores
 on a bounded row sample of the same workload. The sky arm's line also carries
 the paper's own sequential SkyCell (host, one thread) on a smaller sample.

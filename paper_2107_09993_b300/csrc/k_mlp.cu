@@ -2,8 +2,8 @@
 //
 // A small perceptron reads distribution features of a point set and proposes
 // (1) the grid layer of step (a) and (2) 16 filter points that pre-filter
-// step (d). The plain path stays the judge: proposals are snapped to real
-// data points inside sky_skyline, so a bad proposal only costs time.
+// step (d). The plain path still decides the result: proposals are snapped to
+// real data points inside sky_skyline, so a bad proposal only costs time.
 //
 //   k_features   per-dimension 32-bin histograms of the min/max-normalised
 //                values and all pairwise Pearson correlations, over a strided

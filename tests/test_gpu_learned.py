@@ -1,8 +1,7 @@
 """The learned proposal's kernels against the numpy oracle (oracle/mlp.py),
 and the learned path's result against the plain path.
 
-Floating-point tolerances (derived in DESIGN.md, "learned proposal"): the
-kernels accumulate in binary32 where the oracle uses float64 with the same
+Floating-point tolerances: the kernels accumulate in binary32 where the oracle uses float64 with the same
 bfloat16-rounded weights. A dot product of K <= 636 terms of magnitude <= 1
 then differs by at most about K * 2^-24 relative per layer, so outputs are
 compared with rtol = atol = 2e-4, gradients (two more layers of products)
