@@ -155,7 +155,11 @@ typedef enum sky_grid_array {
     SKY_GRID_OCCUPIED = 1,        /* uint32[words]                              */
     SKY_GRID_DOMINATED = 2,       /* uint32[words] (after sky_prune_cells)      */
     SKY_GRID_SURVIVORS = 3,       /* int32[surviving_points] (after pruning)    */
-    SKY_GRID_CELL_MAP = 4         /* float[32]: offset[16] then scale[16]       */
+    SKY_GRID_CELL_MAP = 4,        /* float[32]: offset[16] then scale[16]       */
+    SKY_GRID_SNAP = 5             /* uint64[16] (after pruning with proposals):
+                                   * for proposal j, (ordered binary32 coordinate
+                                   * sum << 32) | row of the data point it was
+                                   * snapped to; all ones when no point is <= it */
 } sky_grid_array;
 
 /* Copies one array of the handle into caller memory d_dst (device) of
@@ -190,6 +194,28 @@ SKY_API sky_status sky_skyline(const float* d_pts, int64_t n, int32_t d, int64_t
 SKY_API sky_status sky_skyline_host(const float* h_pts, int64_t n, int32_t d, int64_t ld,
                             const sky_options* opt, int32_t* h_out_idx, int64_t out_capacity,
                             int64_t* h_out_count, void* stream);
+
+/*
+ * Witness mode of sky_skyline, a checking aid [Definitions 1-3]: the same
+ * skyline (same arguments, same result in d_out_idx / *h_out_count), and for
+ * every row i, d_witness[i] (device, n int32, caller-owned) =
+ *   -1  when i is in the skyline;
+ *   j   the row of a point that dominates point i (Definition 1), when the
+ *       path dropped i: for a point of a dominated cell (step c, Def. 3), a
+ *       point of an occupied cell that is below it in every dimension; for a
+ *       point a snapped proposal removed (step c'), that proposal's row; for
+ *       a point the refinement removed (step d), the survivor that did;
+ *   -2  when step (c) dropped i and no such point was found (an error of the
+ *       path; a correct run never writes it).
+ * So a caller verifies every dropped point with one O(d) test each, without
+ * computing the skyline itself. survivors_only must be 0. Slower than
+ * sky_skyline and allocates per call: workspace plus 4 * 2^(log2_g * d)
+ * bytes of cell scratch from the stream-ordered pool; no CUDA graph.
+ * Synchronises `stream`.
+ */
+SKY_API sky_status sky_skyline_witness(const float* d_pts, int64_t n, int32_t d, int64_t ld,
+                                       const sky_options* opt, int32_t* d_out_idx, int64_t out_capacity,
+                                       int64_t* h_out_count, int32_t* d_witness, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Many independent point sets in one call (a project addition: the paper    */
@@ -489,7 +515,8 @@ SKY_API sky_status sky_last_phase_times(sky_phase_times* out);
  * caller. The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before starting any stream capture on the device. Synchronises `stream`
- * once. Errors are described by sky_noalloc_last_error().
+ * once. Errors are described by sky_noalloc_last_error() (and by
+ * sky_last_error(), which each call also sets).
  */
 #define SKY_NOALLOC_MAX_POINTS 65536
 SKY_API sky_status sky_skyline_noalloc(const float* d_pts, int64_t n, int32_t d, int64_t ld,
@@ -533,6 +560,18 @@ SKY_API sky_status sky_baseline_key_cells(const float* h_pts, int64_t n, int32_t
 
 /* Thread-local detail of the last error of the two baseline calls. */
 SKY_API const char* sky_baseline_last_error(void);
+
+/*
+ * Test aid for the failure path: the poll limit of the bounded device-side
+ * waits of the pipeline (mbarrier waits of the streaming stages, look-back
+ * flags) on the current device, for the calls that start after this one
+ * returns. 0 restores the default (2^22 polls with back-off, well over a
+ * second). With a small limit (e.g. 1) the waits run out: the kernels record
+ * SKY_ERR_TIMEOUT, let their own bulk copies in flight land (those waits keep
+ * the default limit), and return; the call reports SKY_ERR_TIMEOUT and its
+ * output is undefined. The device stays usable. Synchronises the device.
+ */
+SKY_API sky_status sky_set_wait_limit(uint32_t polls);
 
 /* Static text for a status code. */
 SKY_API const char* sky_status_string(sky_status status);

@@ -232,3 +232,24 @@ def skyline_subset(table, row_begin: int, row_count: int, dim_mask: int,
         sub = np.ascontiguousarray(sub[keep])
     f = skyline_sfs if method == "sfs" else skyline_brute
     return (keep[f(sub, threads)] + row_begin).astype(np.int32)
+
+
+def snap_rows(P, F) -> np.ndarray:
+    """The learned pre-filter's snap (the reading that keeps it exact: a
+    proposal may only prune through a real data point). Proposal f becomes
+    the data point q with q <= f in every dimension whose coordinate sum is
+    smallest, the sum taken in IEEE binary32 in dimension order (k = 0, 1,
+    ...), ties to the lower row; -1 when no point is <= f. Returns one row
+    per proposal (int64)."""
+    P, n, d = _pts(P)
+    F = np.asarray(F, dtype=np.float32).reshape(-1, d)
+    s = np.zeros(n, dtype=np.float32)
+    for k in range(d):
+        s = np.add(s, P[:, k], dtype=np.float32)     # binary32, round to nearest
+    out = np.full(F.shape[0], -1, dtype=np.int64)
+    for j, f in enumerate(F):
+        idx = np.flatnonzero(np.all(P <= f, axis=1))
+        if idx.size:
+            sj = s[idx]
+            out[j] = idx[np.flatnonzero(sj == sj.min())[0]]
+    return out

@@ -25,7 +25,7 @@
  *   orc_cell_classes      Definitions 3-5 and 6 (auxiliary key cells) by
  *                         direct enumeration over all cells of one layer.
  *
- * Readings of points the paper leaves open (each repeated in the design doc):
+ * Readings of points the paper leaves open:
  *   - Eq. 1 assumes data in [0,1)^d. General data is mapped with
  *     t = (x - min_k) * s_k, s_k = G / (max_k - min_k), both operations in
  *     IEEE binary32 round-to-nearest with no fused multiply-add, then

@@ -9,7 +9,7 @@ library or a CUDA device is missing, every call raises.
     idx = sky.skyline(points_cuda_f32)          # ascending int32 row ids
 
 Names follow the C ABI: ``skyline`` (sky_skyline), ``skyline_host``
-(sky_skyline_host), ``skyline_sets`` / ``skyline_host_sets``
+(sky_skyline_host), ``skyline_witness`` (sky_skyline_witness), ``skyline_sets`` / ``skyline_host_sets``
 (sky_skyline_sets / sky_skyline_host_sets), ``Grid`` (sky_build_grid / sky_prune_cells /
 sky_grid_stats / sky_grid_copy_out / sky_grid_destroy).
 """
@@ -27,7 +27,7 @@ STATUS = {
     4: "SKY_ERR_OUT_OF_MEMORY", 5: "SKY_ERR_CUDA", 6: "SKY_ERR_TOO_LARGE", 7: "SKY_ERR_TIMEOUT",
     8: "SKY_ERR_NO_DEVICE",
 }
-GRID_CELL_KEY, GRID_OCCUPIED, GRID_DOMINATED, GRID_SURVIVORS, GRID_CELL_MAP = range(5)
+GRID_CELL_KEY, GRID_OCCUPIED, GRID_DOMINATED, GRID_SURVIVORS, GRID_CELL_MAP, GRID_SNAP = range(6)
 
 _i32, _i64, _vp, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t
 
@@ -82,6 +82,7 @@ def load():
     sig = {
         "sky_skyline": ([_vp, _i64, _i32, _i64, P(Options), _vp, _i64, P(_i64), _vp], _i32),
         "sky_skyline_host": ([_vp, _i64, _i32, _i64, P(Options), _vp, _i64, P(_i64), _vp], _i32),
+        "sky_skyline_witness": ([_vp, _i64, _i32, _i64, P(Options), _vp, _i64, P(_i64), _vp, _vp], _i32),
         "sky_skyline_sets": ([P(SkySet), _i32, P(Options), _vp], _i32),
         "sky_skyline_host_sets": ([P(SkySet), _i32, P(Options), _vp], _i32),
         "sky_skyline_chunked": ([_vp, _i32, _i64, _i32, _i64, P(Options), _i64, _i64, _vp, _i64, P(_i64), _vp],
@@ -92,6 +93,7 @@ def load():
         "sky_grid_copy_out": ([_vp, _i32, _vp, _sz], _i32),
         "sky_grid_destroy": ([_vp], None),
         "sky_last_run_stats": ([P(RunStats)], _i32),
+        "sky_set_wait_limit": ([ctypes.c_uint32], _i32),
         "sky_set_phase_timing": ([_i32], _i32),
         "sky_last_phase_times": ([P(PhaseTimes)], _i32),
         "sky_status_string": ([_i32], ctypes.c_char_p),
@@ -173,6 +175,25 @@ def skyline(points, log2_g=None, assume_unit=False, filter_points=None, capacity
         raise SkyError(st, f"{lib.sky_last_error().decode()} (count={cnt.value})")
     _check(st)
     return out[:cnt.value]
+
+
+def skyline_witness(points, log2_g=None, assume_unit=False, filter_points=None, stream=None):
+    """sky_skyline_witness: (skyline row ids, witnesses), both int32 CUDA
+    tensors. witnesses[i] is -1 for a skyline row, else the row of a point
+    that dominates row i (Definition 1); -2 marks a row step (c) dropped
+    without a witness (an error of the path)."""
+    torch = _torch()
+    lib = load()
+    points, n, d, ld = _points(points)
+    out = torch.empty(max(n, 1), dtype=torch.int32, device=points.device)
+    wit = torch.empty(max(n, 1), dtype=torch.int32, device=points.device)
+    cnt = _i64(0)
+    o = _opts(log2_g, assume_unit, filter_points)
+    with torch.cuda.device(points.device):
+        st = lib.sky_skyline_witness(_vp(points.data_ptr()), n, d, ld, ctypes.byref(o), _vp(out.data_ptr()), n,
+                                     ctypes.byref(cnt), _vp(wit.data_ptr()), _stream_ptr(stream))
+    _check(st)
+    return out[:cnt.value], wit[:n]
 
 
 def skyline_host(points, log2_g=None, assume_unit=False, capacity=None, stream=None, out=None):
@@ -277,6 +298,12 @@ def last_run_stats() -> dict:
     return {f: getattr(s, f) for f, _ in RunStats._fields_}
 
 
+def set_wait_limit(polls: int):
+    """sky_set_wait_limit: poll limit of the pipeline's bounded device waits
+    (a test aid for the timeout path; 0 restores the default)."""
+    _check(load().sky_set_wait_limit(int(polls)))
+
+
 def set_phase_timing(enable=True):
     """Device timing of later skyline calls on this thread: True or 1 = events
     between the phases (kernels launched one by one), 2 = events around the
@@ -342,6 +369,12 @@ class Grid:
 
     def cell_map(self):
         return self._copy(GRID_CELL_MAP, 32, _torch().float32)
+
+    def snap_rows(self, n_prop):
+        """Row of the data point each of the first n_prop proposals was
+        snapped to (-1: none), after prune(filter_points); numpy int64."""
+        v = self._copy(GRID_SNAP, 16, _torch().int64).cpu().numpy().view("u8")[:n_prop]
+        return [int(x & 0xffffffff) if x != 0xffffffffffffffff else -1 for x in v]
 
     def close(self):
         if self._h:

@@ -909,8 +909,10 @@ __global__ void __launch_bounds__(kThreads) k_snap(const float* __restrict__ pts
 #pragma unroll
         for (int k = 0; k < DP; ++k)
             if (k < d) sum = __fadd_rn(sum, x[k]);
+        // + 0.0f turns a sum of -0.0 into +0.0, so that equal sums compare
+        // equal in the packed order (ties then go to the lower row)
         const unsigned long long packed =
-            ((unsigned long long)float_to_ordered(sum) << 32) | (unsigned long long)(uint32_t)i;
+            ((unsigned long long)float_to_ordered(__fadd_rn(sum, 0.0f)) << 32) | (unsigned long long)(uint32_t)i;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
             if (j < n_prop) {

@@ -221,22 +221,23 @@ __global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict_
     }
 }
 
-template <int DP>
 // Nine CTAs per SM (40 registers a thread; the compiler's free choice of 48
 // allows eight, which measured 1 % slower on the three 10^6 x 8 sets).
+// WIT: witness mode (see refine_ptile); `wit` is unused otherwise.
+template <int DP, bool WIT>
 __global__ void __launch_bounds__(kTQ + 32, 9) k_refine(const float* __restrict__ X, const uint32_t* __restrict__ C,
                                                      const int32_t* __restrict__ ids,
                                                      const uint32_t* __restrict__ SUB,
                                                      const uint32_t* __restrict__ tend,
                                                      const uint32_t* __restrict__ supmin,
                                                      const uint32_t* __restrict__ order, DevResult* res,
-                                                     uint8_t* keep)
+                                                     uint8_t* keep, int32_t* wit)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     RefineSmem<DP>& sm = *reinterpret_cast<RefineSmem<DP>*>(smem_raw);
     const uint32_t m = res->survivors;
     if (blockIdx.x >= (m + kTQ - 1) / kTQ) return;
-    refine_ptile<DP>(sm, X, C, ids, SUB, tend, supmin, m, order[blockIdx.x], res, keep);
+    refine_ptile<DP, true, WIT>(sm, X, C, ids, SUB, tend, supmin, m, order[blockIdx.x], res, keep, wit);
 }
 
 // Ascending row ids of the kept rows (decoupled look-back over 8 rows per
@@ -326,9 +327,17 @@ cudaError_t launch_refine(const Plan& p, cudaStream_t s)
                                                                    p.supmin);
         k_cost_order<<<1, 1024, 0, s>>>(p.tile_cost, p.res, p.tile_order);
         const int smem = (int)sizeof(RefineSmem<DP>);
-        cudaFuncSetAttribute(k_refine<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_refine<DP><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, p.tile_end, p.supmin,
-                                                              p.tile_order, p.res, p.keep);
+        if (p.witness) {
+            cudaFuncSetAttribute(k_refine<DP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_refine<DP, true><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, p.tile_end,
+                                                                        p.supmin, p.tile_order, p.res, p.keep,
+                                                                        p.witness);
+        } else {
+            cudaFuncSetAttribute(k_refine<DP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_refine<DP, false><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, p.tile_end,
+                                                                         p.supmin, p.tile_order, p.res, p.keep,
+                                                                         nullptr);
+        }
     });
     return cudaGetLastError();
 }

@@ -258,8 +258,10 @@ DevResult* host_result()
 }
 
 // Enqueues steps (a)-(d) on `s` (directly, or into a graph under capture).
+// Witness mode (p.witness set; never captured): `wit_rep` is the cell scratch
+// of launch_witness_cells, run after the survivor pass.
 cudaError_t enqueue_pipeline(Plan& p, const float* prop, int n_prop, int32_t* out, int64_t capacity,
-                             cudaStream_t s, PhaseClock& clk)
+                             cudaStream_t s, PhaseClock& clk, int32_t* wit_rep = nullptr)
 {
     cudaError_t e = launch_build_params(p, s);   // clears the result block first
     clk.mark();
@@ -274,6 +276,7 @@ cudaError_t enqueue_pipeline(Plan& p, const float* prop, int n_prop, int32_t* ou
     // a survivors-only call whose buffer holds n ids receives them directly
     const bool direct = p.survivors_only && capacity >= p.n;
     if (e == cudaSuccess) e = launch_survivors(p, n_prop, s, direct ? reinterpret_cast<uint32_t*>(out) : nullptr);
+    if (e == cudaSuccess && p.witness) e = launch_witness_cells(p, wit_rep, n_prop, s);
     clk.mark();
     if (p.survivors_only) {
         if (e == cudaSuccess && !direct) e = launch_copy_survivors(p, out, capacity, s);
@@ -718,6 +721,24 @@ void plan_carve(Plan& p, void* ws, bool grid_api)
 
 void set_last_error(const char* msg) { t_err = msg ? msg : ""; }
 
+// Setters of every translation unit's wait-limit constant (registered by
+// static initialisers, so the table is a function-local static).
+struct WaitLimitTable {
+    WaitLimitSetter f[32];
+    int n = 0;
+};
+WaitLimitTable& wait_limit_table()
+{
+    static WaitLimitTable t;
+    return t;
+}
+
+void register_wait_limit_setter(WaitLimitSetter f)
+{
+    WaitLimitTable& t = wait_limit_table();
+    if (t.n < 32) t.f[t.n++] = f;
+}
+
 }  // namespace sky
 
 // ===========================================================================
@@ -749,6 +770,14 @@ const char* sky_status_string(sky_status s)
 const char* sky_last_error(void) { return t_err.c_str(); }
 
 const char* sky_version(void) { return "libsky 0.1 (sm_103a)"; }
+
+sky_status sky_set_wait_limit(uint32_t polls)
+{
+    const WaitLimitTable& t = wait_limit_table();
+    for (int i = 0; i < t.n; ++i) SKY_CUDA(t.f[i](polls));
+    SKY_CUDA(cudaDeviceSynchronize());
+    return SKY_OK;
+}
 
 sky_status sky_last_run_stats(sky_run_stats* out)
 {
@@ -859,6 +888,9 @@ sky_status sky_grid_copy_out(const sky_grid* g, sky_grid_array which, void* d_ds
             src = p.surv_idx; need = sizeof(int32_t) * (size_t)r.survivors; break;
         }
         case SKY_GRID_CELL_MAP: src = p.params; need = sizeof(float) * 32; break;
+        case SKY_GRID_SNAP:
+            if (!g->pruned) return fail(SKY_ERR_INVALID_ARGUMENT, "grid not pruned yet");
+            src = p.snap; need = sizeof(unsigned long long) * 16; break;
         default: return fail(SKY_ERR_INVALID_ARGUMENT, "unknown array %d", (int)which);
     }
     if (bytes < need) return fail(SKY_ERR_CAPACITY, "array needs %zu bytes, got %zu", need, bytes);
@@ -885,6 +917,53 @@ sky_status sky_skyline(const float* d_pts, int64_t n, int32_t d, int64_t ld, con
     if (st != SKY_OK) return st;
     return skyline_device(d_pts, n, d, ld, opt, d_out_idx, out_capacity, h_out_count,
                           static_cast<cudaStream_t>(stream));
+}
+
+sky_status sky_skyline_witness(const float* d_pts, int64_t n, int32_t d, int64_t ld, const sky_options* opt,
+                               int32_t* d_out_idx, int64_t out_capacity, int64_t* h_out_count, int32_t* d_witness,
+                               void* stream)
+{
+    t_stats = {};
+    if (!h_out_count) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL count pointer");
+    if (out_capacity < 0 || (out_capacity > 0 && !d_out_idx))
+        return fail(SKY_ERR_INVALID_ARGUMENT, "bad output buffer");
+    if (n > 0 && !d_witness) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL witness buffer");
+    if (reinterpret_cast<uintptr_t>(d_witness) & 3u) return fail(SKY_ERR_INVALID_ARGUMENT, "witness buffer not 4-byte aligned");
+    if (opt && opt->survivors_only != 0)
+        return fail(SKY_ERR_INVALID_ARGUMENT, "witnesses are defined for the skyline (survivors_only = 0)");
+    sky_status st = check_points(d_pts, n, d, ld);
+    if (st != SKY_OK) return st;
+    Inflight f;
+    st = make_plan(f.p, d_pts, n, d, ld, opt);
+    if (st != SKY_OK) return st;
+    if (n == 0) { *h_out_count = 0; return SKY_OK; }
+    Plan& p = f.p;
+    f.capacity = out_capacity;
+    f.n_prop = opt ? opt->n_filter : 0;
+    const float* prop = f.n_prop ? opt->d_filter_pts : nullptr;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    enable_pool_cache();
+    void* ws = nullptr;
+    int32_t* rep = nullptr;
+    const size_t bytes = layout(p, nullptr, false);
+    SKY_CUDA(cudaMallocAsync(&ws, bytes, s));
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rep), sizeof(int32_t) << (p.log2g * p.d), s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(ws, s);
+        return cuda_fail(e, "cudaMallocAsync(witness cells)");
+    }
+    layout(p, static_cast<char*>(ws), false);
+    p.witness = d_witness;
+    e = cudaMemsetAsync(d_witness, 0xff, sizeof(int32_t) * (size_t)n, s);   // -1: kept
+    PhaseClock clk(s, false);
+    if (e == cudaSuccess) e = enqueue_pipeline(p, prop, f.n_prop, d_out_idx, out_capacity, s, clk, rep);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&f.local, p.res, sizeof(DevResult), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(rep, s);
+    cudaFreeAsync(ws, s);
+    const cudaError_t es = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "witness-mode launch");
+    if (es != cudaSuccess) return cuda_fail(es, "stream synchronize");
+    return skyline_finish(f, h_out_count, t_stats);
 }
 
 sky_status sky_skyline_sets(sky_set* sets, int32_t count, const sky_options* opt, void* stream)

@@ -23,6 +23,27 @@ constexpr uint32_t SKY_DEV_ERR_CAPACITY = 4u;
 // Upper bound on polls of any flag or barrier (each poll may suspend briefly).
 constexpr uint32_t kWaitLimit = 1u << 22;
 
+// A smaller poll limit for the pipeline waits (those given an error word),
+// set by sky_set_wait_limit for tests of the timeout path; 0 = kWaitLimit.
+// The waits that let a CTA's own bulk copies land before it exits (no error
+// word) always keep kWaitLimit, so a short limit never leaves a copy in
+// flight. Every translation unit holds its own copy of the constant and
+// registers a setter for it; the library sets them all.
+using WaitLimitSetter = cudaError_t (*)(uint32_t);
+void register_wait_limit_setter(WaitLimitSetter f);   // sky_api.cu
+static __constant__ uint32_t c_wait_limit;
+static cudaError_t set_wait_limit_here(uint32_t v) { return cudaMemcpyToSymbol(c_wait_limit, &v, sizeof(v)); }
+struct WaitLimitRegistrar {
+    explicit WaitLimitRegistrar(WaitLimitSetter f) { register_wait_limit_setter(f); }
+};
+static const WaitLimitRegistrar g_wait_limit_registrar(&set_wait_limit_here);
+
+__device__ __forceinline__ uint32_t wait_limit(const uint32_t* err)
+{
+    const uint32_t l = err ? c_wait_limit : 0u;
+    return l ? l : kWaitLimit;
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -79,7 +100,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 // the limit runs out.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err)
 {
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    const uint32_t lim = wait_limit(err);
+    for (uint32_t i = 0; i < lim; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (i > 32) __nanosleep(64);
     }
@@ -161,11 +183,12 @@ __device__ __forceinline__ uint32_t lookback_prefix(unsigned long long* states, 
     uint32_t exclusive = 0;
     long long base = (long long)tile - 1;
     uint32_t polls = 0;
+    const uint32_t lim = wait_limit(err);
     while (true) {
         long long i = base - lane;
         unsigned long long v = (i >= 0) ? ld_acquire_u64(&states[i]) : (kFlagInc | 0ull);
         while (__any_sync(kFull, (v >> 32) == 0)) {
-            if (++polls > kWaitLimit) {
+            if (++polls > lim) {
                 if (lane == 0 && err) atomicOr(err, SKY_DEV_ERR_TIMEOUT);
                 v = kFlagInc;  // give up: the result is flagged as invalid
                 break;

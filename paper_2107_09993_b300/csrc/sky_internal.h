@@ -77,6 +77,7 @@ struct Plan {
     float* filt = nullptr;           // [16][16] snapped filter points
     unsigned long long* snap = nullptr;  // [16] packed (sum, row) argmin
     DevResult* res = nullptr;
+    int32_t* witness = nullptr;      // witness mode: [n] dominating row of every dropped point (caller's)
     // last sort output
     const uint32_t* sorted_val = nullptr;
     const uint32_t* sorted_key = nullptr;
@@ -161,6 +162,8 @@ cudaError_t launch_sort(Plan& p, cudaStream_t s);
 cudaError_t launch_gather(const Plan& p, cudaStream_t s);
 cudaError_t launch_refine(const Plan& p, cudaStream_t s);
 cudaError_t launch_emit(const Plan& p, int32_t* out, int64_t capacity, cudaStream_t s);
+// k_witness.cu: witnesses of the points step (c) dropped (rep: 2^(log2g d) ints of scratch)
+cudaError_t launch_witness_cells(const Plan& p, int32_t* rep, int n_prop, cudaStream_t s);
 
 // One batched launch (k_batched.cu): device pointers into the workspace.
 struct BatchLaunch {

@@ -50,9 +50,11 @@ void* g_scratch_dev[kMaxDevices] = {};
 
 thread_local char t_msg[256];
 
+// The message goes to both sky_noalloc_last_error() and sky_last_error().
 sky_status noalloc_fail(sky_status s, const char* msg)
 {
     snprintf(t_msg, sizeof(t_msg), "%s", msg);
+    sky::set_last_error(msg);
     return s;
 }
 
@@ -82,6 +84,7 @@ extern "C" sky_status sky_skyline_noalloc(const float* d_pts, int64_t n, int32_t
                                           int64_t* h_out_count, void* stream)
 {
     t_msg[0] = 0;
+    sky::set_last_error("");
     if (!h_out_count) return noalloc_fail(SKY_ERR_INVALID_ARGUMENT, "NULL count pointer");
     if (d < 1 || d > kMaxDim) return noalloc_fail(SKY_ERR_INVALID_ARGUMENT, "d outside [1, 16]");
     if (ld < d) return noalloc_fail(SKY_ERR_INVALID_ARGUMENT, "ld < d");

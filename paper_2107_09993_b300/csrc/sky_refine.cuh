@@ -142,12 +142,14 @@ __device__ __forceinline__ bool bytes_le(const uint32_t* lo, const uint32_t* hi)
 // against register copies of the group maxima. The batched persistent kernel
 // keeps the ring to the end and the maxima in shared memory (fewer registers:
 // measured faster there).
-template <int DP, bool SPARSE = true>
+// WIT (witness mode, a checking aid): every removal of a p by a q also writes
+// wit[row of p] = row of q, a point that dominates p (Definition 1).
+template <int DP, bool SPARSE = true, bool WIT = false>
 __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __restrict__ X,
                                              const uint32_t* __restrict__ C, const int32_t* __restrict__ ids,
                                              const uint32_t* __restrict__ SUB, const uint32_t* __restrict__ TEND,
                                              const uint32_t* __restrict__ SUPMIN, uint32_t m, uint32_t ptile,
-                                             DevResult* res, uint8_t* keep)
+                                             DevResult* res, uint8_t* keep, int32_t* wit = nullptr)
 {
     constexpr int DW = DP / 4;
     constexpr int NG = kTQ / 32;
@@ -475,6 +477,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                             if (dom) {
                                 const uint32_t bit = 1u << (pi & 31);
                                 if (atomicAnd(&sm.livemask[pi >> 5], ~bit) & bit) atomicSub(&sm.live, 1u);
+                                if constexpr (WIT) wit[ids[pbase + pi]] = ids[(int64_t)tt * kTQ + qi];
                             }
                         }
                     };
@@ -648,6 +651,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                             if (dom) {
                                 const uint32_t bit = 1u << (pi & 31);
                                 if (atomicAnd(&sm.livemask[pi >> 5], ~bit) & bit) atomicSub(&sm.live, 1u);
+                                if constexpr (WIT) wit[ids[pbase + pi]] = ids[(int64_t)tt * kTQ + j * 32 + lane];
                             }
                         }
                     }

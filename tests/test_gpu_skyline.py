@@ -114,6 +114,30 @@ def test_filter_proposals_never_change_the_result():
         assert sky.last_run_stats()["n_filter_used"] == 0
 
 
+def test_snapped_rows_match_oracle():
+    """The pre-filter's snap (k_snap) picks, per proposal, the row that the
+    oracle's restatement picks: among the points <= f, the smallest binary32
+    coordinate sum, ties to the lower row; -1 without a candidate. Includes
+    many equal sums (integer grids) and proposals below every point."""
+    rng = np.random.default_rng(21)
+    for case in range(12):
+        d = int(rng.integers(1, 17))
+        n = int(rng.integers(1, 30000))
+        if case % 3 == 2:
+            P = rng.integers(0, 4, size=(n, d)).astype(np.float32)          # heavy ties
+            F = rng.integers(0, 4, size=(16, d)).astype(np.float32)
+        else:
+            P = skydata.generate(["independent", "anticorrelated"][case % 2], n, d, seed=case)
+            F = (rng.random((16, d)) * 0.9).astype(np.float32)
+        F[3] = -1.0                                                             # snaps to nothing
+        g = sky.Grid(dev(P)).prune(dev(F))
+        got = g.snap_rows(16)
+        want = oracle.snap_rows(P, F).tolist()
+        assert got == want, (case, n, d)
+        assert g.stats()["n_filter_used"] == sum(w >= 0 for w in want)
+        g.close()
+
+
 def test_cell_grid_matches_oracle():
     """Steps (a)-(c) bit for bit: keys (Eq. 1), occupancy, dominated cells (Def. 3)."""
     rng = np.random.default_rng(12)

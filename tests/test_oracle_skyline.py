@@ -192,3 +192,24 @@ def test_quadrant_query_definition():
     # an origin below every row changes nothing
     assert oracle.skyline_subset(T, 0, 400, mask, origin=[-1, -1, -1]).tolist() == \
         oracle.skyline_subset(T, 0, 400, mask).tolist()
+
+
+def test_snap_rows_pins():
+    """oracle.snap_rows: smallest binary32 sum among the points <= f, ties to
+    the lower row, -1 without a candidate."""
+    P = np.array([[0.5, 0.5], [0.2, 0.9], [0.9, 0.1], [0.3, 0.3]], dtype=np.float32)
+    F = np.array([[0.6, 0.6], [0.1, 0.1], [1.0, 1.0], [0.9, 0.5]], dtype=np.float32)
+    # f0: rows 0 (1.0) and 3 (0.6) qualify -> 3; f1: none; f2: all, 3 smallest;
+    # f3: rows 0 (1.0), 2 (1.0), 3 (0.6) -> 3
+    assert oracle.snap_rows(P, F).tolist() == [3, -1, 3, 3]
+    # equal sums: the lower row
+    Q = np.array([[0.2, 0.3], [0.3, 0.2]], dtype=np.float32)
+    assert oracle.snap_rows(Q, [[1, 1]]).tolist() == [0]
+    # the sum is binary32 in dimension order: 1 + 2^-24 + 2^-24 rounds to 1
+    # (ties to even at each step), below 1 + 2^-23, although both are
+    # 1 + 2^-23 in exact arithmetic (where the tie would pick row 0)
+    e = np.float32(2.0 ** -24)
+    R = np.array([[np.float32(1.0) + np.float32(2.0 ** -23), 0, 0], [1.0, e, e]], dtype=np.float32)
+    assert oracle.snap_rows(R, [[2, 2, 2]]).tolist() == [1]
+    # a point equal to f qualifies (<=, not <)
+    assert oracle.snap_rows(P, [[0.9, 0.1]]).tolist() == [2]

@@ -16,6 +16,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import skydata
 
 torch = pytest.importorskip("torch")
@@ -62,6 +63,28 @@ def test_noalloc_matches_regular_entry_point_twice():
         want_u = sky.skyline(x, assume_unit=True, log2_g=lg).cpu()
         st, cnt, out = _noalloc(lib, x, n, assume_unit=True, log2_g=lg)
         assert st == 0 and torch.equal(out[:cnt].cpu(), want_u)
+
+
+def test_noalloc_matches_oracle_at_the_limits():
+    """Against the oracle directly (a fault in a kernel both entry points
+    share would pass the comparison above): small sets, and the largest
+    workspace the limits admit -- n = 65,536 points at d = 16 with a 2^16- and
+    a 2^20-cell grid (log2_g * d = 16 and 20), and d = 10 with 2^20 cells."""
+    lib = _bind(sky.load())
+    cases = [("anticorrelated", 65536, 8, None), ("anticorrelated", 129, 3, None),
+             ("anticorrelated", 65536, 16, 1), ("independent", 65536, 10, 2), ("correlated", 65536, 4, 5)]
+    for kind, n, d, lg in cases:
+        P = skydata.generate(kind, n, d, seed=n + 3 * d)
+        x = torch.from_numpy(P).cuda()
+        want = oracle.skyline_sfs(P)
+        kw = {} if lg is None else {"log2_g": lg, "assume_unit": True}
+        for call in range(2):
+            st, cnt, out = _noalloc(lib, x, n, **kw)
+            assert st == 0, (kind, n, d, lg, lib.sky_noalloc_last_error())
+            assert np.array_equal(out[:cnt].cpu().numpy(), want), (kind, n, d, lg, call)
+    # the error message also reaches sky_last_error()
+    st, cnt, out = _noalloc(lib, torch.rand((65537, 2), device="cuda"), 65537)
+    assert st == 6 and b"65536" in lib.sky_last_error()
 
 
 def test_noalloc_refuses_oversized_requests():
