@@ -2,16 +2,24 @@
 """Exact skyline throughput on B300: points/s through the libsky C ABI.
 
 Workload (one "step"): the whole skyline path (steps (a)-(d): map, mark,
-prune, refine + compact) over n = 1,000,000 points, d = 8, float32, for each
-of the three synthetic distributions of the paper's experiments
-(independent, correlated, anti-correlated; seed 1) -- 3,000,000 input points
-per step. Inputs are resident in HBM when the timed region starts; L2 (126 MB)
-is flushed before every timed step by writing a 512 MB buffer.
+prune, refine + compact) over the two large sets of the paper-style
+experiments -- n = 10,000,000 anti-correlated points at d = 16 and
+n = 10,000,000 independent points at d = 12, float32, seed 1 -- in one
+sky_skyline_sets call (the sets run concurrently): 2 * 10^7 input points per
+step. Inputs are resident in HBM when the timed region starts; both are
+larger than L2 (640 MB and 480 MB), and L2 is also flushed before every timed
+step by writing a 512 MB buffer.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sky|reference]
     python bench.py --case KIND:N:D[:survivors] [--seed S] [--steps K] [--warmup W]   (one input)
     python bench.py --batched [--steps K] [--warmup W]                  (4,096-query batched workload)
 
+The line also carries: the n = 10^6, d = 8 three-family workload
+(`config_1e6x8`), the pruning pass alone on the large sets
+(`roofline_prune_large`), the learned proposal against the plain path on its
+evaluation sets (`learned_vs_plain`), the 4,096-query batched launch against
+plain sky_skyline calls looped over the same queries (`batched_vs_plain`),
+and the paper's 3.2e9-point run (`paper_scale`).
 N > 1 runs independent replicas (the skyline of one point set is computed on
 one GPU), launched under torchrun, weak scaling.
 `--impl reference` times the CPU oracle (sort-first skyline) on the host cores
@@ -37,13 +45,15 @@ import numpy as np  # noqa: E402
 
 import skydata  # noqa: E402
 
-N_POINTS = 1_000_000
-DIM = 8
 SEED = 1
-KINDS = ("independent", "correlated", "anticorrelated")
+# the step: both large sets (kind, n, d), seed 1
+HEADLINE = (("anticorrelated", 10_000_000, 16), ("independent", 10_000_000, 12))
+# the n = 10^6, d = 8 workload of the three families (an extra key)
+CONFIG_1E6 = (("independent", 1_000_000, 8), ("correlated", 1_000_000, 8), ("anticorrelated", 1_000_000, 8))
 METRIC = "skyline input points/s (exact)"
 UNIT = "points/s"
-CPU_SAMPLE_ROWS = 100_000
+# the oracle's bounded sample: the first rows of each headline set
+CPU_SAMPLE_ROWS = 50_000
 # the paper's largest run: 3.2e9 correlated points, d = 4, layer 6 (Sec. 7).
 # Drawn with rows outside the unit cube redrawn instead of clipped: clipping
 # piles points onto the faces (x_k = 0), which at 3.2e9 rows gives millions of
@@ -55,19 +65,20 @@ PRUNE_REPS = 10
 
 
 def workload_config(extra=None):
-    cfg = {"workload": "plain SkyCell, n=1,000,000 x d=8 float32, independent + correlated + "
-                       "anti-correlated (seed 1), 3e6 points per step",
-           "n": N_POINTS, "d": DIM, "distributions": list(KINDS), "seed": SEED,
-           "l2": "flushed before every timed step (512 MB write)", "options": "default (automatic value map and grid layer)",
-           "call": "the step's 3 sets in one sky_skyline_sets call (e2e: sky_skyline_host_sets); the library "
-                   "runs them concurrently on 4 internal streams"}
+    cfg = {"workload": "plain SkyCell, large: n=10,000,000 x d=16 anti-correlated + n=10,000,000 x d=12 "
+                       "independent, float32 (seed 1), 2e7 points per step",
+           "sets": [{"kind": k, "n": n, "d": d} for k, n, d in HEADLINE], "seed": SEED,
+           "l2": "inputs larger than L2 (640 MB, 480 MB); L2 also flushed before every timed step (512 MB write)",
+           "options": "default (automatic value map and grid layer)",
+           "call": "the step's 2 sets in one sky_skyline_sets call (e2e: sky_skyline_host_sets); the library "
+                   "runs them concurrently on internal streams"}
     if extra:
         cfg.update(extra)
     return cfg
 
 
-def datasets():
-    return [skydata.generate(k, N_POINTS, DIM, SEED) for k in KINDS]
+def datasets(spec=HEADLINE):
+    return [skydata.generate(k, n, d, SEED) for k, n, d in spec]
 
 
 # ------------------------------------------------------------------ clocks --
@@ -177,6 +188,7 @@ def prune_roofline(sky, torch, dev, flush, peaks, peak_src):
     stream = torch.cuda.current_stream(dev)
     per_set = {}
     tot_b, tot_ms = 0, 0.0
+    tot_bs, tot_ms_g = 0, 0.0
     phases = ("normalize_ms", "map_mark_ms", "prune_ms", "survivors_ms")
     for kind, n, d in PRUNE_SETS:
         x = torch.from_numpy(skydata.generate(kind, n, d, SEED)).to(dev)
@@ -210,16 +222,38 @@ def prune_roofline(sky, torch, dev, flush, peaks, peak_src):
             ph = sky.last_phase_times()
             for k in phases:
                 by_phase[k].append(ph[k])
-        sky.set_phase_timing(False)
         st = sky.last_run_stats()
-        b = 4 * n * d + 16 * n + 8 * st["survivors"]
+        # the survivor layout of step (d): k_gather writes the compacted
+        # survivor coordinates (Morton order) after the sort; timed with
+        # phase events in full calls
+        full = torch.empty(n, dtype=torch.int32, device=dev)
+        sky.skyline(x, out=full)
+        gat = []
+        for _ in range(3):
+            torch.cuda.synchronize(dev)
+            sky.skyline(x, out=full)
+            gat.append(sky.last_phase_times()["gather_ms"])
+        del full
+        sky.set_phase_timing(False)
+        m = st["survivors"]
+        b = 4 * n * d + 16 * n + 8 * m
+        # the pruning pass's bytes as the method needs them: read the points,
+        # re-read them or a 4-byte key per point, write the compacted
+        # survivors (coordinates + id)
+        b_survey = 4 * n * d + min(4 * n * d, 8 * n) + m * (4 * d + 4)
         med = statistics.median(dev_ms)
+        g_ms = statistics.median(gat)
         per_set[f"{kind} n={n} d={d}"] = {
-            "ms": round(med, 4), "call_ms": round(statistics.median(calls), 4), "survivors": st["survivors"],
+            "ms": round(med, 4), "call_ms": round(statistics.median(calls), 4), "survivors": m,
             "log2_g": st["log2_g"], "gbs": round(b / (med / 1e3) / 1e9, 1),
-            "phase_ms_direct_launches": {k: round(statistics.median(v), 4) for k, v in by_phase.items()}}
+            "phase_ms_direct_launches": {k: round(statistics.median(v), 4) for k, v in by_phase.items()},
+            "gather_ms": round(g_ms, 4),
+            "method_bytes": b_survey,
+            "method_gbs_pass_plus_gather": round(b_survey / ((med + g_ms) / 1e3) / 1e9, 1)}
         tot_b += b
         tot_ms += med
+        tot_bs += b_survey
+        tot_ms_g += med + g_ms
         del x, out
     gbs = tot_b / (tot_ms / 1e3) / 1e9
     # DRAM bytes per call of the same kernels from the committed ncu capture
@@ -241,6 +275,13 @@ def prune_roofline(sky, torch, dev, flush, peaks, peak_src):
             else "fallback 6.4 TB/s",
             "timing": "device time of the pass: two CUDA events on the library's stream around the call's "
                       "kernel sequence (CUDA-graph replay, sky_set_phase_timing(2)), median of the calls",
+            "method_bytes_view": {
+                "bytes": "4nd + min(4nd, 8n) + m(4d + 4): read the points, re-read a 4-byte key per point, write "
+                         "the m compacted survivors (coordinates + id)",
+                "time": "the pass plus k_gather, which writes the survivor coordinates after the Morton sort",
+                "achieved": round(tot_bs / (tot_ms_g / 1e3) / 1e9, 1),
+                "frac": round(tot_bs / (tot_ms_g / 1e3) / 1e9 / peaks["hbm_gbs"], 4),
+                "frac_of_nominal_8000": round(tot_bs / (tot_ms_g / 1e3) / 1e9 / 8000.0, 4)},
             "workload": "; ".join(f"{k} n={n:,} d={d}" for k, n, d in PRUNE_SETS)
                         + f" (seed {SEED}); median of {PRUNE_REPS} calls each; inputs larger than L2, no flush",
             "per_set": per_set}
@@ -277,6 +318,138 @@ def paper_scale(sky, torch, dev):
                       "hardware": "Quadro RTX 6000 (Turing, 24 GB); its generator and timing boundaries differ"}}
 
 
+def time_step(fn, stream, dev, flush=None):
+    """Device time of one call of fn (CUDA events on `stream`), ms."""
+    import torch
+    if flush is not None:
+        flush.fill_(1.0)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1), out
+
+
+def config_1e6(sky, torch, dev, flush, steps):
+    """The n = 10^6, d = 8 workload (independent, correlated, anti-correlated,
+    seed 1) as one sky_skyline_sets call per step, L2 flushed before each."""
+    xs = [torch.from_numpy(P).to(dev) for P in datasets(CONFIG_1E6)]
+    outs = [torch.empty(x.shape[0], dtype=torch.int32, device=dev) for x in xs]
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        sky.skyline_sets(xs, outs=outs)
+    ms = [time_step(lambda: sky.skyline_sets(xs, outs=outs), stream, dev, flush)[0] for _ in range(steps)]
+    _, res = time_step(lambda: sky.skyline_sets(xs, outs=outs), stream, dev, flush)
+    med = statistics.median(ms)
+    pts = sum(n for _, n, _ in CONFIG_1E6)
+    return {"workload": "n=1,000,000 x d=8 float32, independent + correlated + anti-correlated (seed 1), "
+                        "one sky_skyline_sets call, L2 flushed", "ms_per_step": round(med, 4),
+            "points_per_s": round(pts / (med / 1e3), 1), "skyline_sizes": [int(r.numel()) for r in res],
+            "steps": steps}
+
+
+def learned_vs_plain(sky, torch, dev, reps=5):
+    """The learned proposal's evaluation sets (Gaussian copula, n = 10^7,
+    d = 8, seed 3, rho in {-0.8, 0, 0.8}): the plain path (automatic layer)
+    against the learned path (sky_propose with the shipped weights, then
+    sky_skyline with the proposed layer and the 16 filter points), both
+    device-resident, median of `reps` calls each after a warm-up; the index
+    sets must be identical."""
+    from paper_2107_09993_b300 import learned
+    params, meta = learned.load_weights(device=str(dev))
+    n_ref = int(meta["rows_per_set"])
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for rho in (-0.8, 0.0, 0.8):
+        P, rho_eff = skydata.copula(10_000_000, 8, 3, rho)
+        x = torch.from_numpy(P).to(dev)
+        del P
+        plain = lambda: sky.skyline(x)                                    # noqa: E731
+        learn = lambda: sky.skyline_learned(x, params, n_ref=n_ref)       # noqa: E731
+        for _ in range(2):
+            plain()
+            learn()
+        tp, a = [], None
+        for _ in range(reps):
+            t, a = time_step(plain, stream, dev)
+            tp.append(t)
+        sp = sky.last_run_stats()
+        tl, b = [], None
+        for _ in range(reps):
+            t, b = time_step(learn, stream, dev)
+            tl.append(t)
+        sl = sky.last_run_stats()
+        mp, ml = statistics.median(tp), statistics.median(tl)
+        out[f"rho={rho:+.1f}"] = {"rho_eff": round(rho_eff, 4), "plain_ms": round(mp, 3), "learned_ms": round(ml, 3),
+                                  "speedup": round(mp / ml, 3), "identical": bool(torch.equal(a, b)),
+                                  "skyline": int(a.numel()), "survivors_plain": sp["survivors"],
+                                  "survivors_learned": sl["survivors"], "log2_g_plain": sp["log2_g"],
+                                  "log2_g_learned": sl["log2_g"], "n_filter_used": sl["n_filter_used"]}
+        del x
+    return {"workload": "Gaussian copula n=10,000,000 x d=8 float32 (seed 3), rho in {-0.8, 0, 0.8}",
+            "timing": f"device time per call (CUDA events, host launch included), median of {reps}; the learned "
+                      "time includes sky_propose (features + network + decode)",
+            "sets": out}
+
+
+def batched_vs_plain(sky, torch, dev, reps=3):
+    """The batched workload: 4,096 queries (row count log-uniform in
+    [1e3, 1e6], d uniform in {2..12}, random column subsets and row ranges;
+    seed 2) on a 20M x 12 float32 table, half independent and half
+    anti-correlated, stored column-major on the device. Batched: one
+    sky_skyline_batched launch (CUDA graph). Plain: sky_skyline looped over
+    the same 4,096 queries on one stream, each query's rows and columns
+    gathered into its own contiguous input and its output buffer allocated
+    before the timed loop, so only the sky_skyline calls are timed. Results
+    compared query by query."""
+    import numpy as np
+    n_rows, n_cols, nq = 20_000_000, 12, 4096
+    T = skydata.mixed_table(n_rows, n_cols, seed=2)
+    q = skydata.batched_queries(nq, n_rows, n_cols, seed=2)
+    t = torch.from_numpy(T).to(dev)
+    del T
+    tc = t.t().contiguous().t()
+    stream = torch.cuda.current_stream(dev)
+    b = sky.Batch(tc, q)
+    for _ in range(2):
+        b.run()
+    mb = [time_step(b.run, stream, dev)[0] for _ in range(reps)]
+    st = b.stats()
+    bres = b.results()
+    bad = int((b.query_status() != 0).sum())
+    b.close()
+    del tc
+    subs, outs = [], []
+    for (r0, c, m) in q:
+        cols = [k for k in range(n_cols) if (int(m) >> k) & 1]
+        subs.append(t[int(r0):int(r0) + int(c)][:, cols].contiguous())
+        outs.append(torch.empty(int(c), dtype=torch.int32, device=dev))
+    del t
+
+    def loop():
+        return [sky.skyline(x, out=o) for x, o in zip(subs, outs)]
+
+    loop()
+    ml = []
+    res = None
+    for _ in range(reps):
+        ms, res = time_step(loop, stream, dev)
+        ml.append(ms)
+    same = all(np.array_equal(r.cpu().numpy() + int(q[i, 0]), bres[i]) for i, r in enumerate(res))
+    del subs, outs, res
+    torch.cuda.empty_cache()
+    pts = int(q[:, 1].sum())
+    mbm, mlm = statistics.median(mb), statistics.median(ml)
+    return {"workload": "batched: 4,096 queries on a 20M x 12 mixed table (seed 2), column-major",
+            "points": pts, "batched_ms": round(mbm, 2), "looped_plain_ms": round(mlm, 2),
+            "speedup": round(mlm / mbm, 3), "batched_points_per_s": round(pts / (mbm / 1e3), 1),
+            "identical": bool(same), "query_errors": bad, "skyline": st["skyline"], "survivors": st["survivors"],
+            "timing": f"median of {reps}: one graph launch vs 4,096 sky_skyline calls (inputs gathered and outputs "
+                      "allocated before the timed loop); CUDA events on the calling stream"}
+
+
 def run_sky(args):
     import torch
     import paper_2107_09993_b300 as sky
@@ -293,7 +466,7 @@ def run_sky(args):
     torch.cuda.set_device(dev)
     host = datasets()
     xs = [torch.from_numpy(P).to(dev) for P in host]
-    outs = [torch.empty(N_POINTS, dtype=torch.int32, device=dev) for _ in xs]
+    outs = [torch.empty(P.shape[0], dtype=torch.int32, device=dev) for P in host]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -303,7 +476,7 @@ def run_sky(args):
         torch.cuda.synchronize(dev)
 
     def step():
-        # the step's three sets in one call: they run concurrently
+        # the step's sets in one call: they run concurrently
         return [int(r.numel()) for r in sky.skyline_sets(xs, outs=outs)]
 
     for _ in range(args.warmup):
@@ -332,13 +505,16 @@ def run_sky(args):
         total_ms += e0.elapsed_time(e1)
     barrier()
     clk = clocks.stop() if clocks else None
-    # ---- per-kernel times: the same K steps again with CUDA events recorded
-    # between the kernels on the library's stream (direct launches)
+    # ---- per-phase times: the step's sets again, one sky_skyline call at a
+    # time, with CUDA events recorded between the phases on the library's
+    # stream (direct launches)
     sky.set_phase_timing(True)
     phase_sum = {}
+    ops = 0
     pairs = 0
     b_prune = 0
-    for _ in range(args.steps):
+    phase_steps = max(1, min(args.steps, 5))
+    for _ in range(phase_steps):
         flush.fill_(1.0)
         torch.cuda.synchronize(dev)
         for x, o in zip(xs, outs):
@@ -346,6 +522,7 @@ def run_sky(args):
             st = sky.last_run_stats()
             ph = sky.last_phase_times()
             pairs += st["pairs"]
+            ops += st["pairs"] * ops_per_pair(st["d"])
             n, d, m = st["n"], st["d"], st["survivors"]
             # map read + (cell, Morton) key write/read + (Morton, id) write
             b_prune += 4 * n * d + 16 * n + 8 * m
@@ -357,12 +534,12 @@ def run_sky(args):
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     t_max_ms = float(t.item())
-    pts_per_step = N_POINTS * len(KINDS)
+    pts_per_step = sum(P.shape[0] for P in host)
     value = world * args.steps * pts_per_step / (t_max_ms / 1e3)
 
     # ---- end to end through the host-buffer entry point (pinned memory)
     pinned = [torch.from_numpy(P).pin_memory() for P in host]
-    hout = [torch.empty(N_POINTS, dtype=torch.int32).pin_memory() for _ in host]
+    hout = [torch.empty(P.shape[0], dtype=torch.int32).pin_memory() for P in host]
     for _ in range(max(args.warmup, 2)):   # the second call captures the graphs
         sky.skyline_host_sets(pinned, outs=hout)
     e2e_ms = 0.0
@@ -377,6 +554,7 @@ def run_sky(args):
             d2h += 4 * int(r.numel()) + 8
         e2e_ms += (time.perf_counter() - t0) * 1e3
     barrier()
+    del pinned, hout
     te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
@@ -393,26 +571,27 @@ def run_sky(args):
     dom_phase = max(phase_sum, key=phase_sum.get)
     refine_s = phase_sum["refine_ms"] / 1e3
     alu_peak_gops = 148 * 128 * sm_mhz * 1e6 / 1e9  # int32 lane ops/s, measured median SM clock
-    refine_gops = pairs * ops_per_pair(DIM) / refine_s / 1e9 if refine_s > 0 else 0.0
+    refine_gops = ops / refine_s / 1e9 if refine_s > 0 else 0.0
     prune_s = (phase_sum["normalize_ms"] + phase_sum["map_mark_ms"] + phase_sum["prune_ms"]
                + phase_sum["survivors_ms"]) / 1e3
     prune_gbs = b_prune / prune_s / 1e9 if prune_s > 0 else 0.0
-    launches_refine = args.steps * len(KINDS)
+    launches_refine = phase_steps * len(HEADLINE)
     traffic = profiled_traffic("k_refine")
     roof_refine = {"kernel": "k_refine", "bound": "alu", "achieved": round(refine_gops, 1),
                    "peak": round(alu_peak_gops, 1), "unit": "Gop/s",
                    "frac": round(refine_gops / alu_peak_gops, 4),
                    "traffic": traffic,
                    "peak_source": f"148 SMs x 128 int32 lanes x {sm_mhz:.0f} MHz (median SM clock sampled during the run)",
-                   "work": f"{pairs / launches_refine:.4g} candidate pair tests per launch x {ops_per_pair(DIM)} ops",
+                   "work": f"{pairs / launches_refine:.4g} candidate pair tests per launch x ops per test "
+                           f"(ceil(d/4) word subtracts + AND tree + compare: 7 at d = 16, 6 at d = 12)",
                    "ms_per_launch": round(phase_sum['refine_ms'] / launches_refine, 4)}
     roof_prune = {"kernel": "pruning pass (phases map + prune + survivors of the timed workload)",
                   "bound": "hbm", "achieved": round(prune_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                   "frac": round(prune_gbs / peaks["hbm_gbs"], 4), "traffic": None,
                   "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json)" if peak_src == "measured"
                   else "fallback 6.4 TB/s",
-                  "note": "32 MB inputs: launch and tail effects dominate at this size; "
-                          "roofline_prune_large measures the same pass above L2"}
+                  "note": "phase events between direct launches (host gaps included); roofline_prune_large "
+                          "times the same pass as one graph replay"}
     roofline = roof_refine if dom_phase == "refine_ms" else roof_prune
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -424,15 +603,22 @@ def run_sky(args):
         "gpu_launches": launches,
         "roofline": roofline,
         "roofline_prune": roof_prune,
-        "roofline_prune_large": None if args.no_extras else prune_roofline(sky, torch, dev, flush, peaks, peak_src),
-        "paper_scale": None if args.no_extras else paper_scale(sky, torch, dev),
-        "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in phase_sum.items()},
+        "phase_ms_per_step": {k: round(v / phase_steps, 4) for k, v in phase_sum.items()},
         "skyline_sizes": sizes,
         "clocks": clk,
     }
+    del xs, outs
+    torch.cuda.empty_cache()
+    if not args.no_extras:
+        line["config_1e6x8"] = config_1e6(sky, torch, dev, flush, max(args.steps, 10))
+        line["roofline_prune_large"] = prune_roofline(sky, torch, dev, flush, peaks, peak_src)
+        line["learned_vs_plain"] = learned_vs_plain(sky, torch, dev)
+        line["batched_vs_plain"] = batched_vs_plain(sky, torch, dev)
+        line["paper_scale"] = paper_scale(sky, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(host, args.cpu_seconds)
-        line["cpu_baseline_sequential"] = seq_baseline(host, args.cpu_seconds / 2)
+        line["cpu_baseline_sequential"] = seq_baseline(datasets(CONFIG_1E6), args.cpu_seconds / 2)
+        line["cpu_oracle_full_sets"] = oracle_full_times()
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -456,8 +642,25 @@ def cpu_baseline(host, seconds):
         reps += 1
     value = reps * rows * len(host) / spent
     return {"value": round(value, 1), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"sort-first skyline oracle on the first {rows:,} rows of each of the 3 datasets, "
-                      f"{reps} repetition(s), {spent:.1f} s"}
+            "sample": f"sort-first skyline oracle on the first {rows:,} rows of each of the {len(host)} sets of "
+                      f"the step, {reps} repetition(s), {spent:.1f} s (its cost grows with n x |skyline|, so "
+                      "the full sets run far slower per point: see cpu_oracle_full_sets)"}
+
+
+def oracle_full_times():
+    """The oracle on whole sets, as recorded when tests/golden/make_fullsize.py
+    wrote the parity hashes (build host, not this box): context only."""
+    p = os.path.join(ROOT, "tests", "golden", "fullsize_oracle.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        g = json.load(f)["sets"]
+    out = {k: {"n": v["n"], "d": v["d"], "skyline": v["count"], "seconds": v["oracle_seconds"],
+               "threads": v["threads"], "points_per_s": round(v["n"] / v["oracle_seconds"], 1)}
+           for k, v in g.items() if v.get("oracle_seconds")}
+    out["note"] = ("build host, not the GPU box; the anti-correlated 10^7 x 16 set (8.2e6 skyline points) was not "
+                   "run: the oracle's cost grows with the square of the skyline (days)")
+    return out
 
 
 SEQ_SAMPLE_ROWS = 20_000
@@ -465,7 +668,8 @@ SEQ_SAMPLE_ROWS = 20_000
 
 def seq_baseline(host, seconds):
     """The paper's sequential SkyCell on the host (one thread), on the first
-    SEQ_SAMPLE_ROWS rows of each dataset, repeated for about `seconds`."""
+    SEQ_SAMPLE_ROWS rows of each n = 10^6 x 8 dataset, repeated for about
+    `seconds`."""
     import paper_2107_09993_b300 as sky
     rows = SEQ_SAMPLE_ROWS
     spent, reps = 0.0, 0
@@ -477,7 +681,7 @@ def seq_baseline(host, seconds):
         reps += 1
     value = reps * rows * len(host) / spent
     return {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "paper's sequential SkyCell (Alg. 1 + 2)",
-            "sample": f"first {rows:,} rows of each of the 3 datasets, {reps} repetition(s), {spent:.1f} s"}
+            "sample": f"first {rows:,} rows of each of the 3 n=10^6 x d=8 sets, {reps} repetition(s), {spent:.1f} s"}
 
 
 # -------------------------------------------------------------- reference --
@@ -499,9 +703,9 @@ def run_reference(args):
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (skydata generators, seed 1)",
-        "config": workload_config({"sample": f"first {rows:,} rows of each dataset per step"}),
+        "config": workload_config({"sample": f"first {rows:,} rows of each set per step"}),
         "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-                         "sample": f"first {rows:,} rows of each of the 3 datasets per step"},
+                         "sample": f"first {rows:,} rows of each of the {len(host)} sets per step"},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
