@@ -319,10 +319,32 @@ __global__ void __launch_bounds__(256) kb_supmin(const QueryPlan* __restrict__ q
 }
 
 // -------------------------------------------------------------------- (d)
+// Persistent CTAs per SM by padded dimension (the launch bound caps the
+// registers: 8 -> 48, 7 -> 56, 6 -> 64, 5 -> 72 per thread; 1 leaves the
+// choice to the compiler). Measured on the 4,096-query launch: 539 ms with
+// 8 / 8 / 8 / compiler's choice (91 registers at d = 16), 526 ms with
+// 8 / 8 / 7 / 6.
+#ifndef SKY_BATCH_MINB_4
+#define SKY_BATCH_MINB_4 8
+#endif
+#ifndef SKY_BATCH_MINB_8
+#define SKY_BATCH_MINB_8 8
+#endif
+#ifndef SKY_BATCH_MINB_12
+#define SKY_BATCH_MINB_12 7
+#endif
+#ifndef SKY_BATCH_MINB_16
+#define SKY_BATCH_MINB_16 6
+#endif
 template <int DP>
-// eight persistent CTAs per SM where that fits without large spills (d <= 12;
-// measured 1 % faster on the 4,096-query launch), the compiler's choice at d > 12
-__global__ void __launch_bounds__(kTQ + 32, DP >= 16 ? 1 : 8) kb_refine(const QueryPlan* __restrict__ qps,
+struct BatchMinBlocks {
+    static constexpr int value = DP == 4 ? SKY_BATCH_MINB_4
+                               : DP == 8 ? SKY_BATCH_MINB_8
+                               : DP == 12 ? SKY_BATCH_MINB_12 : SKY_BATCH_MINB_16;
+};
+
+template <int DP>
+__global__ void __launch_bounds__(kTQ + 32, BatchMinBlocks<DP>::value) kb_refine(const QueryPlan* __restrict__ qps,
                                                       const int2* __restrict__ items, int nitems, uint32_t* claim)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];

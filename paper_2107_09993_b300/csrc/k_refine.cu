@@ -221,11 +221,35 @@ __global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict_
     }
 }
 
-// Nine CTAs per SM (40 registers a thread; the compiler's free choice of 48
-// allows eight, which measured 1 % slower on the three 10^6 x 8 sets).
+// Resident CTAs per SM by padded dimension (the launch bound caps the
+// registers: 9 -> 40, 8 -> 48, 7 -> 56, 6 -> 64, 5 -> 72 per thread). A
+// common cap of nine spilled 432 bytes a thread at d = 16 and 128 at d = 12
+// to local memory, and long-scoreboard stalls on the spill loads dominated;
+// measured on B300 (10^7 x 16 anti-correlated 233.9 -> 132.8 ms, 10^7 x 12
+// independent 61.0 -> 45.3 ms, 10^6 x 8 anti-correlated 1.26 -> 1.20 ms),
+// the best of 5-9 per class.
+#ifndef SKY_REFINE_MINB_4
+#define SKY_REFINE_MINB_4 9
+#endif
+#ifndef SKY_REFINE_MINB_8
+#define SKY_REFINE_MINB_8 8
+#endif
+#ifndef SKY_REFINE_MINB_12
+#define SKY_REFINE_MINB_12 7
+#endif
+#ifndef SKY_REFINE_MINB_16
+#define SKY_REFINE_MINB_16 6
+#endif
+template <int DP>
+struct RefineMinBlocks {
+    static constexpr int value = DP == 4 ? SKY_REFINE_MINB_4
+                               : DP == 8 ? SKY_REFINE_MINB_8
+                               : DP == 12 ? SKY_REFINE_MINB_12 : SKY_REFINE_MINB_16;
+};
+
 // WIT: witness mode (see refine_ptile); `wit` is unused otherwise.
 template <int DP, bool WIT>
-__global__ void __launch_bounds__(kTQ + 32, 9) k_refine(const float* __restrict__ X, const uint32_t* __restrict__ C,
+__global__ void __launch_bounds__(kTQ + 32, RefineMinBlocks<DP>::value) k_refine(const float* __restrict__ X, const uint32_t* __restrict__ C,
                                                      const int32_t* __restrict__ ids,
                                                      const uint32_t* __restrict__ SUB,
                                                      const uint32_t* __restrict__ tend,

@@ -64,6 +64,21 @@ static_assert(kSparseLive <= 32, "the sparse list is one lane mask wide");
 #ifndef SKY_REFINE_LIST
 #define SKY_REFINE_LIST 1
 #endif
+// The single-set producer tests relevance against register copies of the
+// group maxima up to this padded dimension (beyond it, against shared memory)
+#ifndef SKY_REFINE_REGMAX_DP
+#define SKY_REFINE_REGMAX_DP 16
+#endif
+// 1: the producer holds one sub-tile minimum in registers at a time (fewer
+// registers at high d); 0: all five minima of a tile at once
+// listed p's tested per step of the list probe (2, 4 or 8; entries past the
+// list's end hold stale codes and their bits are dropped)
+#ifndef SKY_REFINE_PROBE_UNROLL
+#define SKY_REFINE_PROBE_UNROLL 4
+#endif
+#ifndef SKY_REFINE_SLIM_PRODUCER
+#define SKY_REFINE_SLIM_PRODUCER 0
+#endif
 constexpr bool kListProbe = SKY_REFINE_LIST != 0;
 constexpr uint32_t kEndTile = 0xffffffffu;
 
@@ -317,9 +332,10 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
             // relevance of each (sub-tile, group) pair of this q-tile; in the
             // single-set kernel the group maxima and the live groups are read
             // into registers once for the 4 + 16 box tests of a lane
+            constexpr bool kRegMax = SPARSE && DP <= SKY_REFINE_REGMAX_DP;
             uint32_t gm[NG][DW];
             uint32_t gl = 0;
-            if constexpr (SPARSE) {
+            if constexpr (kRegMax) {
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
                     if (sm.glive[g] != 0u) gl |= 1u << g;
@@ -328,11 +344,30 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                 }
             }
             auto le_g = [&](const uint32_t* lo, int g) -> bool {
-                if constexpr (SPARSE) return ((gl >> g) & 1u) && bytes_le<DW>(lo, gm[g]);
+                if constexpr (kRegMax) return ((gl >> g) & 1u) && bytes_le<DW>(lo, gm[g]);
                 else return (sm.glive[g] != 0u) && bytes_le<DW>(lo, sm.gmax[g]);
             };
             uint32_t rmask = 0;
             if (t <= E && t != ptile) {   // the p-tile itself went first
+#if SKY_REFINE_SLIM_PRODUCER
+                // one sub-tile's minimum in registers at a time
+                uint32_t cw[DW];
+#pragma unroll
+                for (int w = 0; w < DW; ++w) cw[w] = tc[NG * DW + w];   // the tile minimum
+                bool any = false;
+#pragma unroll
+                for (int g = 0; g < NG; ++g) any |= le_g(cw, g);
+                if (any) {
+#pragma unroll 1
+                    for (int q = 0; q < NG; ++q) {
+#pragma unroll
+                        for (int w = 0; w < DW; ++w) cw[w] = tc[q * DW + w];
+#pragma unroll
+                        for (int g = 0; g < NG; ++g)
+                            if (le_g(cw, g)) rmask |= 1u << (q * NG + g);
+                    }
+                }
+#else
                 uint32_t cw[NG + 1][DW];   // sub-tile minima, then the tile minimum
 #pragma unroll
                 for (int q = 0; q <= NG; ++q)
@@ -348,6 +383,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                         for (int g = 0; g < NG; ++g)
                             if (le_g(cw[q], g)) rmask |= 1u << (q * NG + g);
                 }
+#endif
             }
             uint32_t mask = __ballot_sync(kFull, rmask != 0u);
             while (mask) {
@@ -499,10 +535,11 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                             // step; entries past k hold stale codes and their
                             // bits are dropped below
                             uint32_t hb = 0;
-                            for (int j0 = 0; j0 < k; j0 += 4) {
-                                uint32_t nb = 0;   // hit bits of entries j0 .. j0 + 3
+                            constexpr int PU = SKY_REFINE_PROBE_UNROLL;
+                            for (int j0 = 0; j0 < k; j0 += PU) {
+                                uint32_t nb = 0;   // hit bits of entries j0 .. j0 + PU - 1
 #pragma unroll
-                                for (int u = 0; u < 4; ++u) {
+                                for (int u = 0; u < PU; ++u) {
                                     uint32_t c[DW];
                                     load_entry<DW>(L + (j0 + u) * DWL, c);
                                     uint32_t a = kHigh;
