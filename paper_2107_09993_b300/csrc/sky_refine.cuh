@@ -71,6 +71,14 @@ static_assert(kSparseLive <= 32, "the sparse list is one lane mask wide");
 #endif
 // 1: the producer holds one sub-tile minimum in registers at a time (fewer
 // registers at high d); 0: all five minima of a tile at once
+// Fast codes: the list probe first compares 3-bit codes (the top three bits
+// of the 7-bit codes, eight dimensions to a 32-bit word with a guard bit per
+// nibble) and runs the 7-bit test only on the pairs that pass -- a necessary
+// condition, so nothing is lost. Used from this padded dimension up; beyond
+// the compile-time maximum, off.
+#ifndef SKY_REFINE_FAST_MIN_DP
+#define SKY_REFINE_FAST_MIN_DP 16
+#endif
 // listed p's tested per step of the list probe (2, 4 or 8; entries past the
 // list's end hold stale codes and their bits are dropped)
 #ifndef SKY_REFINE_PROBE_UNROLL
@@ -85,11 +93,15 @@ constexpr uint32_t kEndTile = 0xffffffffu;
 template <int DP>
 struct RefineSmem {
     static constexpr int DW = DP / 4;
-    static constexpr int DWL = DW == 3 ? 4 : DW;   // list entry words (vector loads)
+    static constexpr bool kFast = DP >= SKY_REFINE_FAST_MIN_DP;
+    static constexpr int FW = (DP + 7) / 8;        // fast-code words
+    // list entry words (vector loads): fast codes, or the 7-bit codes
+    static constexpr int DWL = kFast ? FW : (DW == 3 ? 4 : DW);
     // bulk-copy destinations: 16-byte aligned whatever the ring depth
     alignas(16) uint32_t qC[kRingStages][kTQ * DW];  // streamed q-tiles (codes)
     alignas(16) float pX[kTQ * DP];      // own p coordinates (exact tests)
     uint32_t pP[kTQ * DW];               // own p codes | 0x80 per byte
+    uint32_t pF[kFast ? kTQ * FW : 1];   // own p fast codes | 0x8 per nibble
     uint32_t livemask[kTQ / 32];         // bit l of word g: p g*32+l is still undominated
     uint32_t gmax[kTQ / 32][DW];         // byte-wise max code of each group's live p's | 0x80 per byte (producer)
     uint32_t glive[kTQ / 32];            // live p's per group (producer)
@@ -100,7 +112,10 @@ struct RefineSmem {
     uint64_t empty[kRingStages];
     alignas(16) uint32_t stc[2][32 * kSubSlots * DW];   // producer: codes of the 32 tiles of a super-tile
     uint64_t cbar[2];                        // producer: their bulk copies
-    alignas(16) uint32_t plist[kTQ / 32][32 * DWL];   // consumer warp w: codes of the listed p's
+    // consumer warp w: codes of the listed p's (in sparse mode, the whole
+    // array holds one list of up to 32 entries of 7-bit codes)
+    alignas(16) uint32_t plist[kTQ / 32][32 * (DWL > 1 ? DWL : 2)];
+    static_assert((kTQ / 32) * 32 * (DWL > 1 ? DWL : 2) >= 32 * (DW == 3 ? 4 : DW), "sparse list fits");
     uint8_t pidx[kTQ / 32][32];                        // and their indices in the tile
     uint32_t live;                       // live p's of the CTA
     uint32_t sparse;                     // 1: the scan continues in sparse mode
@@ -125,6 +140,18 @@ __device__ __forceinline__ void load_entry(const uint32_t* e, uint32_t (&c)[DW])
         c[0] = e[0];
     }
 }
+
+// Fast code word f of a point from its 7-bit code words: nibble b of the
+// low half-byte holds code(8f + b) >> 4, nibble b of the high half-byte
+// code(8f + 4 + b) >> 4 (three bits each, bit 3 clear).
+template <int DW>
+__device__ __forceinline__ uint32_t fast_word(const uint32_t (&c)[DW], int f)
+{
+    const uint32_t lo = (c[2 * f] >> 4) & 0x07070707u;
+    const uint32_t hi = (2 * f + 1 < DW) ? ((c[2 * f + 1] >> 4) & 0x07070707u) : 0u;
+    return lo | (hi << 4);
+}
+constexpr uint32_t kHighNib = 0x88888888u;
 
 __device__ __forceinline__ uint32_t has_zero_byte(uint32_t x)
 {
@@ -176,8 +203,16 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
     const int64_t pbase = (int64_t)ptile * kTQ;
     if (tid < kTQ) {
         const bool valid = pbase + tid < m;
+        uint32_t pc[DW];
 #pragma unroll
-        for (int w = 0; w < DW; ++w) sm.pP[tid * DW + w] = C[(pbase + tid) * DW + w] | kHigh;
+        for (int w = 0; w < DW; ++w) {
+            pc[w] = C[(pbase + tid) * DW + w];
+            sm.pP[tid * DW + w] = pc[w] | kHigh;
+        }
+        if constexpr (RefineSmem<DP>::kFast) {
+#pragma unroll
+            for (int f = 0; f < RefineSmem<DP>::FW; ++f) sm.pF[tid * RefineSmem<DP>::FW + f] = fast_word<DW>(pc, f) | kHighNib;
+        }
 #pragma unroll
         for (int k = 0; k < DP; k += 4)
             *reinterpret_cast<float4*>(&sm.pX[tid * DP + k]) =
@@ -470,6 +505,13 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                 uint32_t Q[DW];
 #pragma unroll
                 for (int w = 0; w < DW; ++w) Q[w] = sm.qC[s][qi * DW + w];
+                constexpr bool kFast = RefineSmem<DP>::kFast;
+                constexpr int FW = RefineSmem<DP>::FW;
+                uint32_t QF[FW];
+                if constexpr (kFast) {
+#pragma unroll
+                    for (int f = 0; f < FW; ++f) QF[f] = fast_word<DW>(Q, f);
+                }
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
                     if (!((gm >> g) & 1u)) continue;   // no live p of group g within reach
@@ -525,8 +567,13 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                             uint32_t* L = sm.plist[warp];
                             if ((mask >> lane) & 1u) {
                                 const int rank = __popc(mask & ((1u << lane) - 1u));
+                                if constexpr (kFast) {
 #pragma unroll
-                                for (int w = 0; w < DW; ++w) L[rank * DWL + w] = sm.pP[pg * DW + w];
+                                    for (int f = 0; f < FW; ++f) L[rank * DWL + f] = sm.pF[pg * FW + f];
+                                } else {
+#pragma unroll
+                                    for (int w = 0; w < DW; ++w) L[rank * DWL + w] = sm.pP[pg * DW + w];
+                                }
                                 sm.pidx[warp][rank] = (uint8_t)pg;
                             }
                             __syncwarp();
@@ -540,12 +587,21 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                                 uint32_t nb = 0;   // hit bits of entries j0 .. j0 + PU - 1
 #pragma unroll
                                 for (int u = 0; u < PU; ++u) {
-                                    uint32_t c[DW];
-                                    load_entry<DW>(L + (j0 + u) * DWL, c);
-                                    uint32_t a = kHigh;
+                                    if constexpr (kFast) {
+                                        uint32_t c[FW];
+                                        load_entry<FW>(L + (j0 + u) * DWL, c);
+                                        uint32_t a = kHighNib;
 #pragma unroll
-                                    for (int w = 0; w < DW; ++w) a &= c[w] - Q[w];
-                                    if (a == kHigh) nb |= 1u << u;
+                                        for (int f = 0; f < FW; ++f) a &= c[f] - QF[f];
+                                        if (a == kHighNib) nb |= 1u << u;
+                                    } else {
+                                        uint32_t c[DW];
+                                        load_entry<DW>(L + (j0 + u) * DWL, c);
+                                        uint32_t a = kHigh;
+#pragma unroll
+                                        for (int w = 0; w < DW; ++w) a &= c[w] - Q[w];
+                                        if (a == kHigh) nb |= 1u << u;
+                                    }
                                 }
                                 hb |= nb << j0;
                             }
@@ -587,7 +643,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
     if (SPARSE && kSparseLive > 0 && sm.sparse && !sm.failed && sm.live != 0u) {
         // ---------------------------------------------------------- sparse mode
         constexpr int NW = NG + 1;                        // all five warps
-        constexpr int DWL = RefineSmem<DP>::DWL;
+        constexpr int DWL = DW == 3 ? 4 : DW;             // 7-bit code words per sparse-list entry
         uint32_t* LC = sm.plist[0];                       // the consumers' lists are free now
         uint8_t* LI = sm.pidx[0];
         if (warp == 0) {
