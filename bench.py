@@ -412,13 +412,22 @@ def batched_vs_plain(sky, torch, dev, reps=3):
     del T
     tc = t.t().contiguous().t()
     stream = torch.cuda.current_stream(dev)
+    # library defaults, then the autotuner's cached choices for this GPU
+    # (tune.py; Batch applies them by default)
+    b0 = sky.Batch(tc, q, tuning=None)
+    for _ in range(2):
+        b0.run()
+    mb0 = [time_step(b0.run, stream, dev)[0] for _ in range(reps)]
+    b0.close()
     b = sky.Batch(tc, q)
+    tuned = b.tuning is not None
     for _ in range(2):
         b.run()
     mb = [time_step(b.run, stream, dev)[0] for _ in range(reps)]
     st = b.stats()
     bres = b.results()
     bad = int((b.query_status() != 0).sum())
+    knobs = {k: v for k, v in (b.tuning or {}).items() if k != "log2g"}
     b.close()
     del tc
     subs, outs = [], []
@@ -443,6 +452,8 @@ def batched_vs_plain(sky, torch, dev, reps=3):
     pts = int(q[:, 1].sum())
     mbm, mlm = statistics.median(mb), statistics.median(ml)
     return {"workload": "batched: 4,096 queries on a 20M x 12 mixed table (seed 2), column-major",
+            "tuning": {"applied": tuned, "source": "paper_2107_09993_b300/tuning.json (tune.py, this GPU's entry)",
+                       "knobs": knobs, "batched_default_ms": round(statistics.median(mb0), 2)},
             "points": pts, "batched_ms": round(mbm, 2), "looped_plain_ms": round(mlm, 2),
             "speedup": round(mlm / mbm, 3), "batched_points_per_s": round(pts / (mbm / 1e3), 1),
             "identical": bool(same), "query_errors": bad, "skyline": st["skyline"], "survivors": st["survivors"],

@@ -291,13 +291,25 @@ typedef struct sky_query {
     float origin[16];             /* used with SKY_QUERY_QUADRANT */
 } sky_query;
 
-/* Tuning knobs (zero-initialise; see paper_2107_09993_b300/tune.py). */
+/* Tuning knobs (zero-initialise; paper_2107_09993_b300/tune.py chooses them
+ * by timing). None changes a result, only the time. The refinement runs one
+ * persistent kernel per padded-dimension class: class c holds the queries of
+ * 4c+1 .. 4c+4 attributes. */
 typedef struct sky_batch_tuning {
     const int32_t* h_log2g;       /* per-query grid layer (host array), or NULL:
                                      automatic; log2_g * d <= 18 in batches     */
     int32_t refine_ctas_per_sm;   /* persistent refinement CTAs per SM (0 = max
-                                     resident)                                  */
-    int32_t reserved[3];
+                                     resident), for classes without their own  */
+    int32_t class_ctas[4];        /* per class CTAs per SM (0 = the value above) */
+    int32_t class_stages[4];      /* per class ring depth of streamed q-tiles:
+                                     4 or 8 (0 = 8)                             */
+    int32_t class_code[4];        /* per class pair test of the list probe:
+                                     0 = library default (3-bit fast codes first
+                                     for class 3 only), 1 = 7-bit codes, 2 = 3-bit
+                                     fast codes first                            */
+    int32_t concurrent_classes;   /* 1: the class kernels run as parallel
+                                     branches of the graph (their tails overlap);
+                                     0: one after another                       */
 } sky_batch_tuning;
 
 typedef struct sky_batch sky_batch;

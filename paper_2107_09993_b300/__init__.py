@@ -402,7 +402,8 @@ class Query(ctypes.Structure):
 
 
 class BatchTuning(ctypes.Structure):
-    _fields_ = [("h_log2g", _vp), ("refine_ctas_per_sm", _i32), ("reserved", _i32 * 3)]
+    _fields_ = [("h_log2g", _vp), ("refine_ctas_per_sm", _i32), ("class_ctas", _i32 * 4),
+                ("class_stages", _i32 * 4), ("class_code", _i32 * 4), ("concurrent_classes", _i32)]
 
 
 class BatchStats(ctypes.Structure):
@@ -449,7 +450,13 @@ class Batch:
     ascending row ids per query."""
 
     def __init__(self, table, queries, log2g=None, refine_ctas_per_sm=0, capacity=None, stream=None,
-                 origins=None):
+                 origins=None, tuning="cache"):
+        """tuning: "cache" (default) applies the autotuner's cached choices
+        for this GPU (tune.py) when the cache has them and no explicit
+        log2g / refine_ctas_per_sm is given; None uses the library defaults;
+        a dict gives the knobs directly: class_ctas, class_stages, class_code
+        (lists of 4), concurrent_classes, layer_offset (per-query list or
+        array added to the automatic layer)."""
         import numpy as np
         torch = _torch()
         lib = _load_batched()
@@ -470,6 +477,21 @@ class Batch:
         self._queries = arr
         tune = BatchTuning()
         self._lg = None
+        knobs = None
+        if isinstance(tuning, dict):
+            knobs = tuning
+        elif tuning == "cache" and log2g is None and not refine_ctas_per_sm:
+            from . import tune as _tune
+            knobs = _tune.settings(q)
+        if knobs:
+            for c in range(4):
+                tune.class_ctas[c] = int(knobs.get("class_ctas", [0] * 4)[c])
+                tune.class_stages[c] = int(knobs.get("class_stages", [0] * 4)[c])
+                tune.class_code[c] = int(knobs.get("class_code", [0] * 4)[c])
+            tune.concurrent_classes = int(knobs.get("concurrent_classes", 0))
+            if log2g is None and knobs.get("log2g") is not None:
+                log2g = knobs["log2g"]
+        self.tuning = knobs
         if log2g is not None:
             self._lg = np.ascontiguousarray(np.asarray(log2g, dtype=np.int32).reshape(-1))
             assert self._lg.size == self.nq

@@ -343,12 +343,15 @@ struct BatchMinBlocks {
                                : DP == 12 ? SKY_BATCH_MINB_12 : SKY_BATCH_MINB_16;
 };
 
-template <int DP>
+// S: ring stages; FAST: fast-code list probe (both chosen per padded-
+// dimension class at launch time, e.g. by the autotuner).
+template <int DP, int S, bool FAST>
 __global__ void __launch_bounds__(kTQ + 32, BatchMinBlocks<DP>::value) kb_refine(const QueryPlan* __restrict__ qps,
                                                       const int2* __restrict__ items, int nitems, uint32_t* claim)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    refine::RefineSmem<DP>& sm = *reinterpret_cast<refine::RefineSmem<DP>*>(smem_raw);
+    using SM = refine::RefineSmem<DP, S, FAST>;
+    SM& sm = *reinterpret_cast<SM*>(smem_raw);
     __shared__ int s_item;
     while (true) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(claim, 1u);
@@ -360,8 +363,8 @@ __global__ void __launch_bounds__(kTQ + 32, BatchMinBlocks<DP>::value) kb_refine
         const QueryPlan& q = qps[w.x];
         const uint32_t m = q.res->survivors;
         if ((uint32_t)w.y < (m + kTQ - 1) / kTQ)
-            refine::refine_ptile<DP, false>(sm, q.X, q.C, q.ids, q.sub, q.tend, q.supmin, m, (uint32_t)w.y, q.res,
-                                            q.keep);
+            refine::refine_ptile<DP, false, false, SM>(sm, q.X, q.C, q.ids, q.sub, q.tend, q.supmin, m, (uint32_t)w.y,
+                                                       q.res, q.keep);
     }
 }
 
@@ -457,26 +460,39 @@ int sm_count()
     return n > 0 ? n : 148;
 }
 
-template <int DP>
-cudaError_t launch_kb_refine(const QueryPlan* qps, const int2* items, int nitems, uint32_t* claim, int ctas_per_sm,
-                             cudaStream_t s)
+template <int DP, int S, bool FAST>
+cudaError_t launch_kb_refine_v(const QueryPlan* qps, const int2* items, int nitems, uint32_t* claim, int ctas_per_sm,
+                               cudaStream_t s)
 {
-    const int smem = (int)sizeof(refine::RefineSmem<DP>);
+    auto* kern = batched::kb_refine<DP, S, FAST>;
+    const int smem = (int)sizeof(refine::RefineSmem<DP, S, FAST>);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(batched::kb_refine<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    int per_sm = ctas_per_sm;
-    if (per_sm <= 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched::kb_refine<DP>, refine::kTQ + 32, smem);
-        if (per_sm < 1) per_sm = 1;
-    }
+    int resident = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, refine::kTQ + 32, smem);
+    if (resident < 1) resident = 1;
+    const int per_sm = (ctas_per_sm <= 0 || ctas_per_sm > resident) ? resident : ctas_per_sm;
     int grid = sm_count() * per_sm;
     if (grid > nitems) grid = nitems;
     if (grid < 1) return cudaSuccess;
-    batched::kb_refine<DP><<<grid, refine::kTQ + 32, smem, s>>>(qps, items, nitems, claim);
+    kern<<<grid, refine::kTQ + 32, smem, s>>>(qps, items, nitems, claim);
     return cudaGetLastError();
+}
+
+// The refinement variant of one padded-dimension class: ring depth 4 or 8
+// (other values: 8), fast codes on or off.
+template <int DP>
+cudaError_t launch_kb_refine(const QueryPlan* qps, const int2* items, int nitems, uint32_t* claim, int ctas_per_sm,
+                             int stages, bool fast, cudaStream_t s)
+{
+    if (stages == 4)
+        return fast ? launch_kb_refine_v<DP, 4, true>(qps, items, nitems, claim, ctas_per_sm, s)
+                    : launch_kb_refine_v<DP, 4, false>(qps, items, nitems, claim, ctas_per_sm, s);
+    return fast ? launch_kb_refine_v<DP, 8, true>(qps, items, nitems, claim, ctas_per_sm, s)
+                : launch_kb_refine_v<DP, 8, false>(qps, items, nitems, claim, ctas_per_sm, s);
 }
 
 }  // namespace
@@ -500,19 +516,40 @@ cudaError_t launch_batched(const BatchLaunch& b, cudaStream_t s)
         kb_gather<<<(unsigned)b.tile_items, kTQ, 0, s>>>(b.qps, b.nq, b.ptile);
         kb_supmin<<<(unsigned)((b.tile_items + 7) / 8), 256, 0, s>>>(b.qps, b.nq, b.ptile, b.tile_items);
     }
+    // step (d): one persistent kernel per padded-dimension class, in turn on
+    // `s`, or (concurrent_classes) as parallel branches on the class streams
+    const bool par = b.concurrent_classes && b.class_streams[0] && b.fork && b.joins[0];
+    if (par) {
+        cudaError_t e = cudaEventRecord(b.fork, s);
+        if (e != cudaSuccess) return e;
+    }
     for (int c = 0; c < 4; ++c) {
         const int n = b.class_items[c];
         if (!n) continue;
         const int2* it = b.items + b.class_begin[c];
         uint32_t* claim = b.claims + 2 + c;
+        cudaStream_t cs = s;
+        if (par) {
+            cs = b.class_streams[c];
+            cudaError_t e = cudaStreamWaitEvent(cs, b.fork, 0);
+            if (e != cudaSuccess) return e;
+        }
+        const int ctas = b.class_ctas[c] > 0 ? b.class_ctas[c] : b.refine_ctas_per_sm;
+        const int st = b.class_stages[c];
+        const bool fast = b.class_fast[c] != 0;
         cudaError_t e = cudaSuccess;
         switch (c) {
-            case 0: e = launch_kb_refine<4>(b.qps, it, n, claim, b.refine_ctas_per_sm, s); break;
-            case 1: e = launch_kb_refine<8>(b.qps, it, n, claim, b.refine_ctas_per_sm, s); break;
-            case 2: e = launch_kb_refine<12>(b.qps, it, n, claim, b.refine_ctas_per_sm, s); break;
-            default: e = launch_kb_refine<16>(b.qps, it, n, claim, b.refine_ctas_per_sm, s); break;
+            case 0: e = launch_kb_refine<4>(b.qps, it, n, claim, ctas, st, fast, cs); break;
+            case 1: e = launch_kb_refine<8>(b.qps, it, n, claim, ctas, st, fast, cs); break;
+            case 2: e = launch_kb_refine<12>(b.qps, it, n, claim, ctas, st, fast, cs); break;
+            default: e = launch_kb_refine<16>(b.qps, it, n, claim, ctas, st, fast, cs); break;
         }
         if (e != cudaSuccess) return e;
+        if (par) {
+            e = cudaEventRecord(b.joins[c], cs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b.joins[c], 0);
+            if (e != cudaSuccess) return e;
+        }
     }
     if (b.chunk_items > 0) kb_emit<<<(unsigned)b.chunk_items, kT, 0, s>>>(b.qps, b.nq, b.pchunk, b.claims + 1);
     kb_finish<<<1, 1024, 0, s>>>(b.qps, b.nq, b.capacity, b.offsets, b.status);

@@ -81,6 +81,19 @@ sky_status sky_batch_create(const float* d_table, int64_t n_rows, int32_t n_cols
         return bfail(SKY_ERR_INVALID_ARGUMENT, "strides must describe a row-major (col_stride 1) or "
                                                "column-major (row_stride 1) table");
     if (tuning && tuning->refine_ctas_per_sm < 0) return bfail(SKY_ERR_INVALID_ARGUMENT, "negative CTAs per SM");
+    if (tuning) {
+        for (int c = 0; c < 4; ++c) {
+            if (tuning->class_ctas[c] < 0) return bfail(SKY_ERR_INVALID_ARGUMENT, "class %d: negative CTAs per SM", c);
+            if (tuning->class_stages[c] != 0 && tuning->class_stages[c] != 4 && tuning->class_stages[c] != 8)
+                return bfail(SKY_ERR_INVALID_ARGUMENT, "class %d: ring depth %d not in {0, 4, 8}", c,
+                             tuning->class_stages[c]);
+            if (tuning->class_code[c] < 0 || tuning->class_code[c] > 2)
+                return bfail(SKY_ERR_INVALID_ARGUMENT, "class %d: pair-test code %d not in {0, 1, 2}", c,
+                             tuning->class_code[c]);
+        }
+        if (tuning->concurrent_classes < 0 || tuning->concurrent_classes > 1)
+            return bfail(SKY_ERR_INVALID_ARGUMENT, "concurrent_classes not in {0, 1}");
+    }
     sky_batch* b = new (std::nothrow) sky_batch();
     if (!b) return bfail(SKY_ERR_OUT_OF_MEMORY, "host allocation failed");
     b->table = d_table;
@@ -89,6 +102,13 @@ sky_status sky_batch_create(const float* d_table, int64_t n_rows, int32_t n_cols
     b->rs = row_stride;
     b->cs = col_stride;
     b->refine_ctas_per_sm = tuning ? tuning->refine_ctas_per_sm : 0;
+    for (int c = 0; c < 4; ++c) {
+        b->launch.class_ctas[c] = tuning ? tuning->class_ctas[c] : 0;
+        b->launch.class_stages[c] = (tuning && tuning->class_stages[c]) ? tuning->class_stages[c] : 8;
+        const int code = tuning ? tuning->class_code[c] : 0;
+        b->launch.class_fast[c] = code == 0 ? (c == 3 ? 1 : 0) : (code == 2 ? 1 : 0);
+    }
+    b->launch.concurrent_classes = tuning && tuning->concurrent_classes == 1;
     const int nq = n_queries;
     b->plans.resize(nq);
     b->off.resize(nq);
@@ -285,6 +305,14 @@ sky_status sky_batch_bind(sky_batch* b, void* d_ws, size_t ws_bytes, int32_t* d_
     L.max_passes = b->max_passes;
     L.max_words = b->max_words;
     L.refine_ctas_per_sm = b->refine_ctas_per_sm;
+    if (L.concurrent_classes && !L.fork) {
+        e = cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming);
+        for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+            e = cudaStreamCreateWithFlags(&L.class_streams[c], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.joins[c], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return bfail(SKY_ERR_CUDA, "class streams: %s", cudaGetErrorString(e));
+    }
     L.out = d_out_idx;
     L.capacity = out_capacity;
     L.offsets = d_out_offsets;
@@ -355,6 +383,11 @@ void sky_batch_destroy(sky_batch* b)
 {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (int c = 0; c < 4; ++c) {
+        if (b->launch.class_streams[c]) cudaStreamDestroy(b->launch.class_streams[c]);
+        if (b->launch.joins[c]) cudaEventDestroy(b->launch.joins[c]);
+    }
+    if (b->launch.fork) cudaEventDestroy(b->launch.fork);
     delete b;
 }
 

@@ -182,6 +182,13 @@ struct BatchLaunch {
     int max_passes = 0;
     int64_t max_words = 1;
     int refine_ctas_per_sm = 0;
+    // per padded-dimension class (d <= 4, 8, 12, 16) refinement variant
+    int class_ctas[4] = {0, 0, 0, 0};       // persistent CTAs per SM (0: refine_ctas_per_sm)
+    int class_stages[4] = {8, 8, 8, 8};     // ring depth: 4 or 8
+    int class_fast[4] = {0, 0, 0, 1};       // fast-code list probe
+    bool concurrent_classes = false;        // class kernels as parallel branches
+    cudaStream_t class_streams[4] = {};     // (owned by the batch)
+    cudaEvent_t fork = nullptr, joins[4] = {};
     int32_t* out = nullptr;
     int64_t capacity = 0;
     int64_t* offsets = nullptr;

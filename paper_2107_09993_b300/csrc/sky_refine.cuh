@@ -90,26 +90,29 @@ static_assert(kSparseLive <= 32, "the sparse list is one lane mask wide");
 constexpr bool kListProbe = SKY_REFINE_LIST != 0;
 constexpr uint32_t kEndTile = 0xffffffffu;
 
-template <int DP>
+// Shared memory of one refinement CTA. S: ring stages; FAST: fast-code
+// list probe (see SKY_REFINE_FAST_MIN_DP for the single-set default).
+template <int DP, int S = kRingStages, bool FAST = (DP >= SKY_REFINE_FAST_MIN_DP)>
 struct RefineSmem {
     static constexpr int DW = DP / 4;
-    static constexpr bool kFast = DP >= SKY_REFINE_FAST_MIN_DP;
+    static constexpr int kStages = S;
+    static constexpr bool kFast = FAST;
     static constexpr int FW = (DP + 7) / 8;        // fast-code words
     // list entry words (vector loads): fast codes, or the 7-bit codes
     static constexpr int DWL = kFast ? FW : (DW == 3 ? 4 : DW);
     // bulk-copy destinations: 16-byte aligned whatever the ring depth
-    alignas(16) uint32_t qC[kRingStages][kTQ * DW];  // streamed q-tiles (codes)
+    alignas(16) uint32_t qC[S][kTQ * DW];  // streamed q-tiles (codes)
     alignas(16) float pX[kTQ * DP];      // own p coordinates (exact tests)
     uint32_t pP[kTQ * DW];               // own p codes | 0x80 per byte
     uint32_t pF[kFast ? kTQ * FW : 1];   // own p fast codes | 0x8 per nibble
     uint32_t livemask[kTQ / 32];         // bit l of word g: p g*32+l is still undominated
     uint32_t gmax[kTQ / 32][DW];         // byte-wise max code of each group's live p's | 0x80 per byte (producer)
     uint32_t glive[kTQ / 32];            // live p's per group (producer)
-    uint32_t stage_tile[kRingStages];
-    uint32_t stage_mask[kRingStages];    // bit 4w+g: sub-tile w may dominate a live p of group g
-    uint32_t stage_sub[kRingStages][kTQ / 32][DW];   // sub-tile minimum codes of the staged tile
-    uint64_t full[kRingStages];
-    uint64_t empty[kRingStages];
+    uint32_t stage_tile[S];
+    uint32_t stage_mask[S];              // bit 4w+g: sub-tile w may dominate a live p of group g
+    uint32_t stage_sub[S][kTQ / 32][DW];   // sub-tile minimum codes of the staged tile
+    uint64_t full[S];
+    uint64_t empty[S];
     alignas(16) uint32_t stc[2][32 * kSubSlots * DW];   // producer: codes of the 32 tiles of a super-tile
     uint64_t cbar[2];                        // producer: their bulk copies
     // consumer warp w: codes of the listed p's (in sparse mode, the whole
@@ -186,8 +189,8 @@ __device__ __forceinline__ bool bytes_le(const uint32_t* lo, const uint32_t* hi)
 // measured faster there).
 // WIT (witness mode, a checking aid): every removal of a p by a q also writes
 // wit[row of p] = row of q, a point that dominates p (Definition 1).
-template <int DP, bool SPARSE = true, bool WIT = false>
-__device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __restrict__ X,
+template <int DP, bool SPARSE = true, bool WIT = false, class SM = RefineSmem<DP>>
+__device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X,
                                              const uint32_t* __restrict__ C, const int32_t* __restrict__ ids,
                                              const uint32_t* __restrict__ SUB, const uint32_t* __restrict__ TEND,
                                              const uint32_t* __restrict__ SUPMIN, uint32_t m, uint32_t ptile,
@@ -195,7 +198,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
 {
     constexpr int DW = DP / 4;
     constexpr int NG = kTQ / 32;
-    constexpr int S = kRingStages;
+    constexpr int S = SM::kStages;
     constexpr uint32_t kBytesC = kTQ * DW * sizeof(uint32_t);
     const uint32_t T = (m + kTQ - 1) / kTQ;
     uint32_t* err = &res->err;
@@ -209,9 +212,9 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
             pc[w] = C[(pbase + tid) * DW + w];
             sm.pP[tid * DW + w] = pc[w] | kHigh;
         }
-        if constexpr (RefineSmem<DP>::kFast) {
+        if constexpr (SM::kFast) {
 #pragma unroll
-            for (int f = 0; f < RefineSmem<DP>::FW; ++f) sm.pF[tid * RefineSmem<DP>::FW + f] = fast_word<DW>(pc, f) | kHighNib;
+            for (int f = 0; f < SM::FW; ++f) sm.pF[tid * SM::FW + f] = fast_word<DW>(pc, f) | kHighNib;
         }
 #pragma unroll
         for (int k = 0; k < DP; k += 4)
@@ -505,8 +508,8 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                 uint32_t Q[DW];
 #pragma unroll
                 for (int w = 0; w < DW; ++w) Q[w] = sm.qC[s][qi * DW + w];
-                constexpr bool kFast = RefineSmem<DP>::kFast;
-                constexpr int FW = RefineSmem<DP>::FW;
+                constexpr bool kFast = SM::kFast;
+                constexpr int FW = SM::FW;
                 uint32_t QF[FW];
                 if constexpr (kFast) {
 #pragma unroll
@@ -563,7 +566,7 @@ __device__ __forceinline__ void refine_ptile(RefineSmem<DP>& sm, const float* __
                         if (mask) {
                             // the listed p's of the group, in lane order, into
                             // this warp's list
-                            constexpr int DWL = RefineSmem<DP>::DWL;
+                            constexpr int DWL = SM::DWL;
                             uint32_t* L = sm.plist[warp];
                             if ((mask >> lane) & 1u) {
                                 const int rank = __popc(mask & ((1u << lane) - 1u));
