@@ -79,6 +79,20 @@ static_assert(kSparseLive <= 32, "the sparse list is one lane mask wide");
 #ifndef SKY_REFINE_FAST_MIN_DP
 #define SKY_REFINE_FAST_MIN_DP 16
 #endif
+// Windows of 32 q-tiles whose sub-tile minima the producer has in flight
+// (bulk copies into a ring of shared-memory buffers): the producer's scan
+// over the windows waits on one of these copies per window, so at high d,
+// where few tiles of a window are relevant, the depth of this ring sets the
+// pace of the stream.
+#ifndef SKY_REFINE_WINDOWS
+#define SKY_REFINE_WINDOWS 2
+#endif
+// 1: the CTA's own p coordinates are staged in shared memory for the exact
+// tests; 0: the exact tests read them from global memory (rare, and the
+// shared memory goes to deeper rings)
+#ifndef SKY_REFINE_PX_SMEM
+#define SKY_REFINE_PX_SMEM 1
+#endif
 // listed p's tested per step of the list probe (2, 4 or 8; entries past the
 // list's end hold stale codes and their bits are dropped)
 #ifndef SKY_REFINE_PROBE_UNROLL
@@ -102,7 +116,8 @@ struct RefineSmem {
     static constexpr int DWL = kFast ? FW : (DW == 3 ? 4 : DW);
     // bulk-copy destinations: 16-byte aligned whatever the ring depth
     alignas(16) uint32_t qC[S][kTQ * DW];  // streamed q-tiles (codes)
-    alignas(16) float pX[kTQ * DP];      // own p coordinates (exact tests)
+    static constexpr int kWindows = SKY_REFINE_WINDOWS;
+    alignas(16) float pX[SKY_REFINE_PX_SMEM ? kTQ * DP : 4];   // own p coordinates (exact tests)
     uint32_t pP[kTQ * DW];               // own p codes | 0x80 per byte
     uint32_t pF[kFast ? kTQ * FW : 1];   // own p fast codes | 0x8 per nibble
     uint32_t livemask[kTQ / 32];         // bit l of word g: p g*32+l is still undominated
@@ -113,8 +128,9 @@ struct RefineSmem {
     uint32_t stage_sub[S][kTQ / 32][DW];   // sub-tile minimum codes of the staged tile
     uint64_t full[S];
     uint64_t empty[S];
-    alignas(16) uint32_t stc[2][32 * kSubSlots * DW];   // producer: codes of the 32 tiles of a super-tile
-    uint64_t cbar[2];                        // producer: their bulk copies
+    alignas(16) uint32_t stc[kWindows][32 * kSubSlots * DW];   // producer: codes of the 32 tiles of a super-tile
+    uint64_t cbar[kWindows];                 // producer: their bulk copies
+    int32_t pend[kWindows];                  // producer: the super-tile held by each buffer
     // consumer warp w: codes of the listed p's (in sparse mode, the whole
     // array holds one list of up to 32 entries of 7-bit codes)
     alignas(16) uint32_t plist[kTQ / 32][32 * (DWL > 1 ? DWL : 2)];
@@ -216,10 +232,12 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
 #pragma unroll
             for (int f = 0; f < SM::FW; ++f) sm.pF[tid * SM::FW + f] = fast_word<DW>(pc, f) | kHighNib;
         }
+#if SKY_REFINE_PX_SMEM
 #pragma unroll
         for (int k = 0; k < DP; k += 4)
             *reinterpret_cast<float4*>(&sm.pX[tid * DP + k]) =
                 *reinterpret_cast<const float4*>(X + (pbase + tid) * DP + k);
+#endif
         const uint32_t vm = __ballot_sync(kFull, valid);
         if ((tid & 31) == 0) sm.livemask[tid >> 5] = vm;
     }
@@ -228,8 +246,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
             mbar_init(&sm.full[s], 1);
             mbar_init(&sm.empty[s], NG);
         }
-        mbar_init(&sm.cbar[0], 1);
-        mbar_init(&sm.cbar[1], 1);
+        for (int b = 0; b < SM::kWindows; ++b) mbar_init(&sm.cbar[b], 1);
         mbar_fence_init();
         sm.live = (m - pbase) < (uint32_t)kTQ ? (m - (uint32_t)pbase) : (uint32_t)kTQ;
         sm.failed = 0;
@@ -328,25 +345,37 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
         }
         // the codes of the 32 tiles of a super-tile: one bulk copy (the code
         // arrays carry 16 bytes of slack past their end); copy k goes to
-        // buffer k & 1 and is that buffer's (k >> 1)-th use
+        // buffer k % NB and is that buffer's (k / NB)-th use; up to NB
+        // windows are in flight ahead of the one being examined
+        constexpr uint32_t NB = (uint32_t)SM::kWindows;
         uint32_t kiss = 0, kcons = 0;   // copies issued / consumed
         auto fetch_super = [&](int sx) {
             const uint32_t t0 = (uint32_t)sx * 32u;
             const uint32_t nt = min(32u, T - t0);
             const uint32_t bytes = (nt * kSubSlots * DW * 4u + 15u) & ~15u;
-            const int bb = (int)(kiss & 1u);
+            const int bb = (int)(kiss % NB);
             __syncwarp();
             if (lane == 0) {
+                sm.pend[bb] = sx;
                 fence_proxy_async_smem();   // generic reads of this buffer are done
                 mbar_arrive_expect_tx(&sm.cbar[bb], bytes);
                 bulk_g2s(sm.stc[bb], SUB + (int64_t)t0 * kSubSlots * DW, bytes, &sm.cbar[bb]);
             }
+            __syncwarp();
             ++kiss;
         };
-        int cur = next_super();
-        if (cur >= 0) fetch_super(cur);
-        while (cur >= 0 && !stop) {
+        auto refill = [&]() {
+            while (kiss - kcons < NB) {
+                const int sx = next_super();
+                if (sx < 0) break;
+                fetch_super(sx);
+            }
+        };
+        refill();
+        while (kcons < kiss && !stop) {
             if (all_dead()) break;
+            const int bf = (int)(kcons % NB);
+            const int cur = sm.pend[bf];
             if (SPARSE && kSparseLive > 0 && __shfl_sync(kFull, sm.live, 0) <= kSparseLive) {
                 // few p's left: the rest of the scan runs in sparse mode,
                 // from this (fetched, not yet examined) super-tile on
@@ -356,13 +385,9 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                 }
                 break;
             }
-            const int nx = next_super();
-            if (nx >= 0) fetch_super(nx);
-            const int bf = (int)(kcons & 1u);
             bool ok = true;
-            if (lane == 0) ok = mbar_wait(&sm.cbar[bf], (kcons >> 1) & 1u, err);
+            if (lane == 0) ok = mbar_wait(&sm.cbar[bf], (kcons / NB) & 1u, err);
             if (!__shfl_sync(kFull, ok ? 1 : 0, 0)) { if (lane == 0) sm.failed = 1u; stop = true; break; }
-            ++kcons;
             if (since >= kSummaryEvery) { summarise(); since = 0; }
             const uint32_t t0 = (uint32_t)cur * 32u;
             const uint32_t t = t0 + lane;
@@ -459,11 +484,13 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                     }
                 }
             }
-            cur = nx;
+            if (stop) break;
+            ++kcons;    // buffer bf is free again
+            refill();
         }
         // code copies that were not consumed land before the exit
         if (lane == 0)
-            for (uint32_t k = kcons; k < kiss; ++k) mbar_wait(&sm.cbar[k & 1u], (k >> 1) & 1u, nullptr);
+            for (uint32_t k = kcons; k < kiss; ++k) mbar_wait(&sm.cbar[k % NB], (k / NB) & 1u, nullptr);
         if (lane == 0 && issued) atomicAdd(&res->tiles, (unsigned long long)issued);
         // end-of-stream marker
         int s;
@@ -544,7 +571,11 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                             if (eq) {
                                 ++exact;
                                 const float* qx = X + ((int64_t)tt * kTQ + qi) * DP;
+#if SKY_REFINE_PX_SMEM
                                 const float* px = &sm.pX[pi * DP];
+#else
+                                const float* px = X + (pbase + pi) * DP;
+#endif
                                 bool le = true, lt = false;
 #pragma unroll
                                 for (int kk = 0; kk < DP; kk += 4) {
@@ -733,7 +764,11 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                             if (eq) {
                                 ++sexact;
                                 const float* qx = X + ((int64_t)tt * kTQ + j * 32 + lane) * DP;
+#if SKY_REFINE_PX_SMEM
                                 const float* px = &sm.pX[pi * DP];
+#else
+                                const float* px = X + (pbase + pi) * DP;
+#endif
                                 bool le = true, lt = false;
 #pragma unroll
                                 for (int kk = 0; kk < DP; kk += 4) {

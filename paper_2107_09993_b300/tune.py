@@ -76,6 +76,9 @@ def layers_for(queries, offsets: dict) -> np.ndarray:
     out = []
     for _, n, m in q:
         d = _dims(m)
+        if d < 1 or d > 16 or int(m) >> 32:
+            out.append(-1)   # automatic: the library checks the query and reports it
+            continue
         lg = auto_log2g(int(n), d) + int(offsets.get(bucket(int(n), d), 0))
         lg = max(0, lg)
         while lg > 0 and lg * d > MAX_GRID_BITS:

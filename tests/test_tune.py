@@ -43,3 +43,10 @@ def test_default_knobs_match_the_library_defaults():
     assert k["class_code"] == [1, 1, 1, 2] and k["class_stages"] == [8] * 4
     assert k["class_ctas"] == [0] * 4 and k["concurrent_classes"] == 0
     assert [tune._class(d) for d in (1, 4, 5, 8, 9, 12, 13, 16)] == [0, 0, 1, 1, 2, 2, 3, 3]
+
+
+def test_layers_leave_invalid_queries_to_the_library():
+    # no column, 17 columns: automatic (-1), so that the library rejects them
+    q = np.array([(0, 5, 0), (0, 5, 0x1ffff), (0, 100, 0b101)], dtype=np.int64)
+    lgs = tune.layers_for(q, {})
+    assert lgs[:2].tolist() == [-1, -1] and lgs[2] == tune.auto_log2g(100, 2)
