@@ -461,6 +461,55 @@ def batched_vs_plain(sky, torch, dev, reps=3):
                       "allocated before the timed loop); CUDA events on the calling stream"}
 
 
+def tournament_vs_prefix_or(sky, torch, dev, reps=3):
+    """Step (c)'s classes by the paper's tournament tree (Algorithm 3, one
+    kernel per tree level, d passes; sky_tournament_cells) on the occupancy
+    of the large sets' layers, against the prefix-OR path's step (c) on the
+    same grid (sky_prune_cells: prefix-OR + dominated bitmap + survivors,
+    Grid API). Device time, median of `reps`; the dominated cells of the two
+    must be equal."""
+    import numpy as np
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for kind, n, d in (("anticorrelated", 10_000_000, 16), ("independent", 10_000_000, 12),
+                       ("anticorrelated", 1_000_000, 8)):
+        x = torch.from_numpy(skydata.generate(kind, n, d, SEED)).to(dev)
+        g = sky.Grid(x)
+        g.prune()
+        lg = g.stats()["log2_g"]
+        occ = g.occupied()
+        dom = g.dominated()
+        t_pre = []
+        for _ in range(reps):
+            g2 = sky.Grid(x, log2_g=lg)
+            torch.cuda.synchronize(dev)
+            ms, _ = time_step(lambda: g2.prune(), stream, dev)
+            t_pre.append(ms)
+            g2.close()
+        t_tt = []
+        cls = None
+        for _ in range(reps):
+            ms, cls = time_step(lambda: sky.tournament_cells(occ, d, lg), stream, dev)
+            t_tt.append(ms)
+        ncell = 1 << (lg * d)
+        w = dom.cpu().numpy().view(np.uint32)
+        want = ((w[np.arange(ncell) >> 5] >> (np.arange(ncell) & 31).astype(np.uint32)) & 1).astype(np.uint8)
+        got = (cls.cpu().numpy() & 1).astype(np.uint8)
+        out[f"{kind} n={n} d={d}"] = {"log2_g": lg, "cells": ncell,
+                                      "tournament_ms": round(statistics.median(t_tt), 3),
+                                      "prefix_or_prune_ms": round(statistics.median(t_pre), 3),
+                                      "tournament_launches": d * (2 * lg * d + 3) + 1,
+                                      "dominated_equal": bool(np.array_equal(got, want)),
+                                      "key_cells": int(((cls >> 1) & 1).sum().item()),
+                                      "candidate_cells": int(((cls >> 2) & 1).sum().item())}
+        g.close()
+        del x
+    return {"what": "step (c) classes: the paper's tournament tree (Algorithm 3, as read: all cells are leaves, "
+                    "one dimension per pass) vs this library's prefix-OR path on the same layer",
+            "timing": f"CUDA events on the calling stream around each call (host launches included), median of {reps}",
+            "sets": out}
+
+
 def run_sky(args):
     import torch
     import paper_2107_09993_b300 as sky
@@ -625,6 +674,7 @@ def run_sky(args):
         line["roofline_prune_large"] = prune_roofline(sky, torch, dev, flush, peaks, peak_src)
         line["learned_vs_plain"] = learned_vs_plain(sky, torch, dev)
         line["batched_vs_plain"] = batched_vs_plain(sky, torch, dev)
+        line["tournament_vs_prefix_or"] = tournament_vs_prefix_or(sky, torch, dev)
         line["paper_scale"] = paper_scale(sky, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(host, args.cpu_seconds)

@@ -217,6 +217,39 @@ SKY_API sky_status sky_skyline_witness(const float* d_pts, int64_t n, int32_t d,
                                        const sky_options* opt, int32_t* d_out_idx, int64_t out_capacity,
                                        int64_t* h_out_count, int32_t* d_witness, void* stream);
 
+/*
+ * The paper's tournament-tree ShrinkKeyCells [Algorithm 3, Sec. 5.2;
+ * Theorem 2] on one grid layer, as a comparison variant of step (c): the
+ * cells of the layer are the leaves of a complete binary tree in the
+ * enumeration order of a rotation of the dimensions; each of d passes runs an
+ * up-sweep of pointers u and a down-sweep of pointers l (one kernel per tree
+ * level), then the dimensions rotate and every leaf's u takes its l. A
+ * pointer is a non-empty cell. Reading (the printed form does not reproduce
+ * Definitions 4-5): all cells are leaves, and a pass compares in one
+ * dimension -- the earlier pointer wins within a line of cells that differ
+ * only in the rotated dimension 0 -- so that after the d passes l(c) is a
+ * non-empty cell e <= c (componentwise) other than c if one exists, else c
+ * when c is non-empty, else none.
+ *
+ *   d_occupied  device bitmap of the layer: bit c of word c / 32 set when
+ *               cell c (key sum_k c[k] << (log2_g k)) holds a point; at least
+ *               max(1, 2^(log2_g d) / 32) words (sky_grid_copy_out's
+ *               SKY_GRID_OCCUPIED array has this layout).
+ *   d_classes   device, one byte per cell: bit 0 dominated (Def. 3: every
+ *               c[k] >= 1 and l(c - (1, ..., 1)) is a cell), bit 1 key cell
+ *               (Def. 4: l(c) = c), bit 2 candidate cell (Def. 5 with the
+ *               auxiliary key cells of Def. 6: not dominated, and l(c) is a
+ *               cell or some c[k] = 2^log2_g - 1).
+ *   d_ws        device workspace of sky_tournament_workspace_size(d, log2_g)
+ *               bytes (20 bytes a cell), 256-byte aligned, caller-owned.
+ * 1 <= d <= 16, log2_g * d <= 27 (SKY_ERR_TOO_LARGE beyond). Asynchronous on
+ * `stream`; allocates nothing. sky_tournament_workspace_size returns 0 for
+ * arguments outside these limits.
+ */
+SKY_API size_t sky_tournament_workspace_size(int32_t d, int32_t log2_g);
+SKY_API sky_status sky_tournament_cells(const uint32_t* d_occupied, int32_t d, int32_t log2_g,
+                                        uint8_t* d_classes, void* d_ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Many independent point sets in one call (a project addition: the paper    */
 /* computes one skyline at a time). Each set is steps (a)-(d) exactly as     */

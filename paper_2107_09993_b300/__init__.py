@@ -94,6 +94,8 @@ def load():
         "sky_grid_destroy": ([_vp], None),
         "sky_last_run_stats": ([P(RunStats)], _i32),
         "sky_set_wait_limit": ([ctypes.c_uint32], _i32),
+        "sky_tournament_workspace_size": ([_i32, _i32], _sz),
+        "sky_tournament_cells": ([_vp, _i32, _i32, _vp, _vp, _sz, _vp], _i32),
         "sky_set_phase_timing": ([_i32], _i32),
         "sky_last_phase_times": ([P(PhaseTimes)], _i32),
         "sky_status_string": ([_i32], ctypes.c_char_p),
@@ -296,6 +298,27 @@ def last_run_stats() -> dict:
     s = RunStats()
     _check(load().sky_last_run_stats(ctypes.byref(s)))
     return {f: getattr(s, f) for f, _ in RunStats._fields_}
+
+
+def tournament_cells(occupied, d: int, log2_g: int, stream=None):
+    """sky_tournament_cells (Algorithm 3 on one layer): `occupied` is the
+    layer's occupancy bitmap as an int32 CUDA tensor of 32-bit words; returns
+    a uint8 CUDA tensor of 2^(log2_g d) class bytes (bit 0 dominated, bit 1
+    key cell, bit 2 candidate cell)."""
+    torch = _torch()
+    lib = load()
+    n = 1 << (int(log2_g) * int(d))
+    ws_bytes = lib.sky_tournament_workspace_size(int(d), int(log2_g))
+    if ws_bytes == 0:
+        raise SkyError(6 if d >= 1 and log2_g >= 0 else 1, f"no tournament for d={d}, log2_g={log2_g}")
+    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=occupied.device)
+    off = (-ws.data_ptr()) % 256
+    cls = torch.empty(n, dtype=torch.uint8, device=occupied.device)
+    with torch.cuda.device(occupied.device):
+        _check(lib.sky_tournament_cells(_vp(occupied.data_ptr()), int(d), int(log2_g), _vp(cls.data_ptr()),
+                                        _vp(ws.data_ptr() + off), ws_bytes, _stream_ptr(stream)))
+    torch.cuda.synchronize(occupied.device)   # the workspace is released on return
+    return cls
 
 
 def set_wait_limit(polls: int):

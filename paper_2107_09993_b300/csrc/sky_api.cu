@@ -17,6 +17,7 @@ using namespace sky;
 
 namespace {
 
+constexpr int kTournamentMaxBits = 27;   // layers of up to 2^27 cells (the dense limit)
 thread_local std::string t_err;
 thread_local sky_run_stats t_stats = {};
 thread_local sky_phase_times t_phase = {};
@@ -964,6 +965,28 @@ sky_status sky_skyline_witness(const float* d_pts, int64_t n, int32_t d, int64_t
     if (e != cudaSuccess) return cuda_fail(e, "witness-mode launch");
     if (es != cudaSuccess) return cuda_fail(es, "stream synchronize");
     return skyline_finish(f, h_out_count, t_stats);
+}
+
+size_t sky_tournament_workspace_size(int32_t d, int32_t log2_g)
+{
+    if (d < 1 || d > kMaxDim || log2_g < 0 || log2_g * d > kTournamentMaxBits) return 0;
+    return tournament_workspace_bytes(d, log2_g);
+}
+
+sky_status sky_tournament_cells(const uint32_t* d_occupied, int32_t d, int32_t log2_g, uint8_t* d_classes, void* d_ws,
+                                size_t ws_bytes, void* stream)
+{
+    if (d < 1 || d > kMaxDim) return fail(SKY_ERR_INVALID_ARGUMENT, "d = %d outside [1, 16]", d);
+    if (log2_g < 0) return fail(SKY_ERR_INVALID_ARGUMENT, "log2_g = %d < 0", log2_g);
+    if (log2_g * d > kTournamentMaxBits)
+        return fail(SKY_ERR_TOO_LARGE, "layer of 2^%d cells above the tournament limit 2^%d", log2_g * d,
+                    kTournamentMaxBits);
+    if (!d_occupied || !d_classes) return fail(SKY_ERR_INVALID_ARGUMENT, "NULL bitmap or class buffer");
+    const size_t need = tournament_workspace_bytes(d, log2_g);
+    if (!d_ws || ws_bytes < need) return fail(SKY_ERR_CAPACITY, "workspace needs %zu bytes", need);
+    if (reinterpret_cast<uintptr_t>(d_ws) & 255u) return fail(SKY_ERR_INVALID_ARGUMENT, "workspace not 256-byte aligned");
+    SKY_CUDA(launch_tournament(d_occupied, d, log2_g, d_classes, d_ws, static_cast<cudaStream_t>(stream)));
+    return SKY_OK;
 }
 
 sky_status sky_skyline_sets(sky_set* sets, int32_t count, const sky_options* opt, void* stream)

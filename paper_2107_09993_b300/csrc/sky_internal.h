@@ -162,6 +162,10 @@ cudaError_t launch_sort(Plan& p, cudaStream_t s);
 cudaError_t launch_gather(const Plan& p, cudaStream_t s);
 cudaError_t launch_refine(const Plan& p, cudaStream_t s);
 cudaError_t launch_emit(const Plan& p, int32_t* out, int64_t capacity, cudaStream_t s);
+// k_tournament.cu: Algorithm 3 (tournament tree) classes of one layer
+size_t tournament_workspace_bytes(int d, int log2g);
+cudaError_t launch_tournament(const uint32_t* occ, int d, int log2g, uint8_t* cls, void* ws, cudaStream_t s);
+int tournament_kernel_count(int d, int log2g);
 // k_witness.cu: witnesses of the points step (c) dropped (rep: 2^(log2g d) ints of scratch)
 cudaError_t launch_witness_cells(const Plan& p, int32_t* rep, int n_prop, cudaStream_t s);
 
