@@ -303,6 +303,7 @@ struct MortonSpread {
 // than both global variants.)
 struct MarkGlobal {
     static constexpr bool kNone = false;
+    static constexpr bool kByte = false;
     uint32_t* occ;
     __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const { atomicOr(occ + word, bits); }
 };
@@ -310,6 +311,7 @@ struct MarkGlobal {
 // load, not a serialised atomic on the same address.
 struct MarkPrivate {
     static constexpr bool kNone = false;
+    static constexpr bool kByte = false;
     uint32_t* s_occ;   // shared memory
     __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const
     {
@@ -318,10 +320,26 @@ struct MarkPrivate {
 };
 struct MarkNone {
     static constexpr bool kNone = true;
+    static constexpr bool kByte = false;
+    __device__ __forceinline__ void mark(uint32_t, uint32_t) const {}
+};
+// MarkByte: one byte per cell, set by a plain store (no read-modify-write
+// at L2); k_occ_pack builds the bitmap from the bytes after the pass.
+struct MarkByte {
+    static constexpr bool kNone = false;
+    static constexpr bool kByte = true;
+    uint8_t* occb;
+    bool check;        // block-uniform: look before storing (clustered data)
+    __device__ __forceinline__ void mark_key(uint32_t key) const
+    {
+        if (check && __ldca(occb + key) != 0) return;
+        occb[key] = 1;
+    }
     __device__ __forceinline__ void mark(uint32_t, uint32_t) const {}
 };
 struct MarkCheck {
     static constexpr bool kNone = false;
+    static constexpr bool kByte = false;
     uint32_t* occ;
     bool check;        // block-uniform
     __device__ __forceinline__ void mark(uint32_t word, uint32_t bits) const
@@ -383,6 +401,10 @@ __device__ __forceinline__ void mark_cell(uint32_t key, const Marker& marker, ui
 {
     const uint32_t word = key >> 5;
     if (dups) *dups += __popc(__match_any_sync(kFull, word)) > 1 ? 1u : 0u;   // converged callers only
+    if constexpr (Marker::kByte) {
+        marker.mark_key(key);
+        return;
+    }
     const uint32_t bit = 1u << (key & 31u);
     const uint32_t am = converged ? kFull : __activemask();
     const int leader = converged ? 0 : __ffs(am) - 1;
@@ -488,7 +510,7 @@ __device__ __forceinline__ void map_keys_unit(const float* __restrict__ r, int r
 // Marking modes of the map kernels: the bitmap itself (through the word cache
 // in the streaming kernel), a private shared-memory copy of a small bitmap,
 // or no marking at all (a second pass that only needs the keys again).
-enum MapMark { kMarkCheck = 0, kMarkSmall = 1, kMarkNone = 2 };
+enum MapMark { kMarkCheck = 0, kMarkSmall = 1, kMarkNone = 2, kMarkByte = 3 };
 
 template <int DP, int MODE>
 __global__ void __launch_bounds__(kThreads) k_map_mark_plain(const float* __restrict__ pts, int64_t n,
@@ -519,6 +541,9 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_plain(const float* __rest
                 map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkPrivate{s_occ}, bad);
             else if (MODE == kMarkNone)
                 map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkNone{}, bad);
+            else if (MODE == kMarkByte)
+                map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey,
+                                   MarkByte{reinterpret_cast<uint8_t*>(occ), false}, bad);
             else
                 map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkGlobal{occ}, bad);
         }
@@ -634,6 +659,20 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
             if (MODE == kMarkSmall) {
 #pragma unroll
                 for (int j = 0; j < RPT; ++j) mark_cell<true>(key[j], MarkPrivate{s_tail});
+            } else if (MODE == kMarkByte) {
+                uint8_t* ob = reinterpret_cast<uint8_t*>(occ);
+                if (s_check != 0u && i > 0) {
+                    uint8_t v[RPT];
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j) v[j] = __ldca(ob + key[j]);
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j)
+                        if (!v[j]) ob[key[j]] = 1;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j)
+                        mark_cell<true>(key[j], MarkByte{ob, false}, (i == 0 && j == 0) ? &dups : nullptr);
+                }
             } else if (MODE == kMarkCheck) {
                 if (s_check != 0u && i > 0) {
                     // looking: every bitmap read of the thread in flight at
@@ -674,12 +713,15 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
                                       bad);
                 else if (MODE == kMarkNone)
                     map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, row, ckey, mkey, MarkNone{}, bad);
+                else if (MODE == kMarkByte)
+                    map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, row, ckey, mkey,
+                                      MarkByte{reinterpret_cast<uint8_t*>(occ), s_check != 0u}, bad, dp);
                 else
                     map_one<DP, true>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, row, ckey, mkey,
                                       MarkCheck{occ, s_check != 0u}, bad, dp);
             }
         }
-        if (MODE == kMarkCheck && i == 0) {
+        if ((MODE == kMarkCheck || MODE == kMarkByte) && i == 0) {
             const uint32_t h = __reduce_add_sync(kFull, dups);
             if ((tid & 31) == 0 && h) atomicAdd(&s_dups, h);
         }
@@ -687,7 +729,8 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
         if (tid == 0) {
             // look before marking from the second chunk on when at least
             // 1/16 of the first chunk's first rows shared their word inside a warp
-            if (MODE == kMarkCheck && i == 0 && s_dups >= (uint32_t)(kThreads / 16)) s_check = 1u;
+            if ((MODE == kMarkCheck || MODE == kMarkByte) && i == 0 && s_dups >= (uint32_t)(kThreads / 16))
+                s_check = 1u;
             if (i + kMapStages < my_chunks) {
                 const int64_t c2 = blockIdx.x + (i + kMapStages) * gridDim.x;
                 fence_proxy_async_smem();
@@ -705,6 +748,9 @@ __global__ void __launch_bounds__(kThreads) k_map_mark_tma(const float* __restri
                 map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkPrivate{s_tail}, bad);
             else if (MODE == kMarkNone)
                 map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkNone{}, bad);
+            else if (MODE == kMarkByte)
+                map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey,
+                                   MarkByte{reinterpret_cast<uint8_t*>(occ), false}, bad);
             else
                 map_one<DP, false>(x, d, log2g, mbits, ms, s_off, s_sc, s_ms, i, ckey, mkey, MarkGlobal{occ}, bad);
         }
@@ -742,6 +788,23 @@ __global__ void __launch_bounds__(kThreads) k_occ_merge(const uint32_t* __restri
 
 // ---------------------------------------------------------------------------
 // One dimension of the prefix-OR over the whole grid (global memory).
+// Bitmap word w from the 32 bytes of cells 32w .. 32w + 31 (each 0 or 1):
+// ((x & 0x01010101) * 0x01020408) >> 24 gathers the low bits of four bytes
+// into a nibble (the partial products land on distinct bits, no carries).
+__global__ void __launch_bounds__(kThreads) k_occ_pack(const uint8_t* __restrict__ occb, uint32_t* occ, int64_t words)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += stride) {
+        const uint4* src = reinterpret_cast<const uint4*>(occb + 32 * w);
+        const uint4 a = __ldcs(src), b = __ldcs(src + 1);
+        const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        uint32_t r = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) r |= (((x[q] & 0x01010101u) * 0x01020408u) >> 24) << (4 * q);
+        occ[w] = r;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_prefix_or_dim(uint32_t* R, int64_t words, int log2g, int k)
 {
     prefix_or_dim(R, words, log2g, k, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
@@ -1335,16 +1398,18 @@ static void map_tma(const Plan& p, int& blocks, size_t smem, int smem_max, int64
     }
     const int per_sm = cached_per_sm;
     blocks = std::min(blocks, per_sm * num_sms());
+    uint32_t* occ = MODE == kMarkByte ? reinterpret_cast<uint32_t*>(p.occb) : p.occ;
     k_map_mark_tma<DP, MODE><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.log2g, p.morton_bits, p.params,
-                                                            p.ckey, p.mkey, p.occ, &p.res->err,
+                                                            p.ckey, p.mkey, occ, &p.res->err,
                                                             MODE == kMarkSmall ? p.occ_stage : nullptr, pw, look);
 }
 
 template <int DP, int MODE>
 static void map_plain(const Plan& p, int blocks, size_t smem, int64_t pw, bool v, cudaStream_t s)
 {
+    uint32_t* occ = MODE == kMarkByte ? reinterpret_cast<uint32_t*>(p.occb) : p.occ;
     k_map_mark_plain<DP, MODE><<<blocks, kThreads, smem, s>>>(p.pts, p.n, p.d, p.ld, v, p.log2g, p.morton_bits,
-                                                              p.params, p.ckey, p.mkey, p.occ, &p.res->err,
+                                                              p.params, p.ckey, p.mkey, occ, &p.res->err,
                                                               MODE == kMarkSmall ? p.occ_stage : nullptr, pw);
 }
 
@@ -1353,7 +1418,8 @@ static void map_plain(const Plan& p, int blocks, size_t smem, int64_t pw, bool v
 cudaError_t launch_map_pass(const Plan& p, bool mark, cudaStream_t s)
 {
     if (p.n == 0) return cudaGetLastError();
-    const int mode = !mark ? kMarkNone : (p.occ_stage != nullptr ? kMarkSmall : kMarkCheck);
+    const int mode = !mark ? kMarkNone
+                           : (p.occ_stage != nullptr ? kMarkSmall : (p.occb != nullptr ? kMarkByte : kMarkCheck));
     const int64_t pw = mode == kMarkSmall ? p.words : 0;
     int blocks = 0;
     const int rpt = map_rpt(pad4(p.d));
@@ -1367,6 +1433,7 @@ cudaError_t launch_map_pass(const Plan& p, bool mark, cudaStream_t s)
         SKY_DISPATCH_DP(p.d, {
             if (mode == kMarkSmall) map_tma<DP, kMarkSmall>(p, blocks, smem, smem_max, pw, s);
             else if (mode == kMarkNone) map_tma<DP, kMarkNone>(p, blocks, smem, smem_max, pw, s);
+            else if (mode == kMarkByte) map_tma<DP, kMarkByte>(p, blocks, smem, smem_max, pw, s);
             else map_tma<DP, kMarkCheck>(p, blocks, smem, smem_max, pw, s);
         });
     } else {
@@ -1376,6 +1443,7 @@ cudaError_t launch_map_pass(const Plan& p, bool mark, cudaStream_t s)
         SKY_DISPATCH_DP(p.d, {
             if (mode == kMarkSmall) map_plain<DP, kMarkSmall>(p, blocks, smem, pw, v, s);
             else if (mode == kMarkNone) map_plain<DP, kMarkNone>(p, blocks, smem, pw, v, s);
+            else if (mode == kMarkByte) map_plain<DP, kMarkByte>(p, blocks, smem, pw, v, s);
             else map_plain<DP, kMarkCheck>(p, blocks, smem, pw, v, s);
         });
     }
@@ -1383,6 +1451,8 @@ cudaError_t launch_map_pass(const Plan& p, bool mark, cudaStream_t s)
         const int64_t cols = (p.words + 31) / 32;
         k_occ_merge<<<(unsigned)(cols * kMergeSplit), kThreads, 0, s>>>(p.occ_stage, blocks, p.words, p.occ);
     }
+    if (mode == kMarkByte)
+        k_occ_pack<<<grid_for(p.words, kThreads, num_sms() * 8), kThreads, 0, s>>>(p.occb, p.occ, p.words);
     return cudaGetLastError();
 }
 
@@ -1411,17 +1481,20 @@ cudaError_t launch_minmax_accumulate(const Plan& p, cudaStream_t s)
 // separate wide k_clear.
 constexpr int64_t kFoldClearWords = int64_t(1) << 13;
 
+// Words the call's first kernel zeroes: the bitmap, or the byte map
+int64_t clear_words(const Plan& p) { return p.occb ? p.words * 8 : p.words; }
+
 bool clear_folded(const Plan& p)
 {
-    return p.map_mode == kMapAuto && p.n > 0 && p.words <= kFoldClearWords;
+    return p.map_mode == kMapAuto && p.n > 0 && clear_words(p) <= kFoldClearWords;
 }
 
 ClearSet clear_of(const Plan& p)
 {
     ClearSet c;
     c.res = p.res;
-    c.occ = p.occ;
-    c.words = p.words;
+    c.occ = p.occb ? reinterpret_cast<uint32_t*>(p.occb) : p.occ;   // the pack rewrites every bitmap word
+    c.words = clear_words(p);
     c.digit_total = p.digit_total;
     c.lb_counter = p.lb_counter;
     c.lb_states = p.lb_states;
@@ -1450,7 +1523,7 @@ cudaError_t launch_params(const Plan& p, cudaStream_t s, bool clear)
 cudaError_t launch_build_params(const Plan& p, cudaStream_t s)
 {
     if (!clear_folded(p))
-        k_clear<<<grid_for(p.words, kThreads * 16, num_sms() * 4), kThreads, 0, s>>>(clear_of(p));
+        k_clear<<<grid_for(clear_words(p), kThreads * 16, num_sms() * 4), kThreads, 0, s>>>(clear_of(p));
     if (p.map_mode == kMapMinMax) launch_mm_reset(p, s);
     if (p.n == 0) return cudaGetLastError();
     if (p.map_mode == kMapMinMax) launch_minmax_accumulate(p, s);
@@ -1467,7 +1540,7 @@ cudaError_t launch_build(const Plan& p, cudaStream_t s)
 int build_kernel_count(const Plan& p)
 {
     if (p.n == 0) return 1;
-    const int merge = p.occ_stage ? 1 : 0;
+    const int merge = (p.occ_stage || p.occb) ? 1 : 0;   // merge of private bitmaps, or pack of the byte map
     if (p.map_mode == kMapMinMax) return 4 + merge;
     return (clear_folded(p) ? 2 : 3) + merge;   // (clear,) parameters, map pass (+ merge)
 }

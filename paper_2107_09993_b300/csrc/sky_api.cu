@@ -18,6 +18,17 @@ using namespace sky;
 namespace {
 
 constexpr int kTournamentMaxBits = 27;   // layers of up to 2^27 cells (the dense limit)
+// Grids above kPrivWords words with at least half as many rows as cells are
+// marked in a byte-per-cell map (plain byte stores, packed into the bitmap
+// afterwards) instead of by global atomicOr on the bitmap, in the single-set
+// path (sky_skyline, the sets calls, the witness mode); the grid API, the
+// chunked path and the no-allocation entry point keep the atomic marking.
+// Measured on B300: 10^7 x 12 independent (2^24 cells) pruning call 226 ->
+// 216 us; at 10^6 rows on 2^24 cells the byte map lost 15-50 us.
+#ifndef SKY_BYTEMAP_MARKING
+#define SKY_BYTEMAP_MARKING 1
+#endif
+constexpr bool kByteMapMarking = SKY_BYTEMAP_MARKING != 0;
 thread_local std::string t_err;
 thread_local sky_run_stats t_stats = {};
 thread_local sky_phase_times t_phase = {};
@@ -146,6 +157,10 @@ size_t layout(Plan& p, char* base, bool grid_api)
     p.lb_states = c.take<unsigned long long>(p.lb_tiles);
     p.occ = c.take<uint32_t>(p.words);
     p.occ_stage = p.words <= kPrivWords ? c.take<uint32_t>((size_t)map_blocks_bound(n) * p.words) : nullptr;
+    // the byte map pays when the rows at least half fill the grid (clearing
+    // and packing 2^(log2g d) bytes then costs less than the atomics saved)
+    p.occb = (p.bytemap && p.words > kPrivWords && n >= p.words * 16) ? c.take<uint8_t>((size_t)p.words * 32)
+                                                                       : nullptr;
     p.pre = c.take<uint32_t>(p.words);
     p.dom = grid_api ? c.take<uint32_t>(p.words) : nullptr;
     p.ckey = c.take<uint32_t>(n);
@@ -395,6 +410,7 @@ sky_status skyline_enqueue(const float* pts, int64_t n, int32_t d, int64_t ld, c
     const int n_prop = opt ? opt->n_filter : 0;
     const float* prop = n_prop ? opt->d_filter_pts : nullptr;
     f.n_prop = n_prop;
+    p.bytemap = kByteMapMarking;
     CacheKey key;
     key.dev = dev; key.pts = pts; key.n = n; key.ld = ld; key.cap = capacity; key.d = d;
     key.log2g = p.log2g; key.mode = p.map_mode; key.n_prop = n_prop; key.timing = timing == 1 ? 1 : 0;
@@ -946,6 +962,7 @@ sky_status sky_skyline_witness(const float* d_pts, int64_t n, int32_t d, int64_t
     enable_pool_cache();
     void* ws = nullptr;
     int32_t* rep = nullptr;
+    p.bytemap = kByteMapMarking;
     const size_t bytes = layout(p, nullptr, false);
     SKY_CUDA(cudaMallocAsync(&ws, bytes, s));
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&rep), sizeof(int32_t) << (p.log2g * p.d), s);

@@ -51,6 +51,8 @@ struct Plan {
     uint32_t* scount = nullptr;      // [kSurvMaxBlocks] survivors per block of step (c)
     uint32_t* occ = nullptr;         // [words] occupancy bitmap
     uint32_t* occ_stage = nullptr;   // [map blocks][words] private bitmaps (grids of <= kPrivWords words)
+    uint8_t* occb = nullptr;         // [32 words] byte-per-cell occupancy of larger grids (byte-map marking)
+    bool bytemap = false;            // layout: give grids above kPrivWords words a byte map
     uint32_t* pre = nullptr;         // [words] inclusive prefix-OR of occ
     uint32_t* dom = nullptr;         // [words] dominated bitmap (grid API only)
     int64_t words = 0;
