@@ -93,6 +93,17 @@ static_assert(kSparseLive <= 32, "the sparse list is one lane mask wide");
 #ifndef SKY_REFINE_PX_SMEM
 #define SKY_REFINE_PX_SMEM 1
 #endif
+// 1: the (sub-tile, group) pairs of a stage are dealt to the consumer warps
+// in turn; 0: consumer warp w takes sub-tile w of every stage. Clock
+// counters (a copy outside the tree) showed the consumer warps waiting 27 %
+// and the producer 46 % of their time at 2*10^6 x 16, but dealing the pairs
+// measured slower on B300 (10^7 x 16 anti-correlated 124.6 -> 155.5 ms,
+// 4,096-query batch 525 -> 631 ms): more sub-tile reloads per warp.
+
+#ifndef SKY_REFINE_BALANCE
+#define SKY_REFINE_BALANCE 0
+#endif
+constexpr bool kBalance = SKY_REFINE_BALANCE != 0;
 // listed p's tested per step of the list probe (2, 4 or 8; entries past the
 // list's end hold stale codes and their bits are dropped)
 #ifndef SKY_REFINE_PROBE_UNROLL
@@ -514,7 +525,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
         }
     } else {
         // ------------------------------------------------------------ consumers
-        const int qi = warp * 32 + lane;
+        int qi = warp * 32 + lane;   // this lane's q of the sub-tile being tested
         uint32_t listed = 0, gscans = 0;   // per warp (32-bit: a CTA lists far fewer than 2^32)
         uint32_t hits = 0, exact = 0;   // per lane
         for (uint32_t k = 0;; ++k) {
@@ -526,25 +537,26 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
             }
             const uint32_t tt = sm.stage_tile[s];
             if (tt == kEndTile) break;
-            const uint32_t gm = (sm.stage_mask[s] >> (warp * NG)) & ((1u << NG) - 1u);
+            const uint32_t smask = sm.stage_mask[s];
             const bool any_live = __shfl_sync(kFull, sm.live != 0u ? 1 : 0, 0) != 0;
-            if (any_live && gm) {
-                uint32_t Mw[DW];
-#pragma unroll
-                for (int w = 0; w < DW; ++w) Mw[w] = sm.stage_sub[s][warp][w];
-                uint32_t Q[DW];
-#pragma unroll
-                for (int w = 0; w < DW; ++w) Q[w] = sm.qC[s][qi * DW + w];
+            if (any_live && smask) {
                 constexpr bool kFast = SM::kFast;
                 constexpr int FW = SM::FW;
-                uint32_t QF[FW];
-                if constexpr (kFast) {
+                uint32_t Mw[DW], Q[DW], QF[FW];
+                // the codes of sub-tile q of the stage: this lane takes q's point lane
+                auto load_sub = [&](int q) {
+                    qi = q * 32 + lane;
 #pragma unroll
-                    for (int f = 0; f < FW; ++f) QF[f] = fast_word<DW>(Q, f);
-                }
+                    for (int w = 0; w < DW; ++w) Mw[w] = sm.stage_sub[s][q][w];
 #pragma unroll
-                for (int g = 0; g < NG; ++g) {
-                    if (!((gm >> g) & 1u)) continue;   // no live p of group g within reach
+                    for (int w = 0; w < DW; ++w) Q[w] = sm.qC[s][qi * DW + w];
+                    if constexpr (kFast) {
+#pragma unroll
+                        for (int f = 0; f < FW; ++f) QF[f] = fast_word<DW>(Q, f);
+                    }
+                };
+                // sub-tile (loaded) against the live p's of group g
+                auto test_group = [&](int g) {
                     ++gscans;
                     const int pg = g * 32 + lane;
                     uint32_t r = kHigh;
@@ -661,6 +673,33 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                                 probe(pa);
                             }
                         }
+                    }
+                };
+                if constexpr (kBalance) {
+                    // the stage's (sub-tile, group) pairs (bit q * NG + g),
+                    // dealt to the consumer warps in turn, so that a stage
+                    // whose work sits in one sub-tile still spreads over
+                    // all warps
+                    uint32_t rank = 0;
+                    int curq = -1;
+                    for (uint32_t mm = smask; mm; mm &= mm - 1u, ++rank) {
+                        if ((int)(rank % (uint32_t)NG) != warp) continue;
+                        const int bit = __ffs(mm) - 1;
+                        const int q = bit / NG;
+                        if (q != curq) {
+                            load_sub(q);
+                            curq = q;
+                        }
+                        test_group(bit % NG);
+                    }
+                } else {
+                    // warp w takes sub-tile w and every group within its reach
+                    const uint32_t gm = (smask >> (warp * NG)) & ((1u << NG) - 1u);
+                    if (gm) {
+                        load_sub(warp);
+#pragma unroll
+                        for (int g = 0; g < NG; ++g)
+                            if ((gm >> g) & 1u) test_group(g);
                     }
                 }
             }
