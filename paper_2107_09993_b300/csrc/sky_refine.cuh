@@ -93,6 +93,14 @@ static_assert(kSparseLive <= 32, "the sparse list is one lane mask wide");
 #ifndef SKY_REFINE_PX_SMEM
 #define SKY_REFINE_PX_SMEM 1
 #endif
+// 1: with fast codes, a block of listed entries is first reduced to one
+// "any pass" word (a running minimum) and the per-entry hit bits are formed
+// only for the rare blocks that hold a pass. Measured on B300 at d = 16: no
+// gain (10^7 x 16 anti-correlated 124.6 -> 125.7 ms), so off
+#ifndef SKY_REFINE_MIN_PROBE
+#define SKY_REFINE_MIN_PROBE 0
+#endif
+constexpr bool kMinProbe = SKY_REFINE_MIN_PROBE != 0;
 // 1: the (sub-tile, group) pairs of a stage are dealt to the consumer warps
 // in turn; 0: consumer warp w takes sub-tile w of every stage. Clock
 // counters (a copy outside the tree) showed the consumer warps waiting 27 %
@@ -103,7 +111,7 @@ static_assert(kSparseLive <= 32, "the sparse list is one lane mask wide");
 #ifndef SKY_REFINE_BALANCE
 #define SKY_REFINE_BALANCE 0
 #endif
-constexpr bool kBalance = SKY_REFINE_BALANCE != 0;
+constexpr bool kBalance = SKY_REFINE_BALANCE == 1;
 // listed p's tested per step of the list probe (2, 4 or 8; entries past the
 // list's end hold stale codes and their bits are dropped)
 #ifndef SKY_REFINE_PROBE_UNROLL
@@ -630,6 +638,24 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                             uint32_t hb = 0;
                             constexpr int PU = SKY_REFINE_PROBE_UNROLL;
                             for (int j0 = 0; j0 < k; j0 += PU) {
+                                if constexpr (kFast && kMinProbe) {
+                                    // the block's entries first: H & ~(d0 & d1) is zero
+                                    // exactly for an entry that passes, so the block
+                                    // holds a pass iff the smallest such word is zero
+                                    // (stale entries past k take part; a pass among
+                                    // them only costs the exact pass below)
+                                    uint32_t miss = 0xffffffffu;
+#pragma unroll
+                                    for (int u = 0; u < PU; ++u) {
+                                        uint32_t c[FW];
+                                        load_entry<FW>(L + (j0 + u) * DWL, c);
+                                        uint32_t a = kHighNib;
+#pragma unroll
+                                        for (int f = 0; f < FW; ++f) a &= c[f] - QF[f];
+                                        miss = min(miss, a ^ kHighNib);
+                                    }
+                                    if (miss != 0u) continue;
+                                }
                                 uint32_t nb = 0;   // hit bits of entries j0 .. j0 + PU - 1
 #pragma unroll
                                 for (int u = 0; u < PU; ++u) {
@@ -693,10 +719,12 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                         test_group(bit % NG);
                     }
                 } else {
-                    // warp w takes sub-tile w and every group within its reach
-                    const uint32_t gm = (smask >> (warp * NG)) & ((1u << NG) - 1u);
+                    // warp w takes sub-tile w (rotated by the stage number
+                    // with SKY_REFINE_BALANCE = 2) and every group within its reach
+                    const int q = SKY_REFINE_BALANCE == 2 ? (int)((warp + k) % (uint32_t)NG) : warp;
+                    const uint32_t gm = (smask >> (q * NG)) & ((1u << NG) - 1u);
                     if (gm) {
-                        load_sub(warp);
+                        load_sub(q);
 #pragma unroll
                         for (int g = 0; g < NG; ++g)
                             if ((gm >> g) & 1u) test_group(g);
