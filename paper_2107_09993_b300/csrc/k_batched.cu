@@ -343,6 +343,14 @@ struct BatchMinBlocks {
                                : DP == 12 ? SKY_BATCH_MINB_12 : SKY_BATCH_MINB_16;
 };
 
+// 1: the batched refinement also finishes p-tiles with few live points in
+// sparse mode and keeps the producer's group maxima in registers, like the
+// single-set kernel; 0: ring to the end, maxima in shared memory
+#ifndef SKY_BATCH_SPARSE
+#define SKY_BATCH_SPARSE 0
+#endif
+constexpr bool kBatchSparse = SKY_BATCH_SPARSE != 0;
+
 // S: ring stages; FAST: fast-code list probe (both chosen per padded-
 // dimension class at launch time, e.g. by the autotuner).
 template <int DP, int S, bool FAST>
@@ -363,8 +371,8 @@ __global__ void __launch_bounds__(kTQ + 32, BatchMinBlocks<DP>::value) kb_refine
         const QueryPlan& q = qps[w.x];
         const uint32_t m = q.res->survivors;
         if ((uint32_t)w.y < (m + kTQ - 1) / kTQ)
-            refine::refine_ptile<DP, false, false, SM>(sm, q.X, q.C, q.ids, q.sub, q.tend, q.supmin, m, (uint32_t)w.y,
-                                                       q.res, q.keep);
+            refine::refine_ptile<DP, kBatchSparse, false, SM>(sm, q.X, q.C, q.ids, q.sub, q.tend, q.supmin, m,
+                                                              (uint32_t)w.y, q.res, q.keep);
     }
 }
 
