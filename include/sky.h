@@ -403,6 +403,37 @@ SKY_API sky_status sky_batch_stats(const sky_batch* batch, void* stream, sky_bat
 SKY_API void sky_batch_destroy(sky_batch* batch);        /* NULL accepted */
 SKY_API const char* sky_batch_last_error(void);          /* thread-local detail */
 
+/*
+ * Batched skylines planned on the device. The query records stay in device
+ * memory (d_queries: n_queries sky_query) and may be written by earlier work
+ * on `stream`; the planning of sky_batch_create (validation, grid layer and
+ * sort-key bits, per-query arrays in the workspace, work items grouped by
+ * padded-dimension class with larger queries first) runs in a kernel, so the
+ * call enqueues the whole batch without synchronising, allocating or copying,
+ * and may be recorded in a CUDA graph. The grids of the batched kernels are
+ * sized by the bounds; the kernels read the planned counts.
+ *
+ * Bounds: n_queries and max_total_rows (the largest sum of row_count over
+ * the valid queries that a call will see). d_ws: at least
+ * sky_batched_device_workspace_size(n_cols, n_queries, max_total_rows) bytes,
+ * 256-byte aligned. Outputs as in sky_batch_bind (d_out_offsets n_queries + 1
+ * int64 CSR, d_query_status n_queries int32), written by the device.
+ * Per-query status: SKY_ERR_INVALID_ARGUMENT for a bad row range, flag or
+ * dim_mask (the query returns no indices); SKY_ERR_TOO_LARGE for every query
+ * when the valid queries hold more than max_total_rows rows (nothing runs);
+ * otherwise as sky_skyline_batched. Grid layers are automatic (log2_g * d
+ * <= 18) and the refinement uses the library's default variants (no tuning).
+ * Returns SKY_ERR_INVALID_ARGUMENT / SKY_ERR_CAPACITY (workspace too small)
+ * before enqueuing anything, SKY_ERR_CUDA when a launch fails; the detail is
+ * in sky_batch_last_error().
+ */
+SKY_API size_t sky_batched_device_workspace_size(int32_t n_cols, int32_t n_queries, int64_t max_total_rows);
+SKY_API sky_status sky_skyline_batched_device(const float* d_table, int64_t n_rows, int32_t n_cols,
+                                              int64_t row_stride, int64_t col_stride, const sky_query* d_queries,
+                                              int32_t n_queries, int64_t max_total_rows, void* d_ws, size_t ws_bytes,
+                                              int32_t* d_out_idx, int64_t out_capacity, int64_t* d_out_offsets,
+                                              int32_t* d_query_status, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Learned proposal (a project addition; the paper has no counterpart). A    */
 /* 3-layer perceptron (636 -> 64 -> 64 -> 264, ReLU, bfloat16 weights, fp32  */

@@ -447,6 +447,9 @@ def _load_batched():
         "sky_batch_stats": ([_vp, _vp, P(BatchStats)], _i32),
         "sky_batch_destroy": ([_vp], None),
         "sky_batch_last_error": ([], ctypes.c_char_p),
+        "sky_batched_device_workspace_size": ([_i32, _i32, _i64], _sz),
+        "sky_skyline_batched_device": ([_vp, _i64, _i32, _i64, _i64, _vp, _i32, _i64, _vp, _sz, _vp, _i64, _vp, _vp,
+                                        _vp], _i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -571,6 +574,86 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+QUERY_RECORD_BYTES = 88   # sizeof(sky_query): int64 row_begin, int64 row_count, uint32 dim_mask, uint32 flags,
+                          # float origin[16]
+
+
+def query_records(row_begin, row_count, dim_mask, origins=None):
+    """sky_query records built on the device from CUDA tensors (row_begin,
+    row_count: int64 [nq]; dim_mask: int [nq], the low 32 bits; origins:
+    optional float32 [nq, 16], a row with any non-NaN value marks a quadrant
+    query). Returns a uint8 CUDA tensor [nq, 88] without a host round trip."""
+    torch = _torch()
+    nq = row_begin.numel()
+    dev = row_begin.device
+    rec = torch.zeros(nq, QUERY_RECORD_BYTES // 4, dtype=torch.int32, device=dev)
+    w64 = rec.view(torch.int64)
+    w64[:, 0] = row_begin.to(torch.int64)
+    w64[:, 1] = row_count.to(torch.int64)
+    m = dim_mask.to(torch.int64) & 0xffffffff
+    rec[:, 4] = torch.where(m >= 2 ** 31, m - 2 ** 32, m).to(torch.int32)
+    if origins is not None:
+        o = origins.to(device=dev, dtype=torch.float32).reshape(nq, 16)
+        quad = ~torch.isnan(o).all(dim=1)
+        rec[:, 5] = quad.to(torch.int32) * QUERY_QUADRANT
+        rec[:, 6:22] = torch.nan_to_num(o, nan=0.0).view(torch.int32)
+    return rec.view(torch.uint8)
+
+
+class DeviceBatch:
+    """Batched skylines planned on the device (sky_skyline_batched_device):
+    the query records live in device memory, the workspace is sized from the
+    bounds (n_queries, max_total_rows), and run() enqueues the whole batch
+    without synchronising, so it can be recorded in a CUDA graph and the
+    records rewritten on the device between launches."""
+
+    def __init__(self, table, n_queries: int, max_total_rows: int, capacity=None):
+        torch = _torch()
+        lib = _load_batched()
+        if table.dim() != 2 or table.dtype != torch.float32 or not table.is_cuda:
+            raise ValueError("table must be a 2-D float32 CUDA tensor")
+        self.table = table
+        self.nq = int(n_queries)
+        self.max_total_rows = int(max_total_rows)
+        n_cols = table.shape[1]
+        self.ws_bytes = lib.sky_batched_device_workspace_size(n_cols, self.nq, self.max_total_rows)
+        if self.ws_bytes == 0:
+            raise SkyError(1, "bad bounds for a device-planned batch")
+        dev = table.device
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=dev)
+        self._ws_ptr = (self.ws.data_ptr() + 255) // 256 * 256
+        self.capacity = self.max_total_rows if capacity is None else int(capacity)
+        self.out = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=dev)
+        self.offsets = torch.zeros(self.nq + 1, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(max(self.nq, 1), dtype=torch.int32, device=dev)
+
+    def run(self, records, stream=None):
+        """Enqueues the batch for `records` (uint8 CUDA tensor [n_queries, 88],
+        see query_records) on `stream` (asynchronous; no host copy)."""
+        torch = _torch()
+        if records.dtype != torch.uint8 or not records.is_cuda or records.numel() != self.nq * QUERY_RECORD_BYTES:
+            raise ValueError("records must be a uint8 CUDA tensor of n_queries x 88 bytes")
+        if not records.is_contiguous() or records.data_ptr() % 8:
+            raise ValueError("records must be contiguous and 8-byte aligned")
+        t = self.table
+        with torch.cuda.device(t.device):
+            _bcheck(_load_batched().sky_skyline_batched_device(
+                _vp(t.data_ptr()), t.shape[0], t.shape[1], t.stride(0), t.stride(1), _vp(records.data_ptr()),
+                self.nq, self.max_total_rows, _vp(self._ws_ptr), self.ws_bytes, _vp(self.out.data_ptr()),
+                self.capacity, _vp(self.offsets.data_ptr()), _vp(self.status.data_ptr()), _stream_ptr(stream)))
+
+    def results(self):
+        """Per-query ascending global row ids (CPU int32 arrays); synchronises."""
+        torch = _torch()
+        torch.cuda.synchronize(self.table.device)
+        off = self.offsets.cpu().numpy()
+        out = self.out.cpu().numpy()
+        return [out[off[i]:off[i + 1]] for i in range(self.nq)]
+
+    def query_status(self):
+        return self.status[:self.nq].cpu().numpy()
 
 
 # ---------------------------------------------------------- learned proposal --

@@ -50,9 +50,18 @@ __device__ __forceinline__ float elem(const QueryPlan& q, int64_t r, int k)
 constexpr uint32_t kOutsideKey = 0xffffffffu;
 
 // ---------------------------------------------------------------- (a)+(b)
+// A count of work items passed as -1 is read from the prefix array (a batch
+// planned on the device, whose counts the host does not know); the grids of
+// such launches are sized by bounds and blocks past the count exit at once.
+__device__ __forceinline__ int64_t items_of(const int64_t* prefix, int nq, int64_t nitems)
+{
+    return nitems >= 0 ? nitems : prefix[nq];
+}
+
 __global__ void __launch_bounds__(kT) kb_map(const QueryPlan* __restrict__ qps, int nq,
                                              const int64_t* __restrict__ pchunk, int64_t nitems)
 {
+    nitems = items_of(pchunk, nq, nitems);
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int qi = find_query(pchunk, nq, item);
         const QueryPlan& q = qps[qi];
@@ -117,6 +126,7 @@ __global__ void __launch_bounds__(kT) kb_survivors(const QueryPlan* __restrict__
     if (threadIdx.x == 0) s_item = atomicAdd(claim, 1u);
     __syncthreads();
     const int64_t item = s_item;
+    if (item >= pchunk[nq]) return;
     const int qi = find_query(pchunk, nq, item);
     const QueryPlan& q = qps[qi];
     const uint32_t tile = (uint32_t)(item - pchunk[qi]);
@@ -172,6 +182,7 @@ __global__ void __launch_bounds__(kT) kb_radix_hist(const QueryPlan* __restrict_
                                                     const int64_t* __restrict__ pchunk, int ps)
 {
     const int64_t item = blockIdx.x;
+    if (item >= pchunk[nq]) return;
     const int qi = find_query(pchunk, nq, item);
     const QueryPlan& q = qps[qi];
     if (ps >= q.passes) return;
@@ -203,6 +214,7 @@ __global__ void __launch_bounds__(kT) kb_radix_scatter(const QueryPlan* __restri
                                                        const int64_t* __restrict__ pchunk, int ps)
 {
     const int64_t item = blockIdx.x;
+    if (item >= pchunk[nq]) return;
     const int qi = find_query(pchunk, nq, item);
     const QueryPlan& q = qps[qi];
     if (ps >= q.passes) return;
@@ -220,6 +232,7 @@ __global__ void __launch_bounds__(kTQ) kb_gather(const QueryPlan* __restrict__ q
 {
     __shared__ uint32_t s_sub[kTQ / 32][4];
     const int64_t item = blockIdx.x;
+    if (item >= ptile[nq]) return;
     const int qi = find_query(ptile, nq, item);
     const QueryPlan& q = qps[qi];
     const uint32_t t = (uint32_t)(item - ptile[qi]);
@@ -301,7 +314,7 @@ __global__ void __launch_bounds__(256) kb_supmin(const QueryPlan* __restrict__ q
 {
     const int lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (item >= items) return;
+    if (item >= items_of(ptile, nq, items)) return;
     const int qi = find_query(ptile, nq, item);
     const QueryPlan& q = qps[qi];
     const uint32_t t0 = (uint32_t)(item - ptile[qi]);
@@ -353,14 +366,21 @@ constexpr bool kBatchSparse = SKY_BATCH_SPARSE != 0;
 
 // S: ring stages; FAST: fast-code list probe (both chosen per padded-
 // dimension class at launch time, e.g. by the autotuner).
+// d_class (a batch planned on the device): the class's first item and item
+// count are d_class[cls] and d_class[4 + cls] instead of `items` / `nitems`.
 template <int DP, int S, bool FAST>
 __global__ void __launch_bounds__(kTQ + 32, BatchMinBlocks<DP>::value) kb_refine(const QueryPlan* __restrict__ qps,
-                                                      const int2* __restrict__ items, int nitems, uint32_t* claim)
+                                                      const int2* __restrict__ items, int nitems, uint32_t* claim,
+                                                      const int* __restrict__ d_class, int cls)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     using SM = refine::RefineSmem<DP, S, FAST>;
     SM& sm = *reinterpret_cast<SM*>(smem_raw);
     __shared__ int s_item;
+    if (d_class) {
+        items += d_class[cls];
+        nitems = d_class[4 + cls];
+    }
     while (true) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(claim, 1u);
         __syncthreads();
@@ -385,6 +405,7 @@ __global__ void __launch_bounds__(kT) kb_emit(const QueryPlan* __restrict__ qps,
     if (threadIdx.x == 0) s_item = atomicAdd(claim, 1u);
     __syncthreads();
     const int64_t item = s_item;
+    if (item >= pchunk[nq]) return;
     const int qi = find_query(pchunk, nq, item);
     const QueryPlan& q = qps[qi];
     const uint32_t tile = (uint32_t)(item - pchunk[qi]);
@@ -431,6 +452,10 @@ __global__ void __launch_bounds__(1024) kb_finish(const QueryPlan* __restrict__ 
         offsets[q] = run;
         const uint32_t err = p.n ? p.res->err : 0u;
         int32_t st = 0;                                   // SKY_OK
+        if (p.invalid) {   // planned on the device: a bad query, or beyond the workspace bound
+            status[q] = p.invalid == 1 ? 1 : 6;          // SKY_ERR_INVALID_ARGUMENT / SKY_ERR_TOO_LARGE
+            continue;
+        }
         if (err & SKY_DEV_ERR_NONFINITE) st = 2;          // SKY_ERR_NONFINITE
         else if (err & SKY_DEV_ERR_TIMEOUT) st = 7;       // SKY_ERR_TIMEOUT
         else if (run + c > capacity) st = 3;              // SKY_ERR_CAPACITY
@@ -444,6 +469,7 @@ __global__ void __launch_bounds__(kT) kb_copy(const QueryPlan* __restrict__ qps,
                                               const int64_t* __restrict__ pchunk, int64_t nitems,
                                               const int64_t* __restrict__ offsets, int32_t* out, int64_t capacity)
 {
+    nitems = items_of(pchunk, nq, nitems);
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int qi = find_query(pchunk, nq, item);
         const QueryPlan& q = qps[qi];
@@ -470,7 +496,7 @@ int sm_count()
 
 template <int DP, int S, bool FAST>
 cudaError_t launch_kb_refine_v(const QueryPlan* qps, const int2* items, int nitems, uint32_t* claim, int ctas_per_sm,
-                               cudaStream_t s)
+                               const int* d_class, int cls, cudaStream_t s)
 {
     auto* kern = batched::kb_refine<DP, S, FAST>;
     const int smem = (int)sizeof(refine::RefineSmem<DP, S, FAST>);
@@ -484,9 +510,9 @@ cudaError_t launch_kb_refine_v(const QueryPlan* qps, const int2* items, int nite
     if (resident < 1) resident = 1;
     const int per_sm = (ctas_per_sm <= 0 || ctas_per_sm > resident) ? resident : ctas_per_sm;
     int grid = sm_count() * per_sm;
-    if (grid > nitems) grid = nitems;
+    if (grid > nitems) grid = nitems;   // device-planned: nitems is the bound
     if (grid < 1) return cudaSuccess;
-    kern<<<grid, refine::kTQ + 32, smem, s>>>(qps, items, nitems, claim);
+    kern<<<grid, refine::kTQ + 32, smem, s>>>(qps, items, nitems, claim, d_class, cls);
     return cudaGetLastError();
 }
 
@@ -494,13 +520,13 @@ cudaError_t launch_kb_refine_v(const QueryPlan* qps, const int2* items, int nite
 // (other values: 8), fast codes on or off.
 template <int DP>
 cudaError_t launch_kb_refine(const QueryPlan* qps, const int2* items, int nitems, uint32_t* claim, int ctas_per_sm,
-                             int stages, bool fast, cudaStream_t s)
+                             int stages, bool fast, const int* d_class, int cls, cudaStream_t s)
 {
     if (stages == 4)
-        return fast ? launch_kb_refine_v<DP, 4, true>(qps, items, nitems, claim, ctas_per_sm, s)
-                    : launch_kb_refine_v<DP, 4, false>(qps, items, nitems, claim, ctas_per_sm, s);
-    return fast ? launch_kb_refine_v<DP, 8, true>(qps, items, nitems, claim, ctas_per_sm, s)
-                : launch_kb_refine_v<DP, 8, false>(qps, items, nitems, claim, ctas_per_sm, s);
+        return fast ? launch_kb_refine_v<DP, 4, true>(qps, items, nitems, claim, ctas_per_sm, d_class, cls, s)
+                    : launch_kb_refine_v<DP, 4, false>(qps, items, nitems, claim, ctas_per_sm, d_class, cls, s);
+    return fast ? launch_kb_refine_v<DP, 8, true>(qps, items, nitems, claim, ctas_per_sm, d_class, cls, s)
+                : launch_kb_refine_v<DP, 8, false>(qps, items, nitems, claim, ctas_per_sm, d_class, cls, s);
 }
 
 }  // namespace
@@ -508,10 +534,13 @@ cudaError_t launch_kb_refine(const QueryPlan* qps, const int2* items, int nitems
 cudaError_t launch_batched(const BatchLaunch& b, cudaStream_t s)
 {
     using namespace batched;
-    cudaMemsetAsync(b.zero_base, 0, b.zero_bytes, s);
+    // a batch planned on the device passes bounds as counts; the kernels read
+    // the actual counts (-1 below) and its planner has zeroed its arrays
+    const bool dev = b.d_class != nullptr;
+    if (!dev) cudaMemsetAsync(b.zero_base, 0, b.zero_bytes, s);
     if (b.chunk_items > 0) {
         const int grid = (int)std::min<int64_t>(b.chunk_items, (int64_t)sm_count() * 8);
-        kb_map<<<grid, kT, 0, s>>>(b.qps, b.nq, b.pchunk, b.chunk_items);
+        kb_map<<<grid, kT, 0, s>>>(b.qps, b.nq, b.pchunk, dev ? -1 : b.chunk_items);
         kb_prefix<<<b.nq, 512, (size_t)b.max_words * 4, s>>>(b.qps);
         kb_survivors<<<(unsigned)b.chunk_items, kT, 0, s>>>(b.qps, b.nq, b.pchunk, b.claims + 0);
         for (int ps = 0; ps < b.max_passes; ++ps) {
@@ -522,7 +551,7 @@ cudaError_t launch_batched(const BatchLaunch& b, cudaStream_t s)
     }
     if (b.tile_items > 0) {
         kb_gather<<<(unsigned)b.tile_items, kTQ, 0, s>>>(b.qps, b.nq, b.ptile);
-        kb_supmin<<<(unsigned)((b.tile_items + 7) / 8), 256, 0, s>>>(b.qps, b.nq, b.ptile, b.tile_items);
+        kb_supmin<<<(unsigned)((b.tile_items + 7) / 8), 256, 0, s>>>(b.qps, b.nq, b.ptile, dev ? -1 : b.tile_items);
     }
     // step (d): one persistent kernel per padded-dimension class, in turn on
     // `s`, or (concurrent_classes) as parallel branches on the class streams
@@ -547,10 +576,10 @@ cudaError_t launch_batched(const BatchLaunch& b, cudaStream_t s)
         const bool fast = b.class_fast[c] != 0;
         cudaError_t e = cudaSuccess;
         switch (c) {
-            case 0: e = launch_kb_refine<4>(b.qps, it, n, claim, ctas, st, fast, cs); break;
-            case 1: e = launch_kb_refine<8>(b.qps, it, n, claim, ctas, st, fast, cs); break;
-            case 2: e = launch_kb_refine<12>(b.qps, it, n, claim, ctas, st, fast, cs); break;
-            default: e = launch_kb_refine<16>(b.qps, it, n, claim, ctas, st, fast, cs); break;
+            case 0: e = launch_kb_refine<4>(b.qps, it, n, claim, ctas, st, fast, b.d_class, c, cs); break;
+            case 1: e = launch_kb_refine<8>(b.qps, it, n, claim, ctas, st, fast, b.d_class, c, cs); break;
+            case 2: e = launch_kb_refine<12>(b.qps, it, n, claim, ctas, st, fast, b.d_class, c, cs); break;
+            default: e = launch_kb_refine<16>(b.qps, it, n, claim, ctas, st, fast, b.d_class, c, cs); break;
         }
         if (e != cudaSuccess) return e;
         if (par) {
@@ -563,7 +592,7 @@ cudaError_t launch_batched(const BatchLaunch& b, cudaStream_t s)
     kb_finish<<<1, 1024, 0, s>>>(b.qps, b.nq, b.capacity, b.offsets, b.status);
     if (b.chunk_items > 0) {
         const int grid = (int)std::min<int64_t>(b.chunk_items, (int64_t)sm_count() * 8);
-        kb_copy<<<grid, kT, 0, s>>>(b.qps, b.nq, b.pchunk, b.chunk_items, b.offsets, b.out, b.capacity);
+        kb_copy<<<grid, kT, 0, s>>>(b.qps, b.nq, b.pchunk, dev ? -1 : b.chunk_items, b.offsets, b.out, b.capacity);
     }
     return cudaGetLastError();
 }

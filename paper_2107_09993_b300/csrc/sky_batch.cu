@@ -391,4 +391,43 @@ void sky_batch_destroy(sky_batch* b)
     delete b;
 }
 
+size_t sky_batched_device_workspace_size(int32_t n_cols, int32_t n_queries, int64_t max_total_rows)
+{
+    if (n_cols < 1 || n_cols > 32 || n_queries < 0 || max_total_rows < 0) return 0;
+    return batched_device_workspace_bytes(n_cols, n_queries, max_total_rows);
+}
+
+sky_status sky_skyline_batched_device(const float* d_table, int64_t n_rows, int32_t n_cols, int64_t row_stride,
+                                      int64_t col_stride, const sky_query* d_queries, int32_t n_queries,
+                                      int64_t max_total_rows, void* d_ws, size_t ws_bytes, int32_t* d_out_idx,
+                                      int64_t out_capacity, int64_t* d_out_offsets, int32_t* d_query_status,
+                                      void* stream)
+{
+    if (n_rows < 0 || n_rows >= (int64_t(1) << 31)) return bfail(SKY_ERR_INVALID_ARGUMENT, "n_rows outside [0, 2^31)");
+    if (n_cols < 1 || n_cols > 32) return bfail(SKY_ERR_INVALID_ARGUMENT, "n_cols outside [1, 32]");
+    if (n_queries < 0 || (n_queries > 0 && !d_queries)) return bfail(SKY_ERR_INVALID_ARGUMENT, "bad query array");
+    if (max_total_rows < 0 || max_total_rows >= (int64_t(1) << 31))
+        return bfail(SKY_ERR_INVALID_ARGUMENT, "max_total_rows outside [0, 2^31)");
+    if (n_rows > 0 && !d_table) return bfail(SKY_ERR_INVALID_ARGUMENT, "NULL table");
+    if (reinterpret_cast<uintptr_t>(d_table) & 3u) return bfail(SKY_ERR_INVALID_ARGUMENT, "table not 4-byte aligned");
+    const bool row_major = col_stride == 1 && row_stride >= n_cols;
+    const bool col_major = row_stride == 1 && col_stride >= n_rows;
+    if (!row_major && !col_major)
+        return bfail(SKY_ERR_INVALID_ARGUMENT, "strides must describe a row-major (col_stride 1) or "
+                                               "column-major (row_stride 1) table");
+    if (!d_out_offsets || (n_queries > 0 && !d_query_status) || out_capacity < 0 || (out_capacity > 0 && !d_out_idx))
+        return bfail(SKY_ERR_INVALID_ARGUMENT, "bad output buffers");
+    const size_t need = batched_device_workspace_bytes(n_cols, n_queries, max_total_rows);
+    if (!d_ws || ws_bytes < need) return bfail(SKY_ERR_CAPACITY, "workspace needs %zu bytes", need);
+    if ((reinterpret_cast<uintptr_t>(d_ws) & 255u) != 0)
+        return bfail(SKY_ERR_INVALID_ARGUMENT, "workspace not 256-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (n_queries == 0) e = cudaMemsetAsync(d_out_offsets, 0, sizeof(int64_t), s);
+    else e = launch_batched_device(d_table, n_rows, n_cols, row_stride, col_stride, d_queries, n_queries, max_total_rows,
+                                   d_ws, ws_bytes, d_out_idx, out_capacity, d_out_offsets, d_query_status, s);
+    if (e != cudaSuccess) return bfail(SKY_ERR_CUDA, "batched launch: %s", cudaGetErrorString(e));
+    return SKY_OK;
+}
+
 }  // extern "C"

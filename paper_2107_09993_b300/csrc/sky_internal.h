@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct sky_query;   // include/sky.h
+
 namespace sky {
 
 // Per-call result block, copied to the host once at the end of a call.
@@ -94,6 +96,7 @@ struct QueryPlan {
     int32_t d, dp, log2g, mbits, passes, dpclass;
     int32_t col[16];
     int32_t quadrant;         // 1: only rows >= origin (every column) take part
+    int32_t invalid;          // planned on the device: 1 bad query, 2 beyond the workspace bound (n = 0)
     float origin[16];
     int64_t words, chunks, tiles;
     uint2* keys;
@@ -195,6 +198,10 @@ struct BatchLaunch {
     bool concurrent_classes = false;        // class kernels as parallel branches
     cudaStream_t class_streams[4] = {};     // (owned by the batch)
     cudaEvent_t fork = nullptr, joins[4] = {};
+    // planned on the device: [0..3] first item, [4..7] items of each class
+    // (the counts above are then bounds, and chunk / tile counts are read
+    // from pchunk[nq] / ptile[nq])
+    const int* d_class = nullptr;
     int32_t* out = nullptr;
     int64_t capacity = 0;
     int64_t* offsets = nullptr;
@@ -202,6 +209,12 @@ struct BatchLaunch {
 };
 cudaError_t launch_batched(const BatchLaunch& b, cudaStream_t s);
 int batched_kernel_count(const BatchLaunch& b);
+// k_bplan.cu: the batch planned on the device (sky_skyline_batched_device)
+size_t batched_device_workspace_bytes(int n_cols, int nq, int64_t max_total_rows);
+cudaError_t launch_batched_device(const float* table, int64_t n_rows, int n_cols, int64_t rs, int64_t cs,
+                                  const ::sky_query* d_queries, int nq, int64_t max_total_rows, void* ws,
+                                  size_t ws_bytes, int32_t* out, int64_t capacity, int64_t* offsets, int32_t* status,
+                                  cudaStream_t s);
 
 constexpr int kMaxAutoLayer = 8;   // the automatic layer never exceeds 8 (256 columns per dimension)
 int auto_log2g(int64_t n, int d);
