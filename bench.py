@@ -429,6 +429,17 @@ def batched_vs_plain(sky, torch, dev, reps=3):
     bad = int((b.query_status() != 0).sum())
     knobs = {k: v for k, v in (b.tuning or {}).items() if k != "log2g"}
     b.close()
+    # the same queries planned on the device (sky_skyline_batched_device):
+    # records in device memory, bound-sized grids, library default variants
+    qd = torch.as_tensor(np.asarray(q, dtype=np.int64)).to(dev)
+    rec = sky.query_records(qd[:, 0], qd[:, 1], qd[:, 2])
+    db = sky.DeviceBatch(tc, nq, int(q[:, 1].sum()))
+    for _ in range(2):
+        db.run(rec)
+    md = [time_step(lambda: db.run(rec), stream, dev)[0] for _ in range(reps)]
+    dres = db.results()
+    dsame = all(np.array_equal(x, y) for x, y in zip(dres, bres)) and bool((db.query_status() == 0).all())
+    del db, dres, rec, qd
     del tc
     subs, outs = [], []
     for (r0, c, m) in q:
@@ -454,6 +465,9 @@ def batched_vs_plain(sky, torch, dev, reps=3):
     return {"workload": "batched: 4,096 queries on a 20M x 12 mixed table (seed 2), column-major",
             "tuning": {"applied": tuned, "source": "paper_2107_09993_b300/tuning.json (tune.py, this GPU's entry)",
                        "knobs": knobs, "batched_default_ms": round(statistics.median(mb0), 2)},
+            "device_planned": {"ms": round(statistics.median(md), 2), "identical": dsame,
+                               "what": "sky_skyline_batched_device: queries in device memory, planned by a kernel, "
+                                       "no host round trip (default variants)"},
             "points": pts, "batched_ms": round(mbm, 2), "looped_plain_ms": round(mlm, 2),
             "speedup": round(mlm / mbm, 3), "batched_points_per_s": round(pts / (mbm / 1e3), 1),
             "identical": bool(same), "query_errors": bad, "skyline": st["skyline"], "survivors": st["survivors"],

@@ -591,8 +591,10 @@ SKY_API sky_status sky_last_phase_times(sky_phase_times* out);
  * caller. The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before starting any stream capture on the device. Synchronises `stream`
- * once. Errors are described by sky_noalloc_last_error() (and by
- * sky_last_error(), which each call also sets).
+ * once, so it cannot be recorded in a CUDA graph: on a stream that is being
+ * captured it returns SKY_ERR_INVALID_ARGUMENT and enqueues nothing. Errors
+ * are described by sky_noalloc_last_error() (and by sky_last_error(), which
+ * each call also sets).
  */
 #define SKY_NOALLOC_MAX_POINTS 65536
 SKY_API sky_status sky_skyline_noalloc(const float* d_pts, int64_t n, int32_t d, int64_t ld,

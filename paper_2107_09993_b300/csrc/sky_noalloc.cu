@@ -96,6 +96,13 @@ extern "C" sky_status sky_skyline_noalloc(const float* d_pts, int64_t n, int32_t
         return noalloc_fail(SKY_ERR_INVALID_ARGUMENT, "bad output buffer");
     if (opt && (opt->n_filter < 0 || opt->n_filter > 16 || (opt->n_filter > 0 && !opt->d_filter_pts)))
         return noalloc_fail(SKY_ERR_INVALID_ARGUMENT, "bad filter proposals");
+    // the call reads the count back (one synchronisation): a stream that is
+    // being captured cannot run it, and is left untouched
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap) != cudaSuccess ||
+        cap != cudaStreamCaptureStatusNone)
+        return noalloc_fail(SKY_ERR_INVALID_ARGUMENT, "stream is being captured: the call synchronises its stream "
+                                                      "and cannot be recorded in a graph");
     if (n == 0) { *h_out_count = 0; return SKY_OK; }
 
     Plan p;

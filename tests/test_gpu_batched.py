@@ -128,8 +128,9 @@ def test_full_batched_workload_every_query():
     """The full batched workload in the bench's launch configuration: 4,096
     queries (seed 2) on the 20M x 12 mixed table (seed 2, column-major on the
     device), one launch. For every query:
-    * the batched result equals the single-set path's on the same rows and
-      columns, in witness mode, and every row it drops carries a row that
+    * the batched result (planned on the host, and again planned on the
+      device) equals the single-set path's on the same rows and columns, in
+      witness mode, and every row it drops carries a row that
       dominates it (Definition 1) -- so every skyline row is returned;
     * the result equals the oracle's whole result (size and SHA-256 from
       tests/golden/fullsize_oracle.json) wherever the oracle could finish
@@ -146,6 +147,15 @@ def test_full_batched_workload_every_query():
     res = b.results()
     assert np.all(b.query_status() == 0)
     b.close()
+    del b
+    # the same batch planned on the device returns the same arrays
+    qd = torch.as_tensor(np.asarray(q, dtype=np.int64)).cuda()
+    db = sky.DeviceBatch(tc, nq, int(q[:, 1].sum()))
+    db.run(sky.query_records(qd[:, 0], qd[:, 1], qd[:, 2]))
+    dres = db.results()
+    assert np.all(db.query_status() == 0)
+    assert all(np.array_equal(x, y) for x, y in zip(dres, res))
+    del db, dres
     del tc
     gold = (golden_fullsize().get("c4") or {}).get("per_query") or [None] * nq
     exact = sampled = 0

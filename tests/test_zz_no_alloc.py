@@ -98,3 +98,25 @@ def test_noalloc_refuses_oversized_requests():
     want = sky.skyline(y).cpu()
     st, cnt, out = _noalloc(lib, y, want.numel() - 1)
     assert st == 3 and cnt == want.numel()
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call synchronises its stream, so under stream capture it returns
+    SKY_ERR_INVALID_ARGUMENT without touching the capture; the captured work
+    and later calls are unaffected."""
+    lib = _bind(sky.load())
+    x = torch.from_numpy(skydata.generate("independent", 1000, 4, seed=5)).cuda()
+    want = sky.skyline(x).cpu()
+    assert _noalloc(lib, x, 1000)[0] == 0          # first call (address look-up) before any capture
+    y = torch.empty_like(x)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        y.copy_(x)
+        st, _, _ = _noalloc(lib, y, 1000)
+    assert st == 1 and b"captured" in lib.sky_noalloc_last_error()
+    y.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, x)
+    st, cnt, out = _noalloc(lib, y, 1000)
+    assert st == 0 and torch.equal(out[:cnt].cpu(), want)
