@@ -157,6 +157,8 @@ struct ClearSet {
     uint32_t* lb_counter = nullptr;            // [4]
     unsigned long long* lb_states = nullptr;   // [lb_tiles]
     int64_t lb_tiles = 0;
+    uint32_t* cidx = nullptr;                  // layer-1 cell index of the refinement
+    int64_t cidx_words = 0;                    // (a multiple of 4)
 };
 
 __device__ __forceinline__ void clear_set(const ClearSet& c, int64_t tid, int64_t nthr)
@@ -172,6 +174,8 @@ __device__ __forceinline__ void clear_set(const ClearSet& c, int64_t tid, int64_
     uint4* o4 = reinterpret_cast<uint4*>(c.occ);
     for (int64_t i = tid; i < q; i += nthr) o4[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int64_t i = q * 4 + tid; i < c.words; i += nthr) c.occ[i] = 0u;
+    uint4* x4 = reinterpret_cast<uint4*>(c.cidx);
+    for (int64_t i = tid; i < c.cidx_words / 4; i += nthr) x4[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 __global__ void __launch_bounds__(kThreads) k_clear(ClearSet c)
@@ -1499,6 +1503,10 @@ ClearSet clear_of(const Plan& p)
     c.lb_counter = p.lb_counter;
     c.lb_states = p.lb_states;
     c.lb_tiles = p.lb_states ? p.lb_tiles : 0;
+    if (p.cidx != nullptr && !p.survivors_only) {   // only the refinement reads it
+        c.cidx = p.cidx;
+        c.cidx_words = int64_t(2) << p.d;
+    }
     return c;
 }
 

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
                                                 const uint32_t* __restrict__ sorted_key, const DevResult* res,
                                                 const float* __restrict__ params, float* X, uint32_t* C,
                                                 int32_t* ids, uint32_t* tmax, uint32_t* subcode,
-                                                uint32_t* tile_end)
+                                                uint32_t* tile_end, uint32_t* cidx)
 {
     constexpr int DW = DP / 4;
     const uint32_t m = res->survivors;
@@ -85,6 +85,19 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
 #pragma unroll
     for (int w = 0; w < DW; ++w) C[j * DW + w] = code[w];
     ids[j] = valid ? (int32_t)row : -1;
+
+    // layer-1 cell index: per cell (bit k: code k >= 64), the first and last
+    // tile holding one of its points, as ~first (cidx[cell]) and last + 1
+    // (cidx[2^d + cell]) by atomicMax into arrays the call's first kernel
+    // zeroed; one update per distinct cell of a warp
+    if (cidx != nullptr) {
+        const uint32_t cell = cell_of_codes<DW>(code);
+        const uint32_t peers = __match_any_sync(kFull, valid ? cell : 0xffffffffu);
+        if (valid && lane == __ffs(peers) - 1) {
+            atomicMax(cidx + cell, ~(uint32_t)blockIdx.x);
+            atomicMax(cidx + (1u << d) + cell, (uint32_t)blockIdx.x + 1u);
+        }
+    }
 
     // byte-wise minimum code of each 32-point sub-tile (slots 0..3) and of
     // the whole tile (slot 4); byte-wise maximum code of the tile's valid
@@ -255,13 +268,15 @@ __global__ void __launch_bounds__(kTQ + 32, RefineMinBlocks<DP>::value) k_refine
                                                      const uint32_t* __restrict__ tend,
                                                      const uint32_t* __restrict__ supmin,
                                                      const uint32_t* __restrict__ order, DevResult* res,
-                                                     uint8_t* keep, int32_t* wit)
+                                                     uint8_t* keep, int32_t* wit, const uint32_t* __restrict__ cidx,
+                                                     int d)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     RefineSmem<DP>& sm = *reinterpret_cast<RefineSmem<DP>*>(smem_raw);
     const uint32_t m = res->survivors;
     if (blockIdx.x >= (m + kTQ - 1) / kTQ) return;
-    refine_ptile<DP, true, WIT>(sm, X, C, ids, SUB, tend, supmin, m, order[blockIdx.x], res, keep, wit);
+    refine_ptile<DP, true, WIT>(sm, X, C, ids, SUB, tend, supmin, m, order[blockIdx.x], res, keep, wit, cidx,
+                                cidx ? cidx + (1u << d) : nullptr);
 }
 
 // Ascending row ids of the kept rows (decoupled look-back over 8 rows per
@@ -336,7 +351,8 @@ cudaError_t launch_gather(const Plan& p, cudaStream_t s)
     const bool v = (p.d % 4 == 0) && (p.ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.pts) & 15u) == 0);
     SKY_DISPATCH_DP(p.d, k_gather<DP><<<(unsigned)tiles, kTQ, 0, s>>>(p.pts, p.d, p.ld, v, p.sorted_val,
                                                                        p.sorted_key, p.res, p.params, p.X, p.C,
-                                                                       p.ids, p.tmax, p.subcode, p.tile_end));
+                                                                       p.ids, p.tmax, p.subcode, p.tile_end,
+                                                                       p.cidx));
     return cudaGetLastError();
 }
 
@@ -355,12 +371,12 @@ cudaError_t launch_refine(const Plan& p, cudaStream_t s)
             cudaFuncSetAttribute(k_refine<DP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             k_refine<DP, true><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, p.tile_end,
                                                                         p.supmin, p.tile_order, p.res, p.keep,
-                                                                        p.witness);
+                                                                        p.witness, p.cidx, p.d);
         } else {
             cudaFuncSetAttribute(k_refine<DP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             k_refine<DP, false><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, p.tile_end,
                                                                          p.supmin, p.tile_order, p.res, p.keep,
-                                                                         nullptr);
+                                                                         nullptr, p.cidx, p.d);
         }
     });
     return cudaGetLastError();

@@ -182,6 +182,7 @@ size_t layout(Plan& p, char* base, bool grid_api)
     p.subcode = c.take<uint32_t>(tiles * 5 * (dp / 4));
     p.tile_end = c.take<uint32_t>(tiles);
     p.supmin = c.take<uint32_t>(((tiles + 31) / 32) * (dp / 4));
+    p.cidx = c.take<uint32_t>(size_t(2) << (p.d > 0 ? p.d : 1));
     p.keep = c.take<uint8_t>(n + 16);
     return c.off;
 }

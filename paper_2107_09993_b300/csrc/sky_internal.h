@@ -77,6 +77,7 @@ struct Plan {
     uint32_t* subcode = nullptr;     // [tiles][5][dp/4] byte-wise min code of each 32-point sub-tile, then of the tile
     uint32_t* tile_end = nullptr;    // [tiles] last q-tile whose first Morton key <= the tile's last key
     uint32_t* supmin = nullptr;      // [ceil(tiles / 32)][dp/4] byte-wise min code of each run of 32 tiles
+    uint32_t* cidx = nullptr;        // [2][2^d] layer-1 cell index: ~first tile, last tile + 1 (0: no point)
     uint8_t* keep = nullptr;         // [n] 1 = skyline
     float* filt = nullptr;           // [16][16] snapped filter points
     unsigned long long* snap = nullptr;  // [16] packed (sum, row) argmin

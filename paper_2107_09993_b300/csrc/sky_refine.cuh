@@ -120,8 +120,161 @@ constexpr bool kBalance = SKY_REFINE_BALANCE == 1;
 #ifndef SKY_REFINE_SLIM_PRODUCER
 #define SKY_REFINE_SLIM_PRODUCER 0
 #endif
+// Layer-1 cell index (see cellwin_next): the producer of the single-set
+// kernel takes its windows from the index from padded dimension
+// SKY_REFINE_INDEX_RING_MIN_DP up, and the sparse mode from
+// SKY_REFINE_INDEX_SPARSE_MIN_DP up, whenever the index pays (index_pays);
+// otherwise both scan consecutive windows. Measured on B300 (ms, seed 1):
+// the ring index took 10^7 x 16 anti-correlated 124.6 -> 112.4, 10^7 x 12
+// independent 46.1 -> 44.5, 2*10^6 x 12 anti-correlated 9.12 -> 8.32,
+// 10^6 x 8 anti-correlated / independent 1.224 / 0.734 -> 1.21 / 0.72; the
+// sparse-mode index then 112.4 -> 107.5 and 44.5 -> 41.3, but at d = 8 it
+// cost 6 % (the five warps each walk every window of the index to deal them
+// out, and at 256 cells the windows are nearly as many as without it).
+#ifndef SKY_REFINE_INDEX_RING_MIN_DP
+#define SKY_REFINE_INDEX_RING_MIN_DP 8
+#endif
+#ifndef SKY_REFINE_INDEX_SPARSE_MIN_DP
+#define SKY_REFINE_INDEX_SPARSE_MIN_DP 12
+#endif
 constexpr bool kListProbe = SKY_REFINE_LIST != 0;
 constexpr uint32_t kEndTile = 0xffffffffu;
+
+// ---- layer-1 cell index -------------------------------------------------
+// A point's layer-1 cell (Eq. 1 at layer 1: two columns per dimension) is
+// read off its 7-bit codes: bit k is set iff code k >= 64. If q dominates p
+// (Definition 1), every code of q is <= p's (monotone map), so every column
+// of q's layer-1 cell is <= p's (the cells are equal or one dominates or
+// partially dominates the other, Definition 3): q's cell is a subset of p's.
+// The cells that can hold a dominator of any live p of a tile are therefore
+// the subsets of U, the union of the live p's cells. The index holds, per
+// cell, the first and last q-tile holding one of its points (stored as
+// ~first and last + 1 with atomicMax, so that a zeroed array means "no
+// point"); the tiles are in Morton order, whose d top bits are the same
+// layer-1 columns (the Morton and code grids are one monotone map at 2^b and
+// 128 columns), so a cell's points are contiguous and its range is tight.
+// The subsets of U are taken in ascending order, 32 at a time (one lane
+// each), and their tile ranges are packed into windows of up to 32
+// consecutive tiles: the tiles to examine, in ascending order, without
+// visiting the tiles of any other cell. The box tests against the live
+// groups' maxima still decide which of those tiles are streamed.
+
+// The four layer-1 bits (bit 6 of each byte) of one word of 7-bit codes.
+__device__ __forceinline__ uint32_t cell_bits4(uint32_t x)
+{
+    return ((((x >> 6) & 0x01010101u) * 0x01020408u) >> 24) & 0xfu;
+}
+
+template <int DW>
+__device__ __forceinline__ uint32_t cell_of_codes(const uint32_t* c)
+{
+    uint32_t cell = 0;
+#pragma unroll
+    for (int w = 0; w < DW; ++w) cell |= cell_bits4(c[w]) << (4 * w);
+    return cell;
+}
+
+// The j-th subset of U in ascending order: the bits of j deposited into the
+// positions of U's set bits.
+__device__ __forceinline__ uint32_t subset_of(uint32_t j, uint32_t U)
+{
+    uint32_t s = 0;
+    for (uint32_t u = U; u != 0u && j != 0u; u &= u - 1u, j >>= 1)
+        if (j & 1u) s |= u & (0u - u);
+    return s;
+}
+
+// Windows (first tile, mask of tiles) over the tile ranges of the subsets of
+// U, clipped to [first, last], produced one per call of next() by one warp.
+// The state lives in shared memory (CellWinState, one per walking warp), so
+// that it holds no registers between calls. A is the alignment of a window's
+// first tile (its sub-tile minima are fetched by one 16-byte aligned bulk
+// copy). If the ranges were not ascending (they are when the tile order
+// groups the cells), a tile may fall into two windows: examined twice, never
+// missed.
+struct CellWinState {
+    uint32_t U, nsub, batch, first, last;
+    uint32_t pend;       // lanes of the batch whose range is not placed yet
+    uint32_t clo, chi;   // the range being placed, while `have`
+    uint32_t cursor;     // one past the last tile of the ranges placed so far (0: none)
+    uint32_t have;
+    uint32_t lo[32], hi[32];   // the current batch's ranges (lo > hi: none)
+};
+
+__device__ __forceinline__ void cellwin_init(CellWinState& st, uint32_t u, uint32_t f, uint32_t l)
+{
+    if ((threadIdx.x & 31) == 0) {
+        st.U = u; st.nsub = 1u << __popc(u); st.batch = 0u; st.first = f; st.last = l;
+        st.pend = 0u; st.clo = st.chi = 0u; st.cursor = 0u; st.have = 0u;
+    }
+    __syncwarp();
+}
+
+template <uint32_t A>
+__device__ __forceinline__ bool cellwin_next(CellWinState& st, const uint32_t* __restrict__ mlo,
+                                             const uint32_t* __restrict__ mhi, uint32_t& t0, uint32_t& wm)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t pend = st.pend, clo = st.clo, chi = st.chi, cursor = st.cursor, batch = st.batch;
+    bool have = st.have != 0u;
+    wm = 0u;
+    t0 = 0u;
+    while (true) {
+        if (!have) {
+            if (pend == 0u) {
+                if (batch * 32u >= st.nsub) break;
+                const uint32_t j = batch * 32u + (uint32_t)lane;
+                uint32_t lo = 1u, hi = 0u;
+                if (j < st.nsub) {
+                    const uint32_t s = subset_of(j, st.U);
+                    const uint32_t a = __ldg(mlo + s), b = __ldg(mhi + s);
+                    if (a != 0u && b != 0u) {
+                        lo = max(~a, st.first);
+                        hi = min(b - 1u, st.last);
+                    }
+                }
+                pend = __ballot_sync(kFull, lo <= hi);
+                st.lo[lane] = lo;
+                st.hi[lane] = hi;
+                __syncwarp();
+                ++batch;
+                continue;
+            }
+            const int b = __ffs(pend) - 1;
+            pend &= pend - 1u;
+            clo = st.lo[b];
+            chi = st.hi[b];
+            if (cursor != 0u && clo + 1u == cursor) clo = cursor;   // the previous range's last tile
+            if (clo > chi) continue;
+            have = true;
+        }
+        if (wm == 0u) t0 = clo & ~(A - 1u);
+        else if (clo < t0 || clo > t0 + 31u) break;   // the range opens the next window
+        const uint32_t end = min(chi, t0 + 31u);
+        wm |= (0xffffffffu >> (31u - (end - t0))) & (0xffffffffu << (clo - t0));
+        if (end == chi) {
+            have = false;
+            cursor = max(cursor, chi + 1u);
+        } else {
+            clo = t0 + 32u;   // the rest of the range opens the next window
+            break;
+        }
+    }
+    __syncwarp();   // every lane has read st.lo / st.hi
+    if (lane == 0) {
+        st.pend = pend; st.clo = clo; st.chi = chi; st.cursor = cursor; st.batch = batch;
+        st.have = have ? 1u : 0u;
+    }
+    __syncwarp();
+    return wm != 0u;
+}
+
+// Use the index when its subset batches are fewer than half the windows of
+// 32 consecutive tiles that a scan of [first, last] would examine.
+__device__ __forceinline__ bool index_pays(uint32_t U, uint32_t first, uint32_t last)
+{
+    return last >= first && (1ull << __popc(U)) <= 16ull * ((uint64_t)(last - first) / 32u + 1u);
+}
 
 // Shared memory of one refinement CTA. S: ring stages; FAST: fast-code
 // list probe (see SKY_REFINE_FAST_MIN_DP for the single-set default).
@@ -149,7 +302,9 @@ struct RefineSmem {
     uint64_t empty[S];
     alignas(16) uint32_t stc[kWindows][32 * kSubSlots * DW];   // producer: codes of the 32 tiles of a super-tile
     uint64_t cbar[kWindows];                 // producer: their bulk copies
-    int32_t pend[kWindows];                  // producer: the super-tile held by each buffer
+    int32_t pend[kWindows];                  // producer: the first tile of the window held by each buffer
+    uint32_t wmask[kWindows];                // producer: the window's tiles to examine (bit i: first tile + i)
+    CellWinState cwin[kTQ / 32 + 1];         // layer-1 cell index walk of each warp (producer: the last)
     // consumer warp w: codes of the listed p's (in sparse mode, the whole
     // array holds one list of up to 32 entries of 7-bit codes)
     alignas(16) uint32_t plist[kTQ / 32][32 * (DWL > 1 ? DWL : 2)];
@@ -229,7 +384,9 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                                              const uint32_t* __restrict__ C, const int32_t* __restrict__ ids,
                                              const uint32_t* __restrict__ SUB, const uint32_t* __restrict__ TEND,
                                              const uint32_t* __restrict__ SUPMIN, uint32_t m, uint32_t ptile,
-                                             DevResult* res, uint8_t* keep, int32_t* wit = nullptr)
+                                             DevResult* res, uint8_t* keep, int32_t* wit = nullptr,
+                                             const uint32_t* __restrict__ MLO = nullptr,
+                                             const uint32_t* __restrict__ MHI = nullptr)
 {
     constexpr int DW = DP / 4;
     constexpr int NG = kTQ / 32;
@@ -339,6 +496,27 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                 win += 32u;
             }
         };
+        // With the layer-1 cell index, the windows cover only the tiles of
+        // the cells that can hold a dominator of a live p (cellwin_next);
+        // otherwise they are the relevant super-tiles.
+        constexpr uint32_t kWinAlign = DW == 4 ? 1u : DW == 2 ? 2u : 4u;   // 16-byte aligned copies
+        bool use_idx = false;
+        if (MLO != nullptr && DP >= SKY_REFINE_INDEX_RING_MIN_DP) {
+            uint32_t U = 0;
+#pragma unroll
+            for (int g = 0; g < NG; ++g)
+                if (sm.glive[g] != 0u) U |= cell_of_codes<DW>(sm.gmax[g]);
+            use_idx = index_pays(U, 0u, E);
+            if (use_idx) cellwin_init(sm.cwin[NG], U, 0u, E);
+        }
+        auto next_window = [&](uint32_t& t0, uint32_t& wm) -> bool {
+            if (use_idx) return cellwin_next<kWinAlign>(sm.cwin[NG], MLO, MHI, t0, wm);
+            const int sx = next_super();
+            if (sx < 0) return false;
+            t0 = (uint32_t)sx * 32u;
+            wm = 0xffffffffu;
+            return true;
+        };
         // the p-tile itself: every (sub-tile, group) pair whose sub-tile
         // minimum is within the group's reach
         {
@@ -362,20 +540,20 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
             __syncwarp();
             if (bmask) { ++issued; ++since; }
         }
-        // the codes of the 32 tiles of a super-tile: one bulk copy (the code
+        // the sub-tile minima of the tiles of a window: one bulk copy (the
         // arrays carry 16 bytes of slack past their end); copy k goes to
         // buffer k % NB and is that buffer's (k / NB)-th use; up to NB
         // windows are in flight ahead of the one being examined
         constexpr uint32_t NB = (uint32_t)SM::kWindows;
         uint32_t kiss = 0, kcons = 0;   // copies issued / consumed
-        auto fetch_super = [&](int sx) {
-            const uint32_t t0 = (uint32_t)sx * 32u;
-            const uint32_t nt = min(32u, T - t0);
+        auto fetch_window = [&](uint32_t t0, uint32_t wm) {
+            const uint32_t nt = min(32u - (uint32_t)__clz(wm), T - t0);
             const uint32_t bytes = (nt * kSubSlots * DW * 4u + 15u) & ~15u;
             const int bb = (int)(kiss % NB);
             __syncwarp();
             if (lane == 0) {
-                sm.pend[bb] = sx;
+                sm.pend[bb] = (int32_t)t0;
+                sm.wmask[bb] = wm;
                 fence_proxy_async_smem();   // generic reads of this buffer are done
                 mbar_arrive_expect_tx(&sm.cbar[bb], bytes);
                 bulk_g2s(sm.stc[bb], SUB + (int64_t)t0 * kSubSlots * DW, bytes, &sm.cbar[bb]);
@@ -385,22 +563,23 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
         };
         auto refill = [&]() {
             while (kiss - kcons < NB) {
-                const int sx = next_super();
-                if (sx < 0) break;
-                fetch_super(sx);
+                uint32_t t0, wm;
+                if (!next_window(t0, wm)) break;
+                fetch_window(t0, wm);
             }
         };
         refill();
         while (kcons < kiss && !stop) {
             if (all_dead()) break;
             const int bf = (int)(kcons % NB);
-            const int cur = sm.pend[bf];
+            const uint32_t t0 = (uint32_t)sm.pend[bf];
+            const uint32_t wmk = sm.wmask[bf];
             if (SPARSE && kSparseLive > 0 && __shfl_sync(kFull, sm.live, 0) <= kSparseLive) {
                 // few p's left: the rest of the scan runs in sparse mode,
-                // from this (fetched, not yet examined) super-tile on
+                // from this (fetched, not yet examined) window on
                 if (lane == 0) {
                     sm.sparse = 1u;
-                    sm.resume = (uint32_t)cur * 32u;
+                    sm.resume = t0;
                 }
                 break;
             }
@@ -408,7 +587,6 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
             if (lane == 0) ok = mbar_wait(&sm.cbar[bf], (kcons / NB) & 1u, err);
             if (!__shfl_sync(kFull, ok ? 1 : 0, 0)) { if (lane == 0) sm.failed = 1u; stop = true; break; }
             if (since >= kSummaryEvery) { summarise(); since = 0; }
-            const uint32_t t0 = (uint32_t)cur * 32u;
             const uint32_t t = t0 + lane;
             const uint32_t* tc = &sm.stc[bf][lane * kSubSlots * DW];
             // relevance of each (sub-tile, group) pair of this q-tile; in the
@@ -430,7 +608,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                 else return (sm.glive[g] != 0u) && bytes_le<DW>(lo, sm.gmax[g]);
             };
             uint32_t rmask = 0;
-            if (t <= E && t != ptile) {   // the p-tile itself went first
+            if (t <= E && t != ptile && ((wmk >> lane) & 1u)) {   // the p-tile itself went first
 #if SKY_REFINE_SLIM_PRODUCER
                 // one sub-tile's minimum in registers at a time
                 uint32_t cw[DW];
@@ -769,12 +947,44 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
         const uint32_t E = sm.scan_end;
         unsigned long long spairs = 0;
         uint32_t shits = 0, sexact = 0;
-        // windows of 32 consecutive q-tiles, dealt to the warps in turn
-        for (uint32_t wbase = sm.resume + (uint32_t)warp * 32u; wbase <= E; wbase += NW * 32u) {
+        // windows of up to 32 q-tiles from the resume point on, dealt to the
+        // warps in turn: consecutive tiles, or, with the layer-1 cell index,
+        // the tiles of the subsets of the listed p's cells (every warp runs
+        // the same generator and takes every NW-th window)
+        const uint32_t R = sm.resume;
+        uint32_t Us = 0;
+        constexpr bool kSparseIdx = DP >= SKY_REFINE_INDEX_SPARSE_MIN_DP;
+        if (MLO != nullptr && kSparseIdx) {
+            if (lane < nl) {
+                uint32_t pc[DW];
+                load_entry<DW>(LC + lane * DWL, pc);
+                Us = cell_of_codes<DW>(pc);
+            }
+            Us = __reduce_or_sync(kFull, Us);
+        }
+        const bool sidx = MLO != nullptr && kSparseIdx && index_pays(Us, R, E);
+        if (sidx) cellwin_init(sm.cwin[warp], Us, R, E);
+        uint32_t wi = 0, wnext = R + (uint32_t)warp * 32u;
+        while (true) {
+            uint32_t wbase, wmk;
+            if (sidx) {
+                bool got;
+                while ((got = cellwin_next<1u>(sm.cwin[warp], MLO, MHI, wbase, wmk))) {
+                    const bool mine = wi % (uint32_t)NW == (uint32_t)warp;
+                    ++wi;
+                    if (mine) break;
+                }
+                if (!got) break;
+            } else {
+                if (wnext > E) break;
+                wbase = wnext;
+                wmk = 0xffffffffu;
+                wnext += NW * 32u;
+            }
             if (__shfl_sync(kFull, sm.live, 0) == 0u) break;
             const uint32_t t = wbase + (uint32_t)lane;
             uint32_t rm = 0;   // listed p's whose codes reach this tile's minimum
-            if (t <= E && t != ptile) {
+            if (t <= E && t != ptile && ((wmk >> lane) & 1u)) {
                 uint32_t mn[DW];
 #pragma unroll
                 for (int w = 0; w < DW; ++w) mn[w] = __ldg(SUB + ((int64_t)t * kSubSlots + NG) * DW + w);
