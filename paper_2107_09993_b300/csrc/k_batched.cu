@@ -280,6 +280,20 @@ __global__ void __launch_bounds__(kTQ) kb_gather(const QueryPlan* __restrict__ q
         }
     }
     q.ids[j] = valid ? (int32_t)row : -1;
+    // layer-1 cell index of the query (zeroed with the query's counters): per
+    // cell (bit k: code k >= 64), ~first and last + 1 of the tiles holding
+    // one of its points; one update per distinct cell of a warp
+    {
+        uint32_t cell = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            if (w < dw) cell |= refine::cell_bits4(code[w]) << (4 * w);
+        const uint32_t peers = __match_any_sync(kFull, valid ? cell : 0xffffffffu);
+        if (valid && lane == __ffs(peers) - 1) {
+            atomicMax(q.cidx + cell, ~t);
+            atomicMax(q.cidx + (1u << q.d) + cell, t + 1u);
+        }
+    }
     __syncthreads();
     if (tid < dw) {
         uint32_t c = s_sub[0][tid];
@@ -392,7 +406,8 @@ __global__ void __launch_bounds__(kTQ + 32, BatchMinBlocks<DP>::value) kb_refine
         const uint32_t m = q.res->survivors;
         if ((uint32_t)w.y < (m + kTQ - 1) / kTQ)
             refine::refine_ptile<DP, kBatchSparse, false, SM>(sm, q.X, q.C, q.ids, q.sub, q.tend, q.supmin, m,
-                                                              (uint32_t)w.y, q.res, q.keep);
+                                                              (uint32_t)w.y, q.res, q.keep, nullptr, q.cidx,
+                                                              q.cidx + (1u << q.d));
     }
 }
 

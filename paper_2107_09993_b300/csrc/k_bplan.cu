@@ -52,8 +52,8 @@ __device__ inline int plan_mbits(int64_t n, int d)
 // and sizes as the host planner's layout). `zero` receives the bytes of the
 // leading arrays that must start at zero (result block, bitmap, look-back
 // states, keep bytes, digit totals).
-__host__ __device__ inline size_t query_bytes(int64_t n_in, int dp, int64_t words, int64_t chunks, int64_t tiles,
-                                              size_t* zero)
+__host__ __device__ inline size_t query_bytes(int64_t n_in, int d, int dp, int64_t words, int64_t chunks,
+                                              int64_t tiles, size_t* zero)
 {
     const size_t n = (size_t)(n_in > 0 ? n_in : 1);
     const size_t ch = (size_t)(chunks > 0 ? chunks : 1);
@@ -66,6 +66,7 @@ __host__ __device__ inline size_t query_bytes(int64_t n_in, int dp, int64_t word
     at += a256(8 * ch);
     at += a256(n + 16);
     at += a256(4 * 256 * 4);
+    at += a256(8 * ((size_t)1 << d));    // layer-1 cell index
     if (zero) *zero = at;
     at += a256(8 * n);                    // keys
     at += a256(4 * (size_t)words);        // prefix-OR
@@ -107,7 +108,7 @@ __host__ inline DevLayout dev_layout(int nq, int n_cols, int64_t max_total_rows)
     // per row the growth of query_bytes with n (rounded up)
     const int cols = n_cols < kMaxDim ? n_cols : kMaxDim;
     const int dpmax = pad4(cols > 0 ? cols : 1);
-    const size_t fixed = query_bytes(0, dpmax, kMaxWords, 1, 1, nullptr) + 24 * 256;
+    const size_t fixed = query_bytes(0, cols > 0 ? cols : 1, dpmax, kMaxWords, 1, 1, nullptr) + 24 * 256;
     const size_t per_row = 35 + 5 * (size_t)dpmax + 1;
     at += fixed * (size_t)nqq + per_row * (size_t)(max_total_rows > 0 ? max_total_rows : 0);
     L.total = at;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kPT) kb_plan(const sky_query* __restrict__ Q, 
             chunks = p.chunks;
             tiles = p.tiles;
             rows = p.n;
-            bytes = (int64_t)query_bytes(p.n, p.dp, p.words, p.chunks, p.tiles, nullptr);
+            bytes = (int64_t)query_bytes(p.n, p.d, p.dp, p.words, p.chunks, p.tiles, nullptr);
             qps[q] = p;
         }
         int64_t tb, tc, tt, tr;
@@ -272,6 +273,7 @@ __global__ void __launch_bounds__(kPT) kb_plan(const sky_query* __restrict__ Q, 
         p.lb_b = reinterpret_cast<unsigned long long*>(take(8 * ch));
         p.keep = reinterpret_cast<uint8_t*>(take(n + 16));
         p.digit_total = reinterpret_cast<uint32_t*>(take(4 * 256 * 4));
+        p.cidx = reinterpret_cast<uint32_t*>(take(8 * ((size_t)1 << p.d)));
         p.keys = reinterpret_cast<uint2*>(take(8 * n));
         p.pre = reinterpret_cast<uint32_t*>(take(4 * (size_t)p.words));
         p.surv_key = reinterpret_cast<uint32_t*>(take(4 * n));

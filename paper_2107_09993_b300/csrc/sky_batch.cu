@@ -34,7 +34,7 @@ sky_status bfail(sky_status s, const char* fmt, ...)
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct QOff {   // byte offsets of one query's arrays inside the workspace
-    size_t res, occ, lb_a, lb_b, keep, dt;                                   // zero region
+    size_t res, occ, lb_a, lb_b, keep, dt, cidx;                             // zero region
     size_t keys, pre, skey, sidx, key2, val2, hist, X, C, ids, sub, tend, supmin, stage;   // other
 };
 
@@ -200,6 +200,7 @@ sky_status sky_batch_create(const float* d_table, int64_t n_rows, int32_t n_cols
         o.lb_b = at; at = a256(at + 8 * (size_t)std::max<int64_t>(p.chunks, 1));
         o.keep = at; at = a256(at + n + 16);
         o.dt = at;   at = a256(at + 4 * 256 * 4);
+        o.cidx = at; at = a256(at + 8 * ((size_t)1 << p.d));
     }
     b->zero_bytes = at - b->zero_begin;
     for (int q = 0; q < nq; ++q) {
@@ -274,6 +275,7 @@ sky_status sky_batch_bind(sky_batch* b, void* d_ws, size_t ws_bytes, int32_t* d_
         p.sub = reinterpret_cast<uint32_t*>(ws + o.sub);
         p.tend = reinterpret_cast<uint32_t*>(ws + o.tend);
         p.supmin = reinterpret_cast<uint32_t*>(ws + o.supmin);
+        p.cidx = reinterpret_cast<uint32_t*>(ws + o.cidx);
         p.keep = reinterpret_cast<uint8_t*>(ws + o.keep);
         p.stage = reinterpret_cast<int32_t*>(ws + o.stage);
         p.res = reinterpret_cast<DevResult*>(ws + o.res);

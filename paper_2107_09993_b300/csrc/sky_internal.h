@@ -117,6 +117,7 @@ struct QueryPlan {
     uint32_t* sub;
     uint32_t* tend;           // [tiles] last q-tile whose first Morton key <= the tile's last key
     uint32_t* supmin;         // [ceil(tiles / 32)][dp / 4] byte-wise minimum code of each run of 32 tiles
+    uint32_t* cidx;           // [2][2^d] layer-1 cell index: ~first tile, last tile + 1 (0: no point)
     uint8_t* keep;
     int32_t* stage;
     DevResult* res;

@@ -2,7 +2,8 @@
 (sky_batched_device_workspace_size, a host function: no GPU needed).
 
 The device planner lays out, per query, the arrays the batched kernels use
-(result block, bitmap, look-back states, keep bytes, digit totals, keys,
+(result block, bitmap, look-back states, keep bytes, digit totals, layer-1
+cell index of 2 * 2^d words, keys,
 prefix-OR, four sort arrays, histograms, coordinates, codes, ids, sub-tile
 minima, tile ends, super-tile minima, stage), each rounded up to 256 bytes,
 after a header (plans, chunk and tile prefixes, work items, class table,
@@ -17,7 +18,7 @@ import pytest
 
 A = 256
 SCAN_TILE, REFINE_TILE = 2048, 128
-PLAN_BYTES = 384          # sizeof(QueryPlan)
+PLAN_BYTES = 392          # sizeof(QueryPlan)
 RESULT_BYTES = 72         # sizeof(DevResult)
 
 
@@ -45,7 +46,7 @@ def query_bytes(n, d):
     ch = max(1, math.ceil(n / SCAN_TILE))
     tl = max(1, math.ceil(n / REFINE_TILE))
     npad = tl * REFINE_TILE
-    sizes = [RESULT_BYTES, 4 * words, 8 * ch, 8 * ch, nn + 16, 4 * 256 * 4,
+    sizes = [RESULT_BYTES, 4 * words, 8 * ch, 8 * ch, nn + 16, 4 * 256 * 4, 8 << d,
              8 * nn, 4 * words, 4 * nn, 4 * nn, 4 * nn, 4 * nn, 4 * 256 * ch,
              4 * npad * dp, npad * dp, 4 * npad, 4 * tl * 5 * (dp // 4) + 16, 4 * tl,
              4 * math.ceil(tl / 32) * (dp // 4), 4 * nn]
