@@ -1121,6 +1121,11 @@ __global__ void __launch_bounds__(kThreads) k_surv_flags(
     __syncthreads();
     const uint32_t D = s_diag;
     const uint32_t cmask = (1u << log2g) - 1u;
+    // Every key the map pass writes is below 2^(log2g d), so masking a probe
+    // with the grid changes nothing; it keeps the probe inside the bitmap
+    // when the map pass gave up (a bounded wait ran out) before writing some
+    // rows' keys and those rows hold whatever the workspace held.
+    const uint32_t gridmask = (uint32_t)((uint64_t(1) << (log2g * d)) - 1u);
     uint32_t cnt = 0;                          // rows kept by this thread
     for (int64_t i = 0; i < my; ++i) {
         const int64_t tile = t0 + i;
@@ -1175,7 +1180,7 @@ __global__ void __launch_bounds__(kThreads) k_surv_flags(
             for (int h = 0; h < H; ++h)
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    wd[h][e] = ((need[h] >> e) & 1u) ? __ldg(pre + ((ks[h][e] - ones) >> 5)) : 0u;
+                    wd[h][e] = ((need[h] >> e) & 1u) ? __ldg(pre + (((ks[h][e] - ones) & gridmask) >> 5)) : 0u;
 #pragma unroll
             for (int h = 0; h < H; ++h)
 #pragma unroll

@@ -31,11 +31,15 @@ namespace {
 constexpr int kWitThreads = 256;
 
 // rep[ckey[i]] = i: every occupied cell receives the row of one of its points
-// (concurrent plain stores of rows of the same cell leave one of them).
-__global__ void __launch_bounds__(kWitThreads) k_wit_rep(const uint32_t* __restrict__ ckey, int64_t n, int32_t* rep)
+// (concurrent plain stores of rows of the same cell leave one of them). The
+// keys are below the cell count; the mask (a no-op for them) keeps the store
+// inside rep if the map pass gave up before writing some keys.
+__global__ void __launch_bounds__(kWitThreads) k_wit_rep(const uint32_t* __restrict__ ckey, int64_t n, uint32_t cmask,
+                                                         int32_t* rep)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) rep[ckey[i]] = (int32_t)i;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        rep[ckey[i] & cmask] = (int32_t)i;
 }
 
 // Inclusive prefix along dimension k: walking each line of 2^log2g cells
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(kWitThreads) k_wit_dropped(const float* __rest
         const uint32_t key = ckey[i];
         int32_t w = -2;
         if (log2g > 0 && all_columns_positive(key, log2g, d)) {
-            const int32_t r = prerep[key - ones];
+            const int32_t r = prerep[(key - ones) & (uint32_t)((uint64_t(1) << (log2g * d)) - 1u)];
             if (r >= 0) w = r;
         }
         for (int j = 0; j < n_prop && w < 0; ++j) {
@@ -114,7 +118,7 @@ cudaError_t launch_witness_cells(const Plan& p, int32_t* rep, int n_prop, cudaSt
     const int64_t cells = int64_t(1) << (p.log2g * p.d);
     cudaError_t e = cudaMemsetAsync(rep, 0xff, sizeof(int32_t) * (size_t)cells, s);
     if (e != cudaSuccess) return e;
-    k_wit_rep<<<grid_of(p.n), kWitThreads, 0, s>>>(p.ckey, p.n, rep);
+    k_wit_rep<<<grid_of(p.n), kWitThreads, 0, s>>>(p.ckey, p.n, (uint32_t)(cells - 1), rep);
     if (p.log2g > 0)
         for (int k = 0; k < p.d; ++k)
             k_wit_prefix<<<grid_of(cells >> p.log2g), kWitThreads, 0, s>>>(rep, cells, p.log2g, k);
