@@ -74,3 +74,34 @@ def test_sets_and_batched_report_timeouts_then_recover():
         r0, c, m = (int(v) for v in q[i])
         assert res[i].tolist() == oracle.skyline_subset(T, r0, c, m).tolist()
     b.close()
+
+
+def _stale_pool(nbytes=256 << 20):
+    """Leaves nbytes of 0xFF bytes in CUDA's default memory pool, where the
+    library's next workspaces come from (its pool keeps freed memory)."""
+    from cuda.bindings import runtime as rt
+    err, ptr = rt.cudaMallocAsync(nbytes, 0)
+    assert err == rt.cudaError_t.cudaSuccess
+    assert rt.cudaMemsetAsync(ptr, 0xFF, nbytes, 0)[0] == rt.cudaError_t.cudaSuccess
+    assert rt.cudaFreeAsync(ptr, 0)[0] == rt.cudaError_t.cudaSuccess
+    assert rt.cudaStreamSynchronize(0)[0] == rt.cudaError_t.cudaSuccess
+
+
+def test_first_call_times_out_on_a_stale_workspace():
+    """A call whose map pass gives up before writing every row's cell key,
+    on a workspace of 0xFF bytes (rows it did not reach keep the key
+    0xFFFFFFFF): the later kernels must stay inside their arrays (the cell
+    keys are masked to the grid), the call reports SKY_ERR_TIMEOUT, and the
+    next call with the default limit returns the oracle's skyline."""
+    P = [skydata.generate(k, 150_000, 7, 9) for k in ("independent", "anticorrelated")]
+    want = [oracle.skyline_sfs(p) for p in P]
+    xs = [torch.from_numpy(p).cuda() for p in P]
+    torch.cuda.synchronize()
+    _stale_pool()
+    sky.set_wait_limit(1)
+    try:
+        assert _expect_timeout(lambda: sky.skyline_sets(xs))
+    finally:
+        sky.set_wait_limit(0)
+    got = [r.cpu().numpy() for r in sky.skyline_sets(xs)]
+    assert all(np.array_equal(g, w) for g, w in zip(got, want))
