@@ -960,11 +960,24 @@ __global__ void __launch_bounds__(kThreads) k_snap(const float* __restrict__ pts
                                                    int n_prop, unsigned long long* snap)
 {
     constexpr int NP = 16;
-    __shared__ float s_f[NP * kMaxDim];
+    // proposals padded to DP with +inf (a padded dimension never rejects),
+    // read back as float4s; proposals past n_prop are -inf (never pass)
+    __shared__ __align__(16) float s_f[NP * DP];
     __shared__ unsigned long long s_best[NP];
-    for (int t = threadIdx.x; t < n_prop * d; t += blockDim.x) s_f[t] = prop[t];
+    for (int t = threadIdx.x; t < NP * DP; t += blockDim.x) {
+        const int j = t / DP, k = t % DP;
+        s_f[t] = j >= n_prop ? -INFINITY : (k < d ? prop[j * d + k] : INFINITY);
+    }
     if (threadIdx.x < NP) s_best[threadIdx.x] = ~0ull;
     __syncthreads();
+    // F = the proposals' componentwise maximum: a row above F in some
+    // dimension is <= no proposal and skips the per-proposal tests
+    float F[DP];
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+        F[k] = -INFINITY;
+        for (int j = 0; j < NP; ++j) F[k] = fmaxf(F[k], s_f[j * DP + k]);
+    }
     unsigned long long best[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) best[j] = ~0ull;
@@ -972,6 +985,23 @@ __global__ void __launch_bounds__(kThreads) k_snap(const float* __restrict__ pts
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         float x[DP];
         load_row<DP>(pts + i * ld, d, vec4, x);
+        // padded dimensions of x are 0 (load_row) and compare <= +inf
+        bool under = true;
+#pragma unroll
+        for (int k = 0; k < DP; ++k) under &= x[k] <= F[k];
+        if (!under) continue;
+        uint32_t pass = 0;   // bit j: x <= proposal j in every dimension
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            bool le = true;
+#pragma unroll
+            for (int k = 0; k < DP; k += 4) {
+                const float4 f = *reinterpret_cast<const float4*>(&s_f[j * DP + k]);
+                le &= (x[k] <= f.x) & (x[k + 1] <= f.y) & (x[k + 2] <= f.z) & (x[k + 3] <= f.w);
+            }
+            pass |= (le ? 1u : 0u) << j;
+        }
+        if (pass == 0u) continue;   // most rows, when few proposals reach the data
         float sum = 0.0f;
 #pragma unroll
         for (int k = 0; k < DP; ++k)
@@ -981,15 +1011,8 @@ __global__ void __launch_bounds__(kThreads) k_snap(const float* __restrict__ pts
         const unsigned long long packed =
             ((unsigned long long)float_to_ordered(__fadd_rn(sum, 0.0f)) << 32) | (unsigned long long)(uint32_t)i;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) {
-            if (j < n_prop) {
-                bool le = true;
-#pragma unroll
-                for (int k = 0; k < DP; ++k)
-                    if (k < d) le &= x[k] <= s_f[j * d + k];
-                if (le && packed < best[j]) best[j] = packed;
-            }
-        }
+        for (int j = 0; j < NP; ++j)
+            if (((pass >> j) & 1u) && packed < best[j]) best[j] = packed;
     }
 #pragma unroll
     for (int j = 0; j < NP; ++j) {

@@ -56,11 +56,22 @@ static_assert(kPUnroll == 1 || kPUnroll == 2, "one or two p's per step");
 // (one lane per tile tests the tile's minimum code against each live p),
 // and test each relevant tile's 128 q's, four per lane, against only the
 // live p's that tile can reach -- no producer, no stage handshakes. 0: off.
+// SKY_REFINE_SPARSE applies below padded dimension 12, SKY_REFINE_SPARSE_HIGH
+// from 12 up (where the sparse walk has the layer-1 cell index): measured on
+// B300 with the index, 10 instead of 6 took 10^7 x 12 independent 41.3 ->
+// 40.5 ms (10^7 x 16 anti-correlated unchanged) but 10^6 x 8 independent
+// 0.72 -> 0.75 ms.
 #ifndef SKY_REFINE_SPARSE
 #define SKY_REFINE_SPARSE 6
 #endif
-constexpr uint32_t kSparseLive = SKY_REFINE_SPARSE;
-static_assert(kSparseLive <= 32, "the sparse list is one lane mask wide");
+#ifndef SKY_REFINE_SPARSE_HIGH
+#define SKY_REFINE_SPARSE_HIGH 10
+#endif
+template <int DP>
+struct SparseLive {
+    static constexpr uint32_t value = DP >= 12 ? SKY_REFINE_SPARSE_HIGH : SKY_REFINE_SPARSE;
+    static_assert(value <= 32, "the sparse list is one lane mask wide");
+};
 #ifndef SKY_REFINE_LIST
 #define SKY_REFINE_LIST 1
 #endif
@@ -87,6 +98,10 @@ static_assert(kSparseLive <= 32, "the sparse list is one lane mask wide");
 #ifndef SKY_REFINE_WINDOWS
 #define SKY_REFINE_WINDOWS 2
 #endif
+// One buffer (no copy in flight ahead of the window being examined) ended a
+// launch with an unspecified launch failure on B300 whose cause was not
+// found by reading the code; it is not built.
+static_assert(SKY_REFINE_WINDOWS >= 2, "at least two window buffers");
 // 1: the CTA's own p coordinates are staged in shared memory for the exact
 // tests; 0: the exact tests read them from global memory (rare, and the
 // shared memory goes to deeper rings)
@@ -373,7 +388,7 @@ __device__ __forceinline__ bool bytes_le(const uint32_t* lo, const uint32_t* hi)
 // minimum exceeds every live group's maximum in some byte is skipped whole;
 // NULL examines every super-tile.
 // SPARSE (the single-set kernel): a p-tile whose live points drop to
-// kSparseLive finishes in sparse mode, and the producer tests relevance
+// SparseLive<DP> finishes in sparse mode, and the producer tests relevance
 // against register copies of the group maxima. The batched persistent kernel
 // keeps the ring to the end and the maxima in shared memory (fewer registers:
 // measured faster there).
@@ -391,6 +406,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
     constexpr int DW = DP / 4;
     constexpr int NG = kTQ / 32;
     constexpr int S = SM::kStages;
+    constexpr uint32_t kSparseLive = SparseLive<DP>::value;
     constexpr uint32_t kBytesC = kTQ * DW * sizeof(uint32_t);
     const uint32_t T = (m + kTQ - 1) / kTQ;
     uint32_t* err = &res->err;
@@ -586,6 +602,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
             bool ok = true;
             if (lane == 0) ok = mbar_wait(&sm.cbar[bf], (kcons / NB) & 1u, err);
             if (!__shfl_sync(kFull, ok ? 1 : 0, 0)) { if (lane == 0) sm.failed = 1u; stop = true; break; }
+            __syncwarp();   // lane 0 observed the copy; the warp barrier orders the others' reads after it
             if (since >= kSummaryEvery) { summarise(); since = 0; }
             const uint32_t t = t0 + lane;
             const uint32_t* tc = &sm.stc[bf][lane * kSubSlots * DW];
