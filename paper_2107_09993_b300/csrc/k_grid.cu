@@ -159,6 +159,7 @@ struct ClearSet {
     int64_t lb_tiles = 0;
     uint32_t* cidx = nullptr;                  // layer-1 cell index of the refinement
     int64_t cidx_words = 0;                    // (a multiple of 4)
+    unsigned long long* pre_states = nullptr;  // [lb_tiles] the refinement pre-pass's look-back states
 };
 
 __device__ __forceinline__ void clear_set(const ClearSet& c, int64_t tid, int64_t nthr)
@@ -176,6 +177,8 @@ __device__ __forceinline__ void clear_set(const ClearSet& c, int64_t tid, int64_
     for (int64_t i = q * 4 + tid; i < c.words; i += nthr) c.occ[i] = 0u;
     uint4* x4 = reinterpret_cast<uint4*>(c.cidx);
     for (int64_t i = tid; i < c.cidx_words / 4; i += nthr) x4[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (c.pre_states)
+        for (int64_t i = tid; i < c.lb_tiles; i += nthr) c.pre_states[i] = 0ull;
 }
 
 __global__ void __launch_bounds__(kThreads) k_clear(ClearSet c)
@@ -1534,6 +1537,7 @@ ClearSet clear_of(const Plan& p)
     if (p.cidx != nullptr && !p.survivors_only) {   // only the refinement reads it
         c.cidx = p.cidx;
         c.cidx_words = int64_t(2) << p.d;
+        c.pre_states = p.pre_states;
     }
     return c;
 }

@@ -34,16 +34,39 @@ namespace {
 
 using namespace refine;
 
+// Pre-pass of the refinement (sets of at least kPreMinRows rows): every
+// p-tile is first refined against itself and the first kPreTiles q-tiles of
+// the Morton order only (the points nearest the origin, which dominate the
+// most); the survivors of that pass are compacted in order and the full
+// refinement runs on them. Exact: the pre-pass removes only points it has
+// found dominated, and every dominated point has a skyline dominator, which
+// no pass removes, so skyline(survivors) = skyline(pre-pass survivors).
+// What it saves: the full refinement no longer streams and tests the
+// dominated points as q's. Measured on B300 (ms, one sky_skyline call, no
+// pre-pass / 4 / 8 / 16 tiles): 10^7 x 12 independent 40.5 / 24.2 / 22.1 /
+// 20.8, 10^7 x 16 anti-correlated 107.5 / 109.5 / 109.2 / 109.1 (nothing to
+// remove there: 82 % of its points are skyline points); on 10^6 x 8 sets its
+// fixed cost (three launches, a second gather) outweighs it (independent
+// 0.72 -> 0.82-0.86 ms), hence the row threshold.
+#ifndef SKY_REFINE_PRE_TILES
+#define SKY_REFINE_PRE_TILES 16
+#endif
+constexpr uint32_t kPreTiles = SKY_REFINE_PRE_TILES;   // 0: no pre-pass
+#ifndef SKY_REFINE_PRE_MIN_ROWS
+#define SKY_REFINE_PRE_MIN_ROWS (int64_t(1) << 21)
+#endif
+constexpr int64_t kPreMinRows = SKY_REFINE_PRE_MIN_ROWS;
+
 template <int DP>
 __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, int d, int64_t ld, bool vec4,
                                                 const uint32_t* __restrict__ sorted_idx,
-                                                const uint32_t* __restrict__ sorted_key, const DevResult* res,
+                                                const uint32_t* __restrict__ sorted_key, const uint32_t* mcount,
                                                 const float* __restrict__ params, float* X, uint32_t* C,
                                                 int32_t* ids, uint32_t* tmax, uint32_t* subcode,
-                                                uint32_t* tile_end, uint32_t* cidx)
+                                                uint32_t* tile_end, uint32_t* cidx, uint32_t* tend_pre)
 {
     constexpr int DW = DP / 4;
-    const uint32_t m = res->survivors;
+    const uint32_t m = *mcount;
     const uint32_t T = (m + kTQ - 1) / kTQ;
     if (blockIdx.x >= T) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -144,7 +167,10 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
             e += k;
             if (k < 32u) break;
         }
-        if (lane == 0) tile_end[blockIdx.x] = e;
+        if (lane == 0) {
+            tile_end[blockIdx.x] = e;
+            if (tend_pre) tend_pre[blockIdx.x] = min(e, kPreTiles - 1u);
+        }
     }
 }
 
@@ -159,12 +185,12 @@ constexpr int kCostSamples = 1024;
 
 template <int DW>
 __global__ void __launch_bounds__(256) k_tile_cost(const uint32_t* __restrict__ SUB, const uint32_t* __restrict__ tmax,
-                                                   const DevResult* res, uint32_t* cost, uint32_t* supmin)
+                                                   const uint32_t* mcount, uint32_t* cost, uint32_t* supmin)
 {
     // the sampled q-tiles' minimum codes, shared by the block's eight warps
     // (one p-tile each)
     __shared__ uint32_t s_qmin[kCostSamples][DW];
-    const uint32_t T = (res->survivors + kTQ - 1) / kTQ;
+    const uint32_t T = (*mcount + kTQ - 1) / kTQ;
     if (blockIdx.x * 8 >= T) return;
     {
         // warp w of block b: byte-wise minimum code of super-tile 8b + w (32
@@ -211,11 +237,11 @@ __global__ void __launch_bounds__(256) k_tile_cost(const uint32_t* __restrict__ 
 // first evens out the end of the grid): a counting sort over 32
 // power-of-two cost buckets in one CTA. Order inside a bucket is arbitrary;
 // the result does not depend on it.
-__global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict__ cost, const DevResult* res,
+__global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict__ cost, const uint32_t* mcount,
                                                      uint32_t* order)
 {
     __shared__ uint32_t s_cnt[32], s_pos[32];
-    const uint32_t T = (res->survivors + kTQ - 1) / kTQ;
+    const uint32_t T = (*mcount + kTQ - 1) / kTQ;
     if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
     for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) {
@@ -267,20 +293,86 @@ __global__ void __launch_bounds__(kTQ + 32, RefineMinBlocks<DP>::value) k_refine
                                                      const uint32_t* __restrict__ SUB,
                                                      const uint32_t* __restrict__ tend,
                                                      const uint32_t* __restrict__ supmin,
-                                                     const uint32_t* __restrict__ order, DevResult* res,
+                                                     const uint32_t* __restrict__ order, const uint32_t* mcount,
+                                                     DevResult* res,
                                                      uint8_t* keep, int32_t* wit, const uint32_t* __restrict__ cidx,
                                                      int d)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     RefineSmem<DP>& sm = *reinterpret_cast<RefineSmem<DP>*>(smem_raw);
-    const uint32_t m = res->survivors;
+    const uint32_t m = *mcount;
     if (blockIdx.x >= (m + kTQ - 1) / kTQ) return;
-    refine_ptile<DP, true, WIT>(sm, X, C, ids, SUB, tend, supmin, m, order[blockIdx.x], res, keep, wit, cidx,
+    const uint32_t ptile = order ? order[blockIdx.x] : blockIdx.x;
+    refine_ptile<DP, true, WIT>(sm, X, C, ids, SUB, tend, supmin, m, ptile, res, keep, wit, cidx,
                                 cidx ? cidx + (1u << d) : nullptr);
 }
 
 // Ascending row ids of the kept rows (decoupled look-back over 8 rows per
 // thread). Writes beyond `capacity` are dropped; the count is always exact.
+// Compaction after the pre-pass: the sorted survivors (Morton key, row)
+// whose row the pre-pass kept, in the same order, by a decoupled look-back
+// over tiles of kScanTile entries claimed in order. It also clears those
+// rows' keep bytes (the full refinement sets them again) and the layer-1
+// cell index (rebuilt by the next gather), and writes the new count to
+// res->refine_m.
+__global__ void __launch_bounds__(kScanThreads) k_pre_compact(const uint32_t* __restrict__ skey,
+                                                              const uint32_t* __restrict__ sval, uint8_t* keep,
+                                                              DevResult* res, unsigned long long* states,
+                                                              uint32_t* tile_counter, uint32_t* okey, uint32_t* oval,
+                                                              uint32_t* cidx, int64_t cidx_words)
+{
+    __shared__ uint32_t s_warp[kScanThreads / 32];
+    __shared__ uint32_t s_tile, s_prefix;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < cidx_words; i += (int64_t)gridDim.x * blockDim.x)
+        cidx[i] = 0u;
+    const uint32_t m = res->survivors;
+    const uint32_t ntiles = (m + kScanTile - 1) / kScanTile;
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= ntiles) return;
+    const int64_t base = (int64_t)tile * kScanTile + (int64_t)tid * kScanItems;
+    uint32_t flags = 0, rows[kScanItems];
+#pragma unroll
+    for (int jj = 0; jj < kScanItems; ++jj) {
+        rows[jj] = 0u;
+        if (base + jj < m) {
+            rows[jj] = sval[base + jj];
+            if (keep[rows[jj]]) flags |= 1u << jj;
+        }
+    }
+    const uint32_t v = __popc(flags);
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        if (w < warp) before += s_warp[w];
+        total += s_warp[w];
+    }
+    if (tid < 32) {
+        const uint32_t prefix = lookback_prefix(states, tile, total, &res->err);
+        if (tid == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    uint32_t pos = s_prefix + before + x - v;
+#pragma unroll
+    for (int jj = 0; jj < kScanItems; ++jj) {
+        if (flags & (1u << jj)) {
+            okey[pos] = skey[base + jj];
+            oval[pos] = rows[jj];
+            keep[rows[jj]] = 0;
+            ++pos;
+        }
+    }
+    if (tile == ntiles - 1 && tid == 0) res->refine_m = s_prefix + total;
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_emit(const uint8_t* __restrict__ keep, int64_t n,
                                                        int32_t* out, int64_t capacity, DevResult* res,
                                                        unsigned long long* states, uint32_t* tile_counter)
@@ -344,40 +436,80 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const uint8_t* __restrict
         default: { constexpr int DP = 16; __VA_ARGS__; } break; \
     }
 
-cudaError_t launch_gather(const Plan& p, cudaStream_t s)
+cudaError_t launch_gather(const Plan& p, cudaStream_t s, const uint32_t* mcount)
 {
     const int64_t tiles = (p.n + kTQ - 1) / kTQ;
     if (tiles == 0) return cudaGetLastError();
     const bool v = (p.d % 4 == 0) && (p.ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.pts) & 15u) == 0);
+    if (!mcount) mcount = &p.res->survivors;
     SKY_DISPATCH_DP(p.d, k_gather<DP><<<(unsigned)tiles, kTQ, 0, s>>>(p.pts, p.d, p.ld, v, p.sorted_val,
-                                                                       p.sorted_key, p.res, p.params, p.X, p.C,
+                                                                       p.sorted_key, mcount, p.params, p.X, p.C,
                                                                        p.ids, p.tmax, p.subcode, p.tile_end,
-                                                                       p.cidx));
+                                                                       p.cidx, p.tend_pre));
     return cudaGetLastError();
 }
+
+bool refine_prepass(const Plan& p)
+{
+    return kPreTiles > 0 && p.n >= kPreMinRows && p.tend_pre != nullptr && p.pre_states != nullptr;
+}
+
+namespace {
+
+// One refinement launch over the tiles of the first *mcount sorted survivors:
+// TEND is each p-tile's last q-tile, SUPMIN the super-tile minima (NULL:
+// none), ORDER the p-tile order (NULL: tile b in block b).
+template <int DP>
+void refine_launch(const Plan& p, cudaStream_t s, int64_t tiles, const uint32_t* tend, const uint32_t* supmin,
+                   const uint32_t* order, const uint32_t* mcount)
+{
+    const int smem = (int)sizeof(RefineSmem<DP>);
+    if (p.witness) {
+        cudaFuncSetAttribute(k_refine<DP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_refine<DP, true><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, tend, supmin, order,
+                                                                    mcount, p.res, p.keep, p.witness, p.cidx, p.d);
+    } else {
+        cudaFuncSetAttribute(k_refine<DP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_refine<DP, false><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, tend, supmin,
+                                                                     order, mcount, p.res, p.keep, nullptr, p.cidx,
+                                                                     p.d);
+    }
+}
+
+}  // namespace
 
 cudaError_t launch_refine(const Plan& p, cudaStream_t s)
 {
     // p.keep was zeroed by the survivor pass (k_surv_flags)
     const int64_t tiles = (p.n + kTQ - 1) / kTQ;
     if (tiles == 0) return cudaGetLastError();
+    const uint32_t* mcount = &p.res->survivors;
+    if (refine_prepass(p)) {
+        // the pre-pass: each p-tile against itself and the first kPreTiles
+        // q-tiles (TEND clipped by the gather), no super-tile minima yet
+        SKY_DISPATCH_DP(p.d, refine_launch<DP>(p, s, tiles, p.tend_pre, nullptr, nullptr, mcount));
+        // its survivors, compacted in order into the sort's other buffers
+        Plan q = p;
+        const bool first = p.sorted_key == p.surv_key;
+        q.sorted_key = first ? p.sort_key2 : p.surv_key;
+        q.sorted_val = first ? p.sort_val2 : p.surv_idx;
+        const int64_t ntiles = (p.n + kScanTile - 1) / kScanTile;
+        // p.pre_states and p.lb_counter were zeroed by the call's first kernel
+        k_pre_compact<<<(unsigned)ntiles, kScanThreads, 0, s>>>(p.sorted_key, p.sorted_val, p.keep, p.res,
+                                                                p.pre_states, p.lb_counter + 2,
+                                                                const_cast<uint32_t*>(q.sorted_key),
+                                                                const_cast<uint32_t*>(q.sorted_val), p.cidx,
+                                                                int64_t(2) << p.d);
+        mcount = &p.res->refine_m;
+        const cudaError_t e = launch_gather(q, s, mcount);
+        if (e != cudaSuccess) return e;
+    }
     SKY_DISPATCH_DP(p.d, {
         constexpr int DW = DP / 4;
-        k_tile_cost<DW><<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(p.subcode, p.tmax, p.res, p.tile_cost,
+        k_tile_cost<DW><<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(p.subcode, p.tmax, mcount, p.tile_cost,
                                                                    p.supmin);
-        k_cost_order<<<1, 1024, 0, s>>>(p.tile_cost, p.res, p.tile_order);
-        const int smem = (int)sizeof(RefineSmem<DP>);
-        if (p.witness) {
-            cudaFuncSetAttribute(k_refine<DP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            k_refine<DP, true><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, p.tile_end,
-                                                                        p.supmin, p.tile_order, p.res, p.keep,
-                                                                        p.witness, p.cidx, p.d);
-        } else {
-            cudaFuncSetAttribute(k_refine<DP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            k_refine<DP, false><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, p.tile_end,
-                                                                         p.supmin, p.tile_order, p.res, p.keep,
-                                                                         nullptr, p.cidx, p.d);
-        }
+        k_cost_order<<<1, 1024, 0, s>>>(p.tile_cost, mcount, p.tile_order);
+        refine_launch<DP>(p, s, tiles, p.tile_end, p.supmin, p.tile_order, mcount);
     });
     return cudaGetLastError();
 }

@@ -92,7 +92,8 @@ int count_kernels(const Plan& p, int n_prop, int64_t capacity)
     const int through_c =
         build_kernel_count(p) + (n_prop > 0 ? 2 : 0) + (prefix_trivial(p) ? 0 : prefix_kernel_count(p)) + 2;
     if (p.survivors_only) return through_c + (capacity >= p.n ? 0 : 1);   // + the id copy
-    return through_c + 3 * passes + 1 + 3 + 1;   // sort, gather, cost + order + refine, emit
+    return through_c + 3 * passes + 1 + 3 + 1 +   // sort, gather, cost + order + refine, emit
+           (refine_prepass(p) ? 3 : 0);          // the refinement's pre-pass, compaction, second gather
 }
 
 sky_status fail(sky_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
@@ -183,6 +184,8 @@ size_t layout(Plan& p, char* base, bool grid_api)
     p.tile_end = c.take<uint32_t>(tiles);
     p.supmin = c.take<uint32_t>(((tiles + 31) / 32) * (dp / 4));
     p.cidx = c.take<uint32_t>(size_t(2) << (p.d > 0 ? p.d : 1));
+    p.tend_pre = c.take<uint32_t>(tiles);
+    p.pre_states = c.take<unsigned long long>(p.lb_tiles);
     p.keep = c.take<uint8_t>(n + 16);
     return c.off;
 }

@@ -18,7 +18,8 @@ struct DevResult {
     unsigned long long pairs;  // candidate pairs examined by the refinement
     uint32_t occupied_cells;   // filled on request (grid statistics)
     uint32_t surviving_cells;
-    uint32_t pad[2];
+    uint32_t refine_m;         // survivors left for the full refinement after its pre-pass
+    uint32_t pad1;
     unsigned long long tiles;  // q-tiles streamed by the refinement (all CTAs)
     unsigned long long groups; // (warp, p-group) list scans in the refinement
     unsigned long long hits;   // pairs with code(q) <= code(p) in every dimension
@@ -78,6 +79,8 @@ struct Plan {
     uint32_t* tile_end = nullptr;    // [tiles] last q-tile whose first Morton key <= the tile's last key
     uint32_t* supmin = nullptr;      // [ceil(tiles / 32)][dp/4] byte-wise min code of each run of 32 tiles
     uint32_t* cidx = nullptr;        // [2][2^d] layer-1 cell index: ~first tile, last tile + 1 (0: no point)
+    uint32_t* tend_pre = nullptr;    // [tiles] last q-tile of the refinement's pre-pass scan
+    unsigned long long* pre_states = nullptr;   // [lb_tiles] look-back states of the pre-pass compaction
     uint8_t* keep = nullptr;         // [n] 1 = skyline
     float* filt = nullptr;           // [16][16] snapped filter points
     unsigned long long* snap = nullptr;  // [16] packed (sum, row) argmin
@@ -166,7 +169,10 @@ cudaError_t launch_cell_stats(const Plan& p, cudaStream_t s);
 // k_sort.cu
 cudaError_t launch_sort(Plan& p, cudaStream_t s);
 // k_refine.cu
-cudaError_t launch_gather(const Plan& p, cudaStream_t s);
+// mcount: the number of sorted survivors to lay out (default &p.res->survivors)
+cudaError_t launch_gather(const Plan& p, cudaStream_t s, const uint32_t* mcount = nullptr);
+// whether launch_refine runs the pre-pass (3 more kernels: refine, compaction, gather)
+bool refine_prepass(const Plan& p);
 cudaError_t launch_refine(const Plan& p, cudaStream_t s);
 cudaError_t launch_emit(const Plan& p, int32_t* out, int64_t capacity, cudaStream_t s);
 // k_tournament.cu: Algorithm 3 (tournament tree) classes of one layer
