@@ -658,7 +658,10 @@ def run_sky(args):
                    "peak_source": f"148 SMs x 128 int32 lanes x {sm_mhz:.0f} MHz (median SM clock sampled during the run)",
                    "work": f"{pairs / launches_refine:.4g} candidate pair tests per launch x ops per test "
                            f"(ceil(d/4) word subtracts + AND tree + compare: 7 at d = 16, 6 at d = 12)",
-                   "ms_per_launch": round(phase_sum['refine_ms'] / launches_refine, 4)}
+                   "ms_per_launch": round(phase_sum['refine_ms'] / launches_refine, 4),
+                   "timing": "per set: the refinement phase (phase events, direct launches) -- from 2^21 rows "
+                             "two k_refine launches (pre-pass, full pass) with the compaction, the second gather "
+                             "and the p-tile ordering between them; pair tests of both launches counted"}
     roof_prune = {"kernel": "pruning pass (phases map + prune + survivors of the timed workload)",
                   "bound": "hbm", "achieved": round(prune_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                   "frac": round(prune_gbs / peaks["hbm_gbs"], 4), "traffic": None,

@@ -34,7 +34,7 @@ namespace {
 
 using namespace refine;
 
-// Pre-pass of the refinement (sets of at least kPreMinRows rows): every
+// Pre-pass of the refinement (at least kPreMinRows rows and survivors): every
 // p-tile is first refined against itself and the first kPreTiles q-tiles of
 // the Morton order only (the points nearest the origin, which dominate the
 // most); the survivors of that pass are compacted in order and the full
@@ -296,12 +296,12 @@ __global__ void __launch_bounds__(kTQ + 32, RefineMinBlocks<DP>::value) k_refine
                                                      const uint32_t* __restrict__ order, const uint32_t* mcount,
                                                      DevResult* res,
                                                      uint8_t* keep, int32_t* wit, const uint32_t* __restrict__ cidx,
-                                                     int d)
+                                                     int d, uint32_t min_m)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     RefineSmem<DP>& sm = *reinterpret_cast<RefineSmem<DP>*>(smem_raw);
     const uint32_t m = *mcount;
-    if (blockIdx.x >= (m + kTQ - 1) / kTQ) return;
+    if (m < min_m || blockIdx.x >= (m + kTQ - 1) / kTQ) return;   // min_m: the pre-pass's survivor threshold
     const uint32_t ptile = order ? order[blockIdx.x] : blockIdx.x;
     refine_ptile<DP, true, WIT>(sm, X, C, ids, SUB, tend, supmin, m, ptile, res, keep, wit, cidx,
                                 cidx ? cidx + (1u << d) : nullptr);
@@ -314,7 +314,8 @@ __global__ void __launch_bounds__(kTQ + 32, RefineMinBlocks<DP>::value) k_refine
 // over tiles of kScanTile entries claimed in order. It also clears those
 // rows' keep bytes (the full refinement sets them again) and the layer-1
 // cell index (rebuilt by the next gather), and writes the new count to
-// res->refine_m.
+// res->refine_m. With fewer than kPreMinRows survivors the pre-pass kernel
+// returned at once, and every entry is kept.
 __global__ void __launch_bounds__(kScanThreads) k_pre_compact(const uint32_t* __restrict__ skey,
                                                               const uint32_t* __restrict__ sval, uint8_t* keep,
                                                               DevResult* res, unsigned long long* states,
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(kScanThreads) k_pre_compact(const uint32_t* __
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < cidx_words; i += (int64_t)gridDim.x * blockDim.x)
         cidx[i] = 0u;
     const uint32_t m = res->survivors;
+    const bool all = (int64_t)m < kPreMinRows;   // the pre-pass did not run: every entry stays
     const uint32_t ntiles = (m + kScanTile - 1) / kScanTile;
     if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
     __syncthreads();
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(kScanThreads) k_pre_compact(const uint32_t* __
         rows[jj] = 0u;
         if (base + jj < m) {
             rows[jj] = sval[base + jj];
-            if (keep[rows[jj]]) flags |= 1u << jj;
+            if (all || keep[rows[jj]]) flags |= 1u << jj;
         }
     }
     const uint32_t v = __popc(flags);
@@ -461,18 +463,19 @@ namespace {
 // none), ORDER the p-tile order (NULL: tile b in block b).
 template <int DP>
 void refine_launch(const Plan& p, cudaStream_t s, int64_t tiles, const uint32_t* tend, const uint32_t* supmin,
-                   const uint32_t* order, const uint32_t* mcount)
+                   const uint32_t* order, const uint32_t* mcount, uint32_t min_m = 0)
 {
     const int smem = (int)sizeof(RefineSmem<DP>);
     if (p.witness) {
         cudaFuncSetAttribute(k_refine<DP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k_refine<DP, true><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, tend, supmin, order,
-                                                                    mcount, p.res, p.keep, p.witness, p.cidx, p.d);
+                                                                    mcount, p.res, p.keep, p.witness, p.cidx, p.d,
+                                                                    min_m);
     } else {
         cudaFuncSetAttribute(k_refine<DP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k_refine<DP, false><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, tend, supmin,
                                                                      order, mcount, p.res, p.keep, nullptr, p.cidx,
-                                                                     p.d);
+                                                                     p.d, min_m);
     }
 }
 
@@ -487,7 +490,8 @@ cudaError_t launch_refine(const Plan& p, cudaStream_t s)
     if (refine_prepass(p)) {
         // the pre-pass: each p-tile against itself and the first kPreTiles
         // q-tiles (TEND clipped by the gather), no super-tile minima yet
-        SKY_DISPATCH_DP(p.d, refine_launch<DP>(p, s, tiles, p.tend_pre, nullptr, nullptr, mcount));
+        SKY_DISPATCH_DP(p.d, refine_launch<DP>(p, s, tiles, p.tend_pre, nullptr, nullptr, mcount,
+                                               (uint32_t)kPreMinRows));
         // its survivors, compacted in order into the sort's other buffers
         Plan q = p;
         const bool first = p.sorted_key == p.surv_key;
