@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
 }
 
 // Cost estimate of each p-tile for the launch order of the refinement: how
-// many q-tiles of an evenly strided sample (at most kCostSamples) have a
+// many q-tiles of an evenly strided sample (at most kCostSamples) up to the
+// p-tile's Morton cutoff (TEND: no later tile is scanned) have a
 // tile-minimum code <= the p-tile's maximum code in every byte, i.e. could
 // hold a dominator of one of its points and would be streamed while any of
 // them is alive. (Measured on the three families at n = 10^6, d = 8, this
@@ -185,7 +186,8 @@ constexpr int kCostSamples = 1024;
 
 template <int DW>
 __global__ void __launch_bounds__(256) k_tile_cost(const uint32_t* __restrict__ SUB, const uint32_t* __restrict__ tmax,
-                                                   const uint32_t* mcount, uint32_t* cost, uint32_t* supmin)
+                                                   const uint32_t* __restrict__ tend, const uint32_t* mcount,
+                                                   uint32_t* cost, uint32_t* supmin)
 {
     // the sampled q-tiles' minimum codes, shared by the block's eight warps
     // (one p-tile each)
@@ -223,7 +225,8 @@ __global__ void __launch_bounds__(256) k_tile_cost(const uint32_t* __restrict__ 
 #pragma unroll
     for (int w = 0; w < DW; ++w) top[w] = tmax[(int64_t)pt * DW + w] | kHigh;
     uint32_t cnt = 0;
-    for (uint32_t i = lane; i < ns; i += 32u) {
+    const uint32_t nse = min(ns, tend[pt] / step + 1u);   // samples at tiles <= the cutoff
+    for (uint32_t i = lane; i < nse; i += 32u) {
         uint32_t r = kHigh;
 #pragma unroll
         for (int w = 0; w < DW; ++w) r &= top[w] - s_qmin[i][w];
@@ -234,30 +237,60 @@ __global__ void __launch_bounds__(256) k_tile_cost(const uint32_t* __restrict__ 
 }
 
 // Launch order of the p-tiles, largest estimated cost first (longest job
-// first evens out the end of the grid): a counting sort over 32
-// power-of-two cost buckets in one CTA. Order inside a bucket is arbitrary;
-// the result does not depend on it.
+// first evens out the end of the grid): a counting sort over the exact cost
+// values (at most kCostOrderBuckets - 1) in one CTA. Order among equal costs
+// is arbitrary; the result does not depend on it. A p-tile of nt
+// consecutive 128-point tiles costs the sum of theirs.
+// (Power-of-two buckets, the earlier form, put every p-tile of half the
+// maximum cost or more into one bucket in arbitrary order; at 2*10^6 x 16
+// anti-correlated the busiest SM then stayed active 20 % past the average.)
+constexpr int kCostOrderBuckets = 2 * kCostSamples;
+
 __global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict__ cost, const uint32_t* mcount,
-                                                     uint32_t* order)
+                                                     uint32_t* order, uint32_t nt)
 {
-    __shared__ uint32_t s_cnt[32], s_pos[32];
-    const uint32_t T = (*mcount + kTQ - 1) / kTQ;
-    if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0u;
+    static_assert(kCostOrderBuckets == 2 * 1024, "two buckets per thread of the scan");
+    __shared__ uint32_t s_cnt[kCostOrderBuckets];
+    __shared__ uint32_t s_warp[32];
+    const uint32_t T0 = (*mcount + kTQ - 1) / kTQ;
+    const uint32_t T = (T0 + nt - 1) / nt;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // bucket of item t: kCostOrderBuckets - 1 - cost, so that ascending
+    // buckets are descending costs
+    auto bucket = [&](uint32_t t) -> uint32_t {
+        uint32_t c = 0;
+        for (uint32_t h = 0; h < nt && t * nt + h < T0; ++h) c += cost[t * nt + h];
+        return (uint32_t)kCostOrderBuckets - 1u - min(c, (uint32_t)kCostOrderBuckets - 1u);
+    };
+    s_cnt[2 * tid] = 0u;
+    s_cnt[2 * tid + 1] = 0u;
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) {
-        const uint32_t b = 31u - (uint32_t)min(31, 32 - __clz((int)cost[t]));   // high cost -> low bucket
-        atomicAdd(&s_cnt[b], 1u);
+    for (uint32_t t = tid; t < T; t += blockDim.x) atomicAdd(&s_cnt[bucket(t)], 1u);
+    __syncthreads();
+    // exclusive scan of the bucket counts (thread i: buckets 2i and 2i + 1)
+    const uint32_t c0 = s_cnt[2 * tid], c1 = s_cnt[2 * tid + 1];
+    uint32_t x = c0 + c1;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s_warp[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;   // inclusive over warps
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (int b = 0; b < 32; ++b) { s_pos[b] = acc; acc += s_cnt[b]; }
-    }
+    const uint32_t before = (warp ? s_warp[warp - 1] : 0u) + x - (c0 + c1);
+    __syncthreads();   // every thread has read its counts
+    s_cnt[2 * tid] = before;
+    s_cnt[2 * tid + 1] = before + c0;
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) {
-        const uint32_t b = 31u - (uint32_t)min(31, 32 - __clz((int)cost[t]));
-        order[atomicAdd(&s_pos[b], 1u)] = t;
-    }
+    for (uint32_t t = tid; t < T; t += blockDim.x) order[atomicAdd(&s_cnt[bucket(t)], 1u)] = t;
 }
 
 // Resident CTAs per SM by padded dimension (the launch bound caps the
@@ -286,8 +319,34 @@ struct RefineMinBlocks {
                                : DP == 12 ? SKY_REFINE_MINB_12 : SKY_REFINE_MINB_16;
 };
 
-// WIT: witness mode (see refine_ptile); `wit` is unused otherwise.
-template <int DP, bool WIT>
+// p's per CTA of the full refinement by padded dimension: from
+// SKY_REFINE_WIDE_MIN_DP up, 256 (two consecutive 128-point tiles, eight
+// groups of 32: each streamed q-tile, its relevance test and its stage
+// hand-offs serve twice the p's); below it, 128. The p coordinates of a
+// 256-point CTA stay in global memory (SKY_REFINE_PX_SMEM_WIDE), so its
+// shared memory and launch bound are those of the 128-point form. The
+// pre-pass keeps 128. Measured on B300 (ms, one sky_skyline call, seed 1,
+// 128 -> 256 p's): 10^7 x 16 anti-correlated 109.1 -> 115.4, 2*10^6 x 16
+// anti-correlated 14.8 -> 19.2, independent 14.2 -> 15.9, correlated 10.7
+// -> 14.9; at d = 12 (from 12 up) 2*10^6 anti-correlated 8.3 -> 10.1,
+// 10^7 independent 20.9 -> 21.1. Streamed q-tiles fell by a third and the
+// instructions by 3 %, but a p-tile's scan is one CTA's serial work: at
+// 2*10^6 x 16 the longest CTA spans the whole launch (ncu: busiest SM active
+// 40.3 M cycles against a 25.7 M average, 29.2 M against 24.4 M with 128
+// p's), and doubling the p's doubles that critical path. So off (32: never).
+#ifndef SKY_REFINE_WIDE_MIN_DP
+#define SKY_REFINE_WIDE_MIN_DP 32
+#endif
+template <int DP>
+struct RefineGroups {
+    static constexpr int value = DP >= SKY_REFINE_WIDE_MIN_DP ? 2 * (kTQ / 32) : kTQ / 32;
+};
+template <int DP, int PG>
+using SetSmem = RefineSmem<DP, kRingStages, (DP >= SKY_REFINE_FAST_MIN_DP), PG>;
+
+// WIT: witness mode (see refine_ptile); `wit` is unused otherwise. PG:
+// groups of 32 p's per CTA (4 or 8).
+template <int DP, bool WIT, int PG>
 __global__ void __launch_bounds__(kTQ + 32, RefineMinBlocks<DP>::value) k_refine(const float* __restrict__ X, const uint32_t* __restrict__ C,
                                                      const int32_t* __restrict__ ids,
                                                      const uint32_t* __restrict__ SUB,
@@ -299,12 +358,14 @@ __global__ void __launch_bounds__(kTQ + 32, RefineMinBlocks<DP>::value) k_refine
                                                      int d, uint32_t min_m)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    RefineSmem<DP>& sm = *reinterpret_cast<RefineSmem<DP>*>(smem_raw);
+    using SM = SetSmem<DP, PG>;
+    SM& sm = *reinterpret_cast<SM*>(smem_raw);
     const uint32_t m = *mcount;
-    if (m < min_m || blockIdx.x >= (m + kTQ - 1) / kTQ) return;   // min_m: the pre-pass's survivor threshold
+    constexpr uint32_t kTP = SM::kTP;
+    if (m < min_m || blockIdx.x >= (m + kTP - 1) / kTP) return;   // min_m: the pre-pass's survivor threshold
     const uint32_t ptile = order ? order[blockIdx.x] : blockIdx.x;
-    refine_ptile<DP, true, WIT>(sm, X, C, ids, SUB, tend, supmin, m, ptile, res, keep, wit, cidx,
-                                cidx ? cidx + (1u << d) : nullptr);
+    refine_ptile<DP, true, WIT, SM>(sm, X, C, ids, SUB, tend, supmin, m, ptile, res, keep, wit, cidx,
+                                    cidx ? cidx + (1u << d) : nullptr);
 }
 
 // Ascending row ids of the kept rows (decoupled look-back over 8 rows per
@@ -458,24 +519,24 @@ bool refine_prepass(const Plan& p)
 
 namespace {
 
-// One refinement launch over the tiles of the first *mcount sorted survivors:
-// TEND is each p-tile's last q-tile, SUPMIN the super-tile minima (NULL:
-// none), ORDER the p-tile order (NULL: tile b in block b).
-template <int DP>
+// One refinement launch over the tiles of the first *mcount sorted survivors,
+// PG groups of 32 p's per CTA: TEND is each 128-point tile's last q-tile,
+// SUPMIN the super-tile minima (NULL: none), ORDER the p-tile order (NULL:
+// p-tile b in block b).
+template <int DP, int PG>
 void refine_launch(const Plan& p, cudaStream_t s, int64_t tiles, const uint32_t* tend, const uint32_t* supmin,
                    const uint32_t* order, const uint32_t* mcount, uint32_t min_m = 0)
 {
-    const int smem = (int)sizeof(RefineSmem<DP>);
+    const int smem = (int)sizeof(SetSmem<DP, PG>);
+    const unsigned grid = (unsigned)((tiles + SetSmem<DP, PG>::kTiles - 1) / SetSmem<DP, PG>::kTiles);
     if (p.witness) {
-        cudaFuncSetAttribute(k_refine<DP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_refine<DP, true><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, tend, supmin, order,
-                                                                    mcount, p.res, p.keep, p.witness, p.cidx, p.d,
-                                                                    min_m);
+        cudaFuncSetAttribute(k_refine<DP, true, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_refine<DP, true, PG><<<grid, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, tend, supmin, order,
+                                                             mcount, p.res, p.keep, p.witness, p.cidx, p.d, min_m);
     } else {
-        cudaFuncSetAttribute(k_refine<DP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_refine<DP, false><<<(unsigned)tiles, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, tend, supmin,
-                                                                     order, mcount, p.res, p.keep, nullptr, p.cidx,
-                                                                     p.d, min_m);
+        cudaFuncSetAttribute(k_refine<DP, false, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_refine<DP, false, PG><<<grid, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, tend, supmin, order,
+                                                              mcount, p.res, p.keep, nullptr, p.cidx, p.d, min_m);
     }
 }
 
@@ -490,8 +551,8 @@ cudaError_t launch_refine(const Plan& p, cudaStream_t s)
     if (refine_prepass(p)) {
         // the pre-pass: each p-tile against itself and the first kPreTiles
         // q-tiles (TEND clipped by the gather), no super-tile minima yet
-        SKY_DISPATCH_DP(p.d, refine_launch<DP>(p, s, tiles, p.tend_pre, nullptr, nullptr, mcount,
-                                               (uint32_t)kPreMinRows));
+        SKY_DISPATCH_DP(p.d, refine_launch<DP, kTQ / 32>(p, s, tiles, p.tend_pre, nullptr, nullptr, mcount,
+                                                         (uint32_t)kPreMinRows));
         // its survivors, compacted in order into the sort's other buffers
         Plan q = p;
         const bool first = p.sorted_key == p.surv_key;
@@ -510,10 +571,11 @@ cudaError_t launch_refine(const Plan& p, cudaStream_t s)
     }
     SKY_DISPATCH_DP(p.d, {
         constexpr int DW = DP / 4;
-        k_tile_cost<DW><<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(p.subcode, p.tmax, mcount, p.tile_cost,
-                                                                   p.supmin);
-        k_cost_order<<<1, 1024, 0, s>>>(p.tile_cost, mcount, p.tile_order);
-        refine_launch<DP>(p, s, tiles, p.tile_end, p.supmin, p.tile_order, mcount);
+        k_tile_cost<DW><<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(p.subcode, p.tmax, p.tile_end, mcount,
+                                                                   p.tile_cost, p.supmin);
+        constexpr int PG = RefineGroups<DP>::value;
+        k_cost_order<<<1, 1024, 0, s>>>(p.tile_cost, mcount, p.tile_order, (uint32_t)SetSmem<DP, PG>::kTiles);
+        refine_launch<DP, PG>(p, s, tiles, p.tile_end, p.supmin, p.tile_order, mcount);
     });
     return cudaGetLastError();
 }

@@ -291,27 +291,43 @@ __device__ __forceinline__ bool index_pays(uint32_t U, uint32_t first, uint32_t 
     return last >= first && (1ull << __popc(U)) <= 16ull * ((uint64_t)(last - first) / 32u + 1u);
 }
 
+// 1: a CTA whose p-tile holds 256 points (PG = 8 groups, see RefineSmem)
+// stages its own p coordinates in shared memory as well; 0: its exact tests
+// read them from global memory, which keeps the CTA at the shared memory of
+// the 128-point form
+#ifndef SKY_REFINE_PX_SMEM_WIDE
+#define SKY_REFINE_PX_SMEM_WIDE 0
+#endif
+
 // Shared memory of one refinement CTA. S: ring stages; FAST: fast-code
-// list probe (see SKY_REFINE_FAST_MIN_DP for the single-set default).
-template <int DP, int S = kRingStages, bool FAST = (DP >= SKY_REFINE_FAST_MIN_DP)>
+// list probe (see SKY_REFINE_FAST_MIN_DP for the single-set default); PG:
+// groups of 32 p's in the CTA's p-tile -- 4 (one 128-point tile, the q-tile
+// size) or 8 (two consecutive tiles: every streamed q-tile and every stage
+// hand-off then serves twice the p's).
+template <int DP, int S = kRingStages, bool FAST = (DP >= SKY_REFINE_FAST_MIN_DP), int PG = kTQ / 32>
 struct RefineSmem {
+    static_assert(PG == kTQ / 32 || PG == 2 * (kTQ / 32), "one or two tiles of p's");
     static constexpr int DW = DP / 4;
     static constexpr int kStages = S;
     static constexpr bool kFast = FAST;
+    static constexpr int kGroups = PG;               // groups of 32 p's
+    static constexpr int kTP = PG * 32;              // p's of the CTA
+    static constexpr int kTiles = kTP / kTQ;         // 128-point tiles of p's
+    static constexpr bool kPxSmem = SKY_REFINE_PX_SMEM && (kTiles == 1 || SKY_REFINE_PX_SMEM_WIDE);
     static constexpr int FW = (DP + 7) / 8;        // fast-code words
     // list entry words (vector loads): fast codes, or the 7-bit codes
     static constexpr int DWL = kFast ? FW : (DW == 3 ? 4 : DW);
     // bulk-copy destinations: 16-byte aligned whatever the ring depth
     alignas(16) uint32_t qC[S][kTQ * DW];  // streamed q-tiles (codes)
     static constexpr int kWindows = SKY_REFINE_WINDOWS;
-    alignas(16) float pX[SKY_REFINE_PX_SMEM ? kTQ * DP : 4];   // own p coordinates (exact tests)
-    uint32_t pP[kTQ * DW];               // own p codes | 0x80 per byte
-    uint32_t pF[kFast ? kTQ * FW : 1];   // own p fast codes | 0x8 per nibble
-    uint32_t livemask[kTQ / 32];         // bit l of word g: p g*32+l is still undominated
-    uint32_t gmax[kTQ / 32][DW];         // byte-wise max code of each group's live p's | 0x80 per byte (producer)
-    uint32_t glive[kTQ / 32];            // live p's per group (producer)
+    alignas(16) float pX[kPxSmem ? kTP * DP : 4];   // own p coordinates (exact tests)
+    uint32_t pP[kTP * DW];               // own p codes | 0x80 per byte
+    uint32_t pF[kFast ? kTP * FW : 1];   // own p fast codes | 0x8 per nibble
+    uint32_t livemask[PG];               // bit l of word g: p g*32+l is still undominated
+    uint32_t gmax[PG][DW];               // byte-wise max code of each group's live p's | 0x80 per byte (producer)
+    uint32_t glive[PG];                  // live p's per group (producer)
     uint32_t stage_tile[S];
-    uint32_t stage_mask[S];              // bit 4w+g: sub-tile w may dominate a live p of group g
+    uint32_t stage_mask[S];              // bit PG*w+g: sub-tile w may dominate a live p of group g
     uint32_t stage_sub[S][kTQ / 32][DW];   // sub-tile minimum codes of the staged tile
     uint64_t full[S];
     uint64_t empty[S];
@@ -377,9 +393,11 @@ __device__ __forceinline__ bool bytes_le(const uint32_t* lo, const uint32_t* hi)
     return r == kHigh;
 }
 
-// Refines p-tile `ptile` (< ceil(m / 128)) of one point set. Called by all
-// kTQ + 32 threads of the CTA with the CTA's shared memory; leaves the
-// shared memory free for the next call (barriers invalidated).
+// Refines p-tile `ptile` (< ceil(m / SM::kTP)) of one point set: the
+// SM::kTP = 128 or 256 survivors from ptile * SM::kTP on (one or two
+// consecutive 128-point tiles). Called by all kTQ + 32 threads of the CTA
+// with the CTA's shared memory; leaves the shared memory free for the next
+// call (barriers invalidated).
 // TEND (optional): per p-tile, the last q-tile that can hold a dominator of
 // one of its points (the tiles are in Morton order, and a dominator's Morton
 // key is never above its victim's: the column maps are monotone), so the
@@ -404,49 +422,62 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                                              const uint32_t* __restrict__ MHI = nullptr)
 {
     constexpr int DW = DP / 4;
-    constexpr int NG = kTQ / 32;
+    constexpr int NG = SM::kGroups;   // groups of 32 p's
+    constexpr int NQ = kTQ / 32;      // q sub-tiles of a streamed tile = consumer warps
+    constexpr int NT = SM::kTiles;    // 128-point tiles of p's
+    constexpr int kTP = SM::kTP;
     constexpr int S = SM::kStages;
     constexpr uint32_t kSparseLive = SparseLive<DP>::value;
     constexpr uint32_t kBytesC = kTQ * DW * sizeof(uint32_t);
     const uint32_t T = (m + kTQ - 1) / kTQ;
     uint32_t* err = &res->err;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t pbase = (int64_t)ptile * kTQ;
+    const int64_t pbase = (int64_t)ptile * kTP;
+    const uint32_t tile0 = ptile * (uint32_t)NT;   // the first of the p-tile's own q-tiles
+    // q-tile t is one of the p-tile's own (streamed first, skipped later)
+    auto own = [&](uint32_t t) -> bool { return t - tile0 < (uint32_t)NT; };
     if (tid < kTQ) {
-        const bool valid = pbase + tid < m;
-        uint32_t pc[DW];
 #pragma unroll
-        for (int w = 0; w < DW; ++w) {
-            pc[w] = C[(pbase + tid) * DW + w];
-            sm.pP[tid * DW + w] = pc[w] | kHigh;
+        for (int h = 0; h < NT; ++h) {
+            const int pi = h * kTQ + tid;
+            // the survivor layout ends with tile T - 1; a second tile past it holds no p
+            const bool in_layout = tile0 + (uint32_t)h < T;
+            const bool valid = pbase + pi < m;
+            uint32_t pc[DW];
+#pragma unroll
+            for (int w = 0; w < DW; ++w) {
+                pc[w] = in_layout ? C[(pbase + pi) * DW + w] : 0x7f7f7f7fu;
+                sm.pP[pi * DW + w] = pc[w] | kHigh;
+            }
+            if constexpr (SM::kFast) {
+#pragma unroll
+                for (int f = 0; f < SM::FW; ++f) sm.pF[pi * SM::FW + f] = fast_word<DW>(pc, f) | kHighNib;
+            }
+            if constexpr (SM::kPxSmem) {
+#pragma unroll
+                for (int k = 0; k < DP; k += 4)
+                    *reinterpret_cast<float4*>(&sm.pX[pi * DP + k]) =
+                        in_layout ? *reinterpret_cast<const float4*>(X + (pbase + pi) * DP + k)
+                                  : make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+            }
+            const uint32_t vm = __ballot_sync(kFull, valid);
+            if ((tid & 31) == 0) sm.livemask[pi >> 5] = vm;
         }
-        if constexpr (SM::kFast) {
-#pragma unroll
-            for (int f = 0; f < SM::FW; ++f) sm.pF[tid * SM::FW + f] = fast_word<DW>(pc, f) | kHighNib;
-        }
-#if SKY_REFINE_PX_SMEM
-#pragma unroll
-        for (int k = 0; k < DP; k += 4)
-            *reinterpret_cast<float4*>(&sm.pX[tid * DP + k]) =
-                *reinterpret_cast<const float4*>(X + (pbase + tid) * DP + k);
-#endif
-        const uint32_t vm = __ballot_sync(kFull, valid);
-        if ((tid & 31) == 0) sm.livemask[tid >> 5] = vm;
     }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&sm.full[s], 1);
-            mbar_init(&sm.empty[s], NG);
+            mbar_init(&sm.empty[s], NQ);
         }
         for (int b = 0; b < SM::kWindows; ++b) mbar_init(&sm.cbar[b], 1);
         mbar_fence_init();
-        sm.live = (m - pbase) < (uint32_t)kTQ ? (m - (uint32_t)pbase) : (uint32_t)kTQ;
+        sm.live = (m - pbase) < (uint32_t)kTP ? (m - (uint32_t)pbase) : (uint32_t)kTP;
         sm.failed = 0;
         sm.sparse = 0;
     }
     __syncthreads();
 
-    if (warp == NG) {
+    if (warp == NQ) {
         // ------------------------------------------------------------ producer
         uint32_t issued = 0;
         auto summarise = [&]() {
@@ -481,7 +512,8 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
         auto all_dead = [&]() -> bool {
             return __shfl_sync(kFull, (sm.live == 0u || sm.failed != 0u) ? 1 : 0, 0) != 0;
         };
-        const uint32_t E = TEND ? min(TEND[ptile], T - 1u) : T - 1u;   // last q-tile to scan
+        // last q-tile to scan (the last own tile's end: the ends are non-decreasing)
+        const uint32_t E = TEND ? min(TEND[min(tile0 + (uint32_t)NT - 1u, T - 1u)], T - 1u) : T - 1u;
         if (lane == 0) sm.scan_end = E;
         const uint32_t SL = E / 32u;                                     // last super-tile
         // Streaming order: the p-tile itself first (its own points kill each
@@ -523,35 +555,41 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
             for (int g = 0; g < NG; ++g)
                 if (sm.glive[g] != 0u) U |= cell_of_codes<DW>(sm.gmax[g]);
             use_idx = index_pays(U, 0u, E);
-            if (use_idx) cellwin_init(sm.cwin[NG], U, 0u, E);
+            if (use_idx) cellwin_init(sm.cwin[NQ], U, 0u, E);
         }
         auto next_window = [&](uint32_t& t0, uint32_t& wm) -> bool {
-            if (use_idx) return cellwin_next<kWinAlign>(sm.cwin[NG], MLO, MHI, t0, wm);
+            if (use_idx) return cellwin_next<kWinAlign>(sm.cwin[NQ], MLO, MHI, t0, wm);
             const int sx = next_super();
             if (sx < 0) return false;
             t0 = (uint32_t)sx * 32u;
             wm = 0xffffffffu;
             return true;
         };
-        // the p-tile itself: every (sub-tile, group) pair whose sub-tile
-        // minimum is within the group's reach
-        {
+        // the p-tile's own q-tiles: every (sub-tile, group) pair whose
+        // sub-tile minimum is within the group's reach (lane q * NG + g);
+        // slot `issued` (< NT <= S) of the ring, not yet used
+        static_assert(NQ * NG <= 32 && NT <= S, "one lane per (sub-tile, group) pair");
+#pragma unroll
+        for (int h = 0; h < NT; ++h) {
+            const uint32_t ot = tile0 + (uint32_t)h;
+            if (ot >= T) break;
             const int q = lane / NG, g = lane % NG;
+            const int s = (int)issued;
             bool rel = false;
-            if (lane < NG * NG && sm.glive[g] != 0u) {
+            if (lane < NQ * NG && sm.glive[g] != 0u) {
                 uint32_t mn[DW];
 #pragma unroll
-                for (int w = 0; w < DW; ++w) mn[w] = __ldg(SUB + ((int64_t)ptile * kSubSlots + q) * DW + w);
+                for (int w = 0; w < DW; ++w) mn[w] = __ldg(SUB + ((int64_t)ot * kSubSlots + q) * DW + w);
                 rel = bytes_le<DW>(mn, sm.gmax[g]);
             }
-            if (lane < NG * DW) sm.stage_sub[0][lane / DW][lane % DW] = __ldg(SUB + (int64_t)ptile * kSubSlots * DW + lane);
+            if (lane < NQ * DW) sm.stage_sub[s][lane / DW][lane % DW] = __ldg(SUB + (int64_t)ot * kSubSlots * DW + lane);
             const uint32_t bmask = __ballot_sync(kFull, rel);
             __syncwarp();   // the lanes' writes before lane 0's arrive on the slot
             if (lane == 0 && bmask) {
-                sm.stage_tile[0] = ptile;
-                sm.stage_mask[0] = bmask;
-                mbar_arrive_expect_tx(&sm.full[0], kBytesC);
-                bulk_g2s(sm.qC[0], C + (int64_t)ptile * kTQ * DW, kBytesC, &sm.full[0]);
+                sm.stage_tile[s] = ot;
+                sm.stage_mask[s] = bmask;
+                mbar_arrive_expect_tx(&sm.full[s], kBytesC);
+                bulk_g2s(sm.qC[s], C + (int64_t)ot * kTQ * DW, kBytesC, &sm.full[s]);
             }
             __syncwarp();
             if (bmask) { ++issued; ++since; }
@@ -607,10 +645,11 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
             const uint32_t t = t0 + lane;
             const uint32_t* tc = &sm.stc[bf][lane * kSubSlots * DW];
             // relevance of each (sub-tile, group) pair of this q-tile; in the
-            // single-set kernel the group maxima and the live groups are read
-            // into registers once for the 4 + 16 box tests of a lane
-            constexpr bool kRegMax = SPARSE && DP <= SKY_REFINE_REGMAX_DP;
-            uint32_t gm[NG][DW];
+            // single-set kernel with four groups the group maxima and the live
+            // groups are read into registers once for the 4 + 16 box tests of
+            // a lane; with eight groups, one group's maximum at a time
+            constexpr bool kRegMax = SPARSE && DP <= SKY_REFINE_REGMAX_DP && NG == NQ;
+            uint32_t gm[kRegMax ? NG : 1][DW];
             uint32_t gl = 0;
             if constexpr (kRegMax) {
 #pragma unroll
@@ -625,18 +664,18 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                 else return (sm.glive[g] != 0u) && bytes_le<DW>(lo, sm.gmax[g]);
             };
             uint32_t rmask = 0;
-            if (t <= E && t != ptile && ((wmk >> lane) & 1u)) {   // the p-tile itself went first
+            if (t <= E && !own(t) && ((wmk >> lane) & 1u)) {   // the own tiles went first
 #if SKY_REFINE_SLIM_PRODUCER
                 // one sub-tile's minimum in registers at a time
                 uint32_t cw[DW];
 #pragma unroll
-                for (int w = 0; w < DW; ++w) cw[w] = tc[NG * DW + w];   // the tile minimum
+                for (int w = 0; w < DW; ++w) cw[w] = tc[NQ * DW + w];   // the tile minimum
                 bool any = false;
 #pragma unroll
                 for (int g = 0; g < NG; ++g) any |= le_g(cw, g);
                 if (any) {
 #pragma unroll 1
-                    for (int q = 0; q < NG; ++q) {
+                    for (int q = 0; q < NQ; ++q) {
 #pragma unroll
                         for (int w = 0; w < DW; ++w) cw[w] = tc[q * DW + w];
 #pragma unroll
@@ -645,20 +684,34 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                     }
                 }
 #else
-                uint32_t cw[NG + 1][DW];   // sub-tile minima, then the tile minimum
+                uint32_t cw[NQ + 1][DW];   // sub-tile minima, then the tile minimum
 #pragma unroll
-                for (int q = 0; q <= NG; ++q)
+                for (int q = 0; q <= NQ; ++q)
 #pragma unroll
                     for (int w = 0; w < DW; ++w) cw[q][w] = tc[q * DW + w];
-                bool any = false;
+                if constexpr (NG == NQ) {
+                    bool any = false;
 #pragma unroll
-                for (int g = 0; g < NG; ++g) any |= le_g(cw[NG], g);
-                if (any) {
+                    for (int g = 0; g < NG; ++g) any |= le_g(cw[NQ], g);
+                    if (any) {
 #pragma unroll
-                    for (int q = 0; q < NG; ++q)
+                        for (int q = 0; q < NQ; ++q)
 #pragma unroll
-                        for (int g = 0; g < NG; ++g)
-                            if (le_g(cw[q], g)) rmask |= 1u << (q * NG + g);
+                            for (int g = 0; g < NG; ++g)
+                                if (le_g(cw[q], g)) rmask |= 1u << (q * NG + g);
+                    }
+                } else {
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) {
+                        if (sm.glive[g] == 0u) continue;
+                        uint32_t gg[DW];
+#pragma unroll
+                        for (int w = 0; w < DW; ++w) gg[w] = sm.gmax[g][w];
+                        if (!bytes_le<DW>(cw[NQ], gg)) continue;   // the tile minimum first
+#pragma unroll
+                        for (int q = 0; q < NQ; ++q)
+                            if (bytes_le<DW>(cw[q], gg)) rmask |= 1u << (q * NG + g);
+                    }
                 }
 #endif
             }
@@ -671,7 +724,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                 if (!claim(s)) { if (lane == 0) sm.failed = 1u; stop = true; break; }
                 // tile b's sub-tile minima to the slot; the warp barrier orders
                 // these writes before lane 0's arrive on the slot
-                if (lane < NG * DW) sm.stage_sub[s][lane / DW][lane % DW] = sm.stc[bf][b * kSubSlots * DW + lane];
+                if (lane < NQ * DW) sm.stage_sub[s][lane / DW][lane % DW] = sm.stc[bf][b * kSubSlots * DW + lane];
                 __syncwarp();
                 if (lane == 0) {
                     const uint32_t tt = t0 + b;
@@ -786,11 +839,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                             if (eq) {
                                 ++exact;
                                 const float* qx = X + ((int64_t)tt * kTQ + qi) * DP;
-#if SKY_REFINE_PX_SMEM
-                                const float* px = &sm.pX[pi * DP];
-#else
-                                const float* px = X + (pbase + pi) * DP;
-#endif
+                                const float* px = SM::kPxSmem ? &sm.pX[pi * DP] : X + (pbase + pi) * DP;
                                 bool le = true, lt = false;
 #pragma unroll
                                 for (int kk = 0; kk < DP; kk += 4) {
@@ -896,7 +945,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                         }
                     }
                 };
-                if constexpr (kBalance) {
+                if constexpr (kBalance && NG == NQ) {
                     // the stage's (sub-tile, group) pairs (bit q * NG + g),
                     // dealt to the consumer warps in turn, so that a stage
                     // whose work sits in one sub-tile still spreads over
@@ -916,7 +965,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                 } else {
                     // warp w takes sub-tile w (rotated by the stage number
                     // with SKY_REFINE_BALANCE = 2) and every group within its reach
-                    const int q = SKY_REFINE_BALANCE == 2 ? (int)((warp + k) % (uint32_t)NG) : warp;
+                    const int q = SKY_REFINE_BALANCE == 2 ? (int)((warp + k) % (uint32_t)NQ) : warp;
                     const uint32_t gm = (smask >> (q * NG)) & ((1u << NG) - 1u);
                     if (gm) {
                         load_sub(q);
@@ -938,7 +987,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
     __syncthreads();
     if (SPARSE && kSparseLive > 0 && sm.sparse && !sm.failed && sm.live != 0u) {
         // ---------------------------------------------------------- sparse mode
-        constexpr int NW = NG + 1;                        // all five warps
+        constexpr int NW = NQ + 1;                        // all five warps
         constexpr int DWL = DW == 3 ? 4 : DW;             // 7-bit code words per sparse-list entry
         uint32_t* LC = sm.plist[0];                       // the consumers' lists are free now
         uint8_t* LI = sm.pidx[0];
@@ -1001,10 +1050,10 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
             if (__shfl_sync(kFull, sm.live, 0) == 0u) break;
             const uint32_t t = wbase + (uint32_t)lane;
             uint32_t rm = 0;   // listed p's whose codes reach this tile's minimum
-            if (t <= E && t != ptile && ((wmk >> lane) & 1u)) {
+            if (t <= E && !own(t) && ((wmk >> lane) & 1u)) {
                 uint32_t mn[DW];
 #pragma unroll
-                for (int w = 0; w < DW; ++w) mn[w] = __ldg(SUB + ((int64_t)t * kSubSlots + NG) * DW + w);
+                for (int w = 0; w < DW; ++w) mn[w] = __ldg(SUB + ((int64_t)t * kSubSlots + NQ) * DW + w);
                 for (int i = 0; i < nl; ++i) {
                     uint32_t pc[DW];
                     load_entry<DW>(LC + i * DWL, pc);
@@ -1058,11 +1107,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                             if (eq) {
                                 ++sexact;
                                 const float* qx = X + ((int64_t)tt * kTQ + j * 32 + lane) * DP;
-#if SKY_REFINE_PX_SMEM
-                                const float* px = &sm.pX[pi * DP];
-#else
-                                const float* px = X + (pbase + pi) * DP;
-#endif
+                                const float* px = SM::kPxSmem ? &sm.pX[pi * DP] : X + (pbase + pi) * DP;
                                 bool le = true, lt = false;
 #pragma unroll
                                 for (int kk = 0; kk < DP; kk += 4) {
@@ -1089,8 +1134,13 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
         if (lane == 0 && we) atomicAdd(&res->exact, (unsigned long long)we);
         __syncthreads();
     }
-    if (tid < kTQ && pbase + tid < m && !sm.failed && ((sm.livemask[tid >> 5] >> (tid & 31)) & 1u))
-        keep[ids[pbase + tid]] = 1;
+    if (tid < kTQ && !sm.failed) {
+#pragma unroll
+        for (int h = 0; h < NT; ++h) {
+            const int pi = h * kTQ + tid;
+            if (pbase + pi < m && ((sm.livemask[pi >> 5] >> (pi & 31)) & 1u)) keep[ids[pbase + pi]] = 1;
+        }
+    }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_inval(&sm.full[s]);

@@ -57,3 +57,18 @@ def test_few_points_far_apart_in_morton_order():
     P[rng.choice(n, 64, replace=False)] = front
     want = oracle.skyline_sfs(P).tolist()
     assert gpu(P) == want
+
+
+@pytest.mark.parametrize("d", [13, 16])
+@pytest.mark.parametrize("kind", ["independent", "anticorrelated", "correlated"])
+def test_high_dimension_ragged_tile_counts(kind, d):
+    """Padded dimension 16 (13 and 16 dimensions): tile counts odd and even,
+    a last tile with one point, sets spanning many CTAs of the refinement,
+    with and without the sparse tail (the 256-point p-tile variant of the
+    refinement, when built, meets the same cases: a last CTA with and
+    without its second tile)."""
+    for n in (129, 255, 256, 257, 385, 1000, 4097, 9001, 33000):
+        P = skydata.generate(kind, n, d, seed=n + d)
+        want = oracle.skyline_sfs(P).tolist()
+        assert gpu(P) == want, (kind, d, n)
+        assert gpu(P, assume_unit=True) == want, (kind, d, n)
