@@ -581,7 +581,7 @@ SKY_API sky_status sky_last_phase_times(sky_phase_times* out);
  *
  * Same arguments and result as sky_skyline, but every piece of scratch memory
  * comes from one fixed array in device global memory that the library
- * reserves at load time (about 10 MiB per GPU that loads the library, held
+ * reserves at load time (about 12 MiB per GPU that loads the library, held
  * until the process exits); the call performs no cudaMalloc, cudaFree or
  * other allocation. Limits: n <= SKY_NOALLOC_MAX_POINTS and a grid of at most
  * 2^20 cells (log2_g * d <= 20; the automatic choice is lowered to fit);

@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
                                                 const uint32_t* __restrict__ sorted_key, const uint32_t* mcount,
                                                 const float* __restrict__ params, float* X, uint32_t* C,
                                                 int32_t* ids, uint32_t* tmax, uint32_t* subcode,
-                                                uint32_t* tile_end, uint32_t* cidx, uint32_t* tend_pre)
+                                                uint32_t* tile_end, uint32_t* cidx, uint32_t* tend_pre,
+                                                uint32_t* tmask)
 {
     constexpr int DW = DP / 4;
     const uint32_t m = *mcount;
@@ -119,6 +120,30 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
         if (valid && lane == __ffs(peers) - 1) {
             atomicMax(cidx + cell, ~(uint32_t)blockIdx.x);
             atomicMax(cidx + (1u << d) + cell, (uint32_t)blockIdx.x + 1u);
+        }
+    }
+
+    // threshold masks of this warp's 32-point sub-tile (the refinement's
+    // mask probe): word k * 8 + l = the lanes whose 3-bit code (the top three
+    // bits of the 7-bit code) in dimension k is <= l; padding points (code
+    // 127) pass only level 7, which every point passes
+    if constexpr (DP >= 12) {
+        if (tmask != nullptr) {
+            uint32_t v[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                // dimensions past the padded ones: every point at level 0
+                const uint32_t c3 = k < DP ? (code[k < DP ? k >> 2 : 0] >> (8 * (k & 3) + 4)) & 7u : 0u;
+#pragma unroll
+                for (int l = 0; l < 8; ++l) {
+                    const uint32_t b = l == 7 ? kFull : __ballot_sync(kFull, c3 <= (uint32_t)l);
+                    const int e = k * 8 + l;
+                    if (lane == (e & 31)) v[e >> 5] = b;
+                }
+            }
+            uint32_t* o = tmask + ((int64_t)blockIdx.x * (kTQ / 32) + warp) * 128;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) o[r * 32 + lane] = v[r];
         }
     }
 
@@ -312,11 +337,28 @@ __global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict_
 #ifndef SKY_REFINE_MINB_16
 #define SKY_REFINE_MINB_16 6
 #endif
+// The mask probe (see sky_refine.cuh) from this padded dimension up (it is
+// built for 12 and 16; larger: off) and its CTAs per SM (72 / 64 registers;
+// five CTAs at d = 12 measured 10^7 x 12 independent 17.3 -> 18.8 ms)
+#ifndef SKY_REFINE_MASK_MIN_DP
+#define SKY_REFINE_MASK_MIN_DP 12
+#endif
+#ifndef SKY_REFINE_MINB_16_MASK
+#define SKY_REFINE_MINB_16_MASK 5
+#endif
+#ifndef SKY_REFINE_MINB_12_MASK
+#define SKY_REFINE_MINB_12_MASK 6
+#endif
+template <int DP>
+struct RefineMask {
+    static constexpr bool value = DP >= 12 && DP >= SKY_REFINE_MASK_MIN_DP;
+};
 template <int DP>
 struct RefineMinBlocks {
     static constexpr int value = DP == 4 ? SKY_REFINE_MINB_4
                                : DP == 8 ? SKY_REFINE_MINB_8
-                               : DP == 12 ? SKY_REFINE_MINB_12 : SKY_REFINE_MINB_16;
+                               : DP == 12 ? (RefineMask<DP>::value ? SKY_REFINE_MINB_12_MASK : SKY_REFINE_MINB_12)
+                               : RefineMask<DP>::value ? SKY_REFINE_MINB_16_MASK : SKY_REFINE_MINB_16;
 };
 
 // p's per CTA of the full refinement by padded dimension: from
@@ -342,7 +384,8 @@ struct RefineGroups {
     static constexpr int value = DP >= SKY_REFINE_WIDE_MIN_DP ? 2 * (kTQ / 32) : kTQ / 32;
 };
 template <int DP, int PG>
-using SetSmem = RefineSmem<DP, kRingStages, (DP >= SKY_REFINE_FAST_MIN_DP), PG>;
+using SetSmem = RefineSmem<DP, RefineMask<DP>::value ? SKY_REFINE_MASK_STAGES : kRingStages,
+                           (DP >= SKY_REFINE_FAST_MIN_DP), PG, RefineMask<DP>::value>;
 
 // WIT: witness mode (see refine_ptile); `wit` is unused otherwise. PG:
 // groups of 32 p's per CTA (4 or 8).
@@ -355,9 +398,9 @@ __global__ void __launch_bounds__(kTQ + 32, RefineMinBlocks<DP>::value) k_refine
                                                      const uint32_t* __restrict__ order, const uint32_t* mcount,
                                                      DevResult* res,
                                                      uint8_t* keep, int32_t* wit, const uint32_t* __restrict__ cidx,
-                                                     int d, uint32_t min_m)
+                                                     int d, uint32_t min_m, const uint32_t* __restrict__ tmask)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(256) unsigned char smem_raw[];
     using SM = SetSmem<DP, PG>;
     SM& sm = *reinterpret_cast<SM*>(smem_raw);
     const uint32_t m = *mcount;
@@ -365,7 +408,7 @@ __global__ void __launch_bounds__(kTQ + 32, RefineMinBlocks<DP>::value) k_refine
     if (m < min_m || blockIdx.x >= (m + kTP - 1) / kTP) return;   // min_m: the pre-pass's survivor threshold
     const uint32_t ptile = order ? order[blockIdx.x] : blockIdx.x;
     refine_ptile<DP, true, WIT, SM>(sm, X, C, ids, SUB, tend, supmin, m, ptile, res, keep, wit, cidx,
-                                    cidx ? cidx + (1u << d) : nullptr);
+                                    cidx ? cidx + (1u << d) : nullptr, tmask);
 }
 
 // Ascending row ids of the kept rows (decoupled look-back over 8 rows per
@@ -508,8 +551,15 @@ cudaError_t launch_gather(const Plan& p, cudaStream_t s, const uint32_t* mcount)
     SKY_DISPATCH_DP(p.d, k_gather<DP><<<(unsigned)tiles, kTQ, 0, s>>>(p.pts, p.d, p.ld, v, p.sorted_val,
                                                                        p.sorted_key, mcount, p.params, p.X, p.C,
                                                                        p.ids, p.tmax, p.subcode, p.tile_end,
-                                                                       p.cidx, p.tend_pre));
+                                                                       p.cidx, p.tend_pre, p.tmask));
     return cudaGetLastError();
+}
+
+bool refine_mask_probe(int d)
+{
+    bool on = false;
+    SKY_DISPATCH_DP(d, on = RefineMask<DP>::value);
+    return on;
 }
 
 bool refine_prepass(const Plan& p)
@@ -532,11 +582,13 @@ void refine_launch(const Plan& p, cudaStream_t s, int64_t tiles, const uint32_t*
     if (p.witness) {
         cudaFuncSetAttribute(k_refine<DP, true, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k_refine<DP, true, PG><<<grid, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, tend, supmin, order,
-                                                             mcount, p.res, p.keep, p.witness, p.cidx, p.d, min_m);
+                                                             mcount, p.res, p.keep, p.witness, p.cidx, p.d, min_m,
+                                                             p.tmask);
     } else {
         cudaFuncSetAttribute(k_refine<DP, false, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k_refine<DP, false, PG><<<grid, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, tend, supmin, order,
-                                                              mcount, p.res, p.keep, nullptr, p.cidx, p.d, min_m);
+                                                              mcount, p.res, p.keep, nullptr, p.cidx, p.d, min_m,
+                                                              p.tmask);
     }
 }
 

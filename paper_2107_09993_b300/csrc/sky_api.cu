@@ -185,6 +185,7 @@ size_t layout(Plan& p, char* base, bool grid_api)
     p.supmin = c.take<uint32_t>(((tiles + 31) / 32) * (dp / 4));
     p.cidx = c.take<uint32_t>(size_t(2) << (p.d > 0 ? p.d : 1));
     p.tend_pre = c.take<uint32_t>(tiles);
+    p.tmask = refine_mask_probe(p.d) ? c.take<uint32_t>(tiles * kMaskWords) : nullptr;
     p.pre_states = c.take<unsigned long long>(p.lb_tiles);
     p.keep = c.take<uint8_t>(n + 16);
     return c.off;
@@ -265,6 +266,7 @@ sky_status status_from_flags(uint32_t err)
 {
     if (err & SKY_DEV_ERR_NONFINITE) return fail(SKY_ERR_NONFINITE, "input holds NaN or infinity");
     if (err & SKY_DEV_ERR_TIMEOUT) return fail(SKY_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (err & SKY_DEV_ERR_LAYOUT) return fail(SKY_ERR_CUDA, "refinement shared memory not 256-byte aligned");
     return SKY_OK;
 }
 

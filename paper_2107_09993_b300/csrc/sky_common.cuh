@@ -19,6 +19,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t SKY_DEV_ERR_NONFINITE = 1u;
 constexpr uint32_t SKY_DEV_ERR_TIMEOUT = 2u;
 constexpr uint32_t SKY_DEV_ERR_CAPACITY = 4u;
+constexpr uint32_t SKY_DEV_ERR_LAYOUT = 8u;   // a shared-memory table not at the alignment its addressing needs
 
 // Upper bound on polls of any flag or barrier (each poll may suspend briefly).
 constexpr uint32_t kWaitLimit = 1u << 22;

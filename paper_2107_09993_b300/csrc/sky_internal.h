@@ -80,6 +80,7 @@ struct Plan {
     uint32_t* supmin = nullptr;      // [ceil(tiles / 32)][dp/4] byte-wise min code of each run of 32 tiles
     uint32_t* cidx = nullptr;        // [2][2^d] layer-1 cell index: ~first tile, last tile + 1 (0: no point)
     uint32_t* tend_pre = nullptr;    // [tiles] last q-tile of the refinement's pre-pass scan
+    uint32_t* tmask = nullptr;       // [tiles][4][128] threshold masks of the 32-point sub-tiles (mask probe)
     unsigned long long* pre_states = nullptr;   // [lb_tiles] look-back states of the pre-pass compaction
     uint8_t* keep = nullptr;         // [n] 1 = skyline
     float* filt = nullptr;           // [16][16] snapped filter points
@@ -127,6 +128,9 @@ struct QueryPlan {
 };
 
 constexpr int kRefineTile = 128;   // points per refinement tile
+// threshold masks per tile for the refinement's mask probe: 4 sub-tiles of
+// 32 points x 16 dimensions x 8 levels of the 3-bit codes
+constexpr int kMaskWords = 4 * 128;
 constexpr int kSurvMaxBlocks = 4096;  // blocks of the survivor passes (at most 6 per SM)
 constexpr int kMapMaxBlocks = 1024;   // blocks of the map pass
 constexpr int64_t kPrivWords = 2048;  // grids of at most 2^16 cells are marked in shared memory first
@@ -173,6 +177,9 @@ cudaError_t launch_sort(Plan& p, cudaStream_t s);
 cudaError_t launch_gather(const Plan& p, cudaStream_t s, const uint32_t* mcount = nullptr);
 // whether launch_refine runs the pre-pass (3 more kernels: refine, compaction, gather)
 bool refine_prepass(const Plan& p);
+// whether the refinement of d-dimensional points uses the mask probe (and
+// the workspace holds p.tmask)
+bool refine_mask_probe(int d);
 cudaError_t launch_refine(const Plan& p, cudaStream_t s);
 cudaError_t launch_emit(const Plan& p, int32_t* out, int64_t capacity, cudaStream_t s);
 // k_tournament.cu: Algorithm 3 (tournament tree) classes of one layer

@@ -13,7 +13,7 @@
 //
 // Limits: n <= SKY_NOALLOC_MAX_POINTS (65,536) points and a grid of at most
 // 2^20 cells (log2_g * d <= 20); anything larger is rejected with
-// SKY_ERR_TOO_LARGE. The array (10 MiB) stays reserved on every GPU that
+// SKY_ERR_TOO_LARGE. The array (12 MiB) stays reserved on every GPU that
 // loads the library until the process exits.
 //
 // Sharing: every call, on every stream and thread, uses the same array, and
@@ -40,7 +40,7 @@ namespace {
 
 constexpr int64_t kMaxPoints = SKY_NOALLOC_MAX_POINTS;
 constexpr int kMaxGridBits = 20;
-constexpr size_t kScratchBytes = size_t(10) << 20;  // 10 MiB; the worst case needs less
+constexpr size_t kScratchBytes = size_t(12) << 20;  // 12 MiB; the worst case (65,536 x 16 at 2^16 cells) needs less
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 

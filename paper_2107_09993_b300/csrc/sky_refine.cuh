@@ -291,6 +291,35 @@ __device__ __forceinline__ bool index_pays(uint32_t U, uint32_t first, uint32_t 
     return last >= first && (1ull << __popc(U)) <= 16ull * ((uint64_t)(last - first) / 32u + 1u);
 }
 
+// Mask probe (single-set kernel, padded dimensions 12 and 16): besides its
+// 7-bit codes, every streamed q-tile carries threshold masks of its 32-point
+// sub-tiles -- for each dimension k and level l of the 3-bit codes (the top
+// three bits of the 7-bit codes), the 32-bit set of the sub-tile's q's whose
+// 3-bit code in k is <= l (written by the gather). A group scan that lists
+// at least SKY_REFINE_MASK_MIN_LIST p's gives every lane one p and ANDs the
+// d masks at that p's levels: the q's of the sub-tile that pass the 3-bit
+// test against it (necessary for dominance: the code map is monotone), 32
+// pairs per lane in about 2.5 instructions per dimension, where the list
+// probe spends about 10 warp instructions per listed p plus the list's
+// construction. The rare passes get the 7-bit and exact tests of the list
+// probe. Measured on B300 (ms, one sky_skyline call, seed 1; list probe ->
+// mask probe from 3 / 2 / 1 listed p's): 10^7 x 16 anti-correlated 108.9 ->
+// 92.9 / 91.2 / 83.7, 2*10^6 x 16 independent 14.2 -> 15.5 / 14.2 / 12.6,
+// correlated 10.6 -> 10.1 / 10.4 / 11.0; at padded dimension 12 (from 1
+// listed p) 10^7 x 12 independent 20.7 -> 17.3, 2*10^6 x 12 anti-correlated
+// 8.19 -> 5.42, correlated (a one-point skyline) 1.09 -> 1.56. A per-stage
+// flag that left the masks out once few p's were live measured 13 % slower
+// on every set.
+#ifndef SKY_REFINE_MASK_MIN_LIST
+#define SKY_REFINE_MASK_MIN_LIST 1
+#endif
+// ring depth with the mask probe (its stages hold codes and masks: 4 KB a
+// tile at d = 16, 3.5 KB at d = 12; 8 stages with four CTAs per SM measured
+// 10^7 x 16 anti-correlated 83.6 -> 97.3 ms)
+#ifndef SKY_REFINE_MASK_STAGES
+#define SKY_REFINE_MASK_STAGES 6
+#endif
+
 // 1: a CTA whose p-tile holds 256 points (PG = 8 groups, see RefineSmem)
 // stages its own p coordinates in shared memory as well; 0: its exact tests
 // read them from global memory, which keeps the CTA at the shared memory of
@@ -303,22 +332,33 @@ __device__ __forceinline__ bool index_pays(uint32_t U, uint32_t first, uint32_t 
 // list probe (see SKY_REFINE_FAST_MIN_DP for the single-set default); PG:
 // groups of 32 p's in the CTA's p-tile -- 4 (one 128-point tile, the q-tile
 // size) or 8 (two consecutive tiles: every streamed q-tile and every stage
-// hand-off then serves twice the p's).
-template <int DP, int S = kRingStages, bool FAST = (DP >= SKY_REFINE_FAST_MIN_DP), int PG = kTQ / 32>
+// hand-off then serves twice the p's); MASK: the mask probe (padded
+// dimension 16; the q-tiles' threshold masks are streamed with their codes).
+template <int DP, int S = kRingStages, bool FAST = (DP >= SKY_REFINE_FAST_MIN_DP), int PG = kTQ / 32,
+          bool MASK = false>
 struct RefineSmem {
     static_assert(PG == kTQ / 32 || PG == 2 * (kTQ / 32), "one or two tiles of p's");
+    static_assert(!MASK || DP >= 12, "the mask probe is built for padded dimensions 12 and 16");
     static constexpr int DW = DP / 4;
     static constexpr int kStages = S;
     static constexpr bool kFast = FAST;
+    static constexpr bool kMask = MASK;
     static constexpr int kGroups = PG;               // groups of 32 p's
     static constexpr int kTP = PG * 32;              // p's of the CTA
     static constexpr int kTiles = kTP / kTQ;         // 128-point tiles of p's
-    static constexpr bool kPxSmem = SKY_REFINE_PX_SMEM && (kTiles == 1 || SKY_REFINE_PX_SMEM_WIDE);
+    static constexpr bool kPxSmem = SKY_REFINE_PX_SMEM && (kTiles == 1 || SKY_REFINE_PX_SMEM_WIDE) && !MASK;
     static constexpr int FW = (DP + 7) / 8;        // fast-code words
     // list entry words (vector loads): fast codes, or the 7-bit codes
     static constexpr int DWL = kFast ? FW : (DW == 3 ? 4 : DW);
     // bulk-copy destinations: 16-byte aligned whatever the ring depth
     alignas(16) uint32_t qC[S][kTQ * DW];  // streamed q-tiles (codes)
+    // streamed q-tiles' threshold masks: sub-tile q, dimension k, level l at
+    // word q * 128 + k * 8 + l; each sub-tile's table 256-byte aligned (its
+    // addresses are formed by replacing the low byte, see the mask probe)
+    alignas(MASK ? 256 : 4) uint32_t qT[MASK ? S : 1][MASK ? kMaskWords : 1];
+    // own p's byte offsets into a sub-tile table half: byte k % 4 of word
+    // k / 4 = (k % 8) * 32 + 4 * (3-bit code of dimension k)
+    alignas(16) uint32_t pO[MASK ? kTP : 1][4];
     static constexpr int kWindows = SKY_REFINE_WINDOWS;
     alignas(16) float pX[kPxSmem ? kTP * DP : 4];   // own p coordinates (exact tests)
     uint32_t pP[kTP * DW];               // own p codes | 0x80 per byte
@@ -419,7 +459,8 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                                              const uint32_t* __restrict__ SUPMIN, uint32_t m, uint32_t ptile,
                                              DevResult* res, uint8_t* keep, int32_t* wit = nullptr,
                                              const uint32_t* __restrict__ MLO = nullptr,
-                                             const uint32_t* __restrict__ MHI = nullptr)
+                                             const uint32_t* __restrict__ MHI = nullptr,
+                                             const uint32_t* __restrict__ TM = nullptr)
 {
     constexpr int DW = DP / 4;
     constexpr int NG = SM::kGroups;   // groups of 32 p's
@@ -429,6 +470,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
     constexpr int S = SM::kStages;
     constexpr uint32_t kSparseLive = SparseLive<DP>::value;
     constexpr uint32_t kBytesC = kTQ * DW * sizeof(uint32_t);
+    constexpr uint32_t kBytesT = SM::kMask ? kMaskWords * sizeof(uint32_t) : 0u;   // the tile's threshold masks
     const uint32_t T = (m + kTQ - 1) / kTQ;
     uint32_t* err = &res->err;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -453,6 +495,20 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
 #pragma unroll
                 for (int f = 0; f < SM::FW; ++f) sm.pF[pi * SM::FW + f] = fast_word<DW>(pc, f) | kHighNib;
             }
+            if constexpr (SM::kMask) {
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    uint32_t o = 0;
+                    if (w < DW) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint32_t l = (pc[w < DW ? w : 0] >> (8 * j + 4)) & 7u;
+                            o |= ((uint32_t)(((4 * w + j) % 8) * 32) + 4u * l) << (8 * j);
+                        }
+                    }
+                    sm.pO[pi][w] = o;
+                }
+            }
             if constexpr (SM::kPxSmem) {
 #pragma unroll
                 for (int k = 0; k < DP; k += 4)
@@ -474,6 +530,14 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
         sm.live = (m - pbase) < (uint32_t)kTP ? (m - (uint32_t)pbase) : (uint32_t)kTP;
         sm.failed = 0;
         sm.sparse = 0;
+        if constexpr (SM::kMask) {
+            // the mask probe forms table addresses by replacing their low byte
+            if (smem_addr(&sm.qT[0][0]) & 255u) {
+                atomicOr(err, SKY_DEV_ERR_LAYOUT);
+                sm.failed = 1u;
+                sm.live = 0u;
+            }
+        }
     }
     __syncthreads();
 
@@ -588,8 +652,9 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
             if (lane == 0 && bmask) {
                 sm.stage_tile[s] = ot;
                 sm.stage_mask[s] = bmask;
-                mbar_arrive_expect_tx(&sm.full[s], kBytesC);
+                mbar_arrive_expect_tx(&sm.full[s], kBytesC + kBytesT);
                 bulk_g2s(sm.qC[s], C + (int64_t)ot * kTQ * DW, kBytesC, &sm.full[s]);
+                if constexpr (SM::kMask) bulk_g2s(sm.qT[s], TM + (int64_t)ot * kMaskWords, kBytesT, &sm.full[s]);
             }
             __syncwarp();
             if (bmask) { ++issued; ++since; }
@@ -730,8 +795,10 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                     const uint32_t tt = t0 + b;
                     sm.stage_tile[s] = tt;
                     sm.stage_mask[s] = bmask;
-                    mbar_arrive_expect_tx(&sm.full[s], kBytesC);
+                    mbar_arrive_expect_tx(&sm.full[s], kBytesC + kBytesT);
                     bulk_g2s(sm.qC[s], C + (int64_t)tt * kTQ * DW, kBytesC, &sm.full[s]);
+                    if constexpr (SM::kMask)
+                        bulk_g2s(sm.qT[s], TM + (int64_t)tt * kMaskWords, kBytesT, &sm.full[s]);
                 }
                 __syncwarp();
                 ++issued;
@@ -857,6 +924,72 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                             }
                         }
                     };
+                    if constexpr (SM::kMask) {
+                        if (__popc(mask) >= SKY_REFINE_MASK_MIN_LIST) {
+                            // mask probe: this lane's p (pg, if listed) against
+                            // the 32 q's of the sub-tile -- the AND of the
+                            // sub-tile's masks at p's 3-bit levels is the set
+                            // of q's whose 3-bit codes are <= p's everywhere
+                            uint32_t mq = ((mask >> lane) & 1u) ? 0xffffffffu : 0u;
+                            const uint4 po = *reinterpret_cast<const uint4*>(&sm.pO[pg][0]);
+                            const uint32_t pw[4] = {po.x, po.y, po.z, po.w};
+                            const uint32_t tb = smem_addr(&sm.qT[s][(qi >> 5) * 128]);   // 256-byte aligned
+                            uint32_t v[DP];
+#pragma unroll
+                            for (int kd = 0; kd < DP; ++kd) {
+                                // the table half's address with its low byte
+                                // replaced by p's offset for dimension kd
+                                const uint32_t a = __byte_perm(tb + (kd < 8 ? 0u : 256u), pw[kd >> 2],
+                                                               0x3214u + (uint32_t)(kd & 3));
+                                asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v[kd]) : "r"(a));
+                            }
+#pragma unroll
+                            for (int kd = 0; kd < DP; ++kd) mq &= v[kd];
+                            if (mq) {   // rare: the 7-bit and exact tests of each passing q
+                                uint32_t pc[DW];
+#pragma unroll
+                                for (int w = 0; w < DW; ++w) pc[w] = sm.pP[pg * DW + w];
+                                while (mq) {
+                                    const int qj = (qi & ~31) + __ffs(mq) - 1;
+                                    mq &= mq - 1u;
+                                    uint32_t D[DW];
+                                    uint32_t a = kHigh;
+#pragma unroll
+                                    for (int w = 0; w < DW; ++w) {
+                                        D[w] = pc[w] - sm.qC[s][qj * DW + w];
+                                        a &= D[w];
+                                    }
+                                    if (a != kHigh) continue;
+                                    ++hits;
+                                    uint32_t eq = 0;
+#pragma unroll
+                                    for (int w = 0; w < DW; ++w) eq |= has_zero_byte(D[w] ^ kHigh);
+                                    bool dom = true;
+                                    if (eq) {
+                                        ++exact;
+                                        const float* qx = X + ((int64_t)tt * kTQ + qj) * DP;
+                                        const float* px = SM::kPxSmem ? &sm.pX[pg * DP] : X + (pbase + pg) * DP;
+                                        bool le = true, lt = false;
+#pragma unroll
+                                        for (int kk = 0; kk < DP; kk += 4) {
+                                            const float4 u = __ldg(reinterpret_cast<const float4*>(qx + kk));
+                                            const float4 w4 = *reinterpret_cast<const float4*>(px + kk);
+                                            le &= (u.x <= w4.x) & (u.y <= w4.y) & (u.z <= w4.z) & (u.w <= w4.w);
+                                            lt |= (u.x < w4.x) | (u.y < w4.y) | (u.z < w4.z) | (u.w < w4.w);
+                                        }
+                                        dom = le && lt;
+                                    }
+                                    if (dom) {
+                                        const uint32_t bit = 1u << lane;
+                                        if (atomicAnd(&sm.livemask[g], ~bit) & bit) atomicSub(&sm.live, 1u);
+                                        if constexpr (WIT) wit[ids[pbase + pg]] = ids[(int64_t)tt * kTQ + qj];
+                                        break;
+                                    }
+                                }
+                            }
+                            return;
+                        }
+                    }
                     if constexpr (kListProbe) {
                         if (mask) {
                             // the listed p's of the group, in lane order, into
