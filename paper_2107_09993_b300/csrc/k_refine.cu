@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kTQ) k_gather(const float* __restrict__ pts, i
     // mask probe): word k * 8 + l = the lanes whose 3-bit code (the top three
     // bits of the 7-bit code) in dimension k is <= l; padding points (code
     // 127) pass only level 7, which every point passes
-    if constexpr (DP >= 12) {
+    if constexpr (DP >= 8) {
         if (tmask != nullptr) {
             uint32_t v[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
@@ -337,9 +337,13 @@ __global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict_
 #ifndef SKY_REFINE_MINB_16
 #define SKY_REFINE_MINB_16 6
 #endif
-// The mask probe (see sky_refine.cuh) from this padded dimension up (it is
-// built for 12 and 16; larger: off) and its CTAs per SM (72 / 64 registers;
-// five CTAs at d = 12 measured 10^7 x 12 independent 17.3 -> 18.8 ms)
+// The mask probe (see sky_refine.cuh) from this padded dimension up (built
+// for 8, 12 and 16; larger: off) and its CTAs per SM (72 / 64 / 48
+// registers; five CTAs at d = 12 measured 10^7 x 12 independent 17.3 ->
+// 18.8 ms). At padded dimension 8 it did not pay (ms, list -> mask probe
+// with 8 / 7 CTAs per SM): 10^6 x 8 anti-correlated 1.20 -> 1.21 / 1.17,
+// independent 0.70 -> 0.72 / 0.74, correlated 0.29 -> 0.36, 2*10^6 x 8
+// anti-correlated 2.29 -> 2.00 / 2.07; hence from 12.
 #ifndef SKY_REFINE_MASK_MIN_DP
 #define SKY_REFINE_MASK_MIN_DP 12
 #endif
@@ -349,14 +353,17 @@ __global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict_
 #ifndef SKY_REFINE_MINB_12_MASK
 #define SKY_REFINE_MINB_12_MASK 6
 #endif
+#ifndef SKY_REFINE_MINB_8_MASK
+#define SKY_REFINE_MINB_8_MASK 8
+#endif
 template <int DP>
 struct RefineMask {
-    static constexpr bool value = DP >= 12 && DP >= SKY_REFINE_MASK_MIN_DP;
+    static constexpr bool value = DP >= 8 && DP >= SKY_REFINE_MASK_MIN_DP;
 };
 template <int DP>
 struct RefineMinBlocks {
     static constexpr int value = DP == 4 ? SKY_REFINE_MINB_4
-                               : DP == 8 ? SKY_REFINE_MINB_8
+                               : DP == 8 ? (RefineMask<DP>::value ? SKY_REFINE_MINB_8_MASK : SKY_REFINE_MINB_8)
                                : DP == 12 ? (RefineMask<DP>::value ? SKY_REFINE_MINB_12_MASK : SKY_REFINE_MINB_12)
                                : RefineMask<DP>::value ? SKY_REFINE_MINB_16_MASK : SKY_REFINE_MINB_16;
 };

@@ -338,7 +338,7 @@ template <int DP, int S = kRingStages, bool FAST = (DP >= SKY_REFINE_FAST_MIN_DP
           bool MASK = false>
 struct RefineSmem {
     static_assert(PG == kTQ / 32 || PG == 2 * (kTQ / 32), "one or two tiles of p's");
-    static_assert(!MASK || DP >= 12, "the mask probe is built for padded dimensions 12 and 16");
+    static_assert(!MASK || DP >= 8, "the mask probe is built for padded dimensions 8 to 16");
     static constexpr int DW = DP / 4;
     static constexpr int kStages = S;
     static constexpr bool kFast = FAST;
