@@ -348,7 +348,21 @@ __global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict_
 #define SKY_REFINE_MASK_MIN_DP 12
 #endif
 #ifndef SKY_REFINE_MINB_16_MASK
-#define SKY_REFINE_MINB_16_MASK 5
+#define SKY_REFINE_MINB_16_MASK 6
+#endif
+// masks only in the stages (see RefineSmem) from this padded dimension up,
+// with this ring depth. Measured on B300 (ms, one call; masks and codes in
+// 6 stages, 5 CTAs per SM -> masks only in 8 stages, 6 CTAs per SM): 10^7 x
+// 16 anti-correlated 83.7 -> 75.9, 2*10^6 x 16 independent 12.7 -> 11.5,
+// anti-correlated 11.8 -> 12.0, correlated 10.7 -> 13.0 (many 3-bit passes,
+// each now reading its q's codes from global memory); at d = 12 (masks
+// only, 8 stages, 7 CTAs) 10^7 x 12 independent 17.2 -> 17.8, hence 16;
+// bench step 101.2 -> 93.2 ms.
+#ifndef SKY_REFINE_MASK_ONLY_MIN_DP
+#define SKY_REFINE_MASK_ONLY_MIN_DP 16
+#endif
+#ifndef SKY_REFINE_MASK_ONLY_STAGES
+#define SKY_REFINE_MASK_ONLY_STAGES 8
 #endif
 #ifndef SKY_REFINE_MINB_12_MASK
 #define SKY_REFINE_MINB_12_MASK 6
@@ -359,6 +373,10 @@ __global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict_
 template <int DP>
 struct RefineMask {
     static constexpr bool value = DP >= 8 && DP >= SKY_REFINE_MASK_MIN_DP;
+    // RefineSmem's MASK: 0 off, 1 masks and codes staged, 2 masks only
+    static constexpr int mode = !value ? 0 : (DP >= SKY_REFINE_MASK_ONLY_MIN_DP && SKY_REFINE_MASK_MIN_LIST <= 1) ? 2 : 1;
+    static constexpr int stages = mode == 2 ? SKY_REFINE_MASK_ONLY_STAGES : mode == 1 ? SKY_REFINE_MASK_STAGES
+                                                                                     : kRingStages;
 };
 template <int DP>
 struct RefineMinBlocks {
@@ -391,8 +409,7 @@ struct RefineGroups {
     static constexpr int value = DP >= SKY_REFINE_WIDE_MIN_DP ? 2 * (kTQ / 32) : kTQ / 32;
 };
 template <int DP, int PG>
-using SetSmem = RefineSmem<DP, RefineMask<DP>::value ? SKY_REFINE_MASK_STAGES : kRingStages,
-                           (DP >= SKY_REFINE_FAST_MIN_DP), PG, RefineMask<DP>::value>;
+using SetSmem = RefineSmem<DP, RefineMask<DP>::stages, (DP >= SKY_REFINE_FAST_MIN_DP), PG, RefineMask<DP>::mode>;
 
 // WIT: witness mode (see refine_ptile); `wit` is unused otherwise. PG:
 // groups of 32 p's per CTA (4 or 8).

@@ -332,33 +332,38 @@ __device__ __forceinline__ bool index_pays(uint32_t U, uint32_t first, uint32_t 
 // list probe (see SKY_REFINE_FAST_MIN_DP for the single-set default); PG:
 // groups of 32 p's in the CTA's p-tile -- 4 (one 128-point tile, the q-tile
 // size) or 8 (two consecutive tiles: every streamed q-tile and every stage
-// hand-off then serves twice the p's); MASK: the mask probe (padded
-// dimension 16; the q-tiles' threshold masks are streamed with their codes).
+// hand-off then serves twice the p's); MASK: the mask probe -- 0 off, 1 the
+// q-tiles' threshold masks streamed with their codes, 2 the masks only (with
+// the mask probe taking every scan, SKY_REFINE_MASK_MIN_LIST <= 1, the
+// staged codes serve only the rare 3-bit passes, which then read their q's
+// 7-bit codes from global memory).
 template <int DP, int S = kRingStages, bool FAST = (DP >= SKY_REFINE_FAST_MIN_DP), int PG = kTQ / 32,
-          bool MASK = false>
+          int MASK = 0>
 struct RefineSmem {
     static_assert(PG == kTQ / 32 || PG == 2 * (kTQ / 32), "one or two tiles of p's");
-    static_assert(!MASK || DP >= 8, "the mask probe is built for padded dimensions 8 to 16");
+    static_assert(MASK == 0 || DP >= 8, "the mask probe is built for padded dimensions 8 to 16");
+    static_assert(MASK != 2 || SKY_REFINE_MASK_MIN_LIST <= 1, "masks only: the list probe never runs");
     static constexpr int DW = DP / 4;
     static constexpr int kStages = S;
     static constexpr bool kFast = FAST;
-    static constexpr bool kMask = MASK;
+    static constexpr bool kMask = MASK != 0;
+    static constexpr bool kMaskOnly = MASK == 2;
     static constexpr int kGroups = PG;               // groups of 32 p's
     static constexpr int kTP = PG * 32;              // p's of the CTA
     static constexpr int kTiles = kTP / kTQ;         // 128-point tiles of p's
-    static constexpr bool kPxSmem = SKY_REFINE_PX_SMEM && (kTiles == 1 || SKY_REFINE_PX_SMEM_WIDE) && !MASK;
+    static constexpr bool kPxSmem = SKY_REFINE_PX_SMEM && (kTiles == 1 || SKY_REFINE_PX_SMEM_WIDE) && MASK == 0;
     static constexpr int FW = (DP + 7) / 8;        // fast-code words
     // list entry words (vector loads): fast codes, or the 7-bit codes
     static constexpr int DWL = kFast ? FW : (DW == 3 ? 4 : DW);
     // bulk-copy destinations: 16-byte aligned whatever the ring depth
-    alignas(16) uint32_t qC[S][kTQ * DW];  // streamed q-tiles (codes)
+    alignas(16) uint32_t qC[kMaskOnly ? 1 : S][kMaskOnly ? 4 : kTQ * DW];  // streamed q-tiles (codes)
     // streamed q-tiles' threshold masks: sub-tile q, dimension k, level l at
     // word q * 128 + k * 8 + l; each sub-tile's table 256-byte aligned (its
     // addresses are formed by replacing the low byte, see the mask probe)
-    alignas(MASK ? 256 : 4) uint32_t qT[MASK ? S : 1][MASK ? kMaskWords : 1];
+    alignas(kMask ? 256 : 4) uint32_t qT[kMask ? S : 1][kMask ? kMaskWords : 1];
     // own p's byte offsets into a sub-tile table half: byte k % 4 of word
     // k / 4 = (k % 8) * 32 + 4 * (3-bit code of dimension k)
-    alignas(16) uint32_t pO[MASK ? kTP : 1][4];
+    alignas(16) uint32_t pO[kMask ? kTP : 1][4];
     static constexpr int kWindows = SKY_REFINE_WINDOWS;
     alignas(16) float pX[kPxSmem ? kTP * DP : 4];   // own p coordinates (exact tests)
     uint32_t pP[kTP * DW];               // own p codes | 0x80 per byte
@@ -469,7 +474,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
     constexpr int kTP = SM::kTP;
     constexpr int S = SM::kStages;
     constexpr uint32_t kSparseLive = SparseLive<DP>::value;
-    constexpr uint32_t kBytesC = kTQ * DW * sizeof(uint32_t);
+    constexpr uint32_t kBytesC = SM::kMaskOnly ? 0u : kTQ * DW * sizeof(uint32_t);   // the tile's codes
     constexpr uint32_t kBytesT = SM::kMask ? kMaskWords * sizeof(uint32_t) : 0u;   // the tile's threshold masks
     const uint32_t T = (m + kTQ - 1) / kTQ;
     uint32_t* err = &res->err;
@@ -653,7 +658,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                 sm.stage_tile[s] = ot;
                 sm.stage_mask[s] = bmask;
                 mbar_arrive_expect_tx(&sm.full[s], kBytesC + kBytesT);
-                bulk_g2s(sm.qC[s], C + (int64_t)ot * kTQ * DW, kBytesC, &sm.full[s]);
+                if constexpr (!SM::kMaskOnly) bulk_g2s(sm.qC[s], C + (int64_t)ot * kTQ * DW, kBytesC, &sm.full[s]);
                 if constexpr (SM::kMask) bulk_g2s(sm.qT[s], TM + (int64_t)ot * kMaskWords, kBytesT, &sm.full[s]);
             }
             __syncwarp();
@@ -796,7 +801,8 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                     sm.stage_tile[s] = tt;
                     sm.stage_mask[s] = bmask;
                     mbar_arrive_expect_tx(&sm.full[s], kBytesC + kBytesT);
-                    bulk_g2s(sm.qC[s], C + (int64_t)tt * kTQ * DW, kBytesC, &sm.full[s]);
+                    if constexpr (!SM::kMaskOnly)
+                        bulk_g2s(sm.qC[s], C + (int64_t)tt * kTQ * DW, kBytesC, &sm.full[s]);
                     if constexpr (SM::kMask)
                         bulk_g2s(sm.qT[s], TM + (int64_t)tt * kMaskWords, kBytesT, &sm.full[s]);
                 }
@@ -871,11 +877,13 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                     qi = q * 32 + lane;
 #pragma unroll
                     for (int w = 0; w < DW; ++w) Mw[w] = sm.stage_sub[s][q][w];
+                    if constexpr (!SM::kMaskOnly) {
 #pragma unroll
-                    for (int w = 0; w < DW; ++w) Q[w] = sm.qC[s][qi * DW + w];
-                    if constexpr (kFast) {
+                        for (int w = 0; w < DW; ++w) Q[w] = sm.qC[s][qi * DW + w];
+                        if constexpr (kFast) {
 #pragma unroll
-                        for (int f = 0; f < FW; ++f) QF[f] = fast_word<DW>(Q, f);
+                            for (int f = 0; f < FW; ++f) QF[f] = fast_word<DW>(Q, f);
+                        }
                     }
                 };
                 // sub-tile (loaded) against the live p's of group g
@@ -956,7 +964,9 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                                     uint32_t a = kHigh;
 #pragma unroll
                                     for (int w = 0; w < DW; ++w) {
-                                        D[w] = pc[w] - sm.qC[s][qj * DW + w];
+                                        const uint32_t qw = SM::kMaskOnly ? __ldg(C + ((int64_t)tt * kTQ + qj) * DW + w)
+                                                                          : sm.qC[s][SM::kMaskOnly ? 0 : qj * DW + w];
+                                        D[w] = pc[w] - qw;
                                         a &= D[w];
                                     }
                                     if (a != kHigh) continue;
@@ -990,7 +1000,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                             return;
                         }
                     }
-                    if constexpr (kListProbe) {
+                    if constexpr (kListProbe && !SM::kMaskOnly) {
                         if (mask) {
                             // the listed p's of the group, in lane order, into
                             // this warp's list
@@ -1063,7 +1073,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                             }
                             __syncwarp();   // the list is rewritten by the next group
                         }
-                    } else {
+                    } else if constexpr (!SM::kMaskOnly) {
                         while (mask) {
                             const int pa = g * 32 + __ffs(mask) - 1;
                             mask &= mask - 1;
