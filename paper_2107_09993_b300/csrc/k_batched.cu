@@ -280,6 +280,25 @@ __global__ void __launch_bounds__(kTQ) kb_gather(const QueryPlan* __restrict__ q
         }
     }
     q.ids[j] = valid ? (int32_t)row : -1;
+    // threshold masks of this warp's 32-point sub-tile for the mask probe
+    // (dp >= 12): word k * 8 + l = the lanes whose 3-bit code in dimension k
+    // is <= l (dimensions past dp: code 0; padding points: code 127)
+    if (q.tmask != nullptr) {
+        uint32_t v[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const uint32_t c3 = (code[k >> 2] >> (8 * (k & 3) + 4)) & 7u;
+#pragma unroll
+            for (int l = 0; l < 8; ++l) {
+                const uint32_t b = l == 7 ? kFull : __ballot_sync(kFull, c3 <= (uint32_t)l);
+                const int e = k * 8 + l;
+                if (lane == (e & 31)) v[e >> 5] = b;
+            }
+        }
+        uint32_t* o = q.tmask + ((int64_t)t * (kTQ / 32) + warp) * 128;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) o[r * 32 + lane] = v[r];
+    }
     // layer-1 cell index of the query (zeroed with the query's counters): per
     // cell (bit k: code k >= 64), ~first and last + 1 of the tiles holding
     // one of its points; one update per distinct cell of a warp
@@ -382,13 +401,24 @@ constexpr bool kBatchSparse = SKY_BATCH_SPARSE != 0;
 // dimension class at launch time, e.g. by the autotuner).
 // d_class (a batch planned on the device): the class's first item and item
 // count are d_class[cls] and d_class[4 + cls] instead of `items` / `nitems`.
+// The mask probe of the single-set refinement in the batched kernel: from
+// padded dimension 12 (masks and codes staged at 12, masks only at 16; the
+// queries' threshold masks are written by kb_gather)
+#ifndef SKY_BATCH_MASK_MIN_DP
+#define SKY_BATCH_MASK_MIN_DP 12
+#endif
+template <int DP>
+struct BatchMask {
+    static constexpr int value = (DP < 12 || DP < SKY_BATCH_MASK_MIN_DP) ? 0 : DP == 16 ? 2 : 1;
+};
+
 template <int DP, int S, bool FAST>
 __global__ void __launch_bounds__(kTQ + 32, BatchMinBlocks<DP>::value) kb_refine(const QueryPlan* __restrict__ qps,
                                                       const int2* __restrict__ items, int nitems, uint32_t* claim,
                                                       const int* __restrict__ d_class, int cls)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    using SM = refine::RefineSmem<DP, S, FAST>;
+    extern __shared__ __align__(256) unsigned char smem_raw[];   // the mask probe's tables are 256-byte aligned
+    using SM = refine::RefineSmem<DP, S, FAST, kTQ / 32, BatchMask<DP>::value>;
     SM& sm = *reinterpret_cast<SM*>(smem_raw);
     __shared__ int s_item;
     if (d_class) {
@@ -407,7 +437,7 @@ __global__ void __launch_bounds__(kTQ + 32, BatchMinBlocks<DP>::value) kb_refine
         if ((uint32_t)w.y < (m + kTQ - 1) / kTQ)
             refine::refine_ptile<DP, kBatchSparse, false, SM>(sm, q.X, q.C, q.ids, q.sub, q.tend, q.supmin, m,
                                                               (uint32_t)w.y, q.res, q.keep, nullptr, q.cidx,
-                                                              q.cidx + (1u << q.d));
+                                                              q.cidx + (1u << q.d), q.tmask);
     }
 }
 
@@ -514,7 +544,7 @@ cudaError_t launch_kb_refine_v(const QueryPlan* qps, const int2* items, int nite
                                const int* d_class, int cls, cudaStream_t s)
 {
     auto* kern = batched::kb_refine<DP, S, FAST>;
-    const int smem = (int)sizeof(refine::RefineSmem<DP, S, FAST>);
+    const int smem = (int)sizeof(refine::RefineSmem<DP, S, FAST, refine::kTQ / 32, batched::BatchMask<DP>::value>);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -533,10 +563,24 @@ cudaError_t launch_kb_refine_v(const QueryPlan* qps, const int2* items, int nite
 
 // The refinement variant of one padded-dimension class: ring depth 4 or 8
 // (other values: 8), fast codes on or off.
+// Ring depth of the classes with the mask probe (0: the tuned or default
+// depth, 4 or 8); their stages hold masks as well, so a shallow ring keeps
+// the persistent CTAs resident. Measured on B300 (4,096-query launch, ms):
+// list probe 519.6; mask probe with the tuned depths (8 for d = 9-12)
+// 477.0, depth 6 447.4, depth 4 430.4. With a fixed depth the autotuner's
+// depth knob applies to the classes below padded dimension 12 only.
+#ifndef SKY_BATCH_MASK_STAGES
+#define SKY_BATCH_MASK_STAGES 4
+#endif
 template <int DP>
 cudaError_t launch_kb_refine(const QueryPlan* qps, const int2* items, int nitems, uint32_t* claim, int ctas_per_sm,
                              int stages, bool fast, const int* d_class, int cls, cudaStream_t s)
 {
+    if constexpr (batched::BatchMask<DP>::value != 0 && SKY_BATCH_MASK_STAGES != 0) {
+        static_assert(SKY_BATCH_MASK_STAGES >= 2 && SKY_BATCH_MASK_STAGES <= 12, "a ring of 2 to 12 stages");
+        return launch_kb_refine_v<DP, SKY_BATCH_MASK_STAGES, (DP >= SKY_REFINE_FAST_MIN_DP)>(
+            qps, items, nitems, claim, ctas_per_sm, d_class, cls, s);
+    }
     if (stages == 4)
         return fast ? launch_kb_refine_v<DP, 4, true>(qps, items, nitems, claim, ctas_per_sm, d_class, cls, s)
                     : launch_kb_refine_v<DP, 4, false>(qps, items, nitems, claim, ctas_per_sm, d_class, cls, s);

@@ -79,6 +79,7 @@ __host__ __device__ inline size_t query_bytes(int64_t n_in, int d, int dp, int64
     at += a256(4 * tl);
     at += a256(4 * ((tl + 31) / 32) * (size_t)(dp / 4));
     at += a256(4 * n);                    // stage
+    if (dp >= 12) at += a256(16 * npad);  // threshold masks (mask probe)
     return at;
 }
 
@@ -109,7 +110,7 @@ __host__ inline DevLayout dev_layout(int nq, int n_cols, int64_t max_total_rows)
     const int cols = n_cols < kMaxDim ? n_cols : kMaxDim;
     const int dpmax = pad4(cols > 0 ? cols : 1);
     const size_t fixed = query_bytes(0, cols > 0 ? cols : 1, dpmax, kMaxWords, 1, 1, nullptr) + 24 * 256;
-    const size_t per_row = 35 + 5 * (size_t)dpmax + 1;
+    const size_t per_row = 35 + 5 * (size_t)dpmax + 1 + (dpmax >= 12 ? 16 : 0);
     at += fixed * (size_t)nqq + per_row * (size_t)(max_total_rows > 0 ? max_total_rows : 0);
     L.total = at;
     return L;
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(kPT) kb_plan(const sky_query* __restrict__ Q, 
         p.tend = reinterpret_cast<uint32_t*>(take(4 * tl));
         p.supmin = reinterpret_cast<uint32_t*>(take(4 * ((tl + 31) / 32) * (size_t)(p.dp / 4)));
         p.stage = reinterpret_cast<int32_t*>(take(4 * n));
+        p.tmask = p.dp >= 12 ? reinterpret_cast<uint32_t*>(take(16 * npad)) : nullptr;
     }
     __syncthreads();
     // 4. refinement items: class-major, larger queries first (buckets of

@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict_
 #define SKY_REFINE_MASK_ONLY_MIN_DP 16
 #endif
 #ifndef SKY_REFINE_MASK_ONLY_STAGES
-#define SKY_REFINE_MASK_ONLY_STAGES 8
+#define SKY_REFINE_MASK_ONLY_STAGES 10
 #endif
 #ifndef SKY_REFINE_MINB_12_MASK
 #define SKY_REFINE_MINB_12_MASK 6

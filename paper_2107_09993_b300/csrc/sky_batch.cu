@@ -35,7 +35,7 @@ size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct QOff {   // byte offsets of one query's arrays inside the workspace
     size_t res, occ, lb_a, lb_b, keep, dt, cidx;                             // zero region
-    size_t keys, pre, skey, sidx, key2, val2, hist, X, C, ids, sub, tend, supmin, stage;   // other
+    size_t keys, pre, skey, sidx, key2, val2, hist, X, C, ids, sub, tend, supmin, stage, tmask;   // other
 };
 
 }  // namespace
@@ -222,6 +222,7 @@ sky_status sky_batch_create(const float* d_table, int64_t n_rows, int32_t n_cols
         o.tend = at;  at = a256(at + 4 * (size_t)std::max<int64_t>(p.tiles, 1));
         o.supmin = at; at = a256(at + 4 * (size_t)((std::max<int64_t>(p.tiles, 1) + 31) / 32) * (size_t)(p.dp / 4));
         o.stage = at; at = a256(at + 4 * n);
+        o.tmask = at; at = a256(at + (p.dp >= 12 ? 16 * npad : 0));   // threshold masks (mask probe)
     }
     b->total = at;
     *ws_bytes = at;
@@ -278,6 +279,7 @@ sky_status sky_batch_bind(sky_batch* b, void* d_ws, size_t ws_bytes, int32_t* d_
         p.cidx = reinterpret_cast<uint32_t*>(ws + o.cidx);
         p.keep = reinterpret_cast<uint8_t*>(ws + o.keep);
         p.stage = reinterpret_cast<int32_t*>(ws + o.stage);
+        p.tmask = p.dp >= 12 ? reinterpret_cast<uint32_t*>(ws + o.tmask) : nullptr;
         p.res = reinterpret_cast<DevResult*>(ws + o.res);
     }
     std::vector<char> hdr(b->hdr_bytes, 0);

@@ -124,6 +124,7 @@ struct QueryPlan {
     uint32_t* cidx;           // [2][2^d] layer-1 cell index: ~first tile, last tile + 1 (0: no point)
     uint8_t* keep;
     int32_t* stage;
+    uint32_t* tmask;          // [tiles][4][128] threshold masks (dp >= 12: the mask probe); NULL below
     DevResult* res;
 };
 

@@ -5,7 +5,8 @@ The device planner lays out, per query, the arrays the batched kernels use
 (result block, bitmap, look-back states, keep bytes, digit totals, layer-1
 cell index of 2 * 2^d words, keys,
 prefix-OR, four sort arrays, histograms, coordinates, codes, ids, sub-tile
-minima, tile ends, super-tile minima, stage), each rounded up to 256 bytes,
+minima, tile ends, super-tile minima, stage, and from 12 padded dimensions
+the refinement's threshold masks of 16 bytes a padded row), each rounded up to 256 bytes,
 after a header (plans, chunk and tile prefixes, work items, class table,
 offsets, counters). It refuses a batch whose arrays do not fit. The bound must
 therefore cover every batch whose valid queries hold at most max_total_rows
@@ -18,7 +19,7 @@ import pytest
 
 A = 256
 SCAN_TILE, REFINE_TILE = 2048, 128
-PLAN_BYTES = 392          # sizeof(QueryPlan)
+PLAN_BYTES = 400          # sizeof(QueryPlan)
 RESULT_BYTES = 72         # sizeof(DevResult)
 
 
@@ -49,7 +50,7 @@ def query_bytes(n, d):
     sizes = [RESULT_BYTES, 4 * words, 8 * ch, 8 * ch, nn + 16, 4 * 256 * 4, 8 << d,
              8 * nn, 4 * words, 4 * nn, 4 * nn, 4 * nn, 4 * nn, 4 * 256 * ch,
              4 * npad * dp, npad * dp, 4 * npad, 4 * tl * 5 * (dp // 4) + 16, 4 * tl,
-             4 * math.ceil(tl / 32) * (dp // 4), 4 * nn]
+             4 * math.ceil(tl / 32) * (dp // 4), 4 * nn, 16 * npad if dp >= 12 else 0]
     return sum(a256(s) for s in sizes)
 
 
