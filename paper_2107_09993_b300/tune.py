@@ -13,6 +13,9 @@ result:
     128 points),
   - the pair test of the list probe (7-bit codes, or 3-bit fast codes first),
   - persistent CTAs per SM (the work split of the (query, p-tile) items);
+  the classes of 9-16 attributes test pairs by threshold masks with a fixed
+  4-stage ring (the library's mask probe), so for them only the CTAs per SM
+  remain a knob;
 * whether the class kernels run one after another or as parallel branches
   of the graph (their tails overlap).
 
@@ -41,6 +44,7 @@ MAX_AUTO_LAYER = 8  # the automatic layer never exceeds 8 (256 columns per dimen
 CTAS = (0, 2, 4)     # persistent CTAs per SM candidates (0: as many as fit)
 STAGES = (8, 4)
 CODES = (1, 2)       # 1: 7-bit codes, 2: 3-bit fast codes first
+MASK_CLASSES = (2, 3)  # classes whose refinement uses the mask probe (depth and pair test fixed)
 
 
 def auto_log2g(n: int, d: int) -> int:
@@ -156,8 +160,9 @@ def tune(table, queries, sample: int = 512, per_bucket: int = 8, repeats: int = 
         if len(sel) == 0:
             continue
         res = []
-        for code in CODES:
-            for st in STAGES:
+        fixed = c in MASK_CLASSES
+        for code in ((best["class_code"][c],) if fixed else CODES):
+            for st in ((best["class_stages"][c],) if fixed else STAGES):
                 for ctas in CTAS:
                     k = json.loads(json.dumps(best))
                     k["class_code"][c], k["class_stages"][c], k["class_ctas"][c] = code, st, ctas
