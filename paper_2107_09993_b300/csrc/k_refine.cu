@@ -22,6 +22,7 @@
 // points are never removed by step (c). Unlike the paper's RefineSkyline,
 // which refines each candidate cell alone, tests cross cell boundaries: a
 // point of one candidate cell can dominate a point of another.
+#include <algorithm>
 #include <cstdint>
 
 #include "sky_common.cuh"
@@ -270,27 +271,74 @@ __global__ void __launch_bounds__(256) k_tile_cost(const uint32_t* __restrict__ 
 // maximum cost or more into one bucket in arbitrary order; at 2*10^6 x 16
 // anti-correlated the busiest SM then stayed active 20 % past the average.)
 constexpr int kCostOrderBuckets = 2 * kCostSamples;
+// Split scans from this padded dimension up (0: never). Split parts run
+// neither the sparse tail nor the super-tile test (their windows must be the
+// same sequence in every part), which cost more than the split saved on
+// 10^6 x 8 sets (anti-correlated 1.20 -> 1.30 ms, independent 0.69 ->
+// 0.84 ms with splits from half the span). Only launches of at most
+// SKY_REFINE_SPLIT_MAX_WAVES waves of p-tiles split: with more, the
+// longest-first order already evens out the end (10^7 x 16 anti-correlated:
+// slots 98.7 % busy) and splitting measured 0.5 % slower there.
+#ifndef SKY_REFINE_SPLIT_MIN_DP
+#define SKY_REFINE_SPLIT_MIN_DP 12
+#endif
+#ifndef SKY_REFINE_SPLIT_MAX_WAVES
+#define SKY_REFINE_SPLIT_MAX_WAVES 32
+#endif
 
+// Split scans: a p-tile's scan is one CTA's serial work, and on sets of a
+// few million points the costliest one can span the whole launch. With
+// `slots` resident CTAs, span = (sum of the costs) / slots; a p-tile costing
+// more than span gets K = min(8, ceil(2 cost / span)) order entries (parts),
+// part k taking every K-th window of the scan (the own tiles go to part 0),
+// and the parts merge their kills (refine_ptile). Since K - 1 < 2 cost /
+// span, the extra entries stay below 2 * slots, and the split p-tiles below
+// slots (kSplitExtra, kSplitSlots). nt = 1 only (128-point p-tiles); slots =
+// 0: no split.
 __global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict__ cost, const uint32_t* mcount,
-                                                     uint32_t* order, uint32_t nt)
+                                                     uint32_t* order, uint32_t nt, uint32_t* part,
+                                                     uint32_t* split, uint32_t slots)
 {
     static_assert(kCostOrderBuckets == 2 * 1024, "two buckets per thread of the scan");
     __shared__ uint32_t s_cnt[kCostOrderBuckets];
     __shared__ uint32_t s_warp[32];
+    __shared__ unsigned long long s_total;
+    __shared__ uint32_t s_slot;
     const uint32_t T0 = (*mcount + kTQ - 1) / kTQ;
     const uint32_t T = (T0 + nt - 1) / nt;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // bucket of item t: kCostOrderBuckets - 1 - cost, so that ascending
-    // buckets are descending costs
-    auto bucket = [&](uint32_t t) -> uint32_t {
+    auto item_cost = [&](uint32_t t) -> uint32_t {
         uint32_t c = 0;
         for (uint32_t h = 0; h < nt && t * nt + h < T0; ++h) c += cost[t * nt + h];
+        return c;
+    };
+    // bucket of item t: kCostOrderBuckets - 1 - cost, so that ascending
+    // buckets are descending costs
+    auto bucket = [&](uint32_t c) -> uint32_t {
         return (uint32_t)kCostOrderBuckets - 1u - min(c, (uint32_t)kCostOrderBuckets - 1u);
     };
+    for (int i = tid; i < kSplitSlots * 5; i += blockDim.x) split[i] = 0u;
     s_cnt[2 * tid] = 0u;
     s_cnt[2 * tid + 1] = 0u;
+    if (tid == 0) { s_total = 0ull; s_slot = 0u; }
     __syncthreads();
-    for (uint32_t t = tid; t < T; t += blockDim.x) atomicAdd(&s_cnt[bucket(t)], 1u);
+    unsigned long long mine = 0;
+    if (slots != 0u)
+        for (uint32_t t = tid; t < T; t += blockDim.x) mine += item_cost(t);
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(kFull, mine, o);
+    if (lane == 0) atomicAdd(&s_total, mine);
+    __syncthreads();
+    const unsigned long long total = s_total;
+    // parts of an item: 2 cost * slots vs total (no split for two-tile p-tiles)
+    auto parts = [&](uint32_t c) -> uint32_t {
+        if (nt != 1u || total == 0ull || (unsigned long long)c * slots <= total) return 1u;
+        const unsigned long long k = (2ull * c * slots + total - 1ull) / total;
+        return (uint32_t)min(k, 8ull);
+    };
+    for (uint32_t t = tid; t < T; t += blockDim.x) {
+        const uint32_t c = item_cost(t);
+        atomicAdd(&s_cnt[bucket(c)], parts(c));
+    }
     __syncthreads();
     // exclusive scan of the bucket counts (thread i: buckets 2i and 2i + 1)
     const uint32_t c0 = s_cnt[2 * tid], c1 = s_cnt[2 * tid + 1];
@@ -311,11 +359,21 @@ __global__ void __launch_bounds__(1024) k_cost_order(const uint32_t* __restrict_
     }
     __syncthreads();
     const uint32_t before = (warp ? s_warp[warp - 1] : 0u) + x - (c0 + c1);
+    if (tid == 0) split[kSplitSlots * 5] = s_warp[31];   // order entries
     __syncthreads();   // every thread has read its counts
     s_cnt[2 * tid] = before;
     s_cnt[2 * tid + 1] = before + c0;
     __syncthreads();
-    for (uint32_t t = tid; t < T; t += blockDim.x) order[atomicAdd(&s_cnt[bucket(t)], 1u)] = t;
+    for (uint32_t t = tid; t < T; t += blockDim.x) {
+        const uint32_t c = item_cost(t);
+        const uint32_t k = parts(c);
+        const uint32_t pos = atomicAdd(&s_cnt[bucket(c)], k);
+        const uint32_t slot = k > 1u ? atomicAdd(&s_slot, 1u) : 0u;
+        for (uint32_t j = 0; j < k; ++j) {
+            order[pos + j] = t;
+            part[pos + j] = j | (k << 8) | (slot << 16);
+        }
+    }
 }
 
 // Resident CTAs per SM by padded dimension (the launch bound caps the
@@ -412,7 +470,9 @@ template <int DP, int PG>
 using SetSmem = RefineSmem<DP, RefineMask<DP>::stages, (DP >= SKY_REFINE_FAST_MIN_DP), PG, RefineMask<DP>::mode>;
 
 // WIT: witness mode (see refine_ptile); `wit` is unused otherwise. PG:
-// groups of 32 p's per CTA (4 or 8).
+// groups of 32 p's per CTA (4 or 8). ORDER / PART / SPLIT (the full pass):
+// the p-tile, part and split record of block b's entry (k_cost_order), and
+// the number of entries; NULL: p-tile b, one part.
 template <int DP, bool WIT, int PG>
 __global__ void __launch_bounds__(kTQ + 32, RefineMinBlocks<DP>::value) k_refine(const float* __restrict__ X, const uint32_t* __restrict__ C,
                                                      const int32_t* __restrict__ ids,
@@ -422,17 +482,21 @@ __global__ void __launch_bounds__(kTQ + 32, RefineMinBlocks<DP>::value) k_refine
                                                      const uint32_t* __restrict__ order, const uint32_t* mcount,
                                                      DevResult* res,
                                                      uint8_t* keep, int32_t* wit, const uint32_t* __restrict__ cidx,
-                                                     int d, uint32_t min_m, const uint32_t* __restrict__ tmask)
+                                                     int d, uint32_t min_m, const uint32_t* __restrict__ tmask,
+                                                     const uint32_t* __restrict__ part, uint32_t* split)
 {
     extern __shared__ __align__(256) unsigned char smem_raw[];
     using SM = SetSmem<DP, PG>;
     SM& sm = *reinterpret_cast<SM*>(smem_raw);
     const uint32_t m = *mcount;
     constexpr uint32_t kTP = SM::kTP;
-    if (m < min_m || blockIdx.x >= (m + kTP - 1) / kTP) return;   // min_m: the pre-pass's survivor threshold
+    const uint32_t entries = part ? split[kSplitSlots * 5] : (m + kTP - 1) / kTP;
+    if (m < min_m || blockIdx.x >= entries) return;   // min_m: the pre-pass's survivor threshold
     const uint32_t ptile = order ? order[blockIdx.x] : blockIdx.x;
+    const uint32_t pinfo = part ? part[blockIdx.x] : (1u << 8);   // part | parts << 8 | slot << 16
     refine_ptile<DP, true, WIT, SM>(sm, X, C, ids, SUB, tend, supmin, m, ptile, res, keep, wit, cidx,
-                                    cidx ? cidx + (1u << d) : nullptr, tmask);
+                                    cidx ? cidx + (1u << d) : nullptr, tmask, pinfo & 0xffu, (pinfo >> 8) & 0xffu,
+                                    split ? split + (size_t)(pinfo >> 16) * 5 : nullptr);
 }
 
 // Ascending row ids of the kept rows (decoupled look-back over 8 rows per
@@ -597,22 +661,41 @@ namespace {
 // PG groups of 32 p's per CTA: TEND is each 128-point tile's last q-tile,
 // SUPMIN the super-tile minima (NULL: none), ORDER the p-tile order (NULL:
 // p-tile b in block b).
+// Resident refinement CTAs of the GPU (the split rule's slots), at most
+// 148 x 9 (the bound kSplitExtra and kSplitSlots are sized for).
+template <int DP>
+uint32_t refine_slots()
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0, n = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        sms = n > 0 ? n : 148;
+    }
+    return (uint32_t)std::min(sms * RefineMinBlocks<DP>::value, 148 * 9);
+}
+
 template <int DP, int PG>
 void refine_launch(const Plan& p, cudaStream_t s, int64_t tiles, const uint32_t* tend, const uint32_t* supmin,
-                   const uint32_t* order, const uint32_t* mcount, uint32_t min_m = 0)
+                   const uint32_t* order, const uint32_t* mcount, uint32_t min_m = 0, bool split = false)
 {
     const int smem = (int)sizeof(SetSmem<DP, PG>);
-    const unsigned grid = (unsigned)((tiles + SetSmem<DP, PG>::kTiles - 1) / SetSmem<DP, PG>::kTiles);
+    // split scans add up to 2 * slots entries (k_cost_order)
+    const unsigned grid = (unsigned)((tiles + SetSmem<DP, PG>::kTiles - 1) / SetSmem<DP, PG>::kTiles) +
+                          (split ? 2u * refine_slots<DP>() : 0u);
+    const uint32_t* part = split ? p.tile_part : nullptr;
+    uint32_t* sst = split ? p.split_state : nullptr;
     if (p.witness) {
         cudaFuncSetAttribute(k_refine<DP, true, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k_refine<DP, true, PG><<<grid, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, tend, supmin, order,
                                                              mcount, p.res, p.keep, p.witness, p.cidx, p.d, min_m,
-                                                             p.tmask);
+                                                             p.tmask, part, sst);
     } else {
         cudaFuncSetAttribute(k_refine<DP, false, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         k_refine<DP, false, PG><<<grid, kTQ + 32, smem, s>>>(p.X, p.C, p.ids, p.subcode, tend, supmin, order,
                                                               mcount, p.res, p.keep, nullptr, p.cidx, p.d, min_m,
-                                                              p.tmask);
+                                                              p.tmask, part, sst);
     }
 }
 
@@ -650,8 +733,13 @@ cudaError_t launch_refine(const Plan& p, cudaStream_t s)
         k_tile_cost<DW><<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(p.subcode, p.tmax, p.tile_end, mcount,
                                                                    p.tile_cost, p.supmin);
         constexpr int PG = RefineGroups<DP>::value;
-        k_cost_order<<<1, 1024, 0, s>>>(p.tile_cost, mcount, p.tile_order, (uint32_t)SetSmem<DP, PG>::kTiles);
-        refine_launch<DP, PG>(p, s, tiles, p.tile_end, p.supmin, p.tile_order, mcount);
+        constexpr uint32_t NT = (uint32_t)SetSmem<DP, PG>::kTiles;
+        const uint32_t slots = (SKY_REFINE_SPLIT_MIN_DP > 0 && DP >= SKY_REFINE_SPLIT_MIN_DP && NT == 1u &&
+                                tiles <= (int64_t)SKY_REFINE_SPLIT_MAX_WAVES * refine_slots<DP>())
+                                   ? refine_slots<DP>() : 0u;   // 0: no split
+        k_cost_order<<<1, 1024, 0, s>>>(p.tile_cost, mcount, p.tile_order, NT, p.tile_part, p.split_state,
+                                        slots);
+        refine_launch<DP, PG>(p, s, tiles, p.tile_end, p.supmin, p.tile_order, mcount, 0, slots > 0u);
     });
     return cudaGetLastError();
 }

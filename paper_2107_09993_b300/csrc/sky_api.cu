@@ -179,7 +179,9 @@ size_t layout(Plan& p, char* base, bool grid_api)
     p.ids = c.take<int32_t>(n_pad);
     p.tmax = c.take<uint32_t>(tiles * (dp / 4));
     p.tile_cost = c.take<uint32_t>(tiles);
-    p.tile_order = c.take<uint32_t>(tiles);
+    p.tile_order = c.take<uint32_t>(tiles + kSplitExtra);
+    p.tile_part = c.take<uint32_t>(tiles + kSplitExtra);
+    p.split_state = c.take<uint32_t>(size_t(kSplitSlots) * 5 + 1);
     p.subcode = c.take<uint32_t>(tiles * 5 * (dp / 4));
     p.tile_end = c.take<uint32_t>(tiles);
     p.supmin = c.take<uint32_t>(((tiles + 31) / 32) * (dp / 4));

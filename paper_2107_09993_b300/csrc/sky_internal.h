@@ -74,7 +74,10 @@ struct Plan {
     int32_t* ids = nullptr;          // [n_pad] row id per sorted survivor
     uint32_t* tmax = nullptr;        // [tiles][dp/4] byte-wise max code of each tile
     uint32_t* tile_cost = nullptr;   // [tiles] cost estimate of each p-tile
-    uint32_t* tile_order = nullptr;  // [tiles] p-tiles, largest cost first
+    uint32_t* tile_order = nullptr;  // [tiles + kSplitExtra] p-tiles, largest cost first (split ones once per part)
+    uint32_t* tile_part = nullptr;   // [tiles + kSplitExtra] part | parts << 8 | split slot << 16 of each entry
+    uint32_t* split_state = nullptr; // [kSplitSlots][5] kills (4 words) and finished parts of each split p-tile,
+                                     // then the number of order entries
     uint32_t* subcode = nullptr;     // [tiles][5][dp/4] byte-wise min code of each 32-point sub-tile, then of the tile
     uint32_t* tile_end = nullptr;    // [tiles] last q-tile whose first Morton key <= the tile's last key
     uint32_t* supmin = nullptr;      // [ceil(tiles / 32)][dp/4] byte-wise min code of each run of 32 tiles
@@ -129,6 +132,11 @@ struct QueryPlan {
 };
 
 constexpr int kRefineTile = 128;   // points per refinement tile
+// Split refinement scans: order entries beyond one per p-tile, and split
+// p-tiles, at most (bounds of the rule in k_cost_order for up to 148 SMs x
+// 9 CTAs)
+constexpr int kSplitExtra = 2 * 148 * 9;
+constexpr int kSplitSlots = 2 * 148 * 9;
 // threshold masks per tile for the refinement's mask probe: 4 sub-tiles of
 // 32 points x 16 dimensions x 8 levels of the 3-bit codes
 constexpr int kMaskWords = 4 * 128;

@@ -369,6 +369,7 @@ struct RefineSmem {
     uint32_t pP[kTP * DW];               // own p codes | 0x80 per byte
     uint32_t pF[kFast ? kTP * FW : 1];   // own p fast codes | 0x8 per nibble
     uint32_t livemask[PG];               // bit l of word g: p g*32+l is still undominated
+    uint32_t validmask[PG];              // the p's of the tile (split scans: the kills are merged)
     uint32_t gmax[PG][DW];               // byte-wise max code of each group's live p's | 0x80 per byte (producer)
     uint32_t glive[PG];                  // live p's per group (producer)
     uint32_t stage_tile[S];
@@ -392,6 +393,7 @@ struct RefineSmem {
     uint32_t scan_end;                   // last q-tile to scan
     uint32_t nlist;                      // live p's listed for the sparse scan
     uint32_t failed;
+    uint32_t lastpart;                   // split scans: this CTA finished the p-tile's last part
 };
 
 // Listed p entry j of a warp's list, DW words into c (16- or 8-byte loads).
@@ -465,7 +467,8 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                                              DevResult* res, uint8_t* keep, int32_t* wit = nullptr,
                                              const uint32_t* __restrict__ MLO = nullptr,
                                              const uint32_t* __restrict__ MHI = nullptr,
-                                             const uint32_t* __restrict__ TM = nullptr)
+                                             const uint32_t* __restrict__ TM = nullptr, uint32_t part = 0,
+                                             uint32_t nparts = 1, uint32_t* split = nullptr)
 {
     constexpr int DW = DP / 4;
     constexpr int NG = SM::kGroups;   // groups of 32 p's
@@ -522,7 +525,10 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                                   : make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
             }
             const uint32_t vm = __ballot_sync(kFull, valid);
-            if ((tid & 31) == 0) sm.livemask[pi >> 5] = vm;
+            if ((tid & 31) == 0) {
+                sm.livemask[pi >> 5] = vm;
+                sm.validmask[pi >> 5] = vm;
+            }
         }
     }
     if (tid == 0) {
@@ -601,7 +607,10 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                 if (win > SL) return -1;
                 const uint32_t sx = win + lane;
                 bool rel = sx <= SL;
-                if (rel && SUPMIN) {
+                // (a split scan's parts deal windows by their position in
+                // this sequence, so for them it must not depend on which p's
+                // are live: no super-tile test; the per-tile test still runs)
+                if (rel && SUPMIN && nparts == 1u) {
                     uint32_t mn[DW];
 #pragma unroll
                     for (int w = 0; w < DW; ++w) mn[w] = __ldg(SUPMIN + (int64_t)sx * DW + w);
@@ -641,7 +650,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
 #pragma unroll
         for (int h = 0; h < NT; ++h) {
             const uint32_t ot = tile0 + (uint32_t)h;
-            if (ot >= T) break;
+            if (ot >= T || part != 0u) break;   // a split scan's first part streams them
             const int q = lane / NG, g = lane % NG;
             const int s = (int)issued;
             bool rel = false;
@@ -685,11 +694,15 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
             __syncwarp();
             ++kiss;
         };
+        // a split scan's part takes every nparts-th window from its part on
+        uint32_t wseq = 0;
         auto refill = [&]() {
             while (kiss - kcons < NB) {
                 uint32_t t0, wm;
                 if (!next_window(t0, wm)) break;
-                fetch_window(t0, wm);
+                const bool mine = nparts == 1u || wseq % nparts == part;
+                ++wseq;
+                if (mine) fetch_window(t0, wm);
             }
         };
         refill();
@@ -698,7 +711,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
             const int bf = (int)(kcons % NB);
             const uint32_t t0 = (uint32_t)sm.pend[bf];
             const uint32_t wmk = sm.wmask[bf];
-            if (SPARSE && kSparseLive > 0 && __shfl_sync(kFull, sm.live, 0) <= kSparseLive) {
+            if (SPARSE && kSparseLive > 0 && nparts == 1u && __shfl_sync(kFull, sm.live, 0) <= kSparseLive) {
                 // few p's left: the rest of the scan runs in sparse mode,
                 // from this (fetched, not yet examined) window on
                 if (lane == 0) {
@@ -814,7 +827,7 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
                 // or are few enough left for sparse mode, from the next tile?
                 if ((issued & 3u) == 0u) {
                     if (all_dead()) { stop = true; break; }
-                    if (SPARSE && kSparseLive > 0 && __shfl_sync(kFull, sm.live, 0) <= kSparseLive) {
+                    if (SPARSE && kSparseLive > 0 && nparts == 1u && __shfl_sync(kFull, sm.live, 0) <= kSparseLive) {
                         if (lane == 0) {
                             sm.sparse = 1u;
                             sm.resume = t0 + (uint32_t)b + 1u;
@@ -1277,7 +1290,21 @@ __device__ __forceinline__ void refine_ptile(SM& sm, const float* __restrict__ X
         if (lane == 0 && we) atomicAdd(&res->exact, (unsigned long long)we);
         __syncthreads();
     }
-    if (tid < kTQ && !sm.failed) {
+    if (nparts > 1u) {
+        // split scan: this part's kills go into the p-tile's record; the
+        // part that finishes last reads every part's kills and writes keep
+        if (tid < NG) atomicOr(&split[tid], sm.validmask[tid] & ~sm.livemask[tid]);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) sm.lastpart = atomicAdd(&split[4], 1u) == nparts - 1u ? 1u : 0u;
+        __syncthreads();
+        if (sm.lastpart) {
+            __threadfence();
+            if (tid < NG) sm.livemask[tid] = sm.validmask[tid] & ~atomicOr(&split[tid], 0u);
+        }
+        __syncthreads();
+    }
+    if (tid < kTQ && !sm.failed && (nparts == 1u || sm.lastpart)) {
 #pragma unroll
         for (int h = 0; h < NT; ++h) {
             const int pi = h * kTQ + tid;
