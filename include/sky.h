@@ -56,7 +56,9 @@ typedef enum sky_status {
     SKY_ERR_NONFINITE = 2,        /* NaN or infinity in the input              */
     SKY_ERR_CAPACITY = 3,         /* output buffer too small; count is set     */
     SKY_ERR_OUT_OF_MEMORY = 4,    /* device workspace allocation failed        */
-    SKY_ERR_CUDA = 5,             /* a CUDA runtime call failed                */
+    SKY_ERR_CUDA = 5,             /* a CUDA runtime call failed (or the        */
+                                  /* refinement's shared memory was not        */
+                                  /* 256-byte aligned; sky_last_error says)    */
     SKY_ERR_TOO_LARGE = 6,        /* grid of 2^(log2_g*d) cells above 2^27     */
     SKY_ERR_TIMEOUT = 7,          /* a bounded device-side wait ran out        */
     SKY_ERR_NO_DEVICE = 8         /* no CUDA device, or not an sm_103 device   */
