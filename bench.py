@@ -657,7 +657,9 @@ def run_sky(args):
                    "traffic": traffic,
                    "peak_source": f"148 SMs x 128 int32 lanes x {sm_mhz:.0f} MHz (median SM clock sampled during the run)",
                    "work": f"{pairs / launches_refine:.4g} candidate pair tests per launch x ops per test "
-                           f"(ceil(d/4) word subtracts + AND tree + compare: 7 at d = 16, 6 at d = 12)",
+                           f"(ceil(d/4) word subtracts + AND tree + compare: 7 at d = 16, 6 at d = 12; the work "
+                           f"measure of the list probe, kept for the mask probe that tests these pairs from "
+                           f"padded dimension 12, 32 per lane with d table loads and ANDs)",
                    "ms_per_launch": round(phase_sum['refine_ms'] / launches_refine, 4),
                    "timing": "per set: the refinement phase (phase events, direct launches) -- from 2^21 rows "
                              "two k_refine launches (pre-pass, full pass) with the compaction, the second gather "
